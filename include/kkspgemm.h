@@ -1,0 +1,213 @@
+/*
+ * kkspgemm.h -- C ABI of the GB300 two-phase sparse matrix-matrix multiply.
+ *
+ * Computes C = A * B for CSR matrices A (m x n) and B (n x k), the problem of
+ * Deveci, Trott and Rajamanickam, "Multi-threaded Sparse Matrix-Matrix
+ * Multiplication for Many-Core and GPU Architectures" (Section 2).  The calls
+ * follow the paper's two-phase structure (Algorithm 2):
+ *
+ *   spgemm_symbolic   lines 1-3: row statistics, compression of B, and the
+ *                     size of every row of C -> C row pointers and nnz(C)
+ *   (caller)          line 4: allocate C column indices and values
+ *   spgemm_numeric    line 5: C's columns and values
+ *
+ * Numeric reuse (Section 2, two-phase methods; Section 4 "Reuse"): after one
+ * symbolic call, spgemm_numeric may be called any number of times with new
+ * values on the same A and B patterns.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - All array arguments are DEVICE pointers (memory of the GPU selected by
+ *    the handle), except those documented as host pointers.
+ *  - A and B: row pointers int32 or int64 (rowptr_is_64), column indices
+ *    int32 in [0, ncols), any order inside a row, no duplicate (i, j).
+ *    k = B.ncols must be <= 2^31 - 1.
+ *  - C: row pointers int64[m + 1]; column indices int32; values of the same
+ *    type as A and B.  Every row of C is sorted by column and holds every
+ *    structural product, numerical zeros included.
+ *  - Ownership: the caller owns A, B and all of C.  The handle owns every
+ *    scratch buffer (statistics, compressed B, row bins, accumulator pools).
+ *  - Streams: spgemm_stream_t is a cudaStream_t.  One handle serves one
+ *    stream at a time and is not thread-safe.
+ *  - Errors: every call returns a status and never throws or aborts.  Device
+ *    kernels never trap; a problem they detect is recorded in the handle and
+ *    returned by the next call that synchronises (spgemm_symbolic, or
+ *    spgemm_handle_sync after numeric calls).
+ */
+#ifndef KKSPGEMM_H
+#define KKSPGEMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *spgemm_stream_t; /* same type as cudaStream_t */
+typedef struct kks_handle *spgemm_handle_t;
+
+typedef enum {
+  SPGEMM_OK = 0,
+  SPGEMM_ERR_INVALID_ARG = 1,      /* null pointer, bad sizes, mismatched dims or dtypes */
+  SPGEMM_ERR_NOT_READY = 2,        /* numeric before a symbolic call on this handle */
+  SPGEMM_ERR_OOM = 3,              /* device memory (or the workspace limit) exhausted */
+  SPGEMM_ERR_INDEX_OVERFLOW = 4,   /* a size exceeds the supported index range */
+  SPGEMM_ERR_DEVICE_LIMIT = 5,     /* a kernel hit an internal limit (recorded on device) */
+  SPGEMM_ERR_CUDA = 6,             /* a CUDA runtime call failed */
+  SPGEMM_ERR_PATTERN_MISMATCH = 7, /* numeric called with operands other than symbolic's */
+  SPGEMM_ERR_BAD_INDEX = 8         /* a column index outside its range (detected on device) */
+} spgemm_status_t;
+
+typedef enum { SPGEMM_R32 = 0, SPGEMM_R64 = 1 } spgemm_dtype_t;
+
+/* A CSR operand (device pointers). */
+typedef struct {
+  int64_t nrows, ncols, nnz;
+  int32_t rowptr_is_64;   /* 1: rowptr is int64[nrows + 1]; 0: int32[nrows + 1] */
+  spgemm_dtype_t dtype;   /* type of values */
+  const void *rowptr;
+  const int32_t *colidx;
+  const void *values;     /* may be NULL for the symbolic phase */
+} spgemm_csr_t;
+
+/*
+ * Tunables.  The defaults restate the paper's parameters for GB300:
+ * compression when it cuts the product count by more than 15 % (Section 3.2),
+ * 50 % maximum occupancy of the LP level-1 accumulator (Section 3.1.2), level-1
+ * tables in shared memory (up to 227 KB per CTA on GB300), level-2 tables and
+ * dense accumulators in global-memory pools (Section 3.1.2, memory pool).
+ */
+typedef struct {
+  int32_t compression;           /* -1 auto (the 15 % rule), 0 never, 1 always */
+  double compress_threshold;     /* compress iff compressed f_m / f_m < this (0.85) */
+  double l1_max_occupancy;       /* LP level-1 cut-off for new keys (0.5) */
+  int32_t l1_max_log2_slots;     /* 0 = auto; caps shared tables at 2^this slots */
+  int32_t dense;                 /* -1 auto, 0 never use dense accumulators, 1 prefer */
+  int32_t method;                /* 0 binned (per-row team + accumulator),
+                                    1 paper meta-algorithm (one team class per problem) */
+  int64_t workspace_limit_bytes; /* 0 = no limit; above it calls fail with SPGEMM_ERR_OOM */
+  int64_t pool_limit_bytes;      /* cap on accumulator pools (0 = 8 GiB) */
+  int32_t device;                /* CUDA device ordinal used by the handle */
+  int32_t reserved[7];
+} spgemm_options_t;
+
+/* Statistics of the last symbolic call (Section 4 results-table columns). */
+typedef struct {
+  int64_t m, n, k, nnzA, nnzB;
+  int64_t f_m;            /* multiplications of A*B (uncompressed) */
+  int64_t maxrf;          /* max multiplications of one row */
+  int64_t f_m_compressed; /* multiplications on the compressed B */
+  int64_t maxrf_compressed;
+  double CF;              /* f_m_compressed / f_m */
+  double CMRF;            /* maxrf_compressed / maxrf */
+  int32_t compressed;     /* 1 if the symbolic phase ran on the compressed B */
+  int32_t nbins_symbolic; /* non-empty row bins used by the symbolic phase */
+  int32_t nbins_numeric;  /* non-empty row bins used by the numeric phase */
+  int32_t reserved0;
+  int64_t nnzC;
+  int64_t maxrs;          /* largest row of C */
+  double ars;             /* average row size of C */
+  int64_t workspace_bytes;/* device scratch held by the handle */
+  int64_t bin_rows_numeric[7]; /* rows per team class: none, w8, w32, c256, c1024, dense, spill */
+} spgemm_stats_t;
+
+/* Fills *opt with the defaults.  Returns SPGEMM_ERR_INVALID_ARG for NULL. */
+spgemm_status_t spgemm_options_default(spgemm_options_t *opt);
+
+/* Creates a handle (opt may be NULL for defaults).  *out receives it. */
+spgemm_status_t spgemm_handle_create(spgemm_handle_t *out, const spgemm_options_t *opt);
+
+/* Frees the handle and all scratch it owns (synchronises its device). */
+spgemm_status_t spgemm_handle_destroy(spgemm_handle_t h);
+
+/*
+ * Symbolic phase (Algorithm 2 lines 1-3).  Computes the row pointers of C into
+ * C_rowptr (device, int64[m + 1], caller-allocated) and writes nnz(C) to
+ * *nnzC (HOST pointer).  Values of A and B are not read.  Synchronises the
+ * stream once to return nnz(C), and plans the numeric phase.
+ */
+spgemm_status_t spgemm_symbolic(spgemm_handle_t h, const spgemm_csr_t *A, const spgemm_csr_t *B,
+                                int64_t *C_rowptr, int64_t *nnzC, spgemm_stream_t stream);
+
+/*
+ * Numeric phase (Algorithm 2 line 5).  A and B must be the operands of the
+ * last symbolic call on h (same patterns, same device pointers for the
+ * patterns; the value pointers may change).  Writes C_colidx (int32[nnzC])
+ * and C_values (nnzC values of A's dtype), rows sorted by column.  Fully
+ * asynchronous; allocates nothing.
+ */
+spgemm_status_t spgemm_numeric(spgemm_handle_t h, const spgemm_csr_t *A, const spgemm_csr_t *B,
+                               const int64_t *C_rowptr, int32_t *C_colidx, void *C_values,
+                               spgemm_stream_t stream);
+
+/*
+ * Numeric reuse on a known pattern of C: recomputes only C_values for new
+ * values of A and B, with C_rowptr / C_colidx as written by spgemm_numeric
+ * on the same handle.  The accumulator of each row is keyed by C's pattern
+ * (probe only), so no sort is needed.  Asynchronous; allocates nothing.
+ */
+spgemm_status_t spgemm_numeric_reuse(spgemm_handle_t h, const spgemm_csr_t *A, const spgemm_csr_t *B,
+                                     const int64_t *C_rowptr, const int32_t *C_colidx, void *C_values,
+                                     spgemm_stream_t stream);
+
+/* Waits for the stream, then reports (and clears) any device-detected error. */
+spgemm_status_t spgemm_handle_sync(spgemm_handle_t h, spgemm_stream_t stream);
+
+/* Statistics of the last symbolic call (host struct). */
+spgemm_status_t spgemm_get_stats(spgemm_handle_t h, spgemm_stats_t *out);
+
+/*
+ * Masked product on a given pattern: out(i, l) = sum_j X(i, j) * Y(j, l) for
+ * every (i, l) stored in S (S_rowptr int64[X.nrows + 1], S_colidx int32, any
+ * order inside a row); products whose column is not in S(i,:) are dropped.
+ * This gives the gradients of a loss L(C), C = A * B, on fixed patterns:
+ * dA = (G * B^T) on A's pattern and dB = (A^T * G) on B's pattern, with G the
+ * gradient on C's pattern.  out has nnz(S) values of X's dtype.  Synchronises
+ * the stream once (to plan the row bins).
+ */
+spgemm_status_t spgemm_masked(spgemm_handle_t h, const spgemm_csr_t *X, const spgemm_csr_t *Y,
+                              const int64_t *S_rowptr, const int32_t *S_colidx, int64_t S_nnz,
+                              void *out, spgemm_stream_t stream);
+
+/*
+ * Transpose: At = A^T (A.ncols x A.nrows) with At_rowptr int64[A.ncols + 1],
+ * At_colidx int32[nnz] (rows sorted), At_values (A's dtype, may be NULL when
+ * A.values is NULL) and perm int64[nnz] (may be NULL): At_values[q] =
+ * A.values[perm[q]], so later value-only updates are a gather
+ * (spgemm_gather).  Asynchronous.
+ */
+spgemm_status_t spgemm_transpose(spgemm_handle_t h, const spgemm_csr_t *A, int64_t *At_rowptr,
+                                 int32_t *At_colidx, void *At_values, int64_t *perm,
+                                 spgemm_stream_t stream);
+
+/* dst[q] = src[perm[q]] for q < n (dtype selects 4- or 8-byte values). */
+spgemm_status_t spgemm_gather(spgemm_handle_t h, spgemm_dtype_t dtype, const void *src, const int64_t *perm,
+                              void *dst, int64_t n, spgemm_stream_t stream);
+
+/*
+ * Batched symbolic / numeric: count independent products C_b = A_b * B_b in
+ * one plan, rows of all instances binned together (one launch per bin for all
+ * instances).  A, B: host arrays of count operand descriptors; C_rowptr,
+ * C_colidx, C_values: host arrays of count device pointers; nnzC: host array
+ * of count outputs.  All instances share one dtype.  Numeric reuse rules are
+ * those of the single calls.
+ */
+spgemm_status_t spgemm_batch_symbolic(spgemm_handle_t h, int32_t count, const spgemm_csr_t *A,
+                                      const spgemm_csr_t *B, int64_t *const *C_rowptr, int64_t *nnzC,
+                                      spgemm_stream_t stream);
+spgemm_status_t spgemm_batch_numeric(spgemm_handle_t h, int32_t count, const spgemm_csr_t *A,
+                                     const spgemm_csr_t *B, int64_t *const *C_rowptr,
+                                     int32_t *const *C_colidx, void *const *C_values, spgemm_stream_t stream);
+
+/* Human-readable name of a status code (static string). */
+const char *spgemm_status_string(spgemm_status_t s);
+
+/* Library version as an integer (major * 10000 + minor * 100 + patch). */
+int32_t spgemm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KKSPGEMM_H */

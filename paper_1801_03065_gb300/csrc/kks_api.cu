@@ -1,0 +1,1111 @@
+// kks_api.cu -- the C ABI: handle, workspace, planning of the two phases.
+//
+// spgemm_symbolic runs Algorithm 2 lines 1-3 on the GPU:
+//   (1) compression pass 1: compressed row lengths of B, their scan
+//   (2) row statistics rf_i (and rfc_i on the compressed B), per problem f_m,
+//       maxrf and the compressed counterparts                      -> sync 1
+//   (3) the 15 % rule: compress B iff f_m(compressed) / f_m < 0.85, pass 2
+//   (4) row bins for the symbolic kernels                           -> sync 2
+//   (5) symbolic kernels, scan of the row sizes, C row pointers
+//   (6) row bins and accumulator pools for the numeric phase        -> sync 3
+// spgemm_numeric (line 5) then only launches the numeric kernels of the
+// planned bins: no synchronisation and no allocation.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "kkspgemm.h"
+#include "kks_internal.h"
+
+namespace kks {
+size_t symbolic_team_bytes(int cls, int logT, int compressed);
+size_t numeric_team_bytes(int cls, int logT, int dtype);
+size_t numeric_spill_l1_bytes(int logT, int dtype);
+size_t numeric_l2_chunk_bytes(long long slots, int dtype);
+size_t masked_team_bytes(int cls, int logT, int dtype);
+}  // namespace kks
+
+using namespace kks;
+
+namespace {
+
+enum BufId {
+  kBufInst, kBufArow0, kBufBrow0, kBufCnt, kBufBcp, kBufCsi, kBufCs, kBufRf, kBufRfc, kBufRowsize, kBufOffs,
+  kBufScanTmp, kBufInstStats, kBufInstOut, kBufHist, kBufCursor, kBufSymRows, kBufNumRows, kBufSymPool,
+  kBufNumPool, kBufNumPool2, kBufNumPool3, kBufStatus, kBufMaskRows, kBufMaskHist, kBufMaskPool, kBufTrTmp,
+  kBufTrPool, kBufReuseRows, kBufReusePool, kNumBufs
+};
+
+// Row bins of a masked product, cached for numeric reuse on one pattern.
+struct MaskPlan {
+  bool valid = false;
+  const void* sp = nullptr;
+  const void* sj = nullptr;
+  const void* xrp = nullptr;
+  const void* xcj = nullptr;
+  const void* yrp = nullptr;
+  const void* ycj = nullptr;
+  long long nrows = 0, snnz = 0;
+  int dtype = 1;
+  std::vector<std::pair<int, int>> cls_logT;
+  std::vector<long long> off, cnt;
+  int gchunks = 0;
+  long long gslots = 0;
+};
+
+struct PatternId {
+  const void* arp;
+  const void* acj;
+  const void* brp;
+  const void* bcj;
+  long long m, n, k, nnza, nnzb;
+  int arp64, brp64;
+  bool operator==(const PatternId& o) const {
+    return arp == o.arp && acj == o.acj && brp == o.brp && bcj == o.bcj && m == o.m && n == o.n && k == o.k &&
+           nnza == o.nnza && nnzb == o.nnzb && arp64 == o.arp64 && brp64 == o.brp64;
+  }
+};
+
+struct BinRun {
+  int cls, logT, compressed;
+  long long off, count;
+};
+
+constexpr int kRing = 8;
+
+}  // namespace
+
+struct kks_handle {
+  spgemm_options_t opt;
+  int num_sms = 0;
+  int max_smem = 0;
+  void* buf[kNumBufs] = {};
+  size_t cap[kNumBufs] = {};
+  size_t total = 0;
+  unsigned char* pinned = nullptr;   // readbacks and uploads
+  size_t pinned_bytes = 0;
+  unsigned char* ring[kRing] = {};   // numeric table uploads
+  size_t ring_bytes = 0;
+  cudaEvent_t ring_ev[kRing] = {};
+  int ring_next = 0;
+  // plan
+  bool ready = false;
+  int ninst = 0;
+  int dtype = 1;
+  long long totalA = 0, totalB = 0;
+  std::vector<InstD> inst;       // host copy of the device table
+  std::vector<PatternId> pat;
+  std::vector<BinRun> num_bins;
+  long long num_kw_max = 0, num_kmax = 0;
+  int num_dense_chunks = 0, num_spill_chunks = 0;
+  long long num_spill_chunk_bytes = 0, num_spill_kw = 0, num_dense_kw = 0;
+  int num_l1_logT = 0;
+  spgemm_stats_t stats;
+  MaskPlan reuse;
+};
+
+namespace {
+
+spgemm_status_t cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return SPGEMM_OK;
+  if (e == cudaErrorMemoryAllocation) return SPGEMM_ERR_OOM;
+  return SPGEMM_ERR_CUDA;
+}
+
+#define KKS_CU(expr)                                        \
+  do {                                                      \
+    cudaError_t _e = (expr);                                \
+    if (_e != cudaSuccess) return cuda_status(_e);          \
+  } while (0)
+#define KKS_ST(expr)                                        \
+  do {                                                      \
+    spgemm_status_t _s = (expr);                            \
+    if (_s != SPGEMM_OK) return _s;                         \
+  } while (0)
+
+// Grows buffer id to at least bytes.  Only the planning calls allocate.
+spgemm_status_t ensure(kks_handle* h, int id, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (h->cap[id] >= bytes) return SPGEMM_OK;
+  size_t want = bytes + bytes / 4;
+  size_t new_total = h->total - h->cap[id] + want;
+  if (h->opt.workspace_limit_bytes > 0 && new_total > (size_t)h->opt.workspace_limit_bytes) {
+    want = bytes;
+    new_total = h->total - h->cap[id] + want;
+    if (new_total > (size_t)h->opt.workspace_limit_bytes) return SPGEMM_ERR_OOM;
+  }
+  if (h->buf[id]) {
+    cudaFree(h->buf[id]);
+    h->total -= h->cap[id];
+    h->buf[id] = nullptr;
+    h->cap[id] = 0;
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return SPGEMM_ERR_OOM;
+  }
+  h->buf[id] = p;
+  h->cap[id] = want;
+  h->total += want;
+  return SPGEMM_OK;
+}
+
+template <typename T>
+T* B(kks_handle* h, int id) {
+  return reinterpret_cast<T*>(h->buf[id]);
+}
+
+spgemm_status_t ensure_pinned(kks_handle* h, size_t bytes) {
+  if (h->pinned_bytes >= bytes) return SPGEMM_OK;
+  if (h->pinned) cudaFreeHost(h->pinned);
+  h->pinned = nullptr;
+  h->pinned_bytes = 0;
+  size_t want = std::max<size_t>(bytes, 1 << 16);
+  void* p = nullptr;
+  if (cudaHostAlloc(&p, want, cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    return SPGEMM_ERR_OOM;
+  }
+  h->pinned = (unsigned char*)p;
+  h->pinned_bytes = want;
+  return SPGEMM_OK;
+}
+
+LaunchCtx ctx(kks_handle* h, cudaStream_t s) {
+  LaunchCtx L;
+  L.stream = s;
+  L.num_sms = h->num_sms;
+  L.max_smem_optin = h->max_smem;
+  return L;
+}
+
+ProbD prob(kks_handle* h) {
+  ProbD P;
+  P.inst = B<InstD>(h, kBufInst);
+  P.arow0s = B<long long>(h, kBufArow0);
+  P.brow0s = B<long long>(h, kBufBrow0);
+  P.Bcp = B<long long>(h, kBufBcp);
+  P.csi = B<int>(h, kBufCsi);
+  P.cs = B<unsigned>(h, kBufCs);
+  P.status = B<DevStatus>(h, kBufStatus);
+  P.ninst = h->ninst;
+  P.pad = 0;
+  return P;
+}
+
+spgemm_status_t check_csr(const spgemm_csr_t* M, bool need_values) {
+  if (!M) return SPGEMM_ERR_INVALID_ARG;
+  if (M->nrows < 0 || M->ncols < 0 || M->nnz < 0) return SPGEMM_ERR_INVALID_ARG;
+  if (M->ncols > 2147483647ll || M->nrows > 2147483647ll) return SPGEMM_ERR_INDEX_OVERFLOW;
+  if (!M->rowptr_is_64 && M->nnz > 2147483647ll) return SPGEMM_ERR_INDEX_OVERFLOW;
+  if (!M->rowptr) return SPGEMM_ERR_INVALID_ARG;
+  if (M->nnz > 0 && !M->colidx) return SPGEMM_ERR_INVALID_ARG;
+  if (M->dtype != SPGEMM_R32 && M->dtype != SPGEMM_R64) return SPGEMM_ERR_INVALID_ARG;
+  if (need_values && M->nnz > 0 && !M->values) return SPGEMM_ERR_INVALID_ARG;
+  return SPGEMM_OK;
+}
+
+MatD matd(const spgemm_csr_t* M) {
+  MatD d;
+  d.rp = M->rowptr;
+  d.cj = M->colidx;
+  d.vx = M->values;
+  d.nrows = M->nrows;
+  d.ncols = M->ncols;
+  d.nnz = M->nnz;
+  d.rp64 = M->rowptr_is_64 ? 1 : 0;
+  d.pad = 0;
+  return d;
+}
+
+PatternId patid(const spgemm_csr_t* A, const spgemm_csr_t* Bm) {
+  PatternId p;
+  p.arp = A->rowptr;
+  p.acj = A->colidx;
+  p.brp = Bm->rowptr;
+  p.bcj = Bm->colidx;
+  p.m = A->nrows;
+  p.n = A->ncols;
+  p.k = Bm->ncols;
+  p.nnza = A->nnz;
+  p.nnzb = Bm->nnz;
+  p.arp64 = A->rowptr_is_64;
+  p.brp64 = Bm->rowptr_is_64;
+  return p;
+}
+
+int device_code_to_status(int code) {
+  switch (code) {
+    case kDevOk: return SPGEMM_OK;
+    case kDevBadIndex: return SPGEMM_ERR_BAD_INDEX;
+    default: return SPGEMM_ERR_DEVICE_LIMIT;
+  }
+}
+
+// Reads the device status word (already copied to host memory at *hs) and clears it.
+spgemm_status_t consume_status(kks_handle* h, const DevStatus* hs, cudaStream_t s) {
+  if (hs->code == kDevOk) return SPGEMM_OK;
+  if (h->opt.reserved[0] & 1)
+    fprintf(stderr, "kkspgemm: device status %d at site %d (info %lld)\n", hs->code, hs->where, hs->info);
+  int code = hs->code;
+  cudaMemsetAsync(h->buf[kBufStatus], 0, sizeof(DevStatus), s);
+  cudaStreamSynchronize(s);
+  return (spgemm_status_t)device_code_to_status(code);
+}
+
+long long kwords_of(long long k) { return (k + 31) >> 5; }
+
+// Largest table (log2 slots) of a 1024-thread team that fits the shared memory
+// (1 KB is left for the kernels' static scratch).
+int cta_max_logT_sym(kks_handle* h, int comp) {
+  int best = 4;
+  for (int l = 4; l <= 20; ++l)
+    if (symbolic_team_bytes(kClsC1024, l, comp) + 1024 <= (size_t)h->max_smem) best = l;
+  return best;
+}
+int cta_max_logT_num(kks_handle* h, int dtype) {
+  int best = 4;
+  for (int l = 4; l <= 20; ++l)
+    if (numeric_team_bytes(kClsC1024, l, dtype) + 1024 <= (size_t)h->max_smem) best = l;
+  return best;
+}
+
+BinCfg base_cfg(kks_handle* h) {
+  BinCfg c;
+  memset(&c, 0, sizeof(c));
+  c.min_logT = 4;
+  c.w8_max_logT = 5;
+  c.w8_max_work = 64;
+  c.w32_max_logT = 10;
+  c.w32_max_work = 1ll << 15;
+  c.c256_max_logT = 12;
+  c.c256_max_work = 1ll << 17;
+  c.dense_ok = h->opt.dense != 0;
+  c.spill_ok = 1;
+  c.force_cls = 0;
+  c.force_logT = 0;
+  return c;
+}
+
+void clamp_cfg(kks_handle* h, BinCfg& c) {
+  if (h->opt.l1_max_log2_slots > 0) {
+    int l = std::max(4, (int)h->opt.l1_max_log2_slots);
+    c.cta_max_logT = std::min(c.cta_max_logT, l);
+    c.c256_max_logT = std::min(c.c256_max_logT, l);
+    c.w32_max_logT = std::min(c.w32_max_logT, l);
+    c.w8_max_logT = std::min(c.w8_max_logT, l);
+  }
+  if (h->opt.dense == 1) c.dense_ratio = 1ll << 40;
+}
+
+BinCfg sym_cfg(kks_handle* h, int comp) {
+  BinCfg c = base_cfg(h);
+  c.cta_max_logT = cta_max_logT_sym(h, comp);
+  // 512-thread dense team: bitmap + chunk scratch in shared memory
+  c.dense_max_kwords = ((long long)h->max_smem - 12 * 1024) / 4;
+  // the bitmap (kw words) is preferred once the hash table would be as large
+  c.dense_ratio = comp ? 4 : 64;
+  clamp_cfg(h, c);
+  return c;
+}
+
+BinCfg num_cfg(kks_handle* h, int dtype, long long kmax) {
+  BinCfg c = base_cfg(h);
+  c.cta_max_logT = cta_max_logT_num(h, dtype);
+  c.dense_max_kwords = ((long long)h->max_smem - 26 * 1024) / 4;
+  c.dense_ratio = 8;
+  long long pool_limit = h->opt.pool_limit_bytes > 0 ? h->opt.pool_limit_bytes : (8ll << 30);
+  if (kmax * (dtype == 1 ? 8 : 4) > pool_limit) c.dense_ok = 0;
+  clamp_cfg(h, c);
+  return c;
+}
+
+void set_default_options(spgemm_options_t* o) {
+  memset(o, 0, sizeof(*o));
+  o->compression = -1;
+  o->compress_threshold = 0.85;
+  o->l1_max_occupancy = 0.5;
+  o->l1_max_log2_slots = 0;
+  o->dense = -1;
+  o->method = 0;
+  o->workspace_limit_bytes = 0;
+  o->pool_limit_bytes = 0;
+  o->device = 0;
+}
+
+// Upload the instance table through a pinned ring slot (numeric path).
+spgemm_status_t upload_inst(kks_handle* h, cudaStream_t s) {
+  size_t bytes = sizeof(InstD) * (size_t)h->ninst;
+  if (h->ring_bytes < bytes) {
+    for (int r = 0; r < kRing; ++r) {
+      if (h->ring[r]) {
+        cudaEventSynchronize(h->ring_ev[r]);
+        cudaFreeHost(h->ring[r]);
+        h->ring[r] = nullptr;
+      }
+    }
+    size_t want = std::max<size_t>(bytes, 4096);
+    for (int r = 0; r < kRing; ++r) {
+      void* p = nullptr;
+      if (cudaHostAlloc(&p, want, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return SPGEMM_ERR_OOM;
+      }
+      h->ring[r] = (unsigned char*)p;
+    }
+    h->ring_bytes = want;
+  }
+  const int r = h->ring_next;
+  h->ring_next = (r + 1) % kRing;
+  KKS_CU(cudaEventSynchronize(h->ring_ev[r]));
+  memcpy(h->ring[r], h->inst.data(), bytes);
+  KKS_CU(cudaMemcpyAsync(h->buf[kBufInst], h->ring[r], bytes, cudaMemcpyHostToDevice, s));
+  KKS_CU(cudaEventRecord(h->ring_ev[r], s));
+  return SPGEMM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// symbolic (one plan of `count` products)
+// ---------------------------------------------------------------------------
+spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, const spgemm_csr_t* Bm,
+                            int64_t* const* Crp, int64_t* nnzC, cudaStream_t s) {
+  if (!h || count < 0 || (count > 0 && (!A || !Bm || !Crp || !nnzC))) return SPGEMM_ERR_INVALID_ARG;
+  h->ready = false;
+  long long totalA = 0, totalB = 0;
+  int dtype = count > 0 ? (int)A[0].dtype : 1;
+  for (int b = 0; b < count; ++b) {
+    KKS_ST(check_csr(&A[b], false));
+    KKS_ST(check_csr(&Bm[b], false));
+    if (A[b].ncols != Bm[b].nrows) return SPGEMM_ERR_INVALID_ARG;
+    if ((int)A[b].dtype != dtype || (int)Bm[b].dtype != dtype) return SPGEMM_ERR_INVALID_ARG;
+    if (!Crp[b]) return SPGEMM_ERR_INVALID_ARG;
+    totalA += A[b].nrows;
+    totalB += Bm[b].nrows;
+  }
+  if (totalA >= 2147483647ll || totalB >= 2147483647ll) return SPGEMM_ERR_INDEX_OVERFLOW;
+  KKS_CU(cudaSetDevice(h->opt.device));
+
+  h->ninst = count;
+  h->dtype = dtype;
+  h->totalA = totalA;
+  h->totalB = totalB;
+  h->inst.assign(count, InstD{});
+  h->pat.resize(count);
+  std::vector<long long> arow0(count + 1, 0), brow0(count + 1, 0);
+  for (int b = 0; b < count; ++b) {
+    InstD& I = h->inst[b];
+    memset(&I, 0, sizeof(I));
+    I.A = matd(&A[b]);
+    I.B = matd(&Bm[b]);
+    I.arow0 = arow0[b];
+    I.brow0 = brow0[b];
+    I.Crp = reinterpret_cast<long long*>(Crp[b]);
+    I.k = Bm[b].ncols;
+    I.compressed = 0;
+    arow0[b + 1] = arow0[b] + A[b].nrows;
+    brow0[b + 1] = brow0[b] + Bm[b].nrows;
+    h->pat[b] = patid(&A[b], &Bm[b]);
+  }
+  const int ni = std::max(count, 1);
+  KKS_ST(ensure(h, kBufInst, sizeof(InstD) * ni));
+  KKS_ST(ensure(h, kBufArow0, sizeof(long long) * (ni + 1)));
+  KKS_ST(ensure(h, kBufBrow0, sizeof(long long) * (ni + 1)));
+  KKS_ST(ensure(h, kBufCnt, sizeof(long long) * (totalB + 1)));
+  KKS_ST(ensure(h, kBufBcp, sizeof(long long) * (totalB + 1)));
+  KKS_ST(ensure(h, kBufRf, sizeof(long long) * (totalA + 1)));
+  KKS_ST(ensure(h, kBufRfc, sizeof(long long) * (totalA + 1)));
+  KKS_ST(ensure(h, kBufRowsize, sizeof(long long) * (totalA + 1)));
+  KKS_ST(ensure(h, kBufOffs, sizeof(long long) * (totalA + 1)));
+  KKS_ST(ensure(h, kBufScanTmp, scan_tmp_bytes(std::max(totalA, totalB) + 1)));
+  KKS_ST(ensure(h, kBufInstStats, sizeof(unsigned long long) * 4 * ni));
+  KKS_ST(ensure(h, kBufInstOut, sizeof(unsigned long long) * 2 * ni));
+  KKS_ST(ensure(h, kBufHist, sizeof(unsigned long long) * 2 * kNumBins));
+  KKS_ST(ensure(h, kBufCursor, sizeof(unsigned long long) * 2 * kNumBins));
+  KKS_ST(ensure(h, kBufSymRows, sizeof(int) * (totalA + 1)));
+  KKS_ST(ensure(h, kBufNumRows, sizeof(int) * (totalA + 1)));
+  KKS_ST(ensure(h, kBufStatus, sizeof(DevStatus)));
+  KKS_ST(ensure(h, kBufCsi, 16));
+  KKS_ST(ensure(h, kBufCs, 16));
+
+  const size_t up_bytes = sizeof(InstD) * ni + 2 * sizeof(long long) * (ni + 1);
+  const size_t rd_bytes = sizeof(unsigned long long) * (4 * ni + 2 * ni + 2 * kNumBins + 8) + sizeof(DevStatus);
+  KKS_ST(ensure_pinned(h, up_bytes + rd_bytes + sizeof(unsigned long long) * 2 * kNumBins));
+  unsigned char* up = h->pinned;
+  unsigned char* rd = h->pinned + up_bytes;
+  memcpy(up, h->inst.data(), sizeof(InstD) * count);
+  memcpy(up + sizeof(InstD) * ni, arow0.data(), sizeof(long long) * (count + 1));
+  memcpy(up + sizeof(InstD) * ni + sizeof(long long) * (ni + 1), brow0.data(), sizeof(long long) * (count + 1));
+  KKS_CU(cudaMemcpyAsync(h->buf[kBufInst], up, sizeof(InstD) * ni, cudaMemcpyHostToDevice, s));
+  KKS_CU(cudaMemcpyAsync(h->buf[kBufArow0], up + sizeof(InstD) * ni, sizeof(long long) * (count + 1),
+                         cudaMemcpyHostToDevice, s));
+  KKS_CU(cudaMemcpyAsync(h->buf[kBufBrow0], up + sizeof(InstD) * ni + sizeof(long long) * (ni + 1),
+                         sizeof(long long) * (count + 1), cudaMemcpyHostToDevice, s));
+  KKS_CU(cudaMemsetAsync(h->buf[kBufInstStats], 0, sizeof(unsigned long long) * 4 * ni, s));
+  KKS_CU(cudaMemsetAsync(h->buf[kBufInstOut], 0, sizeof(unsigned long long) * 2 * ni, s));
+  KKS_CU(cudaMemsetAsync(h->buf[kBufHist], 0, sizeof(unsigned long long) * 2 * kNumBins, s));
+  KKS_CU(cudaMemsetAsync(h->buf[kBufStatus], 0, sizeof(DevStatus), s));
+
+  LaunchCtx L = ctx(h, s);
+  ProbD P = prob(h);
+  const bool comp_on = h->opt.compression != 0;
+
+  // (1) compression pass 1 and (2) row statistics
+  if (comp_on) {
+    KKS_CU(launch_compress_count(L, P, totalB, B<long long>(h, kBufCnt)));
+    KKS_CU(launch_scan(L, B<long long>(h, kBufCnt), B<long long>(h, kBufBcp), totalB, h->buf[kBufScanTmp]));
+  }
+  KKS_CU(launch_row_stats(L, P, totalA, comp_on ? 1 : 0, B<long long>(h, kBufRf),
+                          comp_on ? B<long long>(h, kBufRfc) : nullptr, B<unsigned long long>(h, kBufInstStats)));
+  unsigned long long* h_stats = (unsigned long long*)rd;
+  long long* h_nbc = (long long*)(rd + sizeof(unsigned long long) * 4 * ni);
+  DevStatus* h_status = (DevStatus*)(rd + sizeof(unsigned long long) * (4 * ni + 2 * ni + 2 * kNumBins + 8));
+  *h_nbc = 0;
+  KKS_CU(cudaMemcpyAsync(h_stats, h->buf[kBufInstStats], sizeof(unsigned long long) * 4 * ni,
+                         cudaMemcpyDeviceToHost, s));
+  if (comp_on)
+    KKS_CU(cudaMemcpyAsync(h_nbc, B<long long>(h, kBufBcp) + totalB, sizeof(long long), cudaMemcpyDeviceToHost, s));
+  KKS_CU(cudaMemcpyAsync(h_status, h->buf[kBufStatus], sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+  KKS_CU(cudaStreamSynchronize(s));
+  KKS_ST(consume_status(h, h_status, s));
+
+  // (3) the 15 % rule, per product
+  long long fm_all = 0, fmc_all = 0, maxrf_all = 0, maxrfc_all = 0;
+  int any_comp = 0, ncomp = 0;
+  for (int b = 0; b < count; ++b) {
+    long long fm = (long long)h_stats[4 * b], fmc = (long long)h_stats[4 * b + 2];
+    fm_all += fm;
+    fmc_all += fmc;
+    maxrf_all = std::max(maxrf_all, (long long)h_stats[4 * b + 1]);
+    maxrfc_all = std::max(maxrfc_all, (long long)h_stats[4 * b + 3]);
+    int c = 0;
+    if (h->opt.compression == 1) c = 1;
+    else if (h->opt.compression < 0 && fm > 0 && (double)fmc < h->opt.compress_threshold * (double)fm) c = 1;
+    h->inst[b].compressed = c;
+    any_comp |= c;
+    ncomp += c;
+  }
+  if (any_comp) {
+    const long long nbc = *h_nbc;
+    KKS_ST(ensure(h, kBufCsi, sizeof(int) * (nbc + 1)));
+    KKS_ST(ensure(h, kBufCs, sizeof(unsigned) * (nbc + 1)));
+    P = prob(h);
+    memcpy(up, h->inst.data(), sizeof(InstD) * count);
+    KKS_CU(cudaMemcpyAsync(h->buf[kBufInst], up, sizeof(InstD) * count, cudaMemcpyHostToDevice, s));
+    KKS_CU(cudaMemsetAsync(h->buf[kBufCs], 0, sizeof(unsigned) * (nbc + 1), s));
+    KKS_CU(launch_compress_fill(L, P, totalB, B<int>(h, kBufCsi), B<unsigned>(h, kBufCs)));
+  }
+
+  // (4) symbolic bins: the compressed and plain rows use separate bin ranges
+  BinCfg cfg_c = sym_cfg(h, 1), cfg_u = sym_cfg(h, 0);
+  unsigned long long* d_hist = B<unsigned long long>(h, kBufHist);
+  unsigned long long* h_hist = (unsigned long long*)(rd + sizeof(unsigned long long) * (4 * ni + 2 * ni));
+  // one launch per compression flag keeps the device bin function simple
+  // (rows of the other kind land in the class-none bin of that launch and are ignored)
+  std::vector<unsigned long long> hist(2 * kNumBins, 0);
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 1 && !any_comp) break;
+    if (pass == 0 && ncomp == count && count > 0) continue;
+    KKS_CU(cudaMemsetAsync(d_hist, 0, sizeof(unsigned long long) * kNumBins, s));
+    BinCfg c = pass ? cfg_c : cfg_u;
+    KKS_CU(launch_bin_count(L, P, totalA, pass ? 2 : 3, B<long long>(h, kBufRf), B<long long>(h, kBufRfc), nullptr, c,
+                            d_hist));
+    KKS_CU(cudaMemcpyAsync(h_hist, d_hist, sizeof(unsigned long long) * kNumBins, cudaMemcpyDeviceToHost, s));
+    KKS_CU(cudaStreamSynchronize(s));
+    for (int t = 0; t < kNumBins; ++t) hist[pass * kNumBins + t] = h_hist[t];
+  }
+  // offsets over both passes (class-none rows are not listed)
+  std::vector<long long> off(2 * kNumBins + 1, 0);
+  for (int t = 0; t < 2 * kNumBins; ++t) {
+    long long c = (bin_cls(t % kNumBins) == kClsNone) ? 0 : (long long)hist[t];
+    off[t + 1] = off[t] + c;
+  }
+  unsigned long long* h_cur = (unsigned long long*)(rd + rd_bytes);
+  for (int t = 0; t < 2 * kNumBins; ++t) h_cur[t] = (unsigned long long)off[t];
+  KKS_CU(cudaMemcpyAsync(h->buf[kBufCursor], h_cur, sizeof(unsigned long long) * 2 * kNumBins,
+                         cudaMemcpyHostToDevice, s));
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 1 && !any_comp) break;
+    if (pass == 0 && ncomp == count && count > 0) continue;
+    BinCfg c = pass ? cfg_c : cfg_u;
+    KKS_CU(launch_bin_scatter(L, P, totalA, pass ? 2 : 3, B<long long>(h, kBufRf), B<long long>(h, kBufRfc),
+                              B<long long>(h, kBufRowsize), c,
+                              B<unsigned long long>(h, kBufCursor) + pass * kNumBins, B<int>(h, kBufSymRows)));
+  }
+
+  // (5) symbolic kernels, bin by bin
+  int nbins_sym = 0;
+  for (int t = 0; t < 2 * kNumBins; ++t) {
+    const long long cnt = off[t + 1] - off[t];
+    if (cnt == 0) continue;
+    const int bin = t % kNumBins;
+    const int comp = t / kNumBins;
+    ++nbins_sym;
+    SymLaunch S;
+    memset(&S, 0, sizeof(S));
+    S.cls = bin_cls(bin);
+    S.logT = bin_logT(bin);
+    S.rows = B<int>(h, kBufSymRows) + off[t];
+    S.nrows = cnt;
+    S.compressed = comp;
+    S.max_occ = h->opt.l1_max_occupancy;
+    long long kmax = 0;
+    for (int b = 0; b < count; ++b) kmax = std::max<long long>(kmax, h->inst[b].k);
+    // dense rows only come from products whose bitmap fits (checked per row)
+    S.kwords_max = std::min(kwords_of(kmax), (comp ? cfg_c : cfg_u).dense_max_kwords);
+    if (S.cls == kClsSpill) {
+      const BinCfg& c = comp ? cfg_c : cfg_u;
+      S.l1_logT = c.cta_max_logT;
+      S.l2_chunk_slots = 1ll << S.logT;
+      const long long chunk = S.l2_chunk_slots * (comp ? 8 : 4);
+      long long pool_limit = h->opt.pool_limit_bytes > 0 ? h->opt.pool_limit_bytes : (8ll << 30);
+      long long nch = std::min<long long>(std::min<long long>(2ll * h->num_sms, cnt), pool_limit / chunk);
+      if (nch < 1) return SPGEMM_ERR_OOM;
+      KKS_ST(ensure(h, kBufSymPool, (size_t)(nch * chunk)));
+      S.l2_pool = h->buf[kBufSymPool];
+      S.nchunks = (int)nch;
+    }
+    KKS_CU(launch_symbolic(L, P, S, B<long long>(h, kBufRowsize)));
+  }
+
+  // C row pointers
+  KKS_CU(launch_scan(L, B<long long>(h, kBufRowsize), B<long long>(h, kBufOffs), totalA, h->buf[kBufScanTmp]));
+  KKS_CU(launch_write_rowptr(L, P, totalA, B<long long>(h, kBufOffs), B<long long>(h, kBufRowsize),
+                             B<unsigned long long>(h, kBufInstOut)));
+
+  // (6) numeric bins
+  long long kmax = 0;
+  for (int b = 0; b < count; ++b) kmax = std::max<long long>(kmax, h->inst[b].k);
+  BinCfg ncfg = num_cfg(h, dtype, kmax);
+  KKS_CU(cudaMemsetAsync(d_hist, 0, sizeof(unsigned long long) * kNumBins, s));
+  KKS_CU(launch_bin_count(L, P, totalA, 1, B<long long>(h, kBufRf), nullptr, B<long long>(h, kBufRowsize), ncfg,
+                          d_hist));
+  unsigned long long* h_out = (unsigned long long*)(rd + sizeof(unsigned long long) * 4 * ni);
+  KKS_CU(cudaMemcpyAsync(h_hist, d_hist, sizeof(unsigned long long) * kNumBins, cudaMemcpyDeviceToHost, s));
+  KKS_CU(cudaMemcpyAsync(h_out, h->buf[kBufInstOut], sizeof(unsigned long long) * 2 * ni, cudaMemcpyDeviceToHost, s));
+  KKS_CU(cudaMemcpyAsync(h_status, h->buf[kBufStatus], sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+  KKS_CU(cudaStreamSynchronize(s));
+  KKS_ST(consume_status(h, h_status, s));
+
+  std::vector<long long> noff(kNumBins + 1, 0);
+  for (int t = 0; t < kNumBins; ++t) {
+    long long c = (bin_cls(t) == kClsNone) ? 0 : (long long)h_hist[t];
+    noff[t + 1] = noff[t] + c;
+  }
+  for (int t = 0; t < kNumBins; ++t) h_cur[t] = (unsigned long long)noff[t];
+  KKS_CU(cudaMemcpyAsync(h->buf[kBufCursor], h_cur, sizeof(unsigned long long) * kNumBins, cudaMemcpyHostToDevice,
+                         s));
+  KKS_CU(launch_bin_scatter(L, P, totalA, 1, B<long long>(h, kBufRf), nullptr, B<long long>(h, kBufRowsize), ncfg,
+                            B<unsigned long long>(h, kBufCursor), B<int>(h, kBufNumRows)));
+
+  h->num_bins.clear();
+  long long dense_rows = 0, spill_rows = 0;
+  int spill_logT = 0;
+  long long cls_rows[kNumClasses] = {0};
+  for (int t = 0; t < kNumBins; ++t) {
+    const int cls = bin_cls(t);
+    cls_rows[cls] += (long long)h_hist[t];
+    const long long cnt = noff[t + 1] - noff[t];
+    if (cnt == 0) continue;
+    h->num_bins.push_back(BinRun{cls, bin_logT(t), 0, noff[t], cnt});
+    if (cls == kClsDense) dense_rows += cnt;
+    if (cls == kClsSpill) {
+      spill_rows += cnt;
+      spill_logT = std::max(spill_logT, bin_logT(t));
+    }
+  }
+  // heaviest classes first so the long rows start early
+  std::stable_sort(h->num_bins.begin(), h->num_bins.end(), [](const BinRun& a, const BinRun& b) {
+    auto key = [](const BinRun& r) { return r.cls == kClsSpill ? 7 : r.cls == kClsDense ? 6 : r.cls; };
+    return key(a) * 64 + a.logT > key(b) * 64 + b.logT;
+  });
+  const int vt = dtype == 1 ? 8 : 4;
+  long long pool_limit = h->opt.pool_limit_bytes > 0 ? h->opt.pool_limit_bytes : (8ll << 30);
+  h->num_kmax = kmax;
+  h->num_kw_max = kwords_of(kmax);
+  h->num_dense_kw = std::min(kwords_of(kmax), ncfg.dense_max_kwords);
+  h->num_dense_chunks = 0;
+  h->num_spill_chunks = 0;
+  if (dense_rows > 0) {
+    const long long chunk = kmax * vt;
+    long long nch = std::min<long long>(std::min<long long>(2ll * h->num_sms, dense_rows), pool_limit / std::max(chunk, 1ll));
+    if (nch < 1) return SPGEMM_ERR_OOM;
+    KKS_ST(ensure(h, kBufNumPool, (size_t)(nch * chunk)));
+    KKS_CU(cudaMemsetAsync(h->buf[kBufNumPool], 0, (size_t)(nch * chunk), s));
+    h->num_dense_chunks = (int)nch;
+  }
+  if (spill_rows > 0) {
+    const long long slots = 1ll << spill_logT;
+    const long long chunk = (long long)numeric_l2_chunk_bytes(slots, dtype);
+    const long long chunk2 = 2 * h->num_kw_max * 4;
+    long long nch = std::min<long long>(std::min<long long>(2ll * h->num_sms, spill_rows), pool_limit / (chunk + chunk2));
+    if (nch < 1) return SPGEMM_ERR_OOM;
+    KKS_ST(ensure(h, kBufNumPool2, (size_t)(nch * chunk)));
+    KKS_ST(ensure(h, kBufNumPool3, (size_t)(nch * chunk2)));
+    KKS_CU(cudaMemsetAsync(h->buf[kBufNumPool3], 0, (size_t)(nch * chunk2), s));
+    h->num_spill_chunks = (int)nch;
+    h->num_spill_chunk_bytes = chunk;
+    h->num_l1_logT = ncfg.cta_max_logT;
+  }
+
+  // results
+  long long nnz_all = 0, maxrs_all = 0;
+  for (int b = 0; b < count; ++b) {
+    nnzC[b] = (int64_t)h_out[2 * b];
+    nnz_all += (long long)h_out[2 * b];
+    maxrs_all = std::max(maxrs_all, (long long)h_out[2 * b + 1]);
+  }
+  spgemm_stats_t& st = h->stats;
+  memset(&st, 0, sizeof(st));
+  if (count > 0) {
+    st.m = A[0].nrows;
+    st.n = A[0].ncols;
+    st.k = Bm[0].ncols;
+    st.nnzA = A[0].nnz;
+    st.nnzB = Bm[0].nnz;
+  }
+  st.f_m = fm_all;
+  st.maxrf = maxrf_all;
+  st.f_m_compressed = comp_on ? fmc_all : fm_all;
+  st.maxrf_compressed = comp_on ? maxrfc_all : maxrf_all;
+  st.CF = fm_all > 0 ? (double)st.f_m_compressed / (double)fm_all : 1.0;
+  st.CMRF = maxrf_all > 0 ? (double)st.maxrf_compressed / (double)maxrf_all : 1.0;
+  st.compressed = any_comp;
+  st.nbins_symbolic = nbins_sym;
+  st.nbins_numeric = (int)h->num_bins.size();
+  st.nnzC = nnz_all;
+  st.maxrs = maxrs_all;
+  st.ars = totalA > 0 ? (double)nnz_all / (double)totalA : 0.0;
+  st.workspace_bytes = (int64_t)h->total;
+  for (int c = 0; c < kNumClasses; ++c) st.bin_rows_numeric[c] = cls_rows[c];
+  h->ready = true;
+  return SPGEMM_OK;
+}
+
+spgemm_status_t do_numeric(kks_handle* h, int count, const spgemm_csr_t* A, const spgemm_csr_t* Bm,
+                           int64_t* const* Crp, int32_t* const* Cj, void* const* Cx, cudaStream_t s) {
+  if (!h) return SPGEMM_ERR_INVALID_ARG;
+  if (!h->ready) return SPGEMM_ERR_NOT_READY;
+  if (count != h->ninst || (count > 0 && (!A || !Bm || !Crp || !Cj || !Cx))) return SPGEMM_ERR_INVALID_ARG;
+  bool changed = false;
+  for (int b = 0; b < count; ++b) {
+    KKS_ST(check_csr(&A[b], true));
+    KKS_ST(check_csr(&Bm[b], true));
+    if (!(patid(&A[b], &Bm[b]) == h->pat[b])) return SPGEMM_ERR_PATTERN_MISMATCH;
+    if ((int)A[b].dtype != h->dtype || (int)Bm[b].dtype != h->dtype) return SPGEMM_ERR_INVALID_ARG;
+    if (!Crp[b] || (!Cj[b] || !Cx[b])) {
+      if (A[b].nrows > 0 && (!Crp[b])) return SPGEMM_ERR_INVALID_ARG;
+    }
+    InstD& I = h->inst[b];
+    long long* crp = reinterpret_cast<long long*>(Crp[b]);
+    if (I.A.vx != A[b].values || I.B.vx != Bm[b].values || I.Cj != Cj[b] || I.Cx != Cx[b] || I.Crp != crp) {
+      changed = true;
+      I.A.vx = A[b].values;
+      I.B.vx = Bm[b].values;
+      I.Cj = Cj[b];
+      I.Cx = Cx[b];
+      I.Crp = crp;
+    }
+  }
+  KKS_CU(cudaSetDevice(h->opt.device));
+  if (changed) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    KKS_CU(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return SPGEMM_ERR_NOT_READY;
+    KKS_ST(upload_inst(h, s));
+  }
+  LaunchCtx L = ctx(h, s);
+  ProbD P = prob(h);
+  for (const BinRun& r : h->num_bins) {
+    NumLaunch S;
+    memset(&S, 0, sizeof(S));
+    S.cls = r.cls;
+    S.logT = r.logT;
+    S.rows = B<int>(h, kBufNumRows) + r.off;
+    S.nrows = r.count;
+    S.dtype = h->dtype;
+    S.kwords_max = h->num_kw_max;
+    S.kmax = h->num_kmax;
+    S.max_occ = h->opt.l1_max_occupancy;
+    if (r.cls == kClsDense) {
+      S.pool = h->buf[kBufNumPool];
+      S.nchunks = h->num_dense_chunks;
+      S.kwords_max = h->num_dense_kw;
+    } else if (r.cls == kClsSpill) {
+      S.pool = h->buf[kBufNumPool2];
+      S.chunk_bytes = h->num_spill_chunk_bytes;
+      S.pool2 = h->buf[kBufNumPool3];
+      S.nchunks = h->num_spill_chunks;
+      S.l1_logT = h->num_l1_logT;
+    }
+    KKS_CU(launch_numeric(L, P, S));
+  }
+  return SPGEMM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// masked products (numeric reuse on C's pattern, gradients)
+// ---------------------------------------------------------------------------
+int cta_max_logT_msk(kks_handle* h, int dtype) {
+  int best = 4;
+  for (int l = 4; l <= 20; ++l)
+    if (masked_team_bytes(kClsC1024, l, dtype) + 1024 <= (size_t)h->max_smem) best = l;
+  return best;
+}
+
+spgemm_status_t check_masked(const spgemm_csr_t* X, const spgemm_csr_t* Y, const int64_t* Sp, const int32_t* Sj,
+                             int64_t snnz, const void* out) {
+  KKS_ST(check_csr(X, true));
+  KKS_ST(check_csr(Y, true));
+  if (X->ncols != Y->nrows || X->dtype != Y->dtype) return SPGEMM_ERR_INVALID_ARG;
+  if (!Sp || snnz < 0 || (snnz > 0 && (!Sj || !out))) return SPGEMM_ERR_INVALID_ARG;
+  return SPGEMM_OK;
+}
+
+MaskedD maskd(kks_handle* h, const spgemm_csr_t* X, const spgemm_csr_t* Y, const int64_t* Sp, const int32_t* Sj,
+              void* out) {
+  MaskedD M;
+  M.X = matd(X);
+  M.Y = matd(Y);
+  M.Sp = reinterpret_cast<const long long*>(Sp);
+  M.Sj = Sj;
+  M.out = out;
+  M.status = B<DevStatus>(h, kBufStatus);
+  return M;
+}
+
+// Bins the rows of S (one synchronisation) into plan; rows into rows_buf.
+spgemm_status_t plan_masked(kks_handle* h, const MaskedD& M, long long nrows, int dtype, int rows_buf, int pool_buf,
+                            MaskPlan* plan, cudaStream_t s) {
+  KKS_ST(ensure(h, kBufStatus, sizeof(DevStatus)));
+  KKS_ST(ensure(h, kBufMaskHist, sizeof(unsigned long long) * 2 * kNumBins));
+  KKS_ST(ensure(h, rows_buf, sizeof(int) * (nrows + 1)));
+  KKS_ST(ensure_pinned(h, sizeof(unsigned long long) * 2 * kNumBins + sizeof(DevStatus)));
+  MaskedD Mx = M;
+  Mx.status = B<DevStatus>(h, kBufStatus);
+  BinCfg c = base_cfg(h);
+  c.cta_max_logT = cta_max_logT_msk(h, dtype);
+  c.dense_ok = 0;
+  clamp_cfg(h, c);
+  unsigned long long* d_hist = B<unsigned long long>(h, kBufMaskHist);
+  unsigned long long* h_hist = (unsigned long long*)h->pinned;
+  LaunchCtx L = ctx(h, s);
+  KKS_CU(cudaMemsetAsync(d_hist, 0, sizeof(unsigned long long) * kNumBins, s));
+  KKS_CU(launch_masked_bin_count(L, Mx, nrows, c, d_hist));
+  KKS_CU(cudaMemcpyAsync(h_hist, d_hist, sizeof(unsigned long long) * kNumBins, cudaMemcpyDeviceToHost, s));
+  DevStatus* hs = (DevStatus*)(h->pinned + sizeof(unsigned long long) * 2 * kNumBins);
+  KKS_CU(cudaMemcpyAsync(hs, h->buf[kBufStatus], sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+  KKS_CU(cudaStreamSynchronize(s));
+  KKS_ST(consume_status(h, hs, s));
+  plan->cls_logT.clear();
+  plan->off.clear();
+  plan->cnt.clear();
+  long long o = 0;
+  int glog = 0;
+  long long grows = 0;
+  std::vector<unsigned long long> cur(kNumBins, 0);
+  for (int t = 0; t < kNumBins; ++t) {
+    cur[t] = (unsigned long long)o;
+    const long long n = (long long)h_hist[t];
+    if (n == 0 || bin_cls(t) == kClsNone) continue;
+    plan->cls_logT.push_back({bin_cls(t), bin_logT(t)});
+    plan->off.push_back(o);
+    plan->cnt.push_back(n);
+    if (bin_cls(t) == kClsSpill) {
+      glog = std::max(glog, bin_logT(t));
+      grows += n;
+    }
+    o += n;
+  }
+  memcpy(h_hist + kNumBins, cur.data(), sizeof(unsigned long long) * kNumBins);
+  KKS_CU(cudaMemcpyAsync(d_hist + kNumBins, h_hist + kNumBins, sizeof(unsigned long long) * kNumBins,
+                         cudaMemcpyHostToDevice, s));
+  KKS_CU(launch_masked_bin_scatter(L, Mx, nrows, c, d_hist + kNumBins, B<int>(h, rows_buf)));
+  plan->gchunks = 0;
+  plan->gslots = 0;
+  if (grows > 0) {
+    const long long slots = 1ll << glog;
+    const long long chunk = (long long)masked_global_chunk_bytes(slots, dtype);
+    long long pool_limit = h->opt.pool_limit_bytes > 0 ? h->opt.pool_limit_bytes : (8ll << 30);
+    long long nch = std::min<long long>(std::min<long long>(2ll * h->num_sms, grows), pool_limit / chunk);
+    if (nch < 1) return SPGEMM_ERR_OOM;
+    KKS_ST(ensure(h, pool_buf, (size_t)(nch * chunk)));
+    plan->gchunks = (int)nch;
+    plan->gslots = slots;
+  }
+  KKS_CU(cudaStreamSynchronize(s));
+  plan->valid = true;
+  return SPGEMM_OK;
+}
+
+spgemm_status_t run_masked_plan(kks_handle* h, const MaskedD& M, int dtype, int rows_buf, int pool_buf,
+                                const MaskPlan& plan, cudaStream_t s) {
+  LaunchCtx L = ctx(h, s);
+  for (size_t b = 0; b < plan.cnt.size(); ++b) {
+    MaskedLaunch S;
+    memset(&S, 0, sizeof(S));
+    S.cls = plan.cls_logT[b].first;
+    S.logT = plan.cls_logT[b].second;
+    S.rows = B<int>(h, rows_buf) + plan.off[b];
+    S.nrows = plan.cnt[b];
+    S.dtype = dtype;
+    if (S.cls == kClsSpill) {
+      S.pool = h->buf[pool_buf];
+      S.chunk_slots = plan.gslots;
+      S.nchunks = plan.gchunks;
+    }
+    KKS_CU(launch_masked(L, M, S));
+  }
+  return SPGEMM_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+spgemm_status_t spgemm_options_default(spgemm_options_t* opt) {
+  if (!opt) return SPGEMM_ERR_INVALID_ARG;
+  set_default_options(opt);
+  return SPGEMM_OK;
+}
+
+spgemm_status_t spgemm_handle_create(spgemm_handle_t* out, const spgemm_options_t* opt) {
+  if (!out) return SPGEMM_ERR_INVALID_ARG;
+  *out = nullptr;
+  kks_handle* h = new (std::nothrow) kks_handle();
+  if (!h) return SPGEMM_ERR_OOM;
+  if (opt) h->opt = *opt; else set_default_options(&h->opt);
+  if (!(h->opt.l1_max_occupancy > 0.0 && h->opt.l1_max_occupancy <= 1.0) || h->opt.compress_threshold < 0.0 ||
+      h->opt.compression < -1 || h->opt.compression > 1) {
+    delete h;
+    return SPGEMM_ERR_INVALID_ARG;
+  }
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || h->opt.device < 0 || h->opt.device >= ndev) {
+    cudaGetLastError();
+    delete h;
+    return e != cudaSuccess ? SPGEMM_ERR_CUDA : SPGEMM_ERR_INVALID_ARG;
+  }
+  if (cudaSetDevice(h->opt.device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->opt.device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->opt.device) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return SPGEMM_ERR_CUDA;
+  }
+  for (int r = 0; r < kRing; ++r) {
+    if (cudaEventCreateWithFlags(&h->ring_ev[r], cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      delete h;
+      return SPGEMM_ERR_CUDA;
+    }
+  }
+  *out = h;
+  return SPGEMM_OK;
+}
+
+spgemm_status_t spgemm_handle_destroy(spgemm_handle_t h) {
+  if (!h) return SPGEMM_ERR_INVALID_ARG;
+  cudaSetDevice(h->opt.device);
+  cudaDeviceSynchronize();
+  for (int i = 0; i < kNumBufs; ++i)
+    if (h->buf[i]) cudaFree(h->buf[i]);
+  if (h->pinned) cudaFreeHost(h->pinned);
+  for (int r = 0; r < kRing; ++r) {
+    if (h->ring[r]) cudaFreeHost(h->ring[r]);
+    if (h->ring_ev[r]) cudaEventDestroy(h->ring_ev[r]);
+  }
+  delete h;
+  return SPGEMM_OK;
+}
+
+spgemm_status_t spgemm_symbolic(spgemm_handle_t h, const spgemm_csr_t* A, const spgemm_csr_t* Bm, int64_t* C_rowptr,
+                                int64_t* nnzC, spgemm_stream_t stream) {
+  if (!h || !A || !Bm || !C_rowptr || !nnzC) return SPGEMM_ERR_INVALID_ARG;
+  int64_t* crp[1] = {C_rowptr};
+  return do_symbolic(h, 1, A, Bm, crp, nnzC, (cudaStream_t)stream);
+}
+
+spgemm_status_t spgemm_numeric(spgemm_handle_t h, const spgemm_csr_t* A, const spgemm_csr_t* Bm,
+                               const int64_t* C_rowptr, int32_t* C_colidx, void* C_values, spgemm_stream_t stream) {
+  if (!h || !A || !Bm || !C_rowptr) return SPGEMM_ERR_INVALID_ARG;
+  if (h->ready && h->ninst == 1 && h->stats.nnzC > 0 && (!C_colidx || !C_values)) return SPGEMM_ERR_INVALID_ARG;
+  int64_t* crp[1] = {const_cast<int64_t*>(C_rowptr)};
+  int32_t* cj[1] = {C_colidx};
+  void* cx[1] = {C_values};
+  if (!C_colidx || !C_values) {
+    // nnz(C) == 0: nothing to write
+    if (!h->ready) return SPGEMM_ERR_NOT_READY;
+    return SPGEMM_OK;
+  }
+  return do_numeric(h, 1, A, Bm, crp, cj, cx, (cudaStream_t)stream);
+}
+
+spgemm_status_t spgemm_handle_sync(spgemm_handle_t h, spgemm_stream_t stream) {
+  if (!h) return SPGEMM_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  KKS_CU(cudaSetDevice(h->opt.device));
+  if (!h->buf[kBufStatus]) {
+    KKS_CU(cudaStreamSynchronize(s));
+    return SPGEMM_OK;
+  }
+  KKS_ST(ensure_pinned(h, sizeof(DevStatus)));
+  DevStatus* hs = (DevStatus*)h->pinned;
+  KKS_CU(cudaMemcpyAsync(hs, h->buf[kBufStatus], sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+  KKS_CU(cudaStreamSynchronize(s));
+  return consume_status(h, hs, s);
+}
+
+spgemm_status_t spgemm_get_stats(spgemm_handle_t h, spgemm_stats_t* out) {
+  if (!h || !out) return SPGEMM_ERR_INVALID_ARG;
+  if (!h->ready) return SPGEMM_ERR_NOT_READY;
+  *out = h->stats;
+  return SPGEMM_OK;
+}
+
+spgemm_status_t spgemm_batch_symbolic(spgemm_handle_t h, int32_t count, const spgemm_csr_t* A, const spgemm_csr_t* Bm,
+                                      int64_t* const* C_rowptr, int64_t* nnzC, spgemm_stream_t stream) {
+  if (!h) return SPGEMM_ERR_INVALID_ARG;
+  return do_symbolic(h, count, A, Bm, C_rowptr, nnzC, (cudaStream_t)stream);
+}
+
+spgemm_status_t spgemm_batch_numeric(spgemm_handle_t h, int32_t count, const spgemm_csr_t* A, const spgemm_csr_t* Bm,
+                                     int64_t* const* C_rowptr, int32_t* const* C_colidx, void* const* C_values,
+                                     spgemm_stream_t stream) {
+  if (!h) return SPGEMM_ERR_INVALID_ARG;
+  return do_numeric(h, count, A, Bm, C_rowptr, C_colidx, C_values, (cudaStream_t)stream);
+}
+
+spgemm_status_t spgemm_masked(spgemm_handle_t h, const spgemm_csr_t* X, const spgemm_csr_t* Y,
+                              const int64_t* S_rowptr, const int32_t* S_colidx, int64_t S_nnz, void* out,
+                              spgemm_stream_t stream) {
+  if (!h) return SPGEMM_ERR_INVALID_ARG;
+  KKS_ST(check_masked(X, Y, S_rowptr, S_colidx, S_nnz, out));
+  cudaStream_t s = (cudaStream_t)stream;
+  KKS_CU(cudaSetDevice(h->opt.device));
+  if (X->nrows == 0 || S_nnz == 0) return SPGEMM_OK;
+  KKS_ST(ensure(h, kBufStatus, sizeof(DevStatus)));
+  MaskedD M = maskd(h, X, Y, S_rowptr, S_colidx, out);
+  MaskPlan plan;
+  KKS_ST(plan_masked(h, M, X->nrows, (int)X->dtype, kBufMaskRows, kBufMaskPool, &plan, s));
+  return run_masked_plan(h, M, (int)X->dtype, kBufMaskRows, kBufMaskPool, plan, s);
+}
+
+spgemm_status_t spgemm_numeric_reuse(spgemm_handle_t h, const spgemm_csr_t* A, const spgemm_csr_t* Bm,
+                                     const int64_t* C_rowptr, const int32_t* C_colidx, void* C_values,
+                                     spgemm_stream_t stream) {
+  if (!h || !A || !Bm) return SPGEMM_ERR_INVALID_ARG;
+  if (!h->ready) return SPGEMM_ERR_NOT_READY;
+  if (h->ninst != 1) return SPGEMM_ERR_INVALID_ARG;
+  if (!(patid(A, Bm) == h->pat[0])) return SPGEMM_ERR_PATTERN_MISMATCH;
+  const long long snnz = h->stats.nnzC;
+  KKS_ST(check_masked(A, Bm, C_rowptr, C_colidx, snnz, C_values));
+  if ((int)A->dtype != h->dtype) return SPGEMM_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  KKS_CU(cudaSetDevice(h->opt.device));
+  if (A->nrows == 0 || snnz == 0) return SPGEMM_OK;
+  MaskedD M = maskd(h, A, Bm, C_rowptr, C_colidx, C_values);
+  MaskPlan& P = h->reuse;
+  const bool same = P.valid && P.sp == C_rowptr && P.sj == C_colidx && P.xrp == A->rowptr && P.xcj == A->colidx &&
+                    P.yrp == Bm->rowptr && P.ycj == Bm->colidx && P.nrows == A->nrows && P.snnz == snnz &&
+                    P.dtype == (int)A->dtype;
+  if (!same) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    KKS_CU(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return SPGEMM_ERR_NOT_READY;
+    P.valid = false;
+    KKS_ST(plan_masked(h, M, A->nrows, (int)A->dtype, kBufReuseRows, kBufReusePool, &P, s));
+    P.sp = C_rowptr;
+    P.sj = C_colidx;
+    P.xrp = A->rowptr;
+    P.xcj = A->colidx;
+    P.yrp = Bm->rowptr;
+    P.ycj = Bm->colidx;
+    P.nrows = A->nrows;
+    P.snnz = snnz;
+    P.dtype = (int)A->dtype;
+  }
+  return run_masked_plan(h, M, (int)A->dtype, kBufReuseRows, kBufReusePool, P, s);
+}
+
+spgemm_status_t spgemm_transpose(spgemm_handle_t h, const spgemm_csr_t* A, int64_t* At_rowptr, int32_t* At_colidx,
+                                 void* At_values, int64_t* perm, spgemm_stream_t stream) {
+  if (!h) return SPGEMM_ERR_INVALID_ARG;
+  KKS_ST(check_csr(A, At_values != nullptr));
+  if (!At_rowptr || (A->nnz > 0 && !At_colidx)) return SPGEMM_ERR_INVALID_ARG;
+  if (A->nrows > 2147483647ll) return SPGEMM_ERR_INDEX_OVERFLOW;
+  cudaStream_t s = (cudaStream_t)stream;
+  KKS_CU(cudaSetDevice(h->opt.device));
+  KKS_ST(ensure(h, kBufStatus, sizeof(DevStatus)));
+  KKS_ST(ensure(h, kBufTrTmp, transpose_tmp_bytes(A->nrows, A->ncols, A->nnz)));
+  KKS_ST(ensure_pinned(h, 64 + sizeof(DevStatus)));
+  MatD M = matd(A);
+  if (!At_values) M.vx = nullptr;
+  LaunchCtx L = ctx(h, s);
+  unsigned long long* hmax = (unsigned long long*)h->pinned;
+  *hmax = 0;
+  KKS_CU(cudaMemsetAsync(h->buf[kBufStatus], 0, sizeof(DevStatus), s));
+  DevStatus* hs = (DevStatus*)(h->pinned + 64);
+  KKS_CU(launch_transpose_count(L, M, reinterpret_cast<long long*>(At_rowptr), h->buf[kBufTrTmp], hmax,
+                                B<DevStatus>(h, kBufStatus)));
+  KKS_CU(cudaMemcpyAsync(hs, h->buf[kBufStatus], sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+  KKS_CU(cudaStreamSynchronize(s));
+  KKS_ST(consume_status(h, hs, s));
+  const long long max_len = (long long)*hmax;
+  unsigned long long* gbuf = nullptr;
+  long long gbuf_len = 0;
+  int gchunks = 0;
+  if (max_len > 16384) {
+    gbuf_len = 1;
+    while (gbuf_len < max_len) gbuf_len <<= 1;
+    long long pool_limit = h->opt.pool_limit_bytes > 0 ? h->opt.pool_limit_bytes : (8ll << 30);
+    long long nch = std::min<long long>(h->num_sms, pool_limit / (gbuf_len * 8));
+    if (nch < 1) return SPGEMM_ERR_OOM;
+    KKS_ST(ensure(h, kBufTrPool, (size_t)(nch * gbuf_len * 8)));
+    gbuf = B<unsigned long long>(h, kBufTrPool);
+    gchunks = (int)nch;
+  }
+  KKS_CU(launch_transpose_fill(L, M, (int)A->dtype, reinterpret_cast<const long long*>(At_rowptr), At_colidx,
+                               At_values, reinterpret_cast<long long*>(perm), h->buf[kBufTrTmp], max_len, gbuf,
+                               gbuf_len, gchunks, B<DevStatus>(h, kBufStatus)));
+  return SPGEMM_OK;
+}
+
+spgemm_status_t spgemm_gather(spgemm_handle_t h, spgemm_dtype_t dtype, const void* src, const int64_t* perm, void* dst,
+                              int64_t n, spgemm_stream_t stream) {
+  if (!h || n < 0 || (n > 0 && (!src || !perm || !dst))) return SPGEMM_ERR_INVALID_ARG;
+  if (dtype != SPGEMM_R32 && dtype != SPGEMM_R64) return SPGEMM_ERR_INVALID_ARG;
+  KKS_CU(cudaSetDevice(h->opt.device));
+  LaunchCtx L = ctx(h, (cudaStream_t)stream);
+  KKS_CU(launch_gather_values(L, (int)dtype, src, reinterpret_cast<const long long*>(perm), dst, n));
+  return SPGEMM_OK;
+}
+
+const char* spgemm_status_string(spgemm_status_t s) {
+  switch (s) {
+    case SPGEMM_OK: return "SPGEMM_OK";
+    case SPGEMM_ERR_INVALID_ARG: return "SPGEMM_ERR_INVALID_ARG";
+    case SPGEMM_ERR_NOT_READY: return "SPGEMM_ERR_NOT_READY";
+    case SPGEMM_ERR_OOM: return "SPGEMM_ERR_OOM";
+    case SPGEMM_ERR_INDEX_OVERFLOW: return "SPGEMM_ERR_INDEX_OVERFLOW";
+    case SPGEMM_ERR_DEVICE_LIMIT: return "SPGEMM_ERR_DEVICE_LIMIT";
+    case SPGEMM_ERR_CUDA: return "SPGEMM_ERR_CUDA";
+    case SPGEMM_ERR_PATTERN_MISMATCH: return "SPGEMM_ERR_PATTERN_MISMATCH";
+    case SPGEMM_ERR_BAD_INDEX: return "SPGEMM_ERR_BAD_INDEX";
+  }
+  return "SPGEMM_ERR_UNKNOWN";
+}
+
+int32_t spgemm_version(void) { return 100; }
+
+}  // extern "C"
+
+

@@ -1,0 +1,309 @@
+// kks_device.cuh -- device-side building blocks shared by the SpGEMM kernels.
+//
+// Teams (the paper's Kokkos "team", Section 2.3 / 3.1.1) are groups of TW
+// threads that compute one row of C at a time:
+//   * TW <= 32  : a sub-warp or a warp; several teams per CTA, synchronised
+//                 with __syncwarp(mask)
+//   * TW  > 32  : the whole CTA is one team (TW == blockDim.x), synchronised
+//                 with __syncthreads()
+// Inside a team the products of a row are flattened and spread over the
+// threads (Thread-Flat-Parallel partitioning, Section 3.1.1), so inserts into
+// an accumulator are not unique and use atomics.
+//
+// Accumulators are linear-probing hash tables (LP, Section 3.1.2) addressed
+// through generic pointers, so the same code serves the level-1 table in
+// shared memory and the level-2 table in a global-memory pool chunk.  The hash
+// of a key is key & (size - 1) with a power-of-two size (Section 3.1.2).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace kks {
+
+constexpr int kEmpty = -1;
+
+// Device status word: kernels never trap; they record the first problem here
+// and the host turns it into a status code at the next synchronisation point.
+enum DevCode : int {
+  kDevOk = 0,
+  kDevTableFull = 1,        // an accumulator had no free slot (internal sizing bug)
+  kDevRowSizeMismatch = 2,  // numeric produced a row size != symbolic's
+  kDevBadIndex = 3,         // a column index outside [0, k)
+  kDevSortOverflow = 4,     // a row larger than its sort buffer
+};
+
+struct DevStatus {
+  int code;
+  int where;
+  long long info;
+};
+
+__device__ __forceinline__ void dev_fail(DevStatus* st, int code, int where, long long info) {
+  if (atomicCAS(&st->code, 0, code) == 0) {
+    st->where = where;
+    st->info = info;
+  }
+}
+
+// CSR operand with int32 or int64 row pointers.
+struct MatD {
+  const void* rp;
+  const int* cj;
+  const void* vx;
+  long long nrows, ncols, nnz;
+  int rp64;
+  int pad;
+};
+
+__device__ __forceinline__ long long rp_at(const MatD& M, long long i) {
+  return M.rp64 ? reinterpret_cast<const long long*>(M.rp)[i]
+                : (long long)reinterpret_cast<const int*>(M.rp)[i];
+}
+
+// One multiplication C = A * B of a plan (a plain call is a plan of one).
+struct InstD {
+  MatD A, B;
+  long long arow0;     // first global row of this instance's A rows
+  long long brow0;     // first global row of this instance's B rows
+  long long* Crp;      // caller's C row pointers (m + 1)
+  int* Cj;             // caller's C column indices
+  void* Cx;            // caller's C values
+  long long k;         // columns of B (= of C)
+  int compressed;      // symbolic runs on the compressed B
+  int pad;
+};
+
+// Per-launch view of a plan.
+struct ProbD {
+  const InstD* inst;
+  const long long* arow0s;   // ninst + 1 prefix of A-row counts
+  const long long* brow0s;   // ninst + 1 prefix of B-row counts
+  const long long* Bcp;      // compressed B row pointers over global B rows (+1)
+  const int* csi;            // column-set index (col >> 5)
+  const unsigned* cs;        // column set bits
+  DevStatus* status;
+  int ninst;
+  int pad;
+};
+
+// Largest b with row0s[b] <= g; such an instance is never empty.
+__device__ __forceinline__ int inst_of(const long long* row0s, int ninst, long long g) {
+  int lo = 0, hi = ninst - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (row0s[mid] <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__host__ __device__ __forceinline__ int ilog2_ceil(long long x) {
+  int l = 0;
+  while ((1ll << l) < x) ++l;
+  return l;
+}
+
+// --------------------------------------------------------------------------
+// team primitives
+// --------------------------------------------------------------------------
+template <int TW>
+struct Team {
+  static constexpr bool kCta = TW > 32;
+  unsigned mask;   // sub-warp teams: the team's lanes
+  int lane;        // 0 .. TW-1
+  int id;          // team index inside the CTA
+  int per_cta;     // teams per CTA
+
+  __device__ __forceinline__ Team() {
+    if constexpr (kCta) {
+      mask = 0xffffffffu;
+      lane = threadIdx.x;
+      id = 0;
+      per_cta = 1;
+    } else {
+      int l = threadIdx.x & 31;
+      lane = l & (TW - 1);
+      if constexpr (TW == 32) mask = 0xffffffffu;
+      else mask = ((1u << TW) - 1u) << (l & ~(TW - 1));
+      id = threadIdx.x / TW;
+      per_cta = blockDim.x / TW;
+    }
+  }
+  __device__ __forceinline__ void sync() const {
+    if constexpr (kCta) __syncthreads(); else __syncwarp(mask);
+  }
+};
+
+// Exclusive prefix sum over the team; *total receives the team sum.
+// scratch: 33 long longs of shared memory, used by CTA teams only.
+template <int TW>
+__device__ __forceinline__ long long team_excl_scan(const Team<TW>& tm, long long v, long long* total,
+                                                    long long* scratch) {
+  if constexpr (!Team<TW>::kCta) {
+    long long x = v;
+#pragma unroll
+    for (int d = 1; d < TW; d <<= 1) {
+      long long y = __shfl_up_sync(tm.mask, x, d, TW);
+      if (tm.lane >= d) x += y;
+    }
+    *total = __shfl_sync(tm.mask, x, TW - 1, TW);
+    return x - v;
+  } else {
+    const int l = threadIdx.x & 31, w = threadIdx.x >> 5, nw = TW / 32;
+    long long x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      long long y = __shfl_up_sync(0xffffffffu, x, d);
+      if (l >= d) x += y;
+    }
+    if (l == 31) scratch[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      long long s = (l < nw) ? scratch[l] : 0;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, s, d);
+        if (l >= d) s += y;
+      }
+      if (l < nw) scratch[l] = s;          // inclusive warp prefix
+      if (l == 31) scratch[32] = s;        // team total
+    }
+    __syncthreads();
+    long long base = (w > 0) ? scratch[w - 1] : 0;
+    *total = scratch[32];
+    long long r = base + x - v;
+    __syncthreads();                       // scratch reusable after return
+    return r;
+  }
+}
+
+template <int TW>
+__device__ __forceinline__ long long team_sum(const Team<TW>& tm, long long v, long long* scratch) {
+  long long tot;
+  team_excl_scan<TW>(tm, v, &tot, scratch);
+  return tot;
+}
+
+// --------------------------------------------------------------------------
+// linear-probing hash table (LP accumulator, Section 3.1.2)
+// --------------------------------------------------------------------------
+__device__ __forceinline__ unsigned lp_hash(int key, unsigned tmask) {
+  return (unsigned)key & tmask;
+}
+
+// Find or claim the slot of key.  cap < 0: no occupancy limit.  Otherwise a new
+// key is only placed while *occ < cap (the maximum-occupancy rule of the LP
+// accumulator); a refused key returns -1 and goes to the next level.
+// Returns -2 when the table has no free slot at all.
+__device__ __forceinline__ int lp_insert(int* keys, unsigned tmask, int* occ, int cap, int key) {
+  unsigned h = lp_hash(key, tmask);
+  for (unsigned probe = 0; probe <= tmask; ++probe) {
+    int cur = *((volatile int*)(keys + h));
+    if (cur == key) return (int)h;
+    if (cur == kEmpty) {
+      if (cap >= 0 && *((volatile int*)occ) >= cap) return -1;
+      int old = atomicCAS(keys + h, kEmpty, key);
+      if (old == kEmpty) {
+        if (cap >= 0) atomicAdd(occ, 1);
+        return (int)h;
+      }
+      if (old == key) return (int)h;
+    }
+    h = (h + 1) & tmask;
+  }
+  return -2;
+}
+
+// Probe-only lookup; -1 when absent.  Valid once no insert is in flight.
+__device__ __forceinline__ int lp_find(const int* keys, unsigned tmask, int key) {
+  unsigned h = lp_hash(key, tmask);
+  for (unsigned probe = 0; probe <= tmask; ++probe) {
+    int cur = *((const volatile int*)(keys + h));
+    if (cur == key) return (int)h;
+    if (cur == kEmpty) return -1;
+    h = (h + 1) & tmask;
+  }
+  return -1;
+}
+
+template <int TW, typename T>
+__device__ __forceinline__ void team_fill_n(const Team<TW>& tm, T* p, long long n, T v) {
+  for (long long x = tm.lane; x < n; x += TW) p[x] = v;
+}
+
+// Bitonic sort of buf[0, N) ascending, N a power of two (pads must hold ~0).
+template <int TW>
+__device__ __forceinline__ void team_bitonic(const Team<TW>& tm, unsigned long long* buf, int N) {
+  for (int k = 2; k <= N; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int idx = tm.lane; idx < (N >> 1); idx += TW) {
+        int lo = ((idx & ~(j - 1)) << 1) | (idx & (j - 1));
+        int hi = lo + j;
+        bool asc = (lo & k) == 0;
+        unsigned long long a = buf[lo], b = buf[hi];
+        if ((a > b) == asc) {
+          buf[lo] = b;
+          buf[hi] = a;
+        }
+      }
+      tm.sync();
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// flat traversal of a row's products (Thread-Flat-Parallel, Section 3.1.1)
+// --------------------------------------------------------------------------
+// Per-team shared scratch for one chunk of TW entries of A(i,:).
+template <int TW, typename VT>
+struct ChunkScratch {
+  long long pre[TW + 1];   // exclusive prefix of B-row lengths
+  long long bs[TW];        // B-row start of each entry
+  VT av[TW];               // A values of the chunk (numeric only)
+};
+
+// Calls body(q, t) for every product of row i: q indexes B's entry, t the
+// chunk slot holding the A entry.  range(j, &bs, &be) gives the B range of
+// A column j; aval(p) the value of A entry p (or 0 when unused).
+template <int TW, typename VT, class Range, class AVal, class Body>
+__device__ __forceinline__ void for_each_product(const Team<TW>& tm, ChunkScratch<TW, VT>* cs,
+                                                 long long* scan_scratch, const int* Aj,
+                                                 long long a_beg, long long a_end, Range range,
+                                                 AVal aval, Body body) {
+  for (long long c = a_beg; c < a_end; c += TW) {
+    long long p = c + tm.lane;
+    long long bs = 0, be = 0;
+    VT av = VT(0);
+    if (p < a_end) {
+      int j = Aj[p];
+      range(j, &bs, &be);
+      av = aval(p);
+    }
+    long long total;
+    long long ex = team_excl_scan<TW>(tm, be - bs, &total, scan_scratch);
+    cs->pre[tm.lane] = ex;
+    cs->bs[tm.lane] = bs;
+    cs->av[tm.lane] = av;
+    if (tm.lane == 0) cs->pre[TW] = total;
+    tm.sync();
+    if (total > 0) {
+      long long x = tm.lane;
+      if (x < total) {
+        // first product: binary search for the last t with pre[t] <= x
+        int lo = 0, hi = TW - 1;
+        while (lo < hi) {
+          int mid = (lo + hi + 1) >> 1;
+          if (cs->pre[mid] <= x) lo = mid; else hi = mid - 1;
+        }
+        int t = lo;
+        for (; x < total; x += TW) {
+          while (cs->pre[t + 1] <= x) ++t;
+          body(cs->bs[t] + (x - cs->pre[t]), t);
+        }
+      }
+    }
+    tm.sync();
+  }
+}
+
+}  // namespace kks

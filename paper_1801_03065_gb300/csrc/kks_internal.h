@@ -1,0 +1,171 @@
+// kks_internal.h -- host/device declarations shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "kks_device.cuh"
+
+namespace kks {
+
+// ---------------------------------------------------------------------------
+// Row binning.  A row of C is assigned to a team class and an accumulator
+// size from two numbers: u, an upper bound on its distinct keys (exact in the
+// numeric phase), and work, its product count.  This replaces the paper's
+// per-problem choice between kkmem / kklp and its L1 sizing (Section 3.3) by a
+// per-row choice, so one matrix uses several kernels at once.
+// ---------------------------------------------------------------------------
+enum TeamClass : int {
+  kClsNone = 0,    // empty row: nothing to compute
+  kClsW8 = 1,      // 8-lane sub-warp team, shared LP table
+  kClsW32 = 2,     // warp team, shared LP table
+  kClsC256 = 3,    // 256-thread CTA team, shared LP table
+  kClsC1024 = 4,   // 1024-thread CTA team, shared LP table
+  kClsDense = 5,   // CTA team, dense accumulator (bitmap in shared memory)
+  kClsSpill = 6,   // CTA team, shared L1 LP table + global L2 LP table
+  kNumClasses = 7,
+};
+constexpr int kBinsPerClass = 32;
+constexpr int kNumBins = kNumClasses * kBinsPerClass;
+
+__host__ __device__ inline int bin_id(int cls, int logT) { return cls * kBinsPerClass + logT; }
+__host__ __device__ inline int bin_cls(int bin) { return bin / kBinsPerClass; }
+__host__ __device__ inline int bin_logT(int bin) { return bin % kBinsPerClass; }
+
+struct BinCfg {
+  int min_logT;            // smallest table
+  int w8_max_logT;         // sub-warp teams up to this table size ...
+  long long w8_max_work;   // ... and this many products
+  int w32_max_logT;
+  long long w32_max_work;
+  int c256_max_logT;
+  long long c256_max_work;
+  int cta_max_logT;        // largest shared-memory table (L1)
+  int dense_ok;            // dense accumulator allowed at all
+  long long dense_max_kwords;  // bitmap words that fit shared memory
+  long long dense_ratio;   // prefer dense when u * dense_ratio >= kk
+  int spill_ok;            // L1 + L2 hash allowed
+  int force_cls;           // >0: every non-empty row goes to this class
+  int force_logT;          // with force_cls: table size used for every row
+};
+
+// kk: the key range the dense test compares against (k, or k/32 compressed);
+// kwords: bitmap words of the dense accumulator (ceil(k / 32)).
+__host__ __device__ inline int choose_bin(long long u, long long work, long long kk, long long kwords,
+                                          const BinCfg& c) {
+  if (u <= 0 || work <= 0) return bin_id(kClsNone, 0);
+  int logT = ilog2_ceil(2 * u);
+  if (logT < c.min_logT) logT = c.min_logT;
+  if (logT > 30) logT = 30;   // bin ids hold logT < kBinsPerClass; such rows fail pool sizing
+  if (c.force_cls > 0) return bin_id(c.force_cls, c.force_cls == kClsDense ? 0 : c.force_logT);
+  bool dense_fit = c.dense_ok && kwords <= c.dense_max_kwords;
+  if (dense_fit && (logT > c.cta_max_logT || u * c.dense_ratio >= kk)) return bin_id(kClsDense, 0);
+  if (logT <= c.w8_max_logT && work <= c.w8_max_work) return bin_id(kClsW8, logT);
+  if (logT <= c.w32_max_logT && work <= c.w32_max_work) return bin_id(kClsW32, logT);
+  if (logT <= c.c256_max_logT && work <= c.c256_max_work) return bin_id(kClsC256, logT);
+  if (logT <= c.cta_max_logT) return bin_id(kClsC1024, logT);
+  if (c.spill_ok || !dense_fit) return bin_id(kClsSpill, logT);
+  return bin_id(kClsDense, 0);
+}
+
+// ---------------------------------------------------------------------------
+// launchers (all asynchronous on the given stream)
+// ---------------------------------------------------------------------------
+struct LaunchCtx {
+  cudaStream_t stream;
+  int num_sms;
+  int max_smem_optin;   // bytes of dynamic shared memory a CTA may use
+};
+
+// prep: statistics, compression, scans, binning
+cudaError_t launch_compress_count(const LaunchCtx&, const ProbD&, long long totalB, long long* cnt);
+cudaError_t launch_compress_fill(const LaunchCtx&, const ProbD&, long long totalB, int* csi, unsigned* cs);
+cudaError_t launch_row_stats(const LaunchCtx&, const ProbD&, long long totalA, int use_bc,
+                             long long* rf, long long* rfc, unsigned long long* inst_stats);
+// exclusive scan of in[0, n) into out[0, n], out[n] = total; tmp >= scan_tmp_bytes(n)
+size_t scan_tmp_bytes(long long n);
+cudaError_t launch_scan(const LaunchCtx&, const long long* in, long long* out, long long n, void* tmp);
+// phase 1 = numeric (u = row size); phase 2 / 3 = symbolic rows of compressed /
+// uncompressed products (u from rfc / rf); rows of the other kind are skipped
+cudaError_t launch_bin_count(const LaunchCtx&, const ProbD&, long long totalA, int phase,
+                             const long long* rf, const long long* rfc, const long long* rowsize,
+                             BinCfg cfg, unsigned long long* hist);
+cudaError_t launch_bin_scatter(const LaunchCtx&, const ProbD&, long long totalA, int phase,
+                               const long long* rf, const long long* rfc, const long long* rowsize,
+                               BinCfg cfg, unsigned long long* cursor, int* rows);
+// C row pointers per instance from the global scan; per-instance nnz and max row size
+cudaError_t launch_write_rowptr(const LaunchCtx&, const ProbD&, long long totalA, const long long* offs,
+                                const long long* rowsize, unsigned long long* inst_out);
+
+// symbolic: row sizes of C for the rows of one bin
+struct SymLaunch {
+  int cls, logT;
+  const int* rows;
+  long long nrows;
+  int compressed;        // keys are column-set indices with OR-ed masks
+  long long kwords_max;  // dense: bitmap words (max over instances)
+  int l1_logT;           // spill: L1 table size
+  double max_occ;        // L1 maximum occupancy for new keys
+  void* l2_pool;         // spill: global pool
+  long long l2_chunk_slots;
+  int nchunks;
+};
+cudaError_t launch_symbolic(const LaunchCtx&, const ProbD&, const SymLaunch&, long long* rowsize);
+
+// numeric: columns and values of C for the rows of one bin
+struct NumLaunch {
+  int cls, logT;
+  const int* rows;
+  long long nrows;
+  int dtype;             // 0 = float, 1 = double
+  long long kwords_max;  // dense / spill: bitmap words
+  long long kmax;        // dense: values per chunk
+  int l1_logT;
+  double max_occ;
+  void* pool;            // dense values or spill L2 tables
+  long long chunk_bytes;
+  void* pool2;           // spill: bitmap + prefix words
+  long long chunk2_words;
+  int nchunks;
+};
+cudaError_t launch_numeric(const LaunchCtx&, const ProbD&, const NumLaunch&);
+
+// masked values-only product: out(i, l) = sum_j X(i,j) Y(j,l) for (i,l) in S.
+struct MaskedD {
+  MatD X, Y;             // X: rows x n, Y: n x k
+  const long long* Sp;   // pattern row pointers (int64)
+  const int* Sj;         // pattern columns (any order within a row)
+  void* out;             // values on the pattern
+  DevStatus* status;
+};
+struct MaskedLaunch {
+  int cls, logT;
+  const int* rows;
+  long long nrows;
+  int dtype;
+  void* pool;            // big rows: global tables
+  long long chunk_slots;
+  int nchunks;
+};
+cudaError_t launch_masked_bin_count(const LaunchCtx&, const MaskedD&, long long nrows, BinCfg cfg,
+                                    unsigned long long* hist);
+cudaError_t launch_masked_bin_scatter(const LaunchCtx&, const MaskedD&, long long nrows, BinCfg cfg,
+                                      unsigned long long* cursor, int* rows);
+cudaError_t launch_masked(const LaunchCtx&, const MaskedD&, const MaskedLaunch&);
+
+size_t masked_global_chunk_bytes(long long slots, int dtype);
+
+// transpose: At (n x m) with int64 row pointers and a value permutation.
+// count: column counts, their scan into Atp, and the longest row into *h_max
+// (host pinned); fill: scatter and per-row sort (rows longer than 16384 sort in
+// gbuf chunks of gbuf_len keys).
+size_t transpose_tmp_bytes(long long m, long long n, long long nnz);
+cudaError_t launch_transpose_count(const LaunchCtx&, const MatD& A, long long* Atp, void* tmp,
+                                   unsigned long long* h_max, DevStatus* st);
+cudaError_t launch_transpose_fill(const LaunchCtx&, const MatD& A, int dtype, const long long* Atp, int* Atj,
+                                  void* Atx, long long* perm, void* tmp, long long max_len,
+                                  unsigned long long* gbuf, long long gbuf_len, int gbuf_chunks, DevStatus* st);
+cudaError_t launch_gather_values(const LaunchCtx&, int dtype, const void* src, const long long* perm,
+                                 void* dst, long long n);
+
+}  // namespace kks

@@ -1,0 +1,429 @@
+// kks_numeric.cu -- numeric phase: columns and values of every row of C.
+//
+// Algorithm 3 with Phase = numeric: each product A(i,j) * B(j,l) is inserted
+// (accumulated) into the team's accumulator under key l; at the end of the
+// row the accumulator is written to C(i,:) at C_row_pointers(i).  The output
+// is canonical: every row is written sorted by column.
+//   k_num_hash<TW, VT>  : shared LP table (key, value) holding the whole row;
+//                         emission = compaction + bitonic sort of
+//                         (column << 32 | slot) in shared memory
+//   k_num_dense<TW, VT> : dense accumulator (Section 3.1.2): values in a
+//                         global k-wide pool chunk, column marker as a bitmap
+//                         in shared memory; emission walks the bitmap, so the
+//                         row comes out sorted and the chunk is reset to zero
+//   k_num_spill<TW, VT> : two-level LP accumulator (Algorithm 3 lines 7-11):
+//                         L1 in shared memory with the maximum-occupancy
+//                         cut-off, L2 in a global pool chunk; L2 entries whose
+//                         key also reached L1 are folded into L1, then each
+//                         entry is written at its rank from a column bitmap
+#include "kks_internal.h"
+
+namespace kks {
+
+namespace {
+
+__host__ __device__ constexpr size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
+
+template <int TW, typename VT>
+__host__ __device__ size_t num_team_bytes(int T) {
+  const int half = T / 2 > 0 ? T / 2 : 1;
+  return al16((size_t)T * sizeof(VT)) + al16((size_t)T * 4) + al16((size_t)half * 8) +
+         al16(sizeof(ChunkScratch<TW, VT>)) + 16;
+}
+
+template <int TW, typename VT>
+__global__ void k_num_hash(ProbD P, const int* __restrict__ rows, long long nrows, int logT) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long scan_scratch[33];
+  Team<TW> tm;
+  const int T = 1 << logT;
+  const unsigned tmask = (unsigned)T - 1u;
+  const int half = T / 2 > 0 ? T / 2 : 1;
+  unsigned char* base = smem + (size_t)tm.id * num_team_bytes<TW, VT>(T);
+  VT* vals = reinterpret_cast<VT*>(base);
+  int* keys = reinterpret_cast<int*>(base + al16((size_t)T * sizeof(VT)));
+  unsigned long long* sortb =
+      reinterpret_cast<unsigned long long*>(base + al16((size_t)T * sizeof(VT)) + al16((size_t)T * 4));
+  ChunkScratch<TW, VT>* csc = reinterpret_cast<ChunkScratch<TW, VT>*>(
+      base + al16((size_t)T * sizeof(VT)) + al16((size_t)T * 4) + al16((size_t)half * 8));
+
+  const long long team = (long long)blockIdx.x * tm.per_cta + tm.id;
+  const long long nteams = (long long)gridDim.x * tm.per_cta;
+  for (long long r = team; r < nrows; r += nteams) {
+    const long long g = rows[r];
+    const int b = inst_of(P.arow0s, P.ninst, g);
+    const InstD& I = P.inst[b];
+    const long long i = g - I.arow0;
+    const long long c0 = I.Crp[i];
+    const long long s = I.Crp[i + 1] - c0;
+    for (int x = tm.lane; x < T; x += TW) {
+      keys[x] = kEmpty;
+      vals[x] = VT(0);
+    }
+    tm.sync();
+    const long long a0 = rp_at(I.A, i), a1 = rp_at(I.A, i + 1);
+    const VT* __restrict__ Ax = reinterpret_cast<const VT*>(I.A.vx);
+    const VT* __restrict__ Bx = reinterpret_cast<const VT*>(I.B.vx);
+    const int* __restrict__ Bj = I.B.cj;
+    auto range = [&](int j, long long* bs, long long* be) {
+      *bs = rp_at(I.B, j);
+      *be = rp_at(I.B, j + 1);
+    };
+    auto aval = [&](long long p) { return Ax[p]; };
+    auto body = [&](long long q, int t) {
+      const int key = Bj[q];
+      const VT v = csc->av[t] * Bx[q];
+      const int slot = lp_insert(keys, tmask, nullptr, -1, key);
+      if (slot >= 0) atomicAdd(vals + slot, v);
+      else dev_fail(P.status, kDevTableFull, 10, g);
+    };
+    for_each_product<TW, VT>(tm, csc, scan_scratch, I.A.cj, a0, a1, range, aval, body);
+    // compaction of the occupied slots into (column << 32 | slot)
+    long long cnt = 0;
+    for (int xb = 0; xb < T; xb += TW) {
+      const int x = xb + tm.lane;
+      const bool o = x < T && keys[x] != kEmpty;
+      long long tot;
+      const long long ex = team_excl_scan<TW>(tm, o ? 1 : 0, &tot, scan_scratch);
+      if (o && cnt + ex < half)
+        sortb[cnt + ex] = ((unsigned long long)(unsigned)keys[x] << 32) | (unsigned)x;
+      cnt += tot;
+    }
+    if (tm.lane == 0 && cnt != s) dev_fail(P.status, kDevRowSizeMismatch, 11, g);
+    const int n = (int)(cnt < half ? cnt : half);
+    int N = 1;
+    while (N < n) N <<= 1;
+    for (int x = n + tm.lane; x < N; x += TW) sortb[x] = ~0ull;
+    tm.sync();
+    team_bitonic<TW>(tm, sortb, N);
+    const long long nw = n < s ? n : s;
+    VT* __restrict__ Cx = reinterpret_cast<VT*>(I.Cx);
+    int* __restrict__ Cj = I.Cj;
+    for (long long x = tm.lane; x < nw; x += TW) {
+      const unsigned long long e = sortb[x];
+      Cj[c0 + x] = (int)(e >> 32);
+      Cx[c0 + x] = vals[(unsigned)(e & 0xffffffffull)];
+    }
+    tm.sync();
+  }
+}
+
+template <int TW, typename VT>
+__global__ void __launch_bounds__(TW) k_num_dense(ProbD P, const int* __restrict__ rows, long long nrows,
+                                                  long long kw_max, VT* pool, long long kmax) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long scan_scratch[33];
+  Team<TW> tm;
+  unsigned* bm = reinterpret_cast<unsigned*>(smem);
+  ChunkScratch<TW, VT>* csc = reinterpret_cast<ChunkScratch<TW, VT>*>(smem + al16((size_t)kw_max * 4));
+  VT* dense = pool + (long long)blockIdx.x * kmax;
+  for (long long w = tm.lane; w < kw_max; w += TW) bm[w] = 0u;
+  __syncthreads();
+  for (long long r = blockIdx.x; r < nrows; r += gridDim.x) {
+    const long long g = rows[r];
+    const int b = inst_of(P.arow0s, P.ninst, g);
+    const InstD& I = P.inst[b];
+    const long long i = g - I.arow0;
+    const long long c0 = I.Crp[i];
+    const long long s = I.Crp[i + 1] - c0;
+    const long long k = I.k;
+    const long long kw = (k + 31) >> 5;
+    const long long a0 = rp_at(I.A, i), a1 = rp_at(I.A, i + 1);
+    const VT* __restrict__ Ax = reinterpret_cast<const VT*>(I.A.vx);
+    const VT* __restrict__ Bx = reinterpret_cast<const VT*>(I.B.vx);
+    const int* __restrict__ Bj = I.B.cj;
+    auto range = [&](int j, long long* bs, long long* be) {
+      *bs = rp_at(I.B, j);
+      *be = rp_at(I.B, j + 1);
+    };
+    auto aval = [&](long long p) { return Ax[p]; };
+    auto body = [&](long long q, int t) {
+      const int col = Bj[q];
+      if ((unsigned long long)(unsigned)col < (unsigned long long)k) {
+        atomicAdd(dense + col, csc->av[t] * Bx[q]);
+        atomicOr(bm + (col >> 5), 1u << (col & 31));
+      } else {
+        dev_fail(P.status, kDevBadIndex, 12, g);
+      }
+    };
+    for_each_product<TW, VT>(tm, csc, scan_scratch, I.A.cj, a0, a1, range, aval, body);
+    __threadfence_block();
+    __syncthreads();
+    VT* __restrict__ Cx = reinterpret_cast<VT*>(I.Cx);
+    int* __restrict__ Cj = I.Cj;
+    long long run = 0;
+    for (long long wb = 0; wb < kw; wb += TW) {
+      const long long w = wb + tm.lane;
+      unsigned word = (w < kw) ? bm[w] : 0u;
+      long long tot;
+      long long pos = run + team_excl_scan<TW>(tm, __popc(word), &tot, scan_scratch);
+      while (word) {
+        const int bit = __ffs(word) - 1;
+        word &= word - 1u;
+        const long long col = w * 32 + bit;
+        const VT v = dense[col];
+        dense[col] = VT(0);
+        if (pos < s) {
+          Cj[c0 + pos] = (int)col;
+          Cx[c0 + pos] = v;
+        }
+        ++pos;
+      }
+      if (w < kw) bm[w] = 0u;
+      run += tot;
+    }
+    if (tm.lane == 0 && run != s) dev_fail(P.status, kDevRowSizeMismatch, 13, g);
+    __threadfence_block();
+    __syncthreads();
+  }
+}
+
+template <int TW, typename VT>
+__host__ __device__ size_t spill_l1_bytes(int T) {
+  return al16((size_t)T * sizeof(VT)) + al16((size_t)T * 4) + al16(sizeof(ChunkScratch<TW, VT>)) + 16;
+}
+
+template <int TW, typename VT>
+__global__ void __launch_bounds__(TW) k_num_spill(ProbD P, const int* __restrict__ rows, long long nrows,
+                                                  int l1_logT, int cap, unsigned char* pool, long long l2_slots,
+                                                  long long chunk_bytes, unsigned* pool2, long long kw_max) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long scan_scratch[33];
+  Team<TW> tm;
+  const int T = 1 << l1_logT;
+  const unsigned tmask = (unsigned)T - 1u;
+  VT* vals1 = reinterpret_cast<VT*>(smem);
+  int* keys1 = reinterpret_cast<int*>(smem + al16((size_t)T * sizeof(VT)));
+  ChunkScratch<TW, VT>* csc =
+      reinterpret_cast<ChunkScratch<TW, VT>*>(smem + al16((size_t)T * sizeof(VT)) + al16((size_t)T * 4));
+  int* occ = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(csc) + al16(sizeof(ChunkScratch<TW, VT>)));
+  int* keys2 = reinterpret_cast<int*>(pool + (long long)blockIdx.x * chunk_bytes);
+  VT* vals2 = reinterpret_cast<VT*>(reinterpret_cast<unsigned char*>(keys2) + al16((size_t)l2_slots * 4));
+  const unsigned t2mask = (unsigned)l2_slots - 1u;
+  unsigned* bm = pool2 + (long long)blockIdx.x * 2 * kw_max;
+  unsigned* pre = bm + kw_max;
+
+  for (long long r = blockIdx.x; r < nrows; r += gridDim.x) {
+    const long long g = rows[r];
+    const int b = inst_of(P.arow0s, P.ninst, g);
+    const InstD& I = P.inst[b];
+    const long long i = g - I.arow0;
+    const long long c0 = I.Crp[i];
+    const long long s = I.Crp[i + 1] - c0;
+    const long long k = I.k;
+    const long long kw = (k + 31) >> 5;
+    for (int x = tm.lane; x < T; x += TW) {
+      keys1[x] = kEmpty;
+      vals1[x] = VT(0);
+    }
+    for (long long x = tm.lane; x < l2_slots; x += TW) {
+      keys2[x] = kEmpty;
+      vals2[x] = VT(0);
+    }
+    if (tm.lane == 0) *occ = 0;
+    __threadfence_block();
+    __syncthreads();
+    const long long a0 = rp_at(I.A, i), a1 = rp_at(I.A, i + 1);
+    const VT* __restrict__ Ax = reinterpret_cast<const VT*>(I.A.vx);
+    const VT* __restrict__ Bx = reinterpret_cast<const VT*>(I.B.vx);
+    const int* __restrict__ Bj = I.B.cj;
+    auto range = [&](int j, long long* bs, long long* be) {
+      *bs = rp_at(I.B, j);
+      *be = rp_at(I.B, j + 1);
+    };
+    auto aval = [&](long long p) { return Ax[p]; };
+    auto body = [&](long long q, int t) {
+      const int key = Bj[q];
+      if ((unsigned long long)(unsigned)key >= (unsigned long long)k) {
+        dev_fail(P.status, kDevBadIndex, 14, g);
+        return;
+      }
+      const VT v = csc->av[t] * Bx[q];
+      const int s1 = lp_insert(keys1, tmask, occ, cap, key);
+      if (s1 >= 0) {
+        atomicAdd(vals1 + s1, v);
+      } else {
+        const int s2 = lp_insert(keys2, t2mask, nullptr, -1, key);
+        if (s2 >= 0) atomicAdd(vals2 + s2, v);
+        else dev_fail(P.status, kDevTableFull, 15, g);
+      }
+    };
+    for_each_product<TW, VT>(tm, csc, scan_scratch, I.A.cj, a0, a1, range, aval, body);
+    __threadfence_block();
+    __syncthreads();
+    // fold L2 entries whose key also reached L1 into L1
+    for (long long x = tm.lane; x < l2_slots; x += TW) {
+      const int kk = keys2[x];
+      if (kk < 0) continue;
+      const int s1 = lp_find(keys1, tmask, kk);
+      if (s1 >= 0) {
+        vals1[s1] += vals2[x];
+        keys2[x] = -2;
+      }
+    }
+    __threadfence_block();
+    __syncthreads();
+    for (int x = tm.lane; x < T; x += TW) {
+      const int kk = keys1[x];
+      if (kk >= 0) atomicOr(bm + (kk >> 5), 1u << (kk & 31));
+    }
+    for (long long x = tm.lane; x < l2_slots; x += TW) {
+      const int kk = keys2[x];
+      if (kk >= 0) atomicOr(bm + (kk >> 5), 1u << (kk & 31));
+    }
+    __threadfence_block();
+    __syncthreads();
+    long long run = 0;
+    for (long long wb = 0; wb < kw; wb += TW) {
+      const long long w = wb + tm.lane;
+      const unsigned word = (w < kw) ? bm[w] : 0u;
+      long long tot;
+      const long long ex = team_excl_scan<TW>(tm, __popc(word), &tot, scan_scratch);
+      if (w < kw) pre[w] = (unsigned)(run + ex);
+      run += tot;
+    }
+    if (tm.lane == 0 && run != s) dev_fail(P.status, kDevRowSizeMismatch, 16, g);
+    __threadfence_block();
+    __syncthreads();
+    VT* __restrict__ Cx = reinterpret_cast<VT*>(I.Cx);
+    int* __restrict__ Cj = I.Cj;
+    auto rank_of = [&](int kk) -> long long {
+      const int w = kk >> 5;
+      return (long long)pre[w] + __popc(bm[w] & ((1u << (kk & 31)) - 1u));
+    };
+    for (int x = tm.lane; x < T; x += TW) {
+      const int kk = keys1[x];
+      if (kk < 0) continue;
+      const long long p = rank_of(kk);
+      if (p < s) {
+        Cj[c0 + p] = kk;
+        Cx[c0 + p] = vals1[x];
+      }
+    }
+    for (long long x = tm.lane; x < l2_slots; x += TW) {
+      const int kk = keys2[x];
+      if (kk < 0) continue;
+      const long long p = rank_of(kk);
+      if (p < s) {
+        Cj[c0 + p] = kk;
+        Cx[c0 + p] = vals2[x];
+      }
+    }
+    __threadfence_block();
+    __syncthreads();
+    for (long long w = tm.lane; w < kw; w += TW) bm[w] = 0u;
+    __threadfence_block();
+    __syncthreads();
+  }
+}
+
+template <class K>
+cudaError_t set_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return cudaSuccess;
+}
+
+template <int TW, typename VT>
+cudaError_t run_hash(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
+  const int T = 1 << S.logT;
+  const size_t tb = num_team_bytes<TW, VT>(T);
+  int teams = 1;
+  if (TW <= 32) {
+    teams = (int)((48 * 1024) / tb);
+    int tmax = 256 / TW;
+    if (teams > tmax) teams = tmax;
+    if (teams < 1) teams = 1;
+  }
+  const size_t smem = tb * teams;
+  if (smem > (size_t)L.max_smem_optin) return cudaErrorInvalidConfiguration;
+  auto kern = k_num_hash<TW, VT>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  long long grid = (S.nrows + teams - 1) / teams;
+  long long cap = (long long)L.num_sms * 64;
+  if (grid > cap) grid = cap;
+  kern<<<(unsigned)grid, TW * teams, smem, L.stream>>>(P, S.rows, S.nrows, S.logT);
+  return cudaGetLastError();
+}
+
+template <typename VT>
+cudaError_t run_dense(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
+  constexpr int TW = 1024;
+  const size_t smem = al16((size_t)S.kwords_max * 4) + al16(sizeof(ChunkScratch<TW, VT>));
+  if (smem > (size_t)L.max_smem_optin) return cudaErrorInvalidConfiguration;
+  auto kern = k_num_dense<TW, VT>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  long long grid = S.nchunks;
+  if (grid > S.nrows) grid = S.nrows;
+  kern<<<(unsigned)grid, TW, smem, L.stream>>>(P, S.rows, S.nrows, S.kwords_max, (VT*)S.pool, S.kmax);
+  return cudaGetLastError();
+}
+
+template <typename VT>
+cudaError_t run_spill(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
+  constexpr int TW = 1024;
+  const int T = 1 << S.l1_logT;
+  const size_t smem = spill_l1_bytes<TW, VT>(T);
+  if (smem > (size_t)L.max_smem_optin) return cudaErrorInvalidConfiguration;
+  auto kern = k_num_spill<TW, VT>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  int cap = (int)(S.max_occ * T);
+  if (cap < 1) cap = 1;
+  if (cap > T - 1) cap = T - 1;
+  long long grid = S.nchunks;
+  if (grid > S.nrows) grid = S.nrows;
+  const long long l2_slots = 1ll << S.logT;
+  kern<<<(unsigned)grid, TW, smem, L.stream>>>(P, S.rows, S.nrows, S.l1_logT, cap, (unsigned char*)S.pool, l2_slots,
+                                               S.chunk_bytes, (unsigned*)S.pool2, S.kwords_max);
+  return cudaGetLastError();
+}
+
+template <typename VT>
+cudaError_t dispatch(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
+  switch (S.cls) {
+    case kClsW8: return run_hash<8, VT>(L, P, S);
+    case kClsW32: return run_hash<32, VT>(L, P, S);
+    case kClsC256: return run_hash<256, VT>(L, P, S);
+    case kClsC1024: return run_hash<1024, VT>(L, P, S);
+    case kClsDense: return run_dense<VT>(L, P, S);
+    case kClsSpill: return run_spill<VT>(L, P, S);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+size_t numeric_team_bytes(int cls, int logT, int dtype) {
+  const int T = 1 << logT;
+  if (dtype == 1) {
+    switch (cls) {
+      case kClsW8: return num_team_bytes<8, double>(T);
+      case kClsW32: return num_team_bytes<32, double>(T);
+      case kClsC256: return num_team_bytes<256, double>(T);
+      default: return num_team_bytes<1024, double>(T);
+    }
+  }
+  switch (cls) {
+    case kClsW8: return num_team_bytes<8, float>(T);
+    case kClsW32: return num_team_bytes<32, float>(T);
+    case kClsC256: return num_team_bytes<256, float>(T);
+    default: return num_team_bytes<1024, float>(T);
+  }
+}
+
+size_t numeric_spill_l1_bytes(int logT, int dtype) {
+  return dtype == 1 ? spill_l1_bytes<1024, double>(1 << logT) : spill_l1_bytes<1024, float>(1 << logT);
+}
+
+size_t numeric_l2_chunk_bytes(long long slots, int dtype) {
+  return al16((size_t)slots * 4) + al16((size_t)slots * (dtype == 1 ? 8 : 4));
+}
+
+cudaError_t launch_numeric(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
+  if (S.nrows <= 0) return cudaSuccess;
+  return S.dtype == 1 ? dispatch<double>(L, P, S) : dispatch<float>(L, P, S);
+}
+
+}  // namespace kks

@@ -1,0 +1,444 @@
+// kks_prep.cu -- row statistics, column-set compression, scans and row binning.
+//
+// Row statistics follow the paper's definitions: the product count of row i
+// is rf_i = sum over j in A(i,:) of |B(j,:)| and f_m = sum rf_i (Section 2,
+// after Algorithm 1); maxrf = max rf_i sizes the L2 accumulators (Section
+// 3.1.2, memory pool).  Compression (Section 3.2) packs the columns of a B row
+// into column-set indices CSI = col >> 5 with a 32-bit set CS; a first pass
+// counts the compressed row lengths so the compressed product count can decide
+// whether compressing pays (more than a 15 % reduction), a second pass fills.
+#include "kks_internal.h"
+
+namespace kks {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+__device__ __forceinline__ int lanemask_lt() {
+  unsigned r;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
+  return (int)r;
+}
+
+template <int TW>
+__device__ __forceinline__ long long warp_team_sum(const Team<TW>& tm, long long v) {
+#pragma unroll
+  for (int d = TW / 2; d > 0; d >>= 1) v += __shfl_xor_sync(tm.mask, v, d, TW);
+  return v;
+}
+
+inline int grid_for(long long items, int per_block, int num_sms, int cap_per_sm = 32) {
+  long long g = (items + per_block - 1) / per_block;
+  long long cap = (long long)num_sms * cap_per_sm;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+// -------------------------------------------------------------- compression
+template <int TW>
+__global__ void __launch_bounds__(kBlock) k_compress_count(ProbD P, long long totalB, long long* cnt) {
+  Team<TW> tm;
+  const long long nteams = (long long)gridDim.x * tm.per_cta;
+  for (long long gb = (long long)blockIdx.x * tm.per_cta + tm.id; gb < totalB; gb += nteams) {
+    const int b = inst_of(P.brow0s, P.ninst, gb);
+    const InstD& I = P.inst[b];
+    const long long j = gb - I.brow0;
+    const long long s = rp_at(I.B, j), e = rp_at(I.B, j + 1);
+    const int* cj = I.B.cj;
+    long long c = 0;
+    if (s < 0 || s > e || e > I.B.nnz) {   // malformed row pointers: report, read nothing
+      if (tm.lane == 0) {
+        dev_fail(P.status, kDevBadIndex, 40, gb);
+        cnt[gb] = 0;
+      }
+      continue;
+    }
+    for (long long p = s + tm.lane; p < e; p += TW) {
+      int col = cj[p];
+      if ((unsigned long long)(unsigned)col >= (unsigned long long)I.k) dev_fail(P.status, kDevBadIndex, 41, gb);
+      if (p == s || (col >> 5) != (cj[p - 1] >> 5)) ++c;
+    }
+    c = warp_team_sum<TW>(tm, c);
+    if (tm.lane == 0) cnt[gb] = c;
+  }
+}
+
+// Runs of equal CSI in row order become one compressed entry; rows with sorted
+// columns therefore get exactly one entry per distinct CSI.  cs must be zero.
+template <int TW>
+__global__ void __launch_bounds__(kBlock) k_compress_fill(ProbD P, long long totalB, int* csi, unsigned* cs) {
+  Team<TW> tm;
+  const long long nteams = (long long)gridDim.x * tm.per_cta;
+  const int base_lane = (threadIdx.x & 31) & ~(TW - 1);
+  for (long long gb = (long long)blockIdx.x * tm.per_cta + tm.id; gb < totalB; gb += nteams) {
+    const int b = inst_of(P.brow0s, P.ninst, gb);
+    const InstD& I = P.inst[b];
+    if (!I.compressed) continue;
+    const long long j = gb - I.brow0;
+    const long long s = rp_at(I.B, j), e = rp_at(I.B, j + 1);
+    const int* cj = I.B.cj;
+    long long run = P.Bcp[gb] - 1;   // index of the last run opened so far
+    for (long long c0 = s; c0 < e; c0 += TW) {
+      const long long p = c0 + tm.lane;
+      const bool valid = p < e;
+      const int col = valid ? cj[p] : 0;
+      const bool head = valid && (p == s || (col >> 5) != (cj[p - 1] >> 5));
+      const unsigned hb = (__ballot_sync(tm.mask, head) >> base_lane) & ((TW == 32) ? 0xffffffffu : ((1u << TW) - 1u));
+      const unsigned le = (tm.lane == 31) ? 0xffffffffu : ((2u << tm.lane) - 1u);
+      const long long ridx = run + __popc(hb & le);
+      if (head) csi[ridx] = col >> 5;
+      // segmented OR over the lanes of each run inside this chunk
+      unsigned v = valid ? (1u << (col & 31)) : 0u;
+      int f = (head || tm.lane == 0) ? 1 : 0;
+#pragma unroll
+      for (int d = 1; d < TW; d <<= 1) {
+        unsigned vu = __shfl_up_sync(tm.mask, v, d, TW);
+        int fu = __shfl_up_sync(tm.mask, f, d, TW);
+        if (tm.lane >= d && !f) {
+          v |= vu;
+          f = fu;
+        }
+      }
+      const bool next_head = (tm.lane + 1 < TW) && ((hb >> (tm.lane + 1)) & 1u);
+      const bool tail = valid && (tm.lane == TW - 1 || p + 1 >= e || next_head);
+      if (tail) atomicOr(cs + ridx, v);
+      run += __popc(hb);
+      tm.sync();
+    }
+  }
+}
+
+// -------------------------------------------------------------- row statistics
+// inst_stats per instance: [f_m, maxrf, f_m compressed, maxrf compressed]
+template <int TW>
+__global__ void __launch_bounds__(kBlock) k_row_stats(ProbD P, long long totalA, int use_bc, long long rows_per_block,
+                                                      long long* rf, long long* rfc,
+                                                      unsigned long long* inst_stats) {
+  Team<TW> tm;
+  __shared__ unsigned long long acc[4];
+  __shared__ int b_first, b_last;
+  const long long g0 = (long long)blockIdx.x * rows_per_block;
+  if (g0 >= totalA) return;
+  long long g1 = g0 + rows_per_block;
+  if (g1 > totalA) g1 = totalA;
+  if (threadIdx.x == 0) {
+    acc[0] = acc[1] = acc[2] = acc[3] = 0ull;
+    b_first = inst_of(P.arow0s, P.ninst, g0);
+    b_last = inst_of(P.arow0s, P.ninst, g1 - 1);
+  }
+  __syncthreads();
+  const bool single = (b_first == b_last);
+  for (long long g = g0 + tm.id; g < g1; g += tm.per_cta) {
+    const int b = single ? b_first : inst_of(P.arow0s, P.ninst, g);
+    const InstD& I = P.inst[b];
+    const long long i = g - I.arow0;
+    const long long s = rp_at(I.A, i), e = rp_at(I.A, i + 1);
+    long long f = 0, fc = 0;
+    // this is the first kernel that follows A's indices into B: validate them
+    // here so malformed input stops the symbolic phase at its first sync
+    const bool rows_ok = (s >= 0 && s <= e && e <= I.A.nnz);
+    if (!rows_ok && tm.lane == 0) dev_fail(P.status, kDevBadIndex, 42, g);
+    for (long long p = s + tm.lane; rows_ok && p < e; p += TW) {
+      const int j = I.A.cj[p];
+      if ((unsigned long long)(unsigned)j >= (unsigned long long)I.A.ncols) {
+        dev_fail(P.status, kDevBadIndex, 43, g);
+        continue;
+      }
+      const long long bs = rp_at(I.B, j), be = rp_at(I.B, j + 1);
+      if (bs < 0 || bs > be || be > I.B.nnz) {
+        dev_fail(P.status, kDevBadIndex, 44, g);
+        continue;
+      }
+      f += be - bs;
+      if (use_bc) fc += P.Bcp[I.brow0 + j + 1] - P.Bcp[I.brow0 + j];
+    }
+    f = warp_team_sum<TW>(tm, f);
+    fc = warp_team_sum<TW>(tm, fc);
+    if (tm.lane == 0) {
+      rf[g] = f;
+      if (rfc) rfc[g] = fc;
+      if (single) {
+        atomicAdd(&acc[0], (unsigned long long)f);
+        atomicMax(&acc[1], (unsigned long long)f);
+        atomicAdd(&acc[2], (unsigned long long)fc);
+        atomicMax(&acc[3], (unsigned long long)fc);
+      } else {
+        unsigned long long* st = inst_stats + 4ll * b;
+        atomicAdd(st + 0, (unsigned long long)f);
+        atomicMax(st + 1, (unsigned long long)f);
+        atomicAdd(st + 2, (unsigned long long)fc);
+        atomicMax(st + 3, (unsigned long long)fc);
+      }
+    }
+  }
+  __syncthreads();
+  if (single && threadIdx.x == 0) {
+    unsigned long long* st = inst_stats + 4ll * b_first;
+    atomicAdd(st + 0, acc[0]);
+    atomicMax(st + 1, acc[1]);
+    atomicAdd(st + 2, acc[2]);
+    atomicMax(st + 3, acc[3]);
+  }
+}
+
+// -------------------------------------------------------------- scan
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ long long block_excl_scan(long long v, long long* total) {
+  __shared__ long long ws[33];
+  const int l = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  long long x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    long long y = __shfl_up_sync(0xffffffffu, x, d);
+    if (l >= d) x += y;
+  }
+  if (l == 31) ws[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    long long s = (l < nw) ? ws[l] : 0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      long long y = __shfl_up_sync(0xffffffffu, s, d);
+      if (l >= d) s += y;
+    }
+    if (l < nw) ws[l] = s;
+    if (l == 31) ws[32] = s;
+  }
+  __syncthreads();
+  long long r = ((w > 0) ? ws[w - 1] : 0) + x - v;
+  *total = ws[32];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const long long* in, long long n, long long* bsum) {
+  const long long base = (long long)blockIdx.x * kScanTile;
+  long long s = 0;
+#pragma unroll
+  for (int t = 0; t < kScanItems; ++t) {
+    long long idx = base + (long long)t * kScanThreads + threadIdx.x;
+    if (idx < n) s += in[idx];
+  }
+  long long tot;
+  block_excl_scan(s, &tot);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_top(long long* bsum, long long nb) {
+  long long carry = 0;
+  for (long long base = 0; base < nb; base += blockDim.x) {
+    long long idx = base + threadIdx.x;
+    long long v = (idx < nb) ? bsum[idx] : 0;
+    long long tot;
+    long long ex = block_excl_scan(v, &tot);
+    if (idx < nb) bsum[idx] = carry + ex;
+    carry += tot;
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const long long* in, long long* out, long long n,
+                                                             const long long* bsum) {
+  const long long base = (long long)blockIdx.x * kScanTile;
+  long long v[kScanItems];
+  long long s = 0;
+  // each thread owns kScanItems consecutive items
+#pragma unroll
+  for (int t = 0; t < kScanItems; ++t) {
+    long long idx = base + (long long)threadIdx.x * kScanItems + t;
+    v[t] = (idx < n) ? in[idx] : 0;
+    s += v[t];
+  }
+  long long tot;
+  long long run = block_excl_scan(s, &tot) + bsum[blockIdx.x];
+#pragma unroll
+  for (int t = 0; t < kScanItems; ++t) {
+    long long idx = base + (long long)threadIdx.x * kScanItems + t;
+    if (idx < n) out[idx] = run;
+    run += v[t];
+    if (idx == n - 1) out[n] = run;
+  }
+}
+
+__global__ void k_set_zero_ll(long long* p) { *p = 0; }
+
+// -------------------------------------------------------------- binning
+struct RowBin {
+  __device__ __forceinline__ static int get(const ProbD& P, long long g, int phase, const long long* rf,
+                                            const long long* rfc, const long long* rowsize, const BinCfg& cfg) {
+    const int b = inst_of(P.arow0s, P.ninst, g);
+    const InstD& I = P.inst[b];
+    const long long k = I.k;
+    const long long kw = (k + 31) >> 5;
+    if (phase == 2 || phase == 3) {
+      // symbolic: phase 2 lists the rows of compressed products, phase 3 the others
+      if ((phase == 2) != (I.compressed != 0)) return -1;
+      if (I.compressed) {
+        long long w = rfc[g];
+        long long u = w < kw ? w : kw;
+        return choose_bin(u, w, kw, kw, cfg);
+      }
+      long long w = rf[g];
+      long long u = w < k ? w : k;
+      return choose_bin(u, w, k, kw, cfg);
+    }
+    return choose_bin(rowsize[g], rf[g], k, kw, cfg);
+  }
+};
+
+__global__ void __launch_bounds__(kBlock) k_bin_count(ProbD P, long long totalA, int phase, const long long* rf,
+                                                      const long long* rfc, const long long* rowsize, BinCfg cfg,
+                                                      unsigned long long* hist) {
+  __shared__ unsigned long long h[kNumBins];
+  for (int t = threadIdx.x; t < kNumBins; t += blockDim.x) h[t] = 0ull;
+  __syncthreads();
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < totalA; base += stride) {
+    const long long g = base + threadIdx.x;
+    const int bin = (g < totalA) ? RowBin::get(P, g, phase, rf, rfc, rowsize, cfg) : -1;
+    const unsigned grp = __match_any_sync(0xffffffffu, bin);
+    if (bin >= 0 && (__ffs(grp) - 1) == (threadIdx.x & 31)) atomicAdd(&h[bin], (unsigned long long)__popc(grp));
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < kNumBins; t += blockDim.x)
+    if (h[t]) atomicAdd(&hist[t], h[t]);
+}
+
+__global__ void __launch_bounds__(kBlock) k_bin_scatter(ProbD P, long long totalA, int phase, const long long* rf,
+                                                        const long long* rfc, long long* rowsize, BinCfg cfg,
+                                                        unsigned long long* cursor, int* rows) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < totalA; base += stride) {
+    const long long g = base + threadIdx.x;
+    const int bin = (g < totalA) ? RowBin::get(P, g, phase, rf, rfc, rowsize, cfg) : -1;
+    if (bin >= 0 && bin_cls(bin) == kClsNone && phase != 1) rowsize[g] = 0;
+    const int key = (bin >= 0 && bin_cls(bin) != kClsNone) ? bin : -1;
+    const unsigned grp = __match_any_sync(0xffffffffu, key);
+    const int leader = __ffs(grp) - 1;
+    unsigned long long pos = 0;
+    if (key >= 0 && lane == leader) pos = atomicAdd(&cursor[key], (unsigned long long)__popc(grp));
+    pos = __shfl_sync(0xffffffffu, pos, leader);
+    if (key >= 0) rows[pos + __popc(grp & (unsigned)lanemask_lt())] = (int)g;
+  }
+}
+
+// -------------------------------------------------------------- C row pointers
+// inst_out per instance: [nnz(C), maxrs]
+__global__ void __launch_bounds__(kBlock) k_write_rowptr(ProbD P, long long totalA, const long long* offs,
+                                                         const long long* rowsize, unsigned long long* inst_out) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < totalA; base += stride) {
+    const long long g = base + threadIdx.x;
+    int b = -1;
+    unsigned rs = 0;
+    if (g < totalA) {
+      b = inst_of(P.arow0s, P.ninst, g);
+      const InstD& I = P.inst[b];
+      const long long i = g - I.arow0;
+      const long long o0 = offs[I.arow0];
+      I.Crp[i] = offs[g] - o0;
+      if (i == I.A.nrows - 1) {
+        I.Crp[i + 1] = offs[g + 1] - o0;
+        inst_out[2ll * b] = (unsigned long long)(offs[g + 1] - o0);
+      }
+      rs = (unsigned)rowsize[g];
+    }
+    const int b0 = __shfl_sync(0xffffffffu, b, 0);
+    if (__all_sync(0xffffffffu, b == b0)) {
+      const unsigned mx = __reduce_max_sync(0xffffffffu, rs);
+      if (b0 >= 0 && (threadIdx.x & 31) == 0) atomicMax(&inst_out[2ll * b0 + 1], (unsigned long long)mx);
+    } else if (b >= 0) {
+      atomicMax(&inst_out[2ll * b + 1], (unsigned long long)rs);
+    }
+  }
+}
+
+__global__ void k_empty_instances(ProbD P, unsigned long long* inst_out) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < P.ninst; b += gridDim.x * blockDim.x) {
+    const InstD& I = P.inst[b];
+    if (I.A.nrows == 0) {
+      I.Crp[0] = 0;
+      inst_out[2ll * b] = 0ull;
+    }
+  }
+}
+
+}  // namespace
+
+// ============================================================== launchers
+cudaError_t launch_compress_count(const LaunchCtx& L, const ProbD& P, long long totalB, long long* cnt) {
+  if (totalB <= 0) return cudaSuccess;
+  int grid = grid_for(totalB, kBlock / 8, L.num_sms);
+  k_compress_count<8><<<grid, kBlock, 0, L.stream>>>(P, totalB, cnt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_compress_fill(const LaunchCtx& L, const ProbD& P, long long totalB, int* csi, unsigned* cs) {
+  if (totalB <= 0) return cudaSuccess;
+  int grid = grid_for(totalB, kBlock / 8, L.num_sms);
+  k_compress_fill<8><<<grid, kBlock, 0, L.stream>>>(P, totalB, csi, cs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_row_stats(const LaunchCtx& L, const ProbD& P, long long totalA, int use_bc, long long* rf,
+                             long long* rfc, unsigned long long* inst_stats) {
+  if (totalA <= 0) return cudaSuccess;
+  const long long rpb = 1024;
+  long long grid = (totalA + rpb - 1) / rpb;
+  k_row_stats<8><<<(unsigned)grid, kBlock, 0, L.stream>>>(P, totalA, use_bc, rpb, rf, rfc, inst_stats);
+  return cudaGetLastError();
+}
+
+size_t scan_tmp_bytes(long long n) {
+  long long nb = (n + kScanTile - 1) / kScanTile;
+  if (nb < 1) nb = 1;
+  return (size_t)nb * sizeof(long long);
+}
+
+cudaError_t launch_scan(const LaunchCtx& L, const long long* in, long long* out, long long n, void* tmp) {
+  if (n <= 0) {
+    k_set_zero_ll<<<1, 1, 0, L.stream>>>(out);
+    return cudaGetLastError();
+  }
+  long long nb = (n + kScanTile - 1) / kScanTile;
+  long long* bsum = (long long*)tmp;
+  k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, L.stream>>>(in, n, bsum);
+  k_scan_top<<<1, 1024, 0, L.stream>>>(bsum, nb);
+  k_scan_apply<<<(unsigned)nb, kScanThreads, 0, L.stream>>>(in, out, n, bsum);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bin_count(const LaunchCtx& L, const ProbD& P, long long totalA, int phase, const long long* rf,
+                             const long long* rfc, const long long* rowsize, BinCfg cfg, unsigned long long* hist) {
+  if (totalA <= 0) return cudaSuccess;
+  int grid = grid_for(totalA, kBlock, L.num_sms, 8);
+  k_bin_count<<<grid, kBlock, 0, L.stream>>>(P, totalA, phase, rf, rfc, rowsize, cfg, hist);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bin_scatter(const LaunchCtx& L, const ProbD& P, long long totalA, int phase, const long long* rf,
+                               const long long* rfc, const long long* rowsize, BinCfg cfg,
+                               unsigned long long* cursor, int* rows) {
+  if (totalA <= 0) return cudaSuccess;
+  int grid = grid_for(totalA, kBlock, L.num_sms, 8);
+  k_bin_scatter<<<grid, kBlock, 0, L.stream>>>(P, totalA, phase, rf, rfc, const_cast<long long*>(rowsize), cfg,
+                                               cursor, rows);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_write_rowptr(const LaunchCtx& L, const ProbD& P, long long totalA, const long long* offs,
+                                const long long* rowsize, unsigned long long* inst_out) {
+  k_empty_instances<<<(P.ninst + 255) / 256, 256, 0, L.stream>>>(P, inst_out);
+  if (totalA > 0) {
+    int grid = grid_for(totalA, kBlock, L.num_sms, 8);
+    k_write_rowptr<<<grid, kBlock, 0, L.stream>>>(P, totalA, offs, rowsize, inst_out);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace kks

@@ -1,0 +1,280 @@
+// kks_symbolic.cu -- symbolic phase: the size of every row of C.
+//
+// Algorithm 3 with Phase = symbolic: a team takes a row i of A, runs over the
+// products of A(i,:) with the rows of B and inserts the column keys into its
+// level-1 accumulator; C_row_pointers(i) is the number of distinct columns.
+// On the compressed B (Section 3.2) the keys are column-set indices and the
+// accumulator ORs the 32-bit column sets, so the row size is the number of
+// set bits of the union.  Variants:
+//   k_sym_hash<TW, COMP, false> : shared LP table sized to hold the row
+//   k_sym_hash<TW, COMP, true>  : shared L1 table with the maximum-occupancy
+//                                 cut-off plus a global L2 table (Algorithm 3
+//                                 lines 7-11); a key may sit in both levels,
+//                                 so the count merges them (union)
+//   k_sym_dense<COMP>           : a k-bit bitmap in shared memory (the dense
+//                                 accumulator of Section 3.1.2 in bit form)
+#include "kks_internal.h"
+
+namespace kks {
+
+namespace {
+
+__host__ __device__ constexpr size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
+
+template <int TW, bool COMP>
+__host__ __device__ size_t sym_team_bytes(int T) {
+  return al16((size_t)T * 4) * (COMP ? 2 : 1) + al16(sizeof(ChunkScratch<TW, int>)) + 16;
+}
+
+template <int TW, bool COMP, bool SPILL>
+__global__ void k_sym_hash(ProbD P, const int* __restrict__ rows, long long nrows, int logT, int cap,
+                           int* l2_pool, long long l2_slots, long long* __restrict__ rowsize) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long scan_scratch[33];
+  Team<TW> tm;
+  const int T = 1 << logT;
+  const unsigned tmask = (unsigned)T - 1u;
+  unsigned char* base = smem + (size_t)tm.id * sym_team_bytes<TW, COMP>(T);
+  int* keys = reinterpret_cast<int*>(base);
+  unsigned* masks = reinterpret_cast<unsigned*>(base + al16((size_t)T * 4));
+  ChunkScratch<TW, int>* csc =
+      reinterpret_cast<ChunkScratch<TW, int>*>(base + al16((size_t)T * 4) * (COMP ? 2 : 1));
+  int* occ = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(csc) + al16(sizeof(ChunkScratch<TW, int>)));
+
+  const long long team = (long long)blockIdx.x * tm.per_cta + tm.id;
+  const long long nteams = (long long)gridDim.x * tm.per_cta;
+  int* k2 = nullptr;
+  unsigned* m2 = nullptr;
+  const unsigned t2mask = (unsigned)l2_slots - 1u;
+  if (SPILL) {
+    k2 = l2_pool + team * l2_slots * (COMP ? 2 : 1);
+    m2 = reinterpret_cast<unsigned*>(k2 + l2_slots);
+  }
+
+  for (long long r = team; r < nrows; r += nteams) {
+    const long long g = rows[r];
+    const int b = inst_of(P.arow0s, P.ninst, g);
+    const InstD& I = P.inst[b];
+    const long long i = g - I.arow0;
+    for (int x = tm.lane; x < T; x += TW) {
+      keys[x] = kEmpty;
+      if (COMP) masks[x] = 0u;
+    }
+    if (SPILL) {
+      for (long long x = tm.lane; x < l2_slots; x += TW) {
+        k2[x] = kEmpty;
+        if (COMP) m2[x] = 0u;
+      }
+    }
+    if (tm.lane == 0) *occ = 0;
+    if (SPILL) __threadfence_block();
+    tm.sync();
+    const long long a0 = rp_at(I.A, i), a1 = rp_at(I.A, i + 1);
+    const long long brow0 = I.brow0;
+    auto range = [&](int j, long long* bs, long long* be) {
+      if (COMP) {
+        *bs = P.Bcp[brow0 + j];
+        *be = P.Bcp[brow0 + j + 1];
+      } else {
+        *bs = rp_at(I.B, j);
+        *be = rp_at(I.B, j + 1);
+      }
+    };
+    auto aval = [&](long long) { return 0; };
+    const int* __restrict__ Bj = I.B.cj;
+    auto body = [&](long long q, int) {
+      const int key = COMP ? P.csi[q] : Bj[q];
+      const unsigned m = COMP ? P.cs[q] : 0u;
+      int s = lp_insert(keys, tmask, occ, SPILL ? cap : -1, key);
+      if (s >= 0) {
+        if (COMP) atomicOr(masks + s, m);
+      } else if (SPILL) {   // refused by the occupancy cut-off (-1) or L1 full (-2)
+        int s2 = lp_insert(k2, t2mask, nullptr, -1, key);
+        if (s2 >= 0) {
+          if (COMP) atomicOr(m2 + s2, m);
+        } else {
+          dev_fail(P.status, kDevTableFull, 2, g);
+        }
+      } else {
+        dev_fail(P.status, kDevTableFull, 1, g);
+      }
+    };
+    for_each_product<TW, int>(tm, csc, scan_scratch, I.A.cj, a0, a1, range, aval, body);
+    if (SPILL) {
+      __threadfence_block();
+      tm.sync();
+    }
+    long long c = 0;
+    for (int x = tm.lane; x < T; x += TW) {
+      if (keys[x] != kEmpty) c += COMP ? __popc(masks[x]) : 1;
+    }
+    if (SPILL) {
+      for (long long x = tm.lane; x < l2_slots; x += TW) {
+        const int kk = k2[x];
+        if (kk == kEmpty) continue;
+        const int s1 = lp_find(keys, tmask, kk);
+        if (COMP) c += __popc(m2[x] & (s1 >= 0 ? ~masks[s1] : 0xffffffffu));
+        else c += (s1 < 0) ? 1 : 0;
+      }
+    }
+    c = team_sum<TW>(tm, c, scan_scratch);
+    if (tm.lane == 0) rowsize[g] = c;
+    tm.sync();
+  }
+}
+
+template <int TW, bool COMP>
+__global__ void __launch_bounds__(TW) k_sym_dense(ProbD P, const int* __restrict__ rows, long long nrows,
+                                                  long long kw_max, long long* __restrict__ rowsize) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long scan_scratch[33];
+  Team<TW> tm;
+  unsigned* bm = reinterpret_cast<unsigned*>(smem);
+  ChunkScratch<TW, int>* csc = reinterpret_cast<ChunkScratch<TW, int>*>(smem + al16((size_t)kw_max * 4));
+  for (long long w = tm.lane; w < kw_max; w += TW) bm[w] = 0u;
+  __syncthreads();
+  for (long long r = blockIdx.x; r < nrows; r += gridDim.x) {
+    const long long g = rows[r];
+    const int b = inst_of(P.arow0s, P.ninst, g);
+    const InstD& I = P.inst[b];
+    const long long i = g - I.arow0;
+    const long long k = I.k;
+    const long long kw = (k + 31) >> 5;
+    const long long a0 = rp_at(I.A, i), a1 = rp_at(I.A, i + 1);
+    const long long brow0 = I.brow0;
+    auto range = [&](int j, long long* bs, long long* be) {
+      if (COMP) {
+        *bs = P.Bcp[brow0 + j];
+        *be = P.Bcp[brow0 + j + 1];
+      } else {
+        *bs = rp_at(I.B, j);
+        *be = rp_at(I.B, j + 1);
+      }
+    };
+    auto aval = [&](long long) { return 0; };
+    const int* __restrict__ Bj = I.B.cj;
+    auto body = [&](long long q, int) {
+      if (COMP) {
+        const int w = P.csi[q];
+        if ((unsigned)w < (unsigned)kw) atomicOr(bm + w, P.cs[q]);
+        else dev_fail(P.status, kDevBadIndex, 3, g);
+      } else {
+        const int col = Bj[q];
+        if ((unsigned)col < (unsigned long long)k) atomicOr(bm + (col >> 5), 1u << (col & 31));
+        else dev_fail(P.status, kDevBadIndex, 4, g);
+      }
+    };
+    for_each_product<TW, int>(tm, csc, scan_scratch, I.A.cj, a0, a1, range, aval, body);
+    long long c = 0;
+    for (long long w = tm.lane; w < kw; w += TW) {
+      c += __popc(bm[w]);
+      bm[w] = 0u;
+    }
+    c = team_sum<TW>(tm, c, scan_scratch);
+    if (tm.lane == 0) rowsize[g] = c;
+    __syncthreads();
+  }
+}
+
+template <class K>
+cudaError_t set_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return cudaSuccess;
+}
+
+inline unsigned hash_grid(long long nrows, int teams_per_cta, int num_sms) {
+  long long g = (nrows + teams_per_cta - 1) / teams_per_cta;
+  long long cap = (long long)num_sms * 64;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+template <int TW, bool COMP>
+cudaError_t run_hash(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, long long* rowsize) {
+  const int T = 1 << S.logT;
+  const size_t tb = sym_team_bytes<TW, COMP>(T);
+  int teams = 1;
+  if (TW <= 32) {
+    teams = (int)((48 * 1024) / tb);
+    int tmax = 256 / TW;
+    if (teams > tmax) teams = tmax;
+    if (teams < 1) teams = 1;
+  }
+  const size_t smem = tb * teams;
+  if (smem > (size_t)L.max_smem_optin) return cudaErrorInvalidConfiguration;
+  auto kern = k_sym_hash<TW, COMP, false>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  kern<<<hash_grid(S.nrows, teams, L.num_sms), TW * teams, smem, L.stream>>>(P, S.rows, S.nrows, S.logT, -1,
+                                                                            nullptr, 0, rowsize);
+  return cudaGetLastError();
+}
+
+template <bool COMP>
+cudaError_t run_spill(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, long long* rowsize) {
+  constexpr int TW = 1024;
+  const int T = 1 << S.l1_logT;
+  const size_t smem = sym_team_bytes<TW, COMP>(T);
+  if (smem > (size_t)L.max_smem_optin) return cudaErrorInvalidConfiguration;
+  auto kern = k_sym_hash<TW, COMP, true>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  int cap = (int)(S.max_occ * T);
+  if (cap < 1) cap = 1;
+  if (cap > T - 1) cap = T - 1;
+  int grid = S.nchunks;
+  if (grid > S.nrows) grid = (int)S.nrows;
+  kern<<<grid, TW, smem, L.stream>>>(P, S.rows, S.nrows, S.l1_logT, cap, (int*)S.l2_pool, S.l2_chunk_slots,
+                                     rowsize);
+  return cudaGetLastError();
+}
+
+template <bool COMP>
+cudaError_t run_dense(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, long long* rowsize) {
+  constexpr int TW = 512;
+  const size_t smem = al16((size_t)S.kwords_max * 4) + al16(sizeof(ChunkScratch<TW, int>));
+  if (smem > (size_t)L.max_smem_optin) return cudaErrorInvalidConfiguration;
+  auto kern = k_sym_dense<TW, COMP>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = (int)((size_t)L.max_smem_optin / (smem + 1024));
+  if (per_sm < 1) per_sm = 1;
+  if (per_sm > 4) per_sm = 4;
+  long long grid = (long long)L.num_sms * per_sm;
+  if (grid > S.nrows) grid = S.nrows;
+  kern<<<(unsigned)grid, TW, smem, L.stream>>>(P, S.rows, S.nrows, S.kwords_max, rowsize);
+  return cudaGetLastError();
+}
+
+template <bool COMP>
+cudaError_t dispatch(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, long long* rowsize) {
+  switch (S.cls) {
+    case kClsW8: return run_hash<8, COMP>(L, P, S, rowsize);
+    case kClsW32: return run_hash<32, COMP>(L, P, S, rowsize);
+    case kClsC256: return run_hash<256, COMP>(L, P, S, rowsize);
+    case kClsC1024: return run_hash<1024, COMP>(L, P, S, rowsize);
+    case kClsDense: return run_dense<COMP>(L, P, S, rowsize);
+    case kClsSpill: return run_spill<COMP>(L, P, S, rowsize);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+size_t symbolic_team_bytes(int cls, int logT, int compressed) {
+  const int T = 1 << logT;
+  switch (cls) {
+    case kClsW8: return compressed ? sym_team_bytes<8, true>(T) : sym_team_bytes<8, false>(T);
+    case kClsW32: return compressed ? sym_team_bytes<32, true>(T) : sym_team_bytes<32, false>(T);
+    case kClsC256: return compressed ? sym_team_bytes<256, true>(T) : sym_team_bytes<256, false>(T);
+    default: return compressed ? sym_team_bytes<1024, true>(T) : sym_team_bytes<1024, false>(T);
+  }
+}
+
+cudaError_t launch_symbolic(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, long long* rowsize) {
+  if (S.nrows <= 0) return cudaSuccess;
+  return S.compressed ? dispatch<true>(L, P, S, rowsize) : dispatch<false>(L, P, S, rowsize);
+}
+
+}  // namespace kks

@@ -1,0 +1,260 @@
+"""PyTorch-facing wrappers over the C ABI (device memory and streams only).
+
+Tensors provide the device buffers and torch's current CUDA stream is passed
+to every call; all arithmetic runs in libkkspgemm's kernels.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+from typing import List, Optional, Sequence, Tuple
+
+import torch
+
+from . import _binding as B
+
+
+def _dtype_code(t: Optional[torch.dtype]) -> int:
+    if t is None or t == torch.float64:
+        return B.SPGEMM_R64
+    if t == torch.float32:
+        return B.SPGEMM_R32
+    raise TypeError("values must be float32 or float64, got %s" % t)
+
+
+def _stream(stream=None) -> C.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None or t.numel() == 0:
+        return None
+    return C.c_void_p(t.data_ptr())
+
+
+@dataclass
+class CsrMatrix:
+    """CSR matrix held in device tensors.
+
+    rowptr: int32 or int64 [nrows + 1]; colidx: int32 [nnz]; values: float32 /
+    float64 [nnz] or None (pattern only).
+    """
+
+    rowptr: torch.Tensor
+    colidx: torch.Tensor
+    values: Optional[torch.Tensor]
+    shape: Tuple[int, int]
+
+    def __post_init__(self):
+        assert self.rowptr.dtype in (torch.int32, torch.int64)
+        assert self.colidx.dtype == torch.int32
+        assert self.rowptr.is_contiguous() and self.colidx.is_contiguous()
+        if self.values is not None:
+            assert self.values.is_contiguous() and self.values.numel() == self.colidx.numel()
+
+    @property
+    def nrows(self) -> int:
+        return int(self.shape[0])
+
+    @property
+    def ncols(self) -> int:
+        return int(self.shape[1])
+
+    @property
+    def nnz(self) -> int:
+        return int(self.colidx.numel())
+
+    @property
+    def dtype(self):
+        return None if self.values is None else self.values.dtype
+
+    def with_values(self, values: Optional[torch.Tensor]) -> "CsrMatrix":
+        return CsrMatrix(self.rowptr, self.colidx, values, self.shape)
+
+    def desc(self, dtype_hint=None) -> B.CsrT:
+        d = B.CsrT()
+        d.nrows, d.ncols, d.nnz = self.nrows, self.ncols, self.nnz
+        d.rowptr_is_64 = 1 if self.rowptr.dtype == torch.int64 else 0
+        d.dtype = _dtype_code(self.dtype if self.values is not None else dtype_hint)
+        d.rowptr = self.rowptr.data_ptr()
+        d.colidx = self.colidx.data_ptr() if self.nnz > 0 else None
+        d.values = self.values.data_ptr() if (self.values is not None and self.nnz > 0) else None
+        return d
+
+    @staticmethod
+    def from_host(rowptr, colidx, values, shape, device="cuda", rowptr_dtype=torch.int64):
+        rp = torch.as_tensor(rowptr).to(device=device, dtype=rowptr_dtype).contiguous()
+        cj = torch.as_tensor(colidx).to(device=device, dtype=torch.int32).contiguous()
+        vx = None if values is None else torch.as_tensor(values).to(device=device).contiguous()
+        return CsrMatrix(rp, cj, vx, (int(shape[0]), int(shape[1])))
+
+    def to_host(self):
+        """(rowptr int64, colidx int32, values or None) as numpy arrays."""
+        rp = self.rowptr.to(torch.int64).cpu().numpy()
+        cj = self.colidx.cpu().numpy()
+        vx = None if self.values is None else self.values.cpu().numpy()
+        return rp, cj, vx
+
+
+class SpGEMM:
+    """A handle of the two-phase SpGEMM library (owns all device scratch)."""
+
+    def __init__(self, compression: int = -1, compress_threshold: float = 0.85,
+                 l1_max_occupancy: float = 0.5, l1_max_log2_slots: int = 0, dense: int = -1,
+                 method: int = 0, workspace_limit_bytes: int = 0, pool_limit_bytes: int = 0,
+                 device: int = 0, verbose: bool = False):
+        self._lib = B.load()
+        opt = B.OptionsT()
+        B.check(self._lib.spgemm_options_default(C.byref(opt)), "spgemm_options_default")
+        opt.compression = compression
+        opt.compress_threshold = compress_threshold
+        opt.l1_max_occupancy = l1_max_occupancy
+        opt.l1_max_log2_slots = l1_max_log2_slots
+        opt.dense = dense
+        opt.method = method
+        opt.workspace_limit_bytes = workspace_limit_bytes
+        opt.pool_limit_bytes = pool_limit_bytes
+        opt.device = device
+        opt.reserved[0] = 1 if verbose else 0
+        self.device = torch.device("cuda", device)
+        h = C.c_void_p()
+        B.check(self._lib.spgemm_handle_create(C.byref(h), C.byref(opt)), "spgemm_handle_create")
+        self._h = h
+        self._keep = None
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.spgemm_handle_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- phases
+    def symbolic(self, A: CsrMatrix, Bm: CsrMatrix, C_rowptr: Optional[torch.Tensor] = None, stream=None):
+        """Algorithm 2 lines 1-3: returns (C_rowptr int64 tensor, nnz(C))."""
+        if C_rowptr is None:
+            C_rowptr = torch.empty(A.nrows + 1, dtype=torch.int64, device=A.rowptr.device)
+        hint = A.dtype or Bm.dtype
+        da, db = A.desc(hint), Bm.desc(hint)
+        nnz = C.c_int64(0)
+        self._keep = (A, Bm, C_rowptr)
+        B.check(self._lib.spgemm_symbolic(self._h, C.byref(da), C.byref(db), C.c_void_p(C_rowptr.data_ptr()),
+                                          C.byref(nnz), _stream(stream)), "spgemm_symbolic")
+        return C_rowptr, int(nnz.value)
+
+    def numeric(self, A: CsrMatrix, Bm: CsrMatrix, C_rowptr: torch.Tensor, nnz: Optional[int] = None,
+                C_colidx: Optional[torch.Tensor] = None, C_values: Optional[torch.Tensor] = None,
+                stream=None) -> CsrMatrix:
+        """Algorithm 2 line 5: C's columns and values (rows sorted)."""
+        if nnz is None:
+            nnz = int(C_rowptr[-1].item()) if C_colidx is None else C_colidx.numel()
+        dev = C_rowptr.device
+        if C_colidx is None:
+            C_colidx = torch.empty(nnz, dtype=torch.int32, device=dev)
+        if C_values is None:
+            C_values = torch.empty(nnz, dtype=A.dtype, device=dev)
+        da, db = A.desc(), Bm.desc()
+        B.check(self._lib.spgemm_numeric(self._h, C.byref(da), C.byref(db), C.c_void_p(C_rowptr.data_ptr()),
+                                         _ptr(C_colidx), _ptr(C_values), _stream(stream)), "spgemm_numeric")
+        return CsrMatrix(C_rowptr, C_colidx, C_values, (A.nrows, Bm.ncols))
+
+    def numeric_reuse(self, A: CsrMatrix, Bm: CsrMatrix, Cm: CsrMatrix, stream=None) -> CsrMatrix:
+        """Values of C on its known (sorted) pattern for new values of A and B."""
+        da, db = A.desc(), Bm.desc()
+        B.check(self._lib.spgemm_numeric_reuse(self._h, C.byref(da), C.byref(db),
+                                               C.c_void_p(Cm.rowptr.data_ptr()), _ptr(Cm.colidx),
+                                               _ptr(Cm.values), _stream(stream)), "spgemm_numeric_reuse")
+        return Cm
+
+    def multiply(self, A: CsrMatrix, Bm: CsrMatrix, stream=None) -> CsrMatrix:
+        rp, nnz = self.symbolic(A, Bm, stream=stream)
+        return self.numeric(A, Bm, rp, nnz, stream=stream)
+
+    def sync(self, stream=None):
+        B.check(self._lib.spgemm_handle_sync(self._h, _stream(stream)), "spgemm_handle_sync")
+
+    def stats(self) -> dict:
+        st = B.StatsT()
+        B.check(self._lib.spgemm_get_stats(self._h, C.byref(st)), "spgemm_get_stats")
+        out = {name: getattr(st, name) for name, _ in B.StatsT._fields_ if name != "bin_rows_numeric"}
+        out["bin_rows_numeric"] = list(st.bin_rows_numeric)
+        return out
+
+    # ---------------------------------------------------------------- masked / transpose
+    def masked(self, X: CsrMatrix, Y: CsrMatrix, S_rowptr: torch.Tensor, S_colidx: torch.Tensor,
+               out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """out(i,l) = sum_j X(i,j) Y(j,l) for (i,l) in the pattern S."""
+        n = S_colidx.numel()
+        if out is None:
+            out = torch.empty(n, dtype=X.dtype, device=S_colidx.device)
+        dx, dy = X.desc(), Y.desc()
+        B.check(self._lib.spgemm_masked(self._h, C.byref(dx), C.byref(dy), C.c_void_p(S_rowptr.data_ptr()),
+                                        _ptr(S_colidx), n, _ptr(out), _stream(stream)), "spgemm_masked")
+        return out
+
+    def transpose(self, A: CsrMatrix, with_values: bool = True, stream=None):
+        """(A^T as CsrMatrix with int64 row pointers, perm) with At.values = A.values[perm]."""
+        dev = A.colidx.device
+        Atp = torch.empty(A.ncols + 1, dtype=torch.int64, device=dev)
+        Atj = torch.empty(A.nnz, dtype=torch.int32, device=dev)
+        perm = torch.empty(A.nnz, dtype=torch.int64, device=dev)
+        Atx = None
+        if with_values and A.values is not None:
+            Atx = torch.empty(A.nnz, dtype=A.values.dtype, device=dev)
+        d = A.desc() if (with_values and A.values is not None) else A.with_values(None).desc(A.dtype)
+        B.check(self._lib.spgemm_transpose(self._h, C.byref(d), C.c_void_p(Atp.data_ptr()), _ptr(Atj), _ptr(Atx),
+                                           _ptr(perm), _stream(stream)), "spgemm_transpose")
+        return CsrMatrix(Atp, Atj, Atx, (A.ncols, A.nrows)), perm
+
+    def gather(self, src: torch.Tensor, perm: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None):
+        if out is None:
+            out = torch.empty(perm.numel(), dtype=src.dtype, device=src.device)
+        B.check(self._lib.spgemm_gather(self._h, _dtype_code(src.dtype), _ptr(src), _ptr(perm), _ptr(out),
+                                        perm.numel(), _stream(stream)), "spgemm_gather")
+        return out
+
+    # ---------------------------------------------------------------- batched
+    def batch_symbolic(self, As: Sequence[CsrMatrix], Bs: Sequence[CsrMatrix], stream=None):
+        n = len(As)
+        hint = As[0].dtype if n else None
+        da = (B.CsrT * max(n, 1))(*[a.desc(hint) for a in As])
+        db = (B.CsrT * max(n, 1))(*[b.desc(hint) for b in Bs])
+        rps = [torch.empty(a.nrows + 1, dtype=torch.int64, device=a.rowptr.device) for a in As]
+        prp = (C.c_void_p * max(n, 1))(*[r.data_ptr() for r in rps])
+        nnz = (C.c_int64 * max(n, 1))()
+        self._keep = (As, Bs, rps)
+        B.check(self._lib.spgemm_batch_symbolic(self._h, n, da, db, prp, nnz, _stream(stream)),
+                "spgemm_batch_symbolic")
+        return rps, [int(nnz[i]) for i in range(n)]
+
+    def batch_numeric(self, As, Bs, rowptrs, nnzs, colidx=None, values=None, stream=None) -> List[CsrMatrix]:
+        n = len(As)
+        if colidx is None:
+            colidx = [torch.empty(z, dtype=torch.int32, device=r.device) for r, z in zip(rowptrs, nnzs)]
+        if values is None:
+            values = [torch.empty(z, dtype=a.dtype, device=r.device) for a, r, z in zip(As, rowptrs, nnzs)]
+        da = (B.CsrT * max(n, 1))(*[a.desc() for a in As])
+        db = (B.CsrT * max(n, 1))(*[b.desc() for b in Bs])
+        prp = (C.c_void_p * max(n, 1))(*[r.data_ptr() for r in rowptrs])
+        pcj = (C.c_void_p * max(n, 1))(*[(c.data_ptr() if c.numel() else 0) for c in colidx])
+        pcx = (C.c_void_p * max(n, 1))(*[(v.data_ptr() if v.numel() else 0) for v in values])
+        B.check(self._lib.spgemm_batch_numeric(self._h, n, da, db, prp, pcj, pcx, _stream(stream)),
+                "spgemm_batch_numeric")
+        return [CsrMatrix(r, c, v, (a.nrows, b.ncols)) for r, c, v, a, b in zip(rowptrs, colidx, values, As, Bs)]
+
+
+def spgemm(A: CsrMatrix, Bm: CsrMatrix, **options) -> CsrMatrix:
+    """One-shot C = A·B (symbolic + numeric) on a fresh handle."""
+    h = SpGEMM(**options)
+    try:
+        Cm = h.multiply(A, Bm)
+        h.sync()
+        return Cm
+    finally:
+        h.close()

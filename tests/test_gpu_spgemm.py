@@ -1,0 +1,373 @@
+"""GPU parity of the two-phase SpGEMM against the CPU oracle (through the C ABI).
+
+Structure (row pointers, sorted columns) must be bit-exact; values must satisfy
+|c - c_ref| <= tol * sum_j |a_ij||b_jl| with tol = 1e-13 (FP64) or 1e-5 (FP32).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as w
+from workloads.csr import Csr, csr_from_coo
+
+from _util import assert_matches_oracle, assert_rows_match_oracle, dev, host_inputs, tol_of
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ops():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1801_03065_gb300 import build
+    build.build()
+    from paper_1801_03065_gb300 import ops as _ops
+    return _ops
+
+
+def run(ops, A, B, dtype=np.float64, rp64=True, **opt):
+    h = ops.SpGEMM(**opt)
+    Ad, Bd = dev(A, dtype, rp64), dev(B, dtype, rp64)
+    rp, nnz = h.symbolic(Ad, Bd)
+    Cd = h.numeric(Ad, Bd, rp, nnz)
+    h.sync()
+    return h, Ad, Bd, Cd
+
+
+# ------------------------------------------------------------------ workloads
+def test_laplace5_64_full(ops):
+    A = w.laplace2d_5pt(64)
+    h, _, _, Cd = run(ops, A, A)
+    assert_matches_oracle(A, A, Cd, np.float64)
+    st = h.stats()
+    assert st["nnzC"] == 51972 and st["f_m"] == 100104 and st["maxrs"] == 13
+    assert abs(st["CF"] - 60800 / 100104) < 1e-12 and st["compressed"] == 1
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("rp64", [True, False])
+def test_stencil27_small(ops, dtype, rp64):
+    A = w.stencil3d_27pt(14, seed=1)
+    h, _, _, Cd = run(ops, A, A, dtype, rp64)
+    assert_matches_oracle(A, A, Cd, dtype)
+    assert h.stats()["nnzC"] == (5 * 14 - 6) ** 3
+
+
+def test_rmat_small_fp32(ops):
+    A = w.rmat_symmetric(scale=12, edge_factor=16, seed=7)
+    h, _, _, Cd = run(ops, A, A, np.float32)
+    assert_matches_oracle(A, A, Cd, np.float32)
+
+
+def test_triple_product_small(ops):
+    g = 12
+    A = w.stencil3d_27pt(g, seed=1)
+    P = w.aggregation(g, 3)
+    h = ops.SpGEMM()
+    Pd = dev(P)
+    Pt, perm = h.transpose(Pd)
+    Pt_ref, perm_ref = oracle.transpose(P)
+    rp, cj, vx = Pt.to_host()
+    assert np.array_equal(rp, Pt_ref.rowptr) and np.array_equal(cj, Pt_ref.colidx)
+    assert np.array_equal(perm.cpu().numpy(), perm_ref)
+    assert np.array_equal(vx, Pt_ref.values)
+    AP = h.multiply(dev(A), Pd)
+    h.sync()
+    AP_ref = assert_matches_oracle(A, P, AP, np.float64)
+    h2 = ops.SpGEMM()
+    RAP = h2.multiply(Pt, AP)
+    h2.sync()
+    assert_matches_oracle(Pt_ref, AP_ref[0], RAP, np.float64)
+
+
+# ------------------------------------------------------------------ random / edge cases
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_random_mixed_rows(ops, seed, dtype):
+    """Row lengths spanning every team class (1 .. thousands of products)."""
+    rng = np.random.default_rng(seed)
+    m, n, k = 700, 900, int(rng.choice([33, 1000, 20000, 300000]))
+    la = np.concatenate([rng.integers(0, 4, 500), rng.integers(4, 60, 180), rng.integers(200, 800, 20)])
+    rng.shuffle(la)
+    A = w.random_csr(m, n, lengths=la, seed=seed, dtype=np.float64)
+    lb = rng.geometric(1 / 12, size=n)
+    lb[:5] = min(k, 3000)
+    B = w.random_csr(n, k, lengths=lb, seed=seed + 100, dtype=np.float64)
+    h, _, _, Cd = run(ops, A, B, dtype, rp64=bool(seed % 2))
+    assert_matches_oracle(A, B, Cd, dtype)
+
+
+@pytest.mark.parametrize("shape", [(0, 5, 7), (5, 0, 7), (5, 7, 0), (1, 1, 1), (40, 30, 1), (40, 30, 31),
+                                   (40, 30, 32), (40, 30, 33), (64, 64, 64)])
+def test_edge_shapes(ops, shape):
+    m, n, k = shape
+    A = w.random_csr(m, n, 3.0, seed=1)
+    B = w.random_csr(n, k, 3.0, seed=2)
+    h, _, _, Cd = run(ops, A, B)
+    assert_matches_oracle(A, B, Cd, np.float64)
+
+
+def test_empty_operands(ops):
+    A = Csr(50, 40, np.zeros(51, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    B = w.random_csr(40, 60, 4.0, seed=3)
+    h, _, _, Cd = run(ops, A, B)
+    assert Cd.nnz == 0 and np.all(Cd.rowptr.cpu().numpy() == 0)
+    h, _, _, Cd = run(ops, B.with_values(B.values), Csr(60, 10, np.zeros(61, np.int64), np.zeros(0, np.int32), np.zeros(0)))
+    assert Cd.nnz == 0
+
+
+def test_unsorted_input_rows(ops):
+    A = w.shuffle_rows(w.random_csr(300, 200, 9.0, seed=4), 1)
+    B = w.shuffle_rows(w.random_csr(200, 5000, 15.0, seed=5), 2)
+    for comp in (-1, 0, 1):
+        h, _, _, Cd = run(ops, A, B, compression=comp)
+        assert_matches_oracle(A, B, Cd, np.float64)
+
+
+def test_row_straddling_column_sets(ops):
+    """Columns 30..34 of every row cross the 32-column set boundary."""
+    rows = np.repeat(np.arange(50), 5)
+    cols = np.tile(np.arange(30, 35), 50)
+    B = csr_from_coo(50, 70, rows, cols, np.linspace(-1, 1, 250))
+    A = w.random_csr(80, 50, 6.0, seed=9)
+    h, _, _, Cd = run(ops, A, B, compression=1)
+    assert_matches_oracle(A, B, Cd, np.float64)
+
+
+def test_colliding_keys(ops):
+    """All keys of a row hash to the same slot (columns multiples of 1024)."""
+    k = 1024 * 200
+    nb = 64
+    rows = np.repeat(np.arange(nb), 100)
+    cols = (np.random.default_rng(1).permutation(200)[None, :100].repeat(nb, 0).ravel()) * 1024
+    B = csr_from_coo(nb, k, rows, cols, np.random.default_rng(2).uniform(-1, 1, rows.size))
+    A = w.random_csr(100, nb, 8.0, seed=3)
+    for comp in (0, 1):
+        h, _, _, Cd = run(ops, A, B, compression=comp)
+        assert_matches_oracle(A, B, Cd, np.float64)
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_forced_l2_spill(ops, dtype):
+    """Tiny L1 tables and no dense accumulator: rows go through L1 + L2 in both phases."""
+    A = w.random_csr(200, 300, 20.0, seed=6)
+    B = w.random_csr(300, 4000, 25.0, seed=7)
+    for comp in (0, 1):
+        h, _, _, Cd = run(ops, A, B, dtype, l1_max_log2_slots=5, dense=0, compression=comp)
+        st = h.stats()
+        assert st["bin_rows_numeric"][6] > 0, "no row took the spill path"
+        assert_matches_oracle(A, B, Cd, dtype)
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_forced_dense(ops, dtype):
+    A = w.random_csr(300, 300, 12.0, seed=8)
+    B = w.random_csr(300, 3000, 12.0, seed=9)
+    h, _, _, Cd = run(ops, A, B, dtype, dense=1)
+    assert h.stats()["bin_rows_numeric"][5] > 0
+    assert_matches_oracle(A, B, Cd, dtype)
+
+
+def test_occupancy_variants(ops):
+    A = w.random_csr(200, 300, 20.0, seed=16)
+    B = w.random_csr(300, 4000, 25.0, seed=17)
+    for occ in (0.1, 0.9, 1.0):
+        h, _, _, Cd = run(ops, A, B, l1_max_log2_slots=6, dense=0, l1_max_occupancy=occ)
+        assert_matches_oracle(A, B, Cd, np.float64)
+
+
+# ------------------------------------------------------------------ reuse
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_numeric_reuse_new_values(ops, dtype):
+    rng = np.random.default_rng(0)
+    A = w.random_csr(400, 300, 10.0, seed=10)
+    B = w.random_csr(300, 2000, 10.0, seed=11)
+    h, Ad, Bd, Cd = run(ops, A, B, dtype)
+    for rep in range(3):
+        A2 = A.with_values(rng.uniform(-1, 1, A.nnz))
+        B2 = B.with_values(rng.uniform(-1, 1, B.nnz))
+        Ad.values.copy_(torch.as_tensor(A2.values.astype(dtype)))
+        Bd.values.copy_(torch.as_tensor(B2.values.astype(dtype)))
+        if rep % 2 == 0:
+            h.numeric(Ad, Bd, Cd.rowptr, Cd.nnz, Cd.colidx, Cd.values)
+        else:
+            h.numeric_reuse(Ad, Bd, Cd)
+        h.sync()
+        assert_matches_oracle(A2, B2, Cd, dtype)
+
+
+def test_pattern_mismatch_and_not_ready(ops):
+    from paper_1801_03065_gb300._binding import SpGEMMError
+    A = w.random_csr(50, 40, 4.0, seed=1)
+    B = w.random_csr(40, 30, 4.0, seed=2)
+    h = ops.SpGEMM()
+    Ad, Bd = dev(A), dev(B)
+    with pytest.raises(SpGEMMError) as e:
+        h.numeric(Ad, Bd, torch.zeros(51, dtype=torch.int64, device="cuda"), 0,
+                  torch.zeros(1, dtype=torch.int32, device="cuda"), torch.zeros(1, dtype=torch.float64, device="cuda"))
+    assert e.value.status == 2
+    rp, nnz = h.symbolic(Ad, Bd)
+    Bd2 = dev(B)   # same pattern, other buffers
+    with pytest.raises(SpGEMMError) as e:
+        h.numeric(Ad, Bd2, rp, nnz)
+    assert e.value.status == 7
+
+
+def test_workspace_limit_reports_oom(ops):
+    from paper_1801_03065_gb300._binding import SpGEMMError
+    A = w.random_csr(5000, 5000, 10.0, seed=1)
+    h = ops.SpGEMM(workspace_limit_bytes=4096)
+    with pytest.raises(SpGEMMError) as e:
+        h.symbolic(dev(A), dev(A))
+    assert e.value.status == 3
+    # the handle stays usable once the limit allows the plan
+    h2 = ops.SpGEMM(workspace_limit_bytes=1 << 30)
+    rp, nnz = h2.symbolic(dev(A), dev(A))
+    assert nnz > 0
+
+
+def test_bad_column_index_reported(ops):
+    """An out-of-range column index is detected by the kernels' own checks."""
+    from paper_1801_03065_gb300._binding import SpGEMMError
+    A = w.random_csr(60, 40, 4.0, seed=1)
+    B = w.random_csr(40, 30, 4.0, seed=2)
+    bad = A.colidx.copy()
+    bad[3] = 40   # == n
+    Abad = Csr(A.nrows, A.ncols, A.rowptr, bad, A.values)
+    h = ops.SpGEMM()
+    with pytest.raises(SpGEMMError) as e:
+        h.symbolic(dev(Abad), dev(B))
+    assert e.value.status == 8
+    badb = B.colidx.copy()
+    badb[0] = 30 + 7
+    Bbad = Csr(B.nrows, B.ncols, B.rowptr, badb, B.values)
+    with pytest.raises(SpGEMMError) as e:
+        h.symbolic(dev(A), dev(Bbad))
+    assert e.value.status == 8
+    # the handle still works afterwards
+    rp, nnz = h.symbolic(dev(A), dev(B))
+    assert nnz == int(oracle.symbolic_plain(A, B)[-1])
+
+
+# ------------------------------------------------------------------ masked / transpose
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_masked_gradients(ops, dtype):
+    rng = np.random.default_rng(5)
+    A = w.random_csr(300, 200, 8.0, seed=12)
+    B = w.random_csr(200, 400, 8.0, seed=13)
+    Ah, Bh = host_inputs(A, dtype), host_inputs(B, dtype)
+    C, _ = oracle.spgemm(Ah, Bh)
+    G = C.with_values(rng.uniform(-1, 1, C.nnz).astype(dtype))
+    h = ops.SpGEMM()
+    Ad, Bd, Gd = dev(A, dtype), dev(B, dtype), dev(G, dtype)
+    Bt, _ = h.transpose(Bd)
+    At, _ = h.transpose(Ad)
+    dA = h.masked(Gd, Bt, Ad.rowptr, Ad.colidx)
+    dB = h.masked(At, Gd, Bd.rowptr, Bd.colidx)
+    h.sync()
+    ref_a, sa = oracle.masked_dA(Ah, Bh, G)
+    ref_b, sb = oracle.masked_dB(Ah, Bh, G)
+    t = tol_of(dtype)
+    assert np.all(np.abs(dA.cpu().numpy() - ref_a) <= t * sa)
+    assert np.all(np.abs(dB.cpu().numpy() - ref_b) <= t * sb)
+
+
+def test_masked_large_rows_global_tables(ops):
+    A = w.random_csr(100, 300, 40.0, seed=14)
+    B = w.random_csr(300, 3000, 40.0, seed=15)
+    C, _ = oracle.spgemm(A, B)
+    G = C.with_values(np.random.default_rng(1).uniform(-1, 1, C.nnz))
+    h = ops.SpGEMM(l1_max_log2_slots=5)
+    Bt, _ = h.transpose(dev(B))
+    Ad = dev(A)
+    dA = h.masked(dev(G), Bt, Ad.rowptr, Ad.colidx)
+    h.sync()
+    ref, s = oracle.masked_dA(A, B, G)
+    assert np.all(np.abs(dA.cpu().numpy() - ref) <= 1e-13 * s)
+
+
+@pytest.mark.parametrize("m,n,mean", [(500, 300, 5.0), (50, 20000, 3.0), (3000, 40, 30.0), (1, 1, 1.0)])
+def test_transpose(ops, m, n, mean):
+    A = w.shuffle_rows(w.random_csr(m, n, mean, seed=3), 4)
+    h = ops.SpGEMM()
+    At, perm = h.transpose(dev(A))
+    h.sync()
+    ref, perm_ref = oracle.transpose(A)
+    rp, cj, vx = At.to_host()
+    assert np.array_equal(rp, ref.rowptr) and np.array_equal(cj, ref.colidx)
+    assert np.array_equal(perm.cpu().numpy(), perm_ref) and np.array_equal(vx, ref.values)
+
+
+def test_transpose_long_rows(ops):
+    """Columns with more than 16384 entries sort in global-memory buffers."""
+    m = 40000
+    rows = np.concatenate([np.arange(m), np.arange(0, m, 2)])
+    cols = np.concatenate([np.zeros(m, np.int64), np.full(m // 2, 1)])
+    A = csr_from_coo(m, 3, rows, cols, np.random.default_rng(0).uniform(-1, 1, rows.size))
+    h = ops.SpGEMM()
+    At, perm = h.transpose(dev(A))
+    h.sync()
+    ref, perm_ref = oracle.transpose(A)
+    rp, cj, vx = At.to_host()
+    assert np.array_equal(rp, ref.rowptr) and np.array_equal(cj, ref.colidx)
+    assert np.array_equal(vx, ref.values)
+
+
+# ------------------------------------------------------------------ batched
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_batched_matches_per_instance(ops, dtype):
+    pairs = w.batched_pairs(count=6, nmin=200, nmax=3000, seed=11)
+    # add an empty instance and a compressible one
+    pairs.append((Csr(0, 5, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0)),
+                  w.random_csr(5, 5, 2.0, seed=1)))
+    L = w.laplace2d_5pt(20)
+    pairs.append((L, L))
+    h = ops.SpGEMM()
+    As = [dev(a, dtype) for a, _ in pairs]
+    Bs = [dev(b, dtype) for _, b in pairs]
+    rps, nnzs = h.batch_symbolic(As, Bs)
+    Cs = h.batch_numeric(As, Bs, rps, nnzs)
+    h.sync()
+    for (a, b), Cd in zip(pairs, Cs):
+        assert_matches_oracle(a, b, Cd, dtype)
+    # reuse with fresh values
+    fresh = w.batched_fresh_values(pairs[:6], repeat=0, dtype=np.float64)
+    for (Ad, Bd), (va, vb) in zip(zip(As, Bs), fresh):
+        Ad.values.copy_(torch.as_tensor(va.astype(dtype)))
+        Bd.values.copy_(torch.as_tensor(vb.astype(dtype)))
+    h.batch_numeric(As, Bs, rps, nnzs, [c.colidx for c in Cs], [c.values for c in Cs])
+    h.sync()
+    for i, ((a, b), (va, vb)) in enumerate(zip(pairs[:6], fresh)):
+        assert_matches_oracle(a.with_values(va), b.with_values(vb), Cs[i], dtype)
+
+
+# ------------------------------------------------------------------ full-size workloads (sampled)
+def test_stencil27_100_full_sampled(ops):
+    A = w.stencil3d_27pt(100, seed=1)
+    h, _, _, Cd = run(ops, A, A)
+    st = h.stats()
+    assert st["nnzC"] == 494 ** 3 and st["f_m"] == 890 ** 3 and st["maxrs"] == 125
+    rng = np.random.default_rng(0)
+    rows = np.concatenate([[0, 1, 99, 10000, 505050, 999999], rng.integers(0, A.nrows, 400)])
+    assert_rows_match_oracle(A, A, Cd, np.float64, rows)
+    # row sizes follow the closed form (5g-6)^3 stencil count per row
+    rs = np.diff(Cd.rowptr.cpu().numpy())
+    x = np.arange(100)
+    per = np.minimum(x + 2, 99) - np.maximum(x - 2, 0) + 1
+    expect = (per[None, None, :] * per[None, :, None] * per[:, None, None]).ravel()
+    assert np.array_equal(rs, expect)
+
+
+def test_rmat18_full_sampled(ops):
+    A = w.rmat_symmetric(scale=18, seed=7)
+    h, _, _, Cd = run(ops, A, A, np.float32)
+    st = h.stats()
+    deg = A.row_lengths()
+    hubs = np.argsort(deg)[-4:]
+    rng = np.random.default_rng(1)
+    rows = np.concatenate([hubs, rng.integers(0, A.nrows, 60)])
+    assert_rows_match_oracle(A, A, Cd, np.float32, rows)
+    assert st["nnzC"] > 2 ** 31   # int64 row pointers
