@@ -16,6 +16,6 @@ __version__ = "0.1.0"
 
 def __getattr__(name):
     if name == "ops":
-        from . import ops as _ops
-        return _ops
+        import importlib
+        return importlib.import_module(__name__ + ".ops")
     raise AttributeError(name)
