@@ -1,0 +1,425 @@
+#!/usr/bin/env python
+"""Benchmark of the two-phase SpGEMM hot path on GB300.
+
+Workload (one step): the multigrid-like product on the 27-point stencil of a
+100^3 grid (1 M rows, 26.5 M nonzeros, FP64): C = A·A, then the Galerkin
+triple product Pᵀ·(A·P) with P the 3×3×3 aggregation (1 M × 39 304).  Each
+step runs the paper's NoReuse path for the three products (row statistics,
+compression, symbolic, numeric with sorted rows) and the transpose of P.
+
+Metric: GFLOP/s = 2·f_m / t (f_m = multiplications of the three products),
+whole job over all ranks.  Also reported: numeric-reuse GFLOP/s of A·A, the
+HBM roofline fraction of the A·A numeric phase, end-to-end throughput with
+host buffers, and the CPU oracle on a bounded sample of the workload.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun): every rank multiplies its own copy of the workload
+(independent row blocks; no collective on the data path), scaling "weak".
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "SpGEMM GFLOP/s (sym+num, numeric-reuse), % HBM roofline; batched vs plain"
+WORKLOAD = ("stencil27_100: C = A*A and P^T*(A*P); A = 27-point stencil on a 100^3 grid "
+            "(1,000,000 rows, 26,463,592 nnz, FP64, 26/-1 + U(-1e-3,1e-3), seed 1), "
+            "P = 3x3x3 aggregation (1,000,000 x 39,304)")
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--grid", type=int, default=100, help="stencil grid edge (100 = the full workload)")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
+    return p.parse_args(argv)
+
+
+# ----------------------------------------------------------------------------- helpers
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", delete=False, suffix=".csv")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.file.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        try:
+            os.unlink(self.file.name)
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def csr_bytes(nrows, nnz, vbytes, rp_bytes=8):
+    return (nrows + 1) * rp_bytes + nnz * (4 + vbytes)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+class StencilStep:
+    """Device buffers and library handles of one step (NoReuse A·A and Pᵀ·(A·P))."""
+
+    def __init__(self, A, P, device):
+        import torch
+        from paper_1801_03065_gb300 import ops
+        self.torch, self.ops = torch, ops
+        self.A_host, self.P_host = A, P
+        self.Ad = ops.CsrMatrix.from_host(A.rowptr, A.colidx, A.values, A.shape, device=device)
+        self.Pd = ops.CsrMatrix.from_host(P.rowptr, P.colidx, P.values, P.shape, device=device)
+        self.hAA, self.hAP, self.hRAP, self.hT = ops.SpGEMM(), ops.SpGEMM(), ops.SpGEMM(), ops.SpGEMM()
+        dev = self.Ad.rowptr.device
+        self.rpAA = torch.empty(A.nrows + 1, dtype=torch.int64, device=dev)
+        self.rpAP = torch.empty(A.nrows + 1, dtype=torch.int64, device=dev)
+        self.rpRAP = torch.empty(P.ncols + 1, dtype=torch.int64, device=dev)
+        self.CAA = self.CAP = self.CRAP = None
+        self.Pt = None
+
+    def _out(self, C, rp, nnz, dtype):
+        if C is None or C.nnz != nnz:
+            t = self.torch
+            return self.ops.CsrMatrix(rp, t.empty(nnz, dtype=t.int32, device=rp.device),
+                                      t.empty(nnz, dtype=dtype, device=rp.device), (0, 0))
+        return C
+
+    def step(self):
+        t = self.torch
+        Ad, Pd = self.Ad, self.Pd
+        rp, nnz = self.hAA.symbolic(Ad, Ad, C_rowptr=self.rpAA)
+        self.CAA = self._out(self.CAA, rp, nnz, t.float64)
+        self.hAA.numeric(Ad, Ad, rp, nnz, self.CAA.colidx, self.CAA.values)
+        self.Pt = self.hT.transpose(Pd, out=self.Pt)
+        rp, nnz = self.hAP.symbolic(Ad, Pd, C_rowptr=self.rpAP)
+        self.CAP = self._out(self.CAP, rp, nnz, t.float64)
+        AP = self.hAP.numeric(Ad, Pd, rp, nnz, self.CAP.colidx, self.CAP.values)
+        Pt = self.Pt[0]
+        rp, nnz = self.hRAP.symbolic(Pt, AP, C_rowptr=self.rpRAP)
+        self.CRAP = self._out(self.CRAP, rp, nnz, t.float64)
+        self.hRAP.numeric(Pt, AP, rp, nnz, self.CRAP.colidx, self.CRAP.values)
+
+    def flops(self):
+        return sum(h.stats()["f_m"] for h in (self.hAA, self.hAP, self.hRAP))
+
+    def close(self):
+        for h in (self.hAA, self.hAP, self.hRAP, self.hT):
+            h.close()
+
+
+def time_region(torch, fn, steps):
+    """Per-step CUDA-event times (ms) on the current stream; sync on both sides."""
+    stream = torch.cuda.current_stream()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for s in range(steps):
+        starts[s].record(stream)
+        fn()
+        ends[s].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in zip(starts, ends)]
+
+
+def load_traffic_record(name):
+    """ncu DRAM bytes of a kernel, valid only for the library build it was taken on."""
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        from paper_1801_03065_gb300 import build as pkg_build
+        if rec.get("build_digest") != pkg_build._digest():
+            return None
+        return rec
+    except Exception:
+        return None
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    import workloads as w
+    from paper_1801_03065_gb300 import ops
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+
+    A = w.stencil3d_27pt(args.grid, seed=1)
+    P = w.aggregation(args.grid, 3)
+    S = StencilStep(A, P, device)
+    for _ in range(max(args.warmup, 1)):
+        S.step()
+    torch.cuda.synchronize()
+    flops_step = S.flops()
+    stAA = S.hAA.stats()
+
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local).start()
+    launches0 = ops.launch_count()
+    times = time_region(torch, S.step, args.steps)
+    launches = ops.launch_count() - launches0
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    t_step = sum(times) / len(times)
+    t_tensor = torch.tensor([t_step], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t_tensor, op=dist.ReduceOp.MAX)
+    t_step = float(t_tensor.item())
+    value = world * flops_step * 2.0 / (t_step * 1e-3) / 1e9
+
+    # numeric reuse (Reuse case: numeric phase only) and the roofline of the numeric phase
+    Ad = S.Ad
+    num = lambda: S.hAA.numeric(Ad, Ad, S.CAA.rowptr, S.CAA.nnz, S.CAA.colidx, S.CAA.values)
+    for _ in range(3):
+        num()
+    t_num = statistics.mean(time_region(torch, num, max(args.steps, 5)))
+    reuse = lambda: S.hAA.numeric_reuse(Ad, Ad, S.CAA)
+    for _ in range(3):
+        reuse()
+    t_reuse = statistics.mean(time_region(torch, reuse, max(args.steps, 5)))
+    sym = lambda: S.hAA.symbolic(Ad, Ad, C_rowptr=S.rpAA)
+    t_sym = statistics.mean(time_region(torch, sym, max(args.steps, 5)))
+    S.hAA.sync()
+
+    nnzC = stAA["nnzC"]
+    bytes_num = 2 * csr_bytes(A.nrows, A.nnz, 8) + csr_bytes(A.nrows, nnzC, 8)
+    peak, peak_kind = measured_peaks()
+    achieved = bytes_num / (t_num * 1e-3) / 1e9
+    traffic_rec = load_traffic_record("numeric_stencil27_100.json") if args.grid == 100 else None
+
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.grid == 100 else WORKLOAD.replace("100^3", "%d^3" % args.grid),
+                   "global_batch": world, "flops_per_step": 2 * flops_step,
+                   "l2": "inputs larger than L2 (A = %.0f MB, C = %.0f MB)" % (
+                       csr_bytes(A.nrows, A.nnz, 8) / 1e6, csr_bytes(A.nrows, nnzC, 8) / 1e6),
+                   "parallelism": "one independent problem per GPU (row blocks), no data-path collective"},
+        "phases_ms": {"AA_symbolic": round(t_sym, 4), "AA_numeric": round(t_num, 4),
+                      "AA_numeric_reuse_probe": round(t_reuse, 4)},
+        "numeric_reuse": {"value": round(2.0 * stAA["f_m"] / (t_num * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
+                          "probe_only_value": round(2.0 * stAA["f_m"] / (t_reuse * 1e-3) / 1e9, 3),
+                          "product": "A*A"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                     "traffic": None if traffic_rec is None else traffic_rec.get("traffic_bytes_per_launch"),
+                     "kernel": "numeric phase of A*A (k_num_hash bins; one call of spgemm_numeric)",
+                     "algorithmic_bytes": bytes_num},
+        "stats_AA": {k: stAA[k] for k in ("f_m", "nnzC", "maxrs", "CF", "CMRF", "compressed")},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+
+    if not args.no_e2e:
+        out["e2e"] = run_e2e(torch, S, A, P, args, world, flops_step)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(A, P, args.cpu_budget)
+    S.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def run_e2e(torch, S, A, P, args, world, flops_step):
+    """Same step through the public API from pinned host buffers: H2D of A and P,
+    the step, D2H of C = A·A and Pᵀ·A·P, all inside the timed region."""
+    pin = lambda x: torch.from_numpy(x).pin_memory()
+    hA = [pin(A.rowptr), pin(A.colidx), pin(A.values)]
+    hP = [pin(P.rowptr), pin(P.colidx), pin(P.values)]
+    dA = [S.Ad.rowptr, S.Ad.colidx, S.Ad.values]
+    dP = [S.Pd.rowptr, S.Pd.colidx, S.Pd.values]
+    out_AA = [torch.empty(S.CAA.rowptr.shape, dtype=torch.int64).pin_memory(),
+              torch.empty(S.CAA.nnz, dtype=torch.int32).pin_memory(),
+              torch.empty(S.CAA.nnz, dtype=torch.float64).pin_memory()]
+    out_RAP = [torch.empty(S.CRAP.rowptr.shape, dtype=torch.int64).pin_memory(),
+               torch.empty(S.CRAP.nnz, dtype=torch.int32).pin_memory(),
+               torch.empty(S.CRAP.nnz, dtype=torch.float64).pin_memory()]
+    h2d = sum(t.numel() * t.element_size() for t in hA + hP)
+    d2h = sum(t.numel() * t.element_size() for t in out_AA + out_RAP)
+
+    def e2e_step():
+        for d, h in zip(dA + dP, hA + hP):
+            d.copy_(h, non_blocking=True)
+        S.step()
+        for h, d in zip(out_AA, [S.CAA.rowptr, S.CAA.colidx, S.CAA.values]):
+            h.copy_(d, non_blocking=True)
+        for h, d in zip(out_RAP, [S.CRAP.rowptr, S.CRAP.colidx, S.CRAP.values]):
+            h.copy_(d, non_blocking=True)
+
+    e2e_step()
+    times = time_region(torch, e2e_step, max(3, args.steps // 2))
+    t = sum(times) / len(times)
+    return {"value": round(world * 2.0 * flops_step / (t * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": round(t, 4)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def _row_sample(M, rows):
+    import numpy as np
+    from workloads.csr import Csr
+    lens = M.rowptr[rows + 1] - M.rowptr[rows]
+    rp = np.zeros(rows.size + 1, dtype=np.int64)
+    np.cumsum(lens, out=rp[1:])
+    idx = np.concatenate([np.arange(M.rowptr[r], M.rowptr[r + 1]) for r in rows])
+    return Csr(rows.size, M.ncols, rp, M.colidx[idx], M.values[idx])
+
+
+def oracle_sample_step(A, P, AP, Pt, frac, seed=0):
+    """The oracle on the rows `frac` of each product of the step; returns (seconds, f_m)."""
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(seed)
+    fm = 0
+    t0 = time.perf_counter()
+    for X, Y in ((A, A), (A, P), (Pt, AP)):
+        n = max(1, int(round(frac * X.nrows)))
+        rows = np.sort(rng.choice(X.nrows, size=n, replace=False))
+        Xs = _row_sample(X, rows)
+        oracle.spgemm(Xs, Y, with_bounds=False)
+        fm += oracle.row_flops(Xs, Y)[1]
+    return time.perf_counter() - t0, fm
+
+
+def oracle_prepare(A, P):
+    import oracle
+    AP, _ = oracle.spgemm(A, P, with_bounds=False)
+    Pt, _ = oracle.transpose(P)
+    return AP, Pt
+
+
+def cpu_baseline(A, P, budget):
+    import oracle
+    AP, Pt = oracle_prepare(A, P)
+    t1, _ = oracle_sample_step(A, P, AP, Pt, 0.002)
+    frac = min(1.0, 0.002 * budget / max(t1, 1e-3))
+    t, fm = oracle_sample_step(A, P, AP, Pt, frac, seed=1)
+    return {"value": round(2.0 * fm / t / 1e9, 4), "unit": "GFLOP/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": "%.2f%% of the rows of each product of the step (A*A, A*P, P^T*(AP)), "
+                      "%d multiplications, %.1f s" % (100 * frac, fm, t)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import workloads as w
+    A = w.stencil3d_27pt(args.grid, seed=1)
+    P = w.aggregation(args.grid, 3)
+    AP, Pt = oracle_prepare(A, P)
+    t1, _ = oracle_sample_step(A, P, AP, Pt, 0.002)
+    # each step a bounded sample: about 4 s of oracle work
+    frac = min(1.0, 0.002 * 4.0 / max(t1, 1e-3))
+    for s in range(args.warmup):
+        oracle_sample_step(A, P, AP, Pt, frac, seed=100 + s)
+    ts, fms = [], []
+    for s in range(args.steps):
+        t, fm = oracle_sample_step(A, P, AP, Pt, frac, seed=s)
+        ts.append(t)
+        fms.append(fm)
+    value = 2.0 * sum(fms) / sum(ts) / 1e9
+    sample = "%.2f%% of the rows of each product of the step per step" % (100 * frac)
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GFLOP/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(1e3 * sum(ts) / len(ts), 3), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD if args.grid == 100 else WORKLOAD.replace("100^3", "%d^3" % args.grid),
+                      "global_batch": 1, "parallelism": "host cores (OpenMP)"},
+           "cpu_baseline": {"value": round(value, 4), "unit": "GFLOP/s", "cores": oracle.num_threads(),
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": round(value, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

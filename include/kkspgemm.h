@@ -206,6 +206,10 @@ const char *spgemm_status_string(spgemm_status_t s);
 /* Library version as an integer (major * 10000 + minor * 100 + patch). */
 int32_t spgemm_version(void);
 
+/* Number of CUDA kernels the library has launched in this process (a
+ * diagnostic counter; host-side, no synchronisation). */
+int64_t spgemm_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -67,6 +67,7 @@ SIGNATURES = {
                                        C.POINTER(_P), C.POINTER(_P), C.POINTER(_P), _P]),
     "spgemm_status_string": (C.c_char_p, [C.c_int]),
     "spgemm_version": (C.c_int32, []),
+    "spgemm_launch_count": (C.c_int64, []),
 }
 
 _lib = None

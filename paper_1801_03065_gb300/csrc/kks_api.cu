@@ -30,6 +30,8 @@ size_t masked_team_bytes(int cls, int logT, int dtype);
 
 using namespace kks;
 
+std::atomic<long long> kks::g_launches{0};
+
 namespace {
 
 enum BufId {
@@ -1105,6 +1107,8 @@ const char* spgemm_status_string(spgemm_status_t s) {
 }
 
 int32_t spgemm_version(void) { return 100; }
+
+int64_t spgemm_launch_count(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
 
 }  // extern "C"
 

@@ -1,12 +1,17 @@
 // kks_internal.h -- host/device declarations shared by the library's translation units.
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
 #include "kks_device.cuh"
 
 namespace kks {
+
+// Kernels launched by the library in this process (reported by spgemm_launch_count).
+extern std::atomic<long long> g_launches;
+#define KKS_LAUNCHED() ::kks::g_launches.fetch_add(1, std::memory_order_relaxed)
 
 // ---------------------------------------------------------------------------
 // Row binning.  A row of C is assigned to a team class and an accumulator

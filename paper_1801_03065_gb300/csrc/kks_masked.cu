@@ -273,6 +273,7 @@ cudaError_t run_masked_hash(const LaunchCtx& L, const MaskedD& M, const MaskedLa
   auto kern = k_masked<TW, VT, false>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
+  KKS_LAUNCHED();
   kern<<<grid_cap(S.nrows, teams, L.num_sms, 64), TW * teams, smem, L.stream>>>(M, S.rows, S.nrows, S.logT, nullptr, 0);
   return cudaGetLastError();
 }
@@ -287,6 +288,7 @@ cudaError_t run_masked_global(const LaunchCtx& L, const MaskedD& M, const Masked
   long long grid = S.nchunks;
   if (grid > S.nrows) grid = S.nrows;
   const long long chunk = (long long)msk_team_bytes<TW, VT>((int)S.chunk_slots);
+  KKS_LAUNCHED();
   kern<<<(unsigned)grid, TW, smem, L.stream>>>(M, S.rows, S.nrows, ilog2_ceil(S.chunk_slots),
                                                (unsigned char*)S.pool, chunk);
   return cudaGetLastError();
@@ -327,6 +329,7 @@ size_t masked_team_bytes(int cls, int logT, int dtype) {
 cudaError_t launch_masked_bin_count(const LaunchCtx& L, const MaskedD& M, long long nrows, BinCfg cfg,
                                     unsigned long long* hist) {
   if (nrows <= 0) return cudaSuccess;
+  KKS_LAUNCHED();
   k_masked_bins<<<grid_cap(nrows, 256, L.num_sms, 8), 256, 0, L.stream>>>(M, nrows, 0, cfg, hist, nullptr, nullptr);
   return cudaGetLastError();
 }
@@ -334,6 +337,7 @@ cudaError_t launch_masked_bin_count(const LaunchCtx& L, const MaskedD& M, long l
 cudaError_t launch_masked_bin_scatter(const LaunchCtx& L, const MaskedD& M, long long nrows, BinCfg cfg,
                                       unsigned long long* cursor, int* rows) {
   if (nrows <= 0) return cudaSuccess;
+  KKS_LAUNCHED();
   k_masked_bins<<<grid_cap(nrows, 256, L.num_sms, 8), 256, 0, L.stream>>>(M, nrows, 1, cfg, nullptr, cursor, rows);
   return cudaGetLastError();
 }
@@ -367,10 +371,16 @@ cudaError_t launch_transpose_count(const LaunchCtx& L, const MatD& A, long long*
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(mx, 0, 16, L.stream);
   if (e != cudaSuccess) return e;
-  if (A.nnz > 0) k_tr_count<<<grid_cap(A.nnz, 256, L.num_sms, 16), 256, 0, L.stream>>>(A, cnt, st);
+  if (A.nnz > 0) {
+    KKS_LAUNCHED();
+    k_tr_count<<<grid_cap(A.nnz, 256, L.num_sms, 16), 256, 0, L.stream>>>(A, cnt, st);
+  }
   e = launch_scan(L, (const long long*)cnt, Atp, n, stmp);
   if (e != cudaSuccess) return e;
-  if (n > 0) k_reduce_max_ll<<<grid_cap(n, 256, L.num_sms, 4), 256, 0, L.stream>>>(cnt, n, mx);
+  if (n > 0) {
+    KKS_LAUNCHED();
+    k_reduce_max_ll<<<grid_cap(n, 256, L.num_sms, 4), 256, 0, L.stream>>>(cnt, n, mx);
+  }
   return cudaMemcpyAsync(h_max, mx, sizeof(unsigned long long), cudaMemcpyDeviceToHost, L.stream);
 }
 
@@ -385,6 +395,7 @@ cudaError_t launch_transpose_fill(const LaunchCtx& L, const MatD& A, int dtype, 
   cudaError_t e = cudaMemsetAsync(cursor, 0, sizeof(unsigned long long) * (n + 1), L.stream);
   if (e != cudaSuccess) return e;
   if (A.nnz == 0 || n == 0) return cudaSuccess;
+  KKS_LAUNCHED();
   k_tr_scatter<<<grid_cap(A.nrows, 256, L.num_sms, 16), 256, 0, L.stream>>>(A, Atp, cursor, trow, tperm, st);
   const int vbytes = dtype == 1 ? 8 : 4;
   // rows up to 256 entries: warp teams with shared buffers
@@ -394,6 +405,7 @@ cudaError_t launch_transpose_fill(const LaunchCtx& L, const MatD& A, int dtype, 
     auto kern = k_tr_sort<32, false>;
     e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
+    KKS_LAUNCHED();
     kern<<<grid_cap(n, 8, L.num_sms, 16), 256, smem, L.stream>>>(n, Atp, trow, tperm, Atj, perm, A.vx, Atx, vbytes, 1,
                                                                  cap, nullptr, 0);
   }
@@ -403,11 +415,13 @@ cudaError_t launch_transpose_fill(const LaunchCtx& L, const MatD& A, int dtype, 
     auto kern = k_tr_sort<1024, false>;
     e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
+    KKS_LAUNCHED();
     kern<<<grid_cap(n, 1, L.num_sms, 2), 1024, smem, L.stream>>>(n, Atp, trow, tperm, Atj, perm, A.vx, Atx, vbytes,
                                                                  257, cap, nullptr, 0);
   }
   if (max_len > 16384) {
     auto kern = k_tr_sort<1024, true>;
+    KKS_LAUNCHED();
     kern<<<gbuf_chunks, 1024, 0, L.stream>>>(n, Atp, trow, tperm, Atj, perm, A.vx, Atx, vbytes, 16385, gbuf_len, gbuf,
                                             gbuf_len);
   }
@@ -418,9 +432,9 @@ cudaError_t launch_gather_values(const LaunchCtx& L, int dtype, const void* src,
                                  long long n) {
   if (n <= 0) return cudaSuccess;
   if (dtype == 1)
-    k_gather<double><<<grid_cap(n, 256, L.num_sms, 16), 256, 0, L.stream>>>((const double*)src, perm, (double*)dst, n);
+    { KKS_LAUNCHED(); k_gather<double><<<grid_cap(n, 256, L.num_sms, 16), 256, 0, L.stream>>>((const double*)src, perm, (double*)dst, n); }
   else
-    k_gather<float><<<grid_cap(n, 256, L.num_sms, 16), 256, 0, L.stream>>>((const float*)src, perm, (float*)dst, n);
+    { KKS_LAUNCHED(); k_gather<float><<<grid_cap(n, 256, L.num_sms, 16), 256, 0, L.stream>>>((const float*)src, perm, (float*)dst, n); }
   return cudaGetLastError();
 }
 

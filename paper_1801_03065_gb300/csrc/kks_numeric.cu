@@ -342,6 +342,7 @@ cudaError_t run_hash(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
   long long grid = (S.nrows + teams - 1) / teams;
   long long cap = (long long)L.num_sms * 64;
   if (grid > cap) grid = cap;
+  KKS_LAUNCHED();
   kern<<<(unsigned)grid, TW * teams, smem, L.stream>>>(P, S.rows, S.nrows, S.logT);
   return cudaGetLastError();
 }
@@ -356,6 +357,7 @@ cudaError_t run_dense(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
   if (e != cudaSuccess) return e;
   long long grid = S.nchunks;
   if (grid > S.nrows) grid = S.nrows;
+  KKS_LAUNCHED();
   kern<<<(unsigned)grid, TW, smem, L.stream>>>(P, S.rows, S.nrows, S.kwords_max, (VT*)S.pool, S.kmax);
   return cudaGetLastError();
 }
@@ -375,6 +377,7 @@ cudaError_t run_spill(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
   long long grid = S.nchunks;
   if (grid > S.nrows) grid = S.nrows;
   const long long l2_slots = 1ll << S.logT;
+  KKS_LAUNCHED();
   kern<<<(unsigned)grid, TW, smem, L.stream>>>(P, S.rows, S.nrows, S.l1_logT, cap, (unsigned char*)S.pool, l2_slots,
                                                S.chunk_bytes, (unsigned*)S.pool2, S.kwords_max);
   return cudaGetLastError();

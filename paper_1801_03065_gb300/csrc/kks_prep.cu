@@ -374,6 +374,7 @@ __global__ void k_empty_instances(ProbD P, unsigned long long* inst_out) {
 cudaError_t launch_compress_count(const LaunchCtx& L, const ProbD& P, long long totalB, long long* cnt) {
   if (totalB <= 0) return cudaSuccess;
   int grid = grid_for(totalB, kBlock / 8, L.num_sms);
+  KKS_LAUNCHED();
   k_compress_count<8><<<grid, kBlock, 0, L.stream>>>(P, totalB, cnt);
   return cudaGetLastError();
 }
@@ -381,6 +382,7 @@ cudaError_t launch_compress_count(const LaunchCtx& L, const ProbD& P, long long 
 cudaError_t launch_compress_fill(const LaunchCtx& L, const ProbD& P, long long totalB, int* csi, unsigned* cs) {
   if (totalB <= 0) return cudaSuccess;
   int grid = grid_for(totalB, kBlock / 8, L.num_sms);
+  KKS_LAUNCHED();
   k_compress_fill<8><<<grid, kBlock, 0, L.stream>>>(P, totalB, csi, cs);
   return cudaGetLastError();
 }
@@ -390,6 +392,7 @@ cudaError_t launch_row_stats(const LaunchCtx& L, const ProbD& P, long long total
   if (totalA <= 0) return cudaSuccess;
   const long long rpb = 1024;
   long long grid = (totalA + rpb - 1) / rpb;
+  KKS_LAUNCHED();
   k_row_stats<8><<<(unsigned)grid, kBlock, 0, L.stream>>>(P, totalA, use_bc, rpb, rf, rfc, inst_stats);
   return cudaGetLastError();
 }
@@ -402,13 +405,17 @@ size_t scan_tmp_bytes(long long n) {
 
 cudaError_t launch_scan(const LaunchCtx& L, const long long* in, long long* out, long long n, void* tmp) {
   if (n <= 0) {
+    KKS_LAUNCHED();
     k_set_zero_ll<<<1, 1, 0, L.stream>>>(out);
     return cudaGetLastError();
   }
   long long nb = (n + kScanTile - 1) / kScanTile;
   long long* bsum = (long long*)tmp;
+  KKS_LAUNCHED();
   k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, L.stream>>>(in, n, bsum);
+  KKS_LAUNCHED();
   k_scan_top<<<1, 1024, 0, L.stream>>>(bsum, nb);
+  KKS_LAUNCHED();
   k_scan_apply<<<(unsigned)nb, kScanThreads, 0, L.stream>>>(in, out, n, bsum);
   return cudaGetLastError();
 }
@@ -417,6 +424,7 @@ cudaError_t launch_bin_count(const LaunchCtx& L, const ProbD& P, long long total
                              const long long* rfc, const long long* rowsize, BinCfg cfg, unsigned long long* hist) {
   if (totalA <= 0) return cudaSuccess;
   int grid = grid_for(totalA, kBlock, L.num_sms, 8);
+  KKS_LAUNCHED();
   k_bin_count<<<grid, kBlock, 0, L.stream>>>(P, totalA, phase, rf, rfc, rowsize, cfg, hist);
   return cudaGetLastError();
 }
@@ -426,6 +434,7 @@ cudaError_t launch_bin_scatter(const LaunchCtx& L, const ProbD& P, long long tot
                                unsigned long long* cursor, int* rows) {
   if (totalA <= 0) return cudaSuccess;
   int grid = grid_for(totalA, kBlock, L.num_sms, 8);
+  KKS_LAUNCHED();
   k_bin_scatter<<<grid, kBlock, 0, L.stream>>>(P, totalA, phase, rf, rfc, const_cast<long long*>(rowsize), cfg,
                                                cursor, rows);
   return cudaGetLastError();
@@ -433,9 +442,11 @@ cudaError_t launch_bin_scatter(const LaunchCtx& L, const ProbD& P, long long tot
 
 cudaError_t launch_write_rowptr(const LaunchCtx& L, const ProbD& P, long long totalA, const long long* offs,
                                 const long long* rowsize, unsigned long long* inst_out) {
+  KKS_LAUNCHED();
   k_empty_instances<<<(P.ninst + 255) / 256, 256, 0, L.stream>>>(P, inst_out);
   if (totalA > 0) {
     int grid = grid_for(totalA, kBlock, L.num_sms, 8);
+    KKS_LAUNCHED();
     k_write_rowptr<<<grid, kBlock, 0, L.stream>>>(P, totalA, offs, rowsize, inst_out);
   }
   return cudaGetLastError();

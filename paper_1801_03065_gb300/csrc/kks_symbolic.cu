@@ -206,6 +206,7 @@ cudaError_t run_hash(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, lon
   auto kern = k_sym_hash<TW, COMP, false>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
+  KKS_LAUNCHED();
   kern<<<hash_grid(S.nrows, teams, L.num_sms), TW * teams, smem, L.stream>>>(P, S.rows, S.nrows, S.logT, -1,
                                                                             nullptr, 0, rowsize);
   return cudaGetLastError();
@@ -225,6 +226,7 @@ cudaError_t run_spill(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, lo
   if (cap > T - 1) cap = T - 1;
   int grid = S.nchunks;
   if (grid > S.nrows) grid = (int)S.nrows;
+  KKS_LAUNCHED();
   kern<<<grid, TW, smem, L.stream>>>(P, S.rows, S.nrows, S.l1_logT, cap, (int*)S.l2_pool, S.l2_chunk_slots,
                                      rowsize);
   return cudaGetLastError();
@@ -243,6 +245,7 @@ cudaError_t run_dense(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, lo
   if (per_sm > 4) per_sm = 4;
   long long grid = (long long)L.num_sms * per_sm;
   if (grid > S.nrows) grid = S.nrows;
+  KKS_LAUNCHED();
   kern<<<(unsigned)grid, TW, smem, L.stream>>>(P, S.rows, S.nrows, S.kwords_max, rowsize);
   return cudaGetLastError();
 }

@@ -198,15 +198,22 @@ class SpGEMM:
                                         _ptr(S_colidx), n, _ptr(out), _stream(stream)), "spgemm_masked")
         return out
 
-    def transpose(self, A: CsrMatrix, with_values: bool = True, stream=None):
-        """(A^T as CsrMatrix with int64 row pointers, perm) with At.values = A.values[perm]."""
+    def transpose(self, A: CsrMatrix, with_values: bool = True, out=None, stream=None):
+        """(A^T as CsrMatrix with int64 row pointers, perm) with At.values = A.values[perm].
+
+        out: optional (At, perm) from an earlier call on the same shape to write into.
+        """
         dev = A.colidx.device
-        Atp = torch.empty(A.ncols + 1, dtype=torch.int64, device=dev)
-        Atj = torch.empty(A.nnz, dtype=torch.int32, device=dev)
-        perm = torch.empty(A.nnz, dtype=torch.int64, device=dev)
-        Atx = None
-        if with_values and A.values is not None:
-            Atx = torch.empty(A.nnz, dtype=A.values.dtype, device=dev)
+        if out is not None:
+            At0, perm = out
+            Atp, Atj, Atx = At0.rowptr, At0.colidx, At0.values
+        else:
+            Atp = torch.empty(A.ncols + 1, dtype=torch.int64, device=dev)
+            Atj = torch.empty(A.nnz, dtype=torch.int32, device=dev)
+            perm = torch.empty(A.nnz, dtype=torch.int64, device=dev)
+            Atx = None
+            if with_values and A.values is not None:
+                Atx = torch.empty(A.nnz, dtype=A.values.dtype, device=dev)
         d = A.desc() if (with_values and A.values is not None) else A.with_values(None).desc(A.dtype)
         B.check(self._lib.spgemm_transpose(self._h, C.byref(d), C.c_void_p(Atp.data_ptr()), _ptr(Atj), _ptr(Atx),
                                            _ptr(perm), _stream(stream)), "spgemm_transpose")
@@ -247,6 +254,11 @@ class SpGEMM:
         B.check(self._lib.spgemm_batch_numeric(self._h, n, da, db, prp, pcj, pcx, _stream(stream)),
                 "spgemm_batch_numeric")
         return [CsrMatrix(r, c, v, (a.nrows, b.ncols)) for r, c, v, a, b in zip(rowptrs, colidx, values, As, Bs)]
+
+
+def launch_count() -> int:
+    """Kernels launched by libkkspgemm so far in this process."""
+    return int(B.load().spgemm_launch_count())
 
 
 def spgemm(A: CsrMatrix, Bm: CsrMatrix, **options) -> CsrMatrix:
