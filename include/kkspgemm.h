@@ -181,6 +181,27 @@ spgemm_status_t spgemm_transpose(spgemm_handle_t h, const spgemm_csr_t *A, int64
                                  int32_t *At_colidx, void *At_values, int64_t *perm,
                                  spgemm_stream_t stream);
 
+/*
+ * Transpose without allocating anything (the paper has no counterpart; this
+ * is a deployment convenience).  For callers that cannot allocate GPU memory
+ * when they need the transpose: code running inside a custom allocator or an
+ * out-of-memory handler, where a nested cudaMalloc would recurse or fail, code
+ * that must not synchronise the device as cudaFree does, or processes with a
+ * fixed GPU memory budget.  Same arguments and results as spgemm_transpose,
+ * without a handle.  Its scratch is one fixed 32 MiB device buffer inside the
+ * library, held by every GPU that loads it until the process exits:
+ *  - the first call on a device looks up the buffer's address, so make that
+ *    first call before any stream capture;
+ *  - all calls share the buffer and it keeps the last call's contents (each
+ *    call clears what it needs); calls that overlap on the GPU race on it, so
+ *    serialise them;
+ *  - a problem needing more scratch (about 16 bytes per column of A plus 12
+ *    bytes per nonzero) returns SPGEMM_ERR_OOM before any kernel runs.
+ * Synchronises the stream twice (the longest column, then the status).
+ */
+spgemm_status_t spgemm_transpose_noalloc(const spgemm_csr_t *A, int64_t *At_rowptr, int32_t *At_colidx,
+                                         void *At_values, int64_t *perm, spgemm_stream_t stream);
+
 /* dst[q] = src[perm[q]] for q < n (dtype selects 4- or 8-byte values). */
 spgemm_status_t spgemm_gather(spgemm_handle_t h, spgemm_dtype_t dtype, const void *src, const int64_t *perm,
                               void *dst, int64_t n, spgemm_stream_t stream);

@@ -61,6 +61,7 @@ SIGNATURES = {
     "spgemm_masked": (C.c_int, [_P, C.POINTER(CsrT), C.POINTER(CsrT), _P, _P, C.c_int64, _P, _P]),
     "spgemm_transpose": (C.c_int, [_P, C.POINTER(CsrT), _P, _P, _P, _P, _P]),
     "spgemm_gather": (C.c_int, [_P, C.c_int, _P, _P, _P, C.c_int64, _P]),
+    "spgemm_transpose_noalloc": (C.c_int, [C.POINTER(CsrT), _P, _P, _P, _P, _P]),
     "spgemm_batch_symbolic": (C.c_int, [_P, C.c_int32, C.POINTER(CsrT), C.POINTER(CsrT),
                                         C.POINTER(_P), C.POINTER(C.c_int64), _P]),
     "spgemm_batch_numeric": (C.c_int, [_P, C.c_int32, C.POINTER(CsrT), C.POINTER(CsrT),
