@@ -89,7 +89,10 @@ typedef struct {
   int64_t workspace_limit_bytes; /* 0 = no limit; above it calls fail with SPGEMM_ERR_OOM */
   int64_t pool_limit_bytes;      /* cap on accumulator pools (0 = 8 GiB) */
   int32_t device;                /* CUDA device ordinal used by the handle */
-  int32_t reserved[7];
+  int32_t hash_function;         /* 0 = key & (size - 1) (the paper's), 1 = multiplicative (default) */
+  int32_t verbose;               /* 1: print device-detected errors to stderr */
+  int32_t slots_per_key_log2;    /* hash-table slots per key bound, log2 (0 = default 1: 50 % load) */
+  int32_t reserved[4];
 } spgemm_options_t;
 
 /* Statistics of the last symbolic call (Section 4 results-table columns). */

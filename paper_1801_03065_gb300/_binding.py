@@ -34,7 +34,8 @@ class OptionsT(C.Structure):
                 ("l1_max_occupancy", C.c_double), ("l1_max_log2_slots", C.c_int32),
                 ("dense", C.c_int32), ("method", C.c_int32),
                 ("workspace_limit_bytes", C.c_int64), ("pool_limit_bytes", C.c_int64),
-                ("device", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("device", C.c_int32), ("hash_function", C.c_int32), ("verbose", C.c_int32),
+                ("slots_per_key_log2", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 class StatsT(C.Structure):

@@ -196,7 +196,7 @@ ProbD prob(kks_handle* h) {
   P.cs = B<unsigned>(h, kBufCs);
   P.status = B<DevStatus>(h, kBufStatus);
   P.ninst = h->ninst;
-  P.pad = 0;
+  P.hash_mode = h->opt.hash_function;
   return P;
 }
 
@@ -252,7 +252,7 @@ int device_code_to_status(int code) {
 // Reads the device status word (already copied to host memory at *hs) and clears it.
 spgemm_status_t consume_status(kks_handle* h, const DevStatus* hs, cudaStream_t s) {
   if (hs->code == kDevOk) return SPGEMM_OK;
-  if (h->opt.reserved[0] & 1)
+  if (h->opt.verbose)
     fprintf(stderr, "kkspgemm: device status %d at site %d (info %lld)\n", hs->code, hs->where, hs->info);
   int code = hs->code;
   cudaMemsetAsync(h->buf[kBufStatus], 0, sizeof(DevStatus), s);
@@ -291,6 +291,7 @@ BinCfg base_cfg(kks_handle* h) {
   c.spill_ok = 1;
   c.force_cls = 0;
   c.force_logT = 0;
+  c.slots_log2 = h->opt.slots_per_key_log2 > 0 ? h->opt.slots_per_key_log2 : 1;
   return c;
 }
 
@@ -338,6 +339,8 @@ void set_default_options(spgemm_options_t* o) {
   o->workspace_limit_bytes = 0;
   o->pool_limit_bytes = 0;
   o->device = 0;
+  o->hash_function = 1;
+  o->verbose = 0;
 }
 
 // Upload the instance table through a pinned ring slot (numeric path).
@@ -777,6 +780,8 @@ MaskedD maskd(kks_handle* h, const spgemm_csr_t* X, const spgemm_csr_t* Y, const
   M.Sj = Sj;
   M.out = out;
   M.status = B<DevStatus>(h, kBufStatus);
+  M.hash_mode = h->opt.hash_function;
+  M.pad = 0;
   return M;
 }
 
@@ -885,7 +890,8 @@ spgemm_status_t spgemm_handle_create(spgemm_handle_t* out, const spgemm_options_
   if (!h) return SPGEMM_ERR_OOM;
   if (opt) h->opt = *opt; else set_default_options(&h->opt);
   if (!(h->opt.l1_max_occupancy > 0.0 && h->opt.l1_max_occupancy <= 1.0) || h->opt.compress_threshold < 0.0 ||
-      h->opt.compression < -1 || h->opt.compression > 1) {
+      h->opt.compression < -1 || h->opt.compression > 1 || h->opt.hash_function < 0 || h->opt.hash_function > 1 ||
+      h->opt.slots_per_key_log2 < 0 || h->opt.slots_per_key_log2 > 4) {
     delete h;
     return SPGEMM_ERR_INVALID_ARG;
   }

@@ -84,7 +84,7 @@ struct ProbD {
   const unsigned* cs;        // column set bits
   DevStatus* status;
   int ninst;
-  int pad;
+  int hash_mode;             // LpHash mode of every table of the plan
 };
 
 // Largest b with row0s[b] <= g; such an instance is never empty.
@@ -184,19 +184,36 @@ __device__ __forceinline__ long long team_sum(const Team<TW>& tm, long long v, l
   return tot;
 }
 
+// acc + a * b with one rounding (fused multiply-add)
+__device__ __forceinline__ double fma_acc(double a, double b, double acc) { return fma(a, b, acc); }
+__device__ __forceinline__ float fma_acc(float a, float b, float acc) { return fmaf(a, b, acc); }
+
 // --------------------------------------------------------------------------
 // linear-probing hash table (LP accumulator, Section 3.1.2)
 // --------------------------------------------------------------------------
-__device__ __forceinline__ unsigned lp_hash(int key, unsigned tmask) {
-  return (unsigned)key & tmask;
-}
+// Slot of a key in a table of 2^logT slots.  Mode 0 is the paper's BitwiseAnd
+// of the key with size - 1 (Section 3.1.2).  Mode 1 takes the top logT bits of
+// key * 2654435761 (Fibonacci hashing): stencil rows hold runs of consecutive
+// columns spaced by the grid strides, which BitwiseAnd packs into long linear
+// probing clusters.
+struct LpHash {
+  unsigned mask;
+  int shift;
+  int mode;
+  __device__ __forceinline__ LpHash(int logT, int mode_)
+      : mask((1u << logT) - 1u), shift(32 - logT), mode(logT > 0 ? mode_ : 0) {}
+  __device__ __forceinline__ unsigned operator()(int key) const {
+    return mode ? (((unsigned)key * 2654435761u) >> shift) : ((unsigned)key & mask);
+  }
+};
 
 // Find or claim the slot of key.  cap < 0: no occupancy limit.  Otherwise a new
 // key is only placed while *occ < cap (the maximum-occupancy rule of the LP
 // accumulator); a refused key returns -1 and goes to the next level.
 // Returns -2 when the table has no free slot at all.
-__device__ __forceinline__ int lp_insert(int* keys, unsigned tmask, int* occ, int cap, int key) {
-  unsigned h = lp_hash(key, tmask);
+__device__ __forceinline__ int lp_insert(int* keys, const LpHash& hs, int* occ, int cap, int key) {
+  const unsigned tmask = hs.mask;
+  unsigned h = hs(key);
   for (unsigned probe = 0; probe <= tmask; ++probe) {
     int cur = *((volatile int*)(keys + h));
     if (cur == key) return (int)h;
@@ -214,9 +231,43 @@ __device__ __forceinline__ int lp_insert(int* keys, unsigned tmask, int* occ, in
   return -2;
 }
 
+// Team-wide insert of one key per active lane (keys of one call pairwise
+// distinct or equal keys resolved by the CAS).  The probe loop runs while any
+// lane of the team is unresolved, so its trip count is uniform and the body is
+// a short predicated step: lanes with short probe chains do not diverge from
+// the team.  Returns the slot, -1 for inactive lanes, -2 if the table is full.
+__device__ __forceinline__ int lp_insert_team(unsigned team_mask, int* keys, const LpHash& hs, bool active,
+                                              int key) {
+  unsigned h = active ? hs(key) : 0u;
+  bool pending = active;
+  int slot = -1;
+  unsigned probes = 0;
+  while (__any_sync(team_mask, pending)) {
+    if (pending) {
+      const int cur = *((volatile int*)(keys + h));
+      bool claim = cur == key;
+      if (cur == kEmpty) {
+        const int old = atomicCAS(keys + h, kEmpty, key);
+        claim = (old == kEmpty || old == key);
+      }
+      if (claim) {
+        slot = (int)h;
+        pending = false;
+      } else if (++probes > hs.mask) {
+        slot = -2;
+        pending = false;
+      } else {
+        h = (h + 1) & hs.mask;
+      }
+    }
+  }
+  return slot;
+}
+
 // Probe-only lookup; -1 when absent.  Valid once no insert is in flight.
-__device__ __forceinline__ int lp_find(const int* keys, unsigned tmask, int key) {
-  unsigned h = lp_hash(key, tmask);
+__device__ __forceinline__ int lp_find(const int* keys, const LpHash& hs, int key) {
+  const unsigned tmask = hs.mask;
+  unsigned h = hs(key);
   for (unsigned probe = 0; probe <= tmask; ++probe) {
     int cur = *((const volatile int*)(keys + h));
     if (cur == key) return (int)h;

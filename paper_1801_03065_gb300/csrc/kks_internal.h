@@ -52,6 +52,7 @@ struct BinCfg {
   int spill_ok;            // L1 + L2 hash allowed
   int force_cls;           // >0: every non-empty row goes to this class
   int force_logT;          // with force_cls: table size used for every row
+  int slots_log2;          // table slots per key bound, log2 (1: at most 50 % load)
 };
 
 // kk: the key range the dense test compares against (k, or k/32 compressed);
@@ -59,7 +60,7 @@ struct BinCfg {
 __host__ __device__ inline int choose_bin(long long u, long long work, long long kk, long long kwords,
                                           const BinCfg& c) {
   if (u <= 0 || work <= 0) return bin_id(kClsNone, 0);
-  int logT = ilog2_ceil(2 * u);
+  int logT = ilog2_ceil(u) + (c.slots_log2 > 0 ? c.slots_log2 : 1);
   if (logT < c.min_logT) logT = c.min_logT;
   if (logT > 30) logT = 30;   // bin ids hold logT < kBinsPerClass; such rows fail pool sizing
   if (c.force_cls > 0) return bin_id(c.force_cls, c.force_cls == kClsDense ? 0 : c.force_logT);
@@ -142,6 +143,8 @@ struct MaskedD {
   const int* Sj;         // pattern columns (any order within a row)
   void* out;             // values on the pattern
   DevStatus* status;
+  int hash_mode;
+  int pad;
 };
 struct MaskedLaunch {
   int cls, logT;

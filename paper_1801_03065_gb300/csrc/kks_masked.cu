@@ -35,7 +35,7 @@ __global__ void k_masked(MaskedD M, const int* __restrict__ rows, long long nrow
   __shared__ long long scan_scratch[33];
   Team<TW> tm;
   const int T = 1 << logT;
-  const unsigned tmask = (unsigned)T - 1u;
+  const LpHash tmask(logT, M.hash_mode);
   const int half = T / 2 > 0 ? T / 2 : 1;
   unsigned char* base;
   ChunkScratch<TW, VT>* csc;

@@ -37,7 +37,7 @@ __global__ void k_num_hash(ProbD P, const int* __restrict__ rows, long long nrow
   __shared__ long long scan_scratch[33];
   Team<TW> tm;
   const int T = 1 << logT;
-  const unsigned tmask = (unsigned)T - 1u;
+  const LpHash tmask(logT, P.hash_mode);
   const int half = T / 2 > 0 ? T / 2 : 1;
   unsigned char* base = smem + (size_t)tm.id * num_team_bytes<TW, VT>(T);
   VT* vals = reinterpret_cast<VT*>(base);
@@ -105,6 +105,195 @@ __global__ void k_num_hash(ProbD P, const int* __restrict__ rows, long long nrow
       Cx[c0 + x] = vals[(unsigned)(e & 0xffffffffull)];
     }
     tm.sync();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Warp / sub-warp teams (TW <= 32).  Products go into the LP table with plain
+// read-modify-writes of the values: no two lanes ever update one slot in the
+// same step, so no floating-point atomics are needed.
+//  * sequential mode (the chunk's B rows average >= TW/2 entries): one B row
+//    per pass, so the keys of a pass are distinct (the paper's Thread-Sequential
+//    guarantee of unique inserts, Section 3.1.1);
+//  * flat mode (short B rows): products of several B rows share a pass; equal
+//    keys are grouped with __match_any_sync, their values summed through a
+//    per-team exchange buffer, and only the group's first lane updates.
+// ---------------------------------------------------------------------------
+template <int TW, typename VT>
+__host__ __device__ size_t warp_team_bytes(int T) {
+  const int half = T / 2 > 0 ? T / 2 : 1;
+  return al16((size_t)T * sizeof(VT)) + al16((size_t)T * 4) + al16((size_t)half * 8) +
+         al16(sizeof(ChunkScratch<TW, VT>)) + al16((size_t)TW * sizeof(VT));
+}
+
+template <int TW, typename VT>
+__global__ void __launch_bounds__(256, 3) k_num_warp(ProbD P, const int* __restrict__ rows, long long nrows, int logT) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Team<TW> tm;
+  const int T = 1 << logT;
+  const LpHash tmask(logT, P.hash_mode);
+  const int half = T / 2 > 0 ? T / 2 : 1;
+  unsigned char* base = smem + (size_t)tm.id * warp_team_bytes<TW, VT>(T);
+  VT* vals = reinterpret_cast<VT*>(base);
+  int* keys = reinterpret_cast<int*>(base + al16((size_t)T * sizeof(VT)));
+  unsigned long long* sortb =
+      reinterpret_cast<unsigned long long*>(base + al16((size_t)T * sizeof(VT)) + al16((size_t)T * 4));
+  ChunkScratch<TW, VT>* csc = reinterpret_cast<ChunkScratch<TW, VT>*>(
+      base + al16((size_t)T * sizeof(VT)) + al16((size_t)T * 4) + al16((size_t)half * 8));
+  VT* xchg = reinterpret_cast<VT*>(reinterpret_cast<unsigned char*>(csc) + al16(sizeof(ChunkScratch<TW, VT>)));
+  const unsigned lane_lt = (1u << tm.lane) - 1u;
+  const int lane_base = (threadIdx.x & 31) & ~(TW - 1);
+
+  const long long team = (long long)blockIdx.x * tm.per_cta + tm.id;
+  const long long nteams = (long long)gridDim.x * tm.per_cta;
+  for (long long r = team; r < nrows; r += nteams) {
+    const long long g = rows[r];
+    const int b = inst_of(P.arow0s, P.ninst, g);
+    const InstD& I = P.inst[b];
+    const long long i = g - I.arow0;
+    const long long c0 = I.Crp[i];
+    const long long s = I.Crp[i + 1] - c0;
+    for (int x = tm.lane; x < T; x += TW) {
+      keys[x] = kEmpty;
+      vals[x] = VT(0);
+    }
+    __syncwarp(tm.mask);
+    const long long a0 = rp_at(I.A, i), a1 = rp_at(I.A, i + 1);
+    const VT* __restrict__ Ax = reinterpret_cast<const VT*>(I.A.vx);
+    const VT* __restrict__ Bx = reinterpret_cast<const VT*>(I.B.vx);
+    const int* __restrict__ Bj = I.B.cj;
+    const int* __restrict__ Aj = I.A.cj;
+    for (long long c = a0; c < a1; c += TW) {
+      const long long p = c + tm.lane;
+      long long bs = 0;
+      int len = 0;
+      VT av = VT(0);
+      if (p < a1) {
+        const int j = Aj[p];
+        bs = rp_at(I.B, j);
+        len = (int)(rp_at(I.B, j + 1) - bs);
+        av = Ax[p];
+      }
+      const int nc = (a1 - c) < TW ? (int)(a1 - c) : TW;
+      int tot = len;
+#pragma unroll
+      for (int d = TW / 2; d > 0; d >>= 1) tot += __shfl_xor_sync(tm.mask, tot, d, TW);
+      if (2 * tot >= nc * TW) {
+        // sequential: one B row per pass, distinct keys inside a pass; the
+        // first TW entries of kU passes are loaded together to overlap their
+        // latencies, then inserted pass by pass
+        constexpr int kU = 4;
+        for (int t0 = 0; t0 < nc; t0 += kU) {
+          int key[kU], lent[kU];
+          long long bst[kU];
+          VT at[kU], bv[kU];
+#pragma unroll
+          for (int u = 0; u < kU; ++u) {
+            const int t = (t0 + u < nc) ? t0 + u : nc - 1;
+            bst[u] = __shfl_sync(tm.mask, bs, t, TW);
+            const int l = __shfl_sync(tm.mask, len, t, TW);
+            at[u] = __shfl_sync(tm.mask, av, t, TW);
+            lent[u] = (t0 + u < nc) ? l : 0;
+            key[u] = -1;
+            bv[u] = VT(0);
+            if (tm.lane < lent[u]) {
+              key[u] = Bj[bst[u] + tm.lane];
+              bv[u] = Bx[bst[u] + tm.lane];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < kU; ++u) {
+            // one fused multiply-add per product: the FP64 pipe is the scarce unit
+            const int slot = lp_insert_team(tm.mask, keys, tmask, key[u] >= 0, key[u]);
+            if (slot >= 0) vals[slot] = fma_acc(at[u], bv[u], vals[slot]);
+            else if (slot == -2) dev_fail(P.status, kDevTableFull, 17, g);
+            if (lent[u] > TW) {   // the rest of a long B row: still one row, distinct keys
+              for (int x = tm.lane + TW; x < lent[u]; x += TW) {
+                const int kk = Bj[bst[u] + x];
+                const VT bb = Bx[bst[u] + x];
+                const int slot = lp_insert(keys, tmask, nullptr, -1, kk);
+                if (slot >= 0) vals[slot] = fma_acc(at[u], bb, vals[slot]);
+                else dev_fail(P.status, kDevTableFull, 17, g);
+              }
+            }
+            __syncwarp(tm.mask);
+          }
+        }
+      } else {
+        // flat: the chunk's products spread over the lanes
+        int ex = len;
+#pragma unroll
+        for (int d = 1; d < TW; d <<= 1) {
+          const int y = __shfl_up_sync(tm.mask, ex, d, TW);
+          if (tm.lane >= d) ex += y;
+        }
+        ex -= len;
+        csc->pre[tm.lane] = ex;
+        csc->bs[tm.lane] = bs;
+        csc->av[tm.lane] = av;
+        if (tm.lane == 0) csc->pre[TW] = tot;
+        __syncwarp(tm.mask);
+        int t = 0;
+        for (int xb = 0; xb < tot; xb += TW) {
+          const int x = xb + tm.lane;
+          int key = -1 - tm.lane;   // inactive lanes: a distinct negative key
+          VT v = VT(0);
+          if (x < tot) {
+            while (csc->pre[t + 1] <= x) ++t;
+            const long long q = csc->bs[t] + (x - csc->pre[t]);
+            key = Bj[q];
+            v = csc->av[t] * Bx[q];
+          }
+          const unsigned grp = (__match_any_sync(tm.mask, key) >> lane_base) & ((TW == 32) ? 0xffffffffu : ((1u << TW) - 1u));
+          const bool leader = (grp & lane_lt) == 0;
+          if (__any_sync(tm.mask, __popc(grp) > 1)) {
+            xchg[tm.lane] = v;
+            __syncwarp(tm.mask);
+            if (leader) {
+              unsigned rest = grp & ~(1u << tm.lane);
+              while (rest) {
+                const int o = __ffs(rest) - 1;
+                rest &= rest - 1u;
+                v += xchg[o];
+              }
+            }
+            __syncwarp(tm.mask);
+          }
+          if (x < tot && leader) {
+            const int slot = lp_insert(keys, tmask, nullptr, -1, key);
+            if (slot >= 0) vals[slot] += v;
+            else dev_fail(P.status, kDevTableFull, 18, g);
+          }
+          __syncwarp(tm.mask);
+        }
+      }
+    }
+    // compaction of the occupied slots into (column << 32 | slot)
+    int cnt = 0;
+    for (int xb = 0; xb < T; xb += TW) {
+      const int x = xb + tm.lane;
+      const bool o = x < T && keys[x] != kEmpty;
+      const unsigned bal = (__ballot_sync(tm.mask, o) >> lane_base) & ((TW == 32) ? 0xffffffffu : ((1u << TW) - 1u));
+      const int pos = cnt + __popc(bal & lane_lt);
+      if (o && pos < half) sortb[pos] = ((unsigned long long)(unsigned)keys[x] << 32) | (unsigned)x;
+      cnt += __popc(bal);
+    }
+    if (tm.lane == 0 && cnt != s) dev_fail(P.status, kDevRowSizeMismatch, 19, g);
+    const int n = cnt < half ? cnt : half;
+    int N = 1;
+    while (N < n) N <<= 1;
+    for (int x = n + tm.lane; x < N; x += TW) sortb[x] = ~0ull;
+    __syncwarp(tm.mask);
+    team_bitonic<TW>(tm, sortb, N);
+    const long long nw = n < s ? n : s;
+    VT* __restrict__ Cx = reinterpret_cast<VT*>(I.Cx);
+    int* __restrict__ Cj = I.Cj;
+    for (long long x = tm.lane; x < nw; x += TW) {
+      const unsigned long long e = sortb[x];
+      Cj[c0 + x] = (int)(e >> 32);
+      Cx[c0 + x] = vals[(unsigned)(e & 0xffffffffull)];
+    }
+    __syncwarp(tm.mask);
   }
 }
 
@@ -191,7 +380,7 @@ __global__ void __launch_bounds__(TW) k_num_spill(ProbD P, const int* __restrict
   __shared__ long long scan_scratch[33];
   Team<TW> tm;
   const int T = 1 << l1_logT;
-  const unsigned tmask = (unsigned)T - 1u;
+  const LpHash tmask(l1_logT, P.hash_mode);
   VT* vals1 = reinterpret_cast<VT*>(smem);
   int* keys1 = reinterpret_cast<int*>(smem + al16((size_t)T * sizeof(VT)));
   ChunkScratch<TW, VT>* csc =
@@ -199,7 +388,7 @@ __global__ void __launch_bounds__(TW) k_num_spill(ProbD P, const int* __restrict
   int* occ = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(csc) + al16(sizeof(ChunkScratch<TW, VT>)));
   int* keys2 = reinterpret_cast<int*>(pool + (long long)blockIdx.x * chunk_bytes);
   VT* vals2 = reinterpret_cast<VT*>(reinterpret_cast<unsigned char*>(keys2) + al16((size_t)l2_slots * 4));
-  const unsigned t2mask = (unsigned)l2_slots - 1u;
+  const LpHash t2mask(ilog2_ceil(l2_slots), P.hash_mode);
   unsigned* bm = pool2 + (long long)blockIdx.x * 2 * kw_max;
   unsigned* pre = bm + kw_max;
 
@@ -347,6 +536,27 @@ cudaError_t run_hash(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
   return cudaGetLastError();
 }
 
+template <int TW, typename VT>
+cudaError_t run_warp(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
+  const int T = 1 << S.logT;
+  const size_t tb = warp_team_bytes<TW, VT>(T);
+  int teams = (int)((48 * 1024) / tb);
+  const int tmax = 256 / TW;
+  if (teams > tmax) teams = tmax;
+  if (teams < 1) teams = 1;
+  const size_t smem = tb * teams;
+  if (smem > (size_t)L.max_smem_optin) return cudaErrorInvalidConfiguration;
+  auto kern = k_num_warp<TW, VT>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  long long grid = (S.nrows + teams - 1) / teams;
+  const long long cap = (long long)L.num_sms * 64;
+  if (grid > cap) grid = cap;
+  KKS_LAUNCHED();
+  kern<<<(unsigned)grid, TW * teams, smem, L.stream>>>(P, S.rows, S.nrows, S.logT);
+  return cudaGetLastError();
+}
+
 template <typename VT>
 cudaError_t run_dense(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
   constexpr int TW = 1024;
@@ -386,8 +596,8 @@ cudaError_t run_spill(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
 template <typename VT>
 cudaError_t dispatch(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
   switch (S.cls) {
-    case kClsW8: return run_hash<8, VT>(L, P, S);
-    case kClsW32: return run_hash<32, VT>(L, P, S);
+    case kClsW8: return run_warp<8, VT>(L, P, S);
+    case kClsW32: return run_warp<32, VT>(L, P, S);
     case kClsC256: return run_hash<256, VT>(L, P, S);
     case kClsC1024: return run_hash<1024, VT>(L, P, S);
     case kClsDense: return run_dense<VT>(L, P, S);

@@ -33,7 +33,7 @@ __global__ void k_sym_hash(ProbD P, const int* __restrict__ rows, long long nrow
   __shared__ long long scan_scratch[33];
   Team<TW> tm;
   const int T = 1 << logT;
-  const unsigned tmask = (unsigned)T - 1u;
+  const LpHash tmask(logT, P.hash_mode);
   unsigned char* base = smem + (size_t)tm.id * sym_team_bytes<TW, COMP>(T);
   int* keys = reinterpret_cast<int*>(base);
   unsigned* masks = reinterpret_cast<unsigned*>(base + al16((size_t)T * 4));
@@ -45,7 +45,7 @@ __global__ void k_sym_hash(ProbD P, const int* __restrict__ rows, long long nrow
   const long long nteams = (long long)gridDim.x * tm.per_cta;
   int* k2 = nullptr;
   unsigned* m2 = nullptr;
-  const unsigned t2mask = (unsigned)l2_slots - 1u;
+  const LpHash t2mask(ilog2_ceil(l2_slots), P.hash_mode);
   if (SPILL) {
     k2 = l2_pool + team * l2_slots * (COMP ? 2 : 1);
     m2 = reinterpret_cast<unsigned*>(k2 + l2_slots);

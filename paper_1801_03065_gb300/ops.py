@@ -104,7 +104,8 @@ class SpGEMM:
     def __init__(self, compression: int = -1, compress_threshold: float = 0.85,
                  l1_max_occupancy: float = 0.5, l1_max_log2_slots: int = 0, dense: int = -1,
                  method: int = 0, workspace_limit_bytes: int = 0, pool_limit_bytes: int = 0,
-                 device: int = 0, verbose: bool = False):
+                 device: int = 0, hash_function: int = 1, slots_per_key_log2: int = 0,
+                 verbose: bool = False):
         self._lib = B.load()
         opt = B.OptionsT()
         B.check(self._lib.spgemm_options_default(C.byref(opt)), "spgemm_options_default")
@@ -117,7 +118,9 @@ class SpGEMM:
         opt.workspace_limit_bytes = workspace_limit_bytes
         opt.pool_limit_bytes = pool_limit_bytes
         opt.device = device
-        opt.reserved[0] = 1 if verbose else 0
+        opt.hash_function = hash_function
+        opt.slots_per_key_log2 = slots_per_key_log2
+        opt.verbose = 1 if verbose else 0
         self.device = torch.device("cuda", device)
         h = C.c_void_p()
         B.check(self._lib.spgemm_handle_create(C.byref(h), C.byref(opt)), "spgemm_handle_create")
