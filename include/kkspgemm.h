@@ -112,7 +112,7 @@ typedef struct {
   int64_t maxrs;          /* largest row of C */
   double ars;             /* average row size of C */
   int64_t workspace_bytes;/* device scratch held by the handle */
-  int64_t bin_rows_numeric[7]; /* rows per team class: none, w8, w32, c256, c1024, dense, spill */
+  int64_t bin_rows_numeric[8]; /* rows per team class: none, w8, w32, c256, c1024, dense, spill, thread */
 } spgemm_stats_t;
 
 /* Fills *opt with the defaults.  Returns SPGEMM_ERR_INVALID_ARG for NULL. */
@@ -166,12 +166,18 @@ spgemm_status_t spgemm_get_stats(spgemm_handle_t h, spgemm_stats_t *out);
  * order inside a row); products whose column is not in S(i,:) are dropped.
  * This gives the gradients of a loss L(C), C = A * B, on fixed patterns:
  * dA = (G * B^T) on A's pattern and dB = (A^T * G) on B's pattern, with G the
- * gradient on C's pattern.  out has nnz(S) values of X's dtype.  Synchronises
- * the stream once (to plan the row bins).
+ * gradient on C's pattern.  out has nnz(S) values of X's dtype.  The first call
+ * on a set of patterns synchronises the stream once (to plan the row bins);
+ * later calls with the same X, Y and S pattern pointers reuse the plan and are
+ * asynchronous (value pointers may change between calls).
+ * X_perm / Y_perm (device int64, may be NULL): when given, the value of X's
+ * entry p is X.values[X_perm[p]] (likewise for Y), so a transpose built by
+ * spgemm_transpose can take the current values of its source without a gather.
  */
 spgemm_status_t spgemm_masked(spgemm_handle_t h, const spgemm_csr_t *X, const spgemm_csr_t *Y,
                               const int64_t *S_rowptr, const int32_t *S_colidx, int64_t S_nnz,
-                              void *out, spgemm_stream_t stream);
+                              void *out, const int64_t *X_perm, const int64_t *Y_perm,
+                              spgemm_stream_t stream);
 
 /*
  * Transpose: At = A^T (A.ncols x A.nrows) with At_rowptr int64[A.ncols + 1],

@@ -45,7 +45,7 @@ class StatsT(C.Structure):
                 ("CF", C.c_double), ("CMRF", C.c_double), ("compressed", C.c_int32),
                 ("nbins_symbolic", C.c_int32), ("nbins_numeric", C.c_int32), ("reserved0", C.c_int32),
                 ("nnzC", C.c_int64), ("maxrs", C.c_int64), ("ars", C.c_double),
-                ("workspace_bytes", C.c_int64), ("bin_rows_numeric", C.c_int64 * 7)]
+                ("workspace_bytes", C.c_int64), ("bin_rows_numeric", C.c_int64 * 8)]
 
 
 # name -> (restype, argtypes); mirrors include/kkspgemm.h
@@ -59,7 +59,7 @@ SIGNATURES = {
     "spgemm_numeric_reuse": (C.c_int, [_P, C.POINTER(CsrT), C.POINTER(CsrT), _P, _P, _P, _P]),
     "spgemm_handle_sync": (C.c_int, [_P, _P]),
     "spgemm_get_stats": (C.c_int, [_P, C.POINTER(StatsT)]),
-    "spgemm_masked": (C.c_int, [_P, C.POINTER(CsrT), C.POINTER(CsrT), _P, _P, C.c_int64, _P, _P]),
+    "spgemm_masked": (C.c_int, [_P, C.POINTER(CsrT), C.POINTER(CsrT), _P, _P, C.c_int64, _P, _P, _P, _P]),
     "spgemm_transpose": (C.c_int, [_P, C.POINTER(CsrT), _P, _P, _P, _P, _P]),
     "spgemm_gather": (C.c_int, [_P, C.c_int, _P, _P, _P, C.c_int64, _P]),
     "spgemm_transpose_noalloc": (C.c_int, [C.POINTER(CsrT), _P, _P, _P, _P, _P]),

@@ -107,6 +107,7 @@ struct kks_handle {
   int num_l1_logT = 0;
   spgemm_stats_t stats;
   MaskPlan reuse;
+  MaskPlan masked;   // last plan of spgemm_masked (reused while the patterns are unchanged)
 };
 
 namespace {
@@ -292,6 +293,7 @@ BinCfg base_cfg(kks_handle* h) {
   c.force_cls = 0;
   c.force_logT = 0;
   c.slots_log2 = h->opt.slots_per_key_log2 > 0 ? h->opt.slots_per_key_log2 : 1;
+  c.t1_max_work = 0;
   return c;
 }
 
@@ -780,6 +782,8 @@ MaskedD maskd(kks_handle* h, const spgemm_csr_t* X, const spgemm_csr_t* Y, const
   M.Sj = Sj;
   M.out = out;
   M.status = B<DevStatus>(h, kBufStatus);
+  M.xperm = nullptr;
+  M.yperm = nullptr;
   M.hash_mode = h->opt.hash_function;
   M.pad = 0;
   return M;
@@ -797,6 +801,7 @@ spgemm_status_t plan_masked(kks_handle* h, const MaskedD& M, long long nrows, in
   BinCfg c = base_cfg(h);
   c.cta_max_logT = cta_max_logT_msk(h, dtype);
   c.dense_ok = 0;
+  c.t1_max_work = 64;   // rows with <= 8 pattern entries and <= 64 products: one thread each
   clamp_cfg(h, c);
   unsigned long long* d_hist = B<unsigned long long>(h, kBufMaskHist);
   unsigned long long* h_hist = (unsigned long long*)h->pinned;
@@ -994,7 +999,7 @@ spgemm_status_t spgemm_batch_numeric(spgemm_handle_t h, int32_t count, const spg
 
 spgemm_status_t spgemm_masked(spgemm_handle_t h, const spgemm_csr_t* X, const spgemm_csr_t* Y,
                               const int64_t* S_rowptr, const int32_t* S_colidx, int64_t S_nnz, void* out,
-                              spgemm_stream_t stream) {
+                              const int64_t* X_perm, const int64_t* Y_perm, spgemm_stream_t stream) {
   if (!h) return SPGEMM_ERR_INVALID_ARG;
   KKS_ST(check_masked(X, Y, S_rowptr, S_colidx, S_nnz, out));
   cudaStream_t s = (cudaStream_t)stream;
@@ -1002,9 +1007,30 @@ spgemm_status_t spgemm_masked(spgemm_handle_t h, const spgemm_csr_t* X, const sp
   if (X->nrows == 0 || S_nnz == 0) return SPGEMM_OK;
   KKS_ST(ensure(h, kBufStatus, sizeof(DevStatus)));
   MaskedD M = maskd(h, X, Y, S_rowptr, S_colidx, out);
-  MaskPlan plan;
-  KKS_ST(plan_masked(h, M, X->nrows, (int)X->dtype, kBufMaskRows, kBufMaskPool, &plan, s));
-  return run_masked_plan(h, M, (int)X->dtype, kBufMaskRows, kBufMaskPool, plan, s);
+  M.xperm = reinterpret_cast<const long long*>(X_perm);
+  M.yperm = reinterpret_cast<const long long*>(Y_perm);
+  // the row bins depend only on the three patterns: plan once, then reuse
+  MaskPlan& P = h->masked;
+  const bool same = P.valid && P.sp == S_rowptr && P.sj == S_colidx && P.xrp == X->rowptr && P.xcj == X->colidx &&
+                    P.yrp == Y->rowptr && P.ycj == Y->colidx && P.nrows == X->nrows && P.snnz == S_nnz &&
+                    P.dtype == (int)X->dtype;
+  if (!same) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    KKS_CU(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return SPGEMM_ERR_NOT_READY;
+    P.valid = false;
+    KKS_ST(plan_masked(h, M, X->nrows, (int)X->dtype, kBufMaskRows, kBufMaskPool, &P, s));
+    P.sp = S_rowptr;
+    P.sj = S_colidx;
+    P.xrp = X->rowptr;
+    P.xcj = X->colidx;
+    P.yrp = Y->rowptr;
+    P.ycj = Y->colidx;
+    P.nrows = X->nrows;
+    P.snnz = S_nnz;
+    P.dtype = (int)X->dtype;
+  }
+  return run_masked_plan(h, M, (int)X->dtype, kBufMaskRows, kBufMaskPool, P, s);
 }
 
 spgemm_status_t spgemm_numeric_reuse(spgemm_handle_t h, const spgemm_csr_t* A, const spgemm_csr_t* Bm,

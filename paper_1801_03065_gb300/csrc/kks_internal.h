@@ -28,8 +28,10 @@ enum TeamClass : int {
   kClsC1024 = 4,   // 1024-thread CTA team, shared LP table
   kClsDense = 5,   // CTA team, dense accumulator (bitmap in shared memory)
   kClsSpill = 6,   // CTA team, shared L1 LP table + global L2 LP table
-  kNumClasses = 7,
+  kClsT1 = 7,      // one thread per row, keys and accumulators in registers
+  kNumClasses = 8,
 };
+constexpr int kT1MaxKeys = 8;   // rows of class T1 have at most this many keys
 constexpr int kBinsPerClass = 32;
 constexpr int kNumBins = kNumClasses * kBinsPerClass;
 
@@ -53,6 +55,7 @@ struct BinCfg {
   int force_cls;           // >0: every non-empty row goes to this class
   int force_logT;          // with force_cls: table size used for every row
   int slots_log2;          // table slots per key bound, log2 (1: at most 50 % load)
+  long long t1_max_work;   // > 0: rows with u <= kT1MaxKeys and work <= this go to class T1
 };
 
 // kk: the key range the dense test compares against (k, or k/32 compressed);
@@ -64,6 +67,7 @@ __host__ __device__ inline int choose_bin(long long u, long long work, long long
   if (logT < c.min_logT) logT = c.min_logT;
   if (logT > 30) logT = 30;   // bin ids hold logT < kBinsPerClass; such rows fail pool sizing
   if (c.force_cls > 0) return bin_id(c.force_cls, c.force_cls == kClsDense ? 0 : c.force_logT);
+  if (c.t1_max_work > 0 && u <= kT1MaxKeys && work <= c.t1_max_work) return bin_id(kClsT1, 0);
   bool dense_fit = c.dense_ok && kwords <= c.dense_max_kwords;
   if (dense_fit && (logT > c.cta_max_logT || u * c.dense_ratio >= kk)) return bin_id(kClsDense, 0);
   if (logT <= c.w8_max_logT && work <= c.w8_max_work) return bin_id(kClsW8, logT);
@@ -143,6 +147,8 @@ struct MaskedD {
   const int* Sj;         // pattern columns (any order within a row)
   void* out;             // values on the pattern
   DevStatus* status;
+  const long long* xperm;  // optional: the value of X's entry p is X.vx[xperm[p]]
+  const long long* yperm;  // optional: the value of Y's entry q is Y.vx[yperm[q]]
   int hash_mode;
   int pad;
 };

@@ -51,6 +51,9 @@ __global__ void k_masked(MaskedD M, const int* __restrict__ rows, long long nrow
   VT* acc = reinterpret_cast<VT*>(base + al16((size_t)T * 4) * 2);
   const VT* __restrict__ Xx = reinterpret_cast<const VT*>(M.X.vx);
   const VT* __restrict__ Yx = reinterpret_cast<const VT*>(M.Y.vx);
+  // values may be read through a permutation (a transpose's values without a gather)
+  auto XV = [&](long long p) -> VT { return Xx[M.xperm ? M.xperm[p] : p]; };
+  auto YV = [&](long long q) -> VT { return Yx[M.yperm ? M.yperm[q] : q]; };
   const int* __restrict__ Yj = M.Y.cj;
   VT* __restrict__ out = reinterpret_cast<VT*>(M.out);
 
@@ -79,10 +82,10 @@ __global__ void k_masked(MaskedD M, const int* __restrict__ rows, long long nrow
       *bs = rp_at(M.Y, j);
       *be = rp_at(M.Y, j + 1);
     };
-    auto aval = [&](long long p) { return Xx[p]; };
+    auto aval = [&](long long p) { return XV(p); };
     auto body = [&](long long q, int t) {
       const int slot = lp_find(keys, tmask, Yj[q]);
-      if (slot >= 0) atomicAdd(acc + pos[slot], csc->av[t] * Yx[q]);
+      if (slot >= 0) atomicAdd(acc + pos[slot], csc->av[t] * YV(q));
     };
     for_each_product<TW, VT>(tm, csc, scan_scratch, M.X.cj, a0, a1, range, aval, body);
     if (GTAB) {
@@ -93,6 +96,274 @@ __global__ void k_masked(MaskedD M, const int* __restrict__ rows, long long nrow
     for (long long p = tm.lane; p < sw; p += TW) out[s0 + p] = acc[p];
     if (GTAB) __threadfence_block();
     tm.sync();
+  }
+}
+
+// Warp / sub-warp teams (TW <= 32): the same probe-only accumulation without
+// floating-point atomics.  One Y row per pass when Y rows are long (distinct
+// keys, so distinct positions), otherwise the chunk's products are spread over
+// the lanes and equal keys are summed through match_any before one lane
+// updates the position.
+template <int TW, typename VT>
+__host__ __device__ size_t mskw_team_bytes(int T) {
+  const int half = T / 2 > 0 ? T / 2 : 1;
+  return al16((size_t)T * 4) * 2 + al16((size_t)half * sizeof(VT)) + al16(sizeof(ChunkScratch<TW, VT>)) +
+         al16((size_t)TW * sizeof(VT));
+}
+
+template <int TW, typename VT>
+__global__ void __launch_bounds__(256) k_masked_warp(MaskedD M, const int* __restrict__ rows, long long nrows,
+                                                     int logT) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Team<TW> tm;
+  const int T = 1 << logT;
+  const LpHash tmask(logT, M.hash_mode);
+  const int half = T / 2 > 0 ? T / 2 : 1;
+  unsigned char* base = smem + (size_t)tm.id * mskw_team_bytes<TW, VT>(T);
+  int* keys = reinterpret_cast<int*>(base);
+  int* pos = reinterpret_cast<int*>(base + al16((size_t)T * 4));
+  VT* acc = reinterpret_cast<VT*>(base + al16((size_t)T * 4) * 2);
+  ChunkScratch<TW, VT>* csc =
+      reinterpret_cast<ChunkScratch<TW, VT>*>(base + al16((size_t)T * 4) * 2 + al16((size_t)half * sizeof(VT)));
+  VT* xchg = reinterpret_cast<VT*>(reinterpret_cast<unsigned char*>(csc) + al16(sizeof(ChunkScratch<TW, VT>)));
+  const VT* __restrict__ Xx = reinterpret_cast<const VT*>(M.X.vx);
+  const VT* __restrict__ Yx = reinterpret_cast<const VT*>(M.Y.vx);
+  // values may be read through a permutation (a transpose's values without a gather)
+  auto XV = [&](long long p) -> VT { return Xx[M.xperm ? M.xperm[p] : p]; };
+  auto YV = [&](long long q) -> VT { return Yx[M.yperm ? M.yperm[q] : q]; };
+  const int* __restrict__ Yj = M.Y.cj;
+  const int* __restrict__ Xj = M.X.cj;
+  VT* __restrict__ out = reinterpret_cast<VT*>(M.out);
+  const unsigned lane_lt = (1u << tm.lane) - 1u;
+  const int lane_base = (threadIdx.x & 31) & ~(TW - 1);
+  const unsigned tbits = (TW == 32) ? 0xffffffffu : ((1u << TW) - 1u);
+
+  const long long team = (long long)blockIdx.x * tm.per_cta + tm.id;
+  const long long nteams = (long long)gridDim.x * tm.per_cta;
+  for (long long r = team; r < nrows; r += nteams) {
+    const long long i = rows[r];
+    const long long s0 = M.Sp[i];
+    const long long s = M.Sp[i + 1] - s0;
+    const long long a0 = rp_at(M.X, i), a1 = rp_at(M.X, i + 1);
+    // the first chunk of X(i,:) is fetched before the pattern is keyed, so the
+    // two chains of dependent loads overlap
+    long long bs = 0;
+    int len = 0;
+    VT av = VT(0);
+    if (a0 + tm.lane < a1) {
+      const int j = Xj[a0 + tm.lane];
+      bs = rp_at(M.Y, j);
+      len = (int)(rp_at(M.Y, j + 1) - bs);
+      av = XV(a0 + tm.lane);
+    }
+    const int pk = (tm.lane < s) ? M.Sj[s0 + tm.lane] : 0;
+    for (int x = tm.lane; x < T; x += TW) keys[x] = kEmpty;
+    __syncwarp(tm.mask);
+    for (long long p = tm.lane; p < s; p += TW) {
+      const int slot = lp_insert(keys, tmask, nullptr, -1, p < TW ? pk : M.Sj[s0 + p]);
+      if (slot >= 0 && p < half) {
+        pos[slot] = (int)p;
+        acc[p] = VT(0);
+      } else {
+        dev_fail(M.status, kDevTableFull, 22, i);
+      }
+    }
+    __syncwarp(tm.mask);
+    for (long long c = a0; c < a1; c += TW) {
+      if (c != a0) {
+        const long long p = c + tm.lane;
+        bs = 0;
+        len = 0;
+        av = VT(0);
+        if (p < a1) {
+          const int j = Xj[p];
+          bs = rp_at(M.Y, j);
+          len = (int)(rp_at(M.Y, j + 1) - bs);
+          av = XV(p);
+        }
+      }
+      const int nc = (a1 - c) < TW ? (int)(a1 - c) : TW;
+      int tot = len;
+#pragma unroll
+      for (int d = TW / 2; d > 0; d >>= 1) tot += __shfl_xor_sync(tm.mask, tot, d, TW);
+      if (2 * tot >= nc * TW) {
+        // one Y row per pass; the first TW entries of kU passes load together
+        constexpr int kU = 4;
+        for (int t0 = 0; t0 < nc; t0 += kU) {
+          int key[kU], lent[kU];
+          long long bst[kU];
+          VT at[kU], yv[kU];
+#pragma unroll
+          for (int u = 0; u < kU; ++u) {
+            const int t = (t0 + u < nc) ? t0 + u : nc - 1;
+            bst[u] = __shfl_sync(tm.mask, bs, t, TW);
+            const int l = __shfl_sync(tm.mask, len, t, TW);
+            at[u] = __shfl_sync(tm.mask, av, t, TW);
+            lent[u] = (t0 + u < nc) ? l : 0;
+            key[u] = -1;
+            yv[u] = VT(0);
+            if (tm.lane < lent[u]) {
+              key[u] = Yj[bst[u] + tm.lane];
+              yv[u] = YV(bst[u] + tm.lane);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < kU; ++u) {
+            if (key[u] >= 0) {
+              const int slot = lp_find(keys, tmask, key[u]);
+              if (slot >= 0) {
+                const int q = pos[slot];
+                acc[q] = fma_acc(at[u], yv[u], acc[q]);
+              }
+            }
+            for (int x = tm.lane + TW; x < lent[u]; x += TW) {
+              const int slot = lp_find(keys, tmask, Yj[bst[u] + x]);
+              if (slot >= 0) {
+                const int q = pos[slot];
+                acc[q] = fma_acc(at[u], YV(bst[u] + x), acc[q]);
+              }
+            }
+            __syncwarp(tm.mask);
+          }
+        }
+      } else {
+        int ex = len;
+#pragma unroll
+        for (int d = 1; d < TW; d <<= 1) {
+          const int y = __shfl_up_sync(tm.mask, ex, d, TW);
+          if (tm.lane >= d) ex += y;
+        }
+        ex -= len;
+        csc->pre[tm.lane] = ex;
+        csc->bs[tm.lane] = bs;
+        csc->av[tm.lane] = av;
+        if (tm.lane == 0) csc->pre[TW] = tot;
+        __syncwarp(tm.mask);
+        int t = 0;
+        for (int xb = 0; xb < tot; xb += TW) {
+          const int x = xb + tm.lane;
+          int q = -1 - tm.lane;   // inactive or masked-out lanes: a distinct negative id
+          VT v = VT(0);
+          if (x < tot) {
+            while (csc->pre[t + 1] <= x) ++t;
+            const long long yq = csc->bs[t] + (x - csc->pre[t]);
+            const int slot = lp_find(keys, tmask, Yj[yq]);
+            if (slot >= 0) {
+              q = pos[slot];
+              v = csc->av[t] * YV(yq);
+            }
+          }
+          const unsigned grp = (__match_any_sync(tm.mask, q) >> lane_base) & tbits;
+          const bool leader = (grp & lane_lt) == 0;
+          if (__any_sync(tm.mask, __popc(grp) > 1)) {
+            xchg[tm.lane] = v;
+            __syncwarp(tm.mask);
+            if (leader) {
+              unsigned rest = grp & ~(1u << tm.lane);
+              while (rest) {
+                const int o = __ffs(rest) - 1;
+                rest &= rest - 1u;
+                v += xchg[o];
+              }
+            }
+            __syncwarp(tm.mask);
+          }
+          if (q >= 0 && leader) acc[q] += v;
+          __syncwarp(tm.mask);
+        }
+      }
+    }
+    const long long sw = s < half ? s : half;
+    for (long long p = tm.lane; p < sw; p += TW) out[s0 + p] = acc[p];
+    __syncwarp(tm.mask);
+  }
+}
+
+// One thread per row for rows with at most kT1MaxKeys pattern entries and a
+// few products (Thread-Sequential with a team of one, Section 3.1.1): the
+// pattern's keys and their accumulators stay in registers, a product is
+// matched by comparing with every key, and all rows of the bin are in flight
+// at once, which hides the chains of dependent loads of short rows.
+// STAGED = false: one product at a time (rows whose Y rows hold one or two
+// entries); STAGED = true: loads staged in groups (longer Y rows).
+// The matching key is found with integer compares and the product goes to one
+// accumulator in shared memory: a predicated FMA per key would issue
+// kT1MaxKeys FP64 instructions per product on the scarce FP64 pipe.
+template <typename VT, bool STAGED>
+__global__ void __launch_bounds__(256, 4) k_masked_thread(MaskedD M, const int* __restrict__ rows, long long nrows) {
+  __shared__ VT accs[kT1MaxKeys][256];
+  const VT* __restrict__ Xx = reinterpret_cast<const VT*>(M.X.vx);
+  const VT* __restrict__ Yx = reinterpret_cast<const VT*>(M.Y.vx);
+  // values may be read through a permutation (a transpose's values without a gather)
+  auto XV = [&](long long p) -> VT { return Xx[M.xperm ? M.xperm[p] : p]; };
+  auto YV = [&](long long q) -> VT { return Yx[M.yperm ? M.yperm[q] : q]; };
+  const int* __restrict__ Yj = M.Y.cj;
+  const int* __restrict__ Xj = M.X.cj;
+  VT* __restrict__ out = reinterpret_cast<VT*>(M.out);
+  const int tid = threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += stride) {
+    const long long i = rows[r];
+    const long long s0 = M.Sp[i];
+    const int s = (int)(M.Sp[i + 1] - s0);
+    const long long a0 = rp_at(M.X, i), a1 = rp_at(M.X, i + 1);
+    int key[kT1MaxKeys];
+#pragma unroll
+    for (int t = 0; t < kT1MaxKeys; ++t) {
+      key[t] = (t < s) ? M.Sj[s0 + t] : -1;
+      accs[t][tid] = VT(0);
+    }
+    auto add = [&](int c, VT a, VT y) {
+      int hit = -1;
+#pragma unroll
+      for (int t = 0; t < kT1MaxKeys; ++t) hit = (key[t] == c) ? t : hit;
+      if (hit >= 0) accs[hit][tid] = fma_acc(a, y, accs[hit][tid]);
+    };
+    if (!STAGED) {
+      for (long long p = a0; p < a1; ++p) {
+        const int j = Xj[p];
+        const VT a = XV(p);
+        const long long b0 = rp_at(M.Y, j), b1 = rp_at(M.Y, j + 1);
+        for (long long q = b0; q < b1; ++q) add(Yj[q], a, YV(q));
+      }
+    }
+    // staged loads: 4 entries of X(i,:), then their Y ranges, then the Y
+    // entries 4 at a time, so each thread keeps several loads in flight
+    constexpr int kX = 4, kQ = 4;
+    for (long long c0 = STAGED ? a0 : a1; c0 < a1; c0 += kX) {
+      int j[kX];
+      VT a[kX];
+      long long b0[kX], b1[kX];
+#pragma unroll
+      for (int u = 0; u < kX; ++u) {
+        const bool ok = c0 + u < a1;
+        j[u] = ok ? Xj[c0 + u] : -1;
+        a[u] = ok ? XV(c0 + u) : VT(0);
+      }
+#pragma unroll
+      for (int u = 0; u < kX; ++u) {
+        b0[u] = j[u] >= 0 ? rp_at(M.Y, j[u]) : 0;
+        b1[u] = j[u] >= 0 ? rp_at(M.Y, j[u] + 1) : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < kX; ++u) {
+        for (long long q = b0[u]; q < b1[u]; q += kQ) {
+          int c[kQ];
+          VT y[kQ];
+#pragma unroll
+          for (int v = 0; v < kQ; ++v) {
+            const bool ok = q + v < b1[u];
+            c[v] = ok ? Yj[q + v] : -1;
+            y[v] = ok ? YV(q + v) : VT(0);
+          }
+#pragma unroll
+          for (int v = 0; v < kQ; ++v) add(c[v], a[u], y[v]);
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < kT1MaxKeys; ++t)
+      if (t < s) out[s0 + t] = accs[t][tid];
   }
 }
 
@@ -133,6 +404,8 @@ __global__ void k_masked_bins(MaskedD M, long long nrows, int phase, BinCfg cfg,
       } else {
         bin = choose_bin(s, w > 0 ? w : (s > 0 ? 1 : 0), M.Y.ncols, (M.Y.ncols + 31) >> 5, cfg);
         if (bin_cls(bin) == kClsNone) bin = -1;
+        // thread-per-row rows: staged loads once Y rows average more than 2 entries
+        if (bin >= 0 && bin_cls(bin) == kClsT1 && w > 2 * (a1 - a0)) bin = bin_id(kClsT1, 1);
       }
     }
     const unsigned grp = __match_any_sync(0xffffffffu, bin);
@@ -278,6 +551,24 @@ cudaError_t run_masked_hash(const LaunchCtx& L, const MaskedD& M, const MaskedLa
   return cudaGetLastError();
 }
 
+template <int TW, typename VT>
+cudaError_t run_masked_warp(const LaunchCtx& L, const MaskedD& M, const MaskedLaunch& S) {
+  const int T = 1 << S.logT;
+  const size_t tb = mskw_team_bytes<TW, VT>(T);
+  int teams = (int)((48 * 1024) / tb);
+  const int tmax = 256 / TW;
+  if (teams > tmax) teams = tmax;
+  if (teams < 1) teams = 1;
+  const size_t smem = tb * teams;
+  if (smem > (size_t)L.max_smem_optin) return cudaErrorInvalidConfiguration;
+  auto kern = k_masked_warp<TW, VT>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  KKS_LAUNCHED();
+  kern<<<grid_cap(S.nrows, teams, L.num_sms, 64), TW * teams, smem, L.stream>>>(M, S.rows, S.nrows, S.logT);
+  return cudaGetLastError();
+}
+
 template <typename VT>
 cudaError_t run_masked_global(const LaunchCtx& L, const MaskedD& M, const MaskedLaunch& S) {
   constexpr int TW = 1024;
@@ -297,8 +588,16 @@ cudaError_t run_masked_global(const LaunchCtx& L, const MaskedD& M, const Masked
 template <typename VT>
 cudaError_t masked_dispatch(const LaunchCtx& L, const MaskedD& M, const MaskedLaunch& S) {
   switch (S.cls) {
-    case kClsW8: return run_masked_hash<8, VT>(L, M, S);
-    case kClsW32: return run_masked_hash<32, VT>(L, M, S);
+    case kClsT1: {
+      KKS_LAUNCHED();
+      if (S.logT == 0)
+        k_masked_thread<VT, false><<<grid_cap(S.nrows, 256, L.num_sms, 32), 256, 0, L.stream>>>(M, S.rows, S.nrows);
+      else
+        k_masked_thread<VT, true><<<grid_cap(S.nrows, 256, L.num_sms, 32), 256, 0, L.stream>>>(M, S.rows, S.nrows);
+      return cudaGetLastError();
+    }
+    case kClsW8: return run_masked_warp<8, VT>(L, M, S);
+    case kClsW32: return run_masked_warp<32, VT>(L, M, S);
     case kClsC256: return run_masked_hash<256, VT>(L, M, S);
     case kClsC1024: return run_masked_hash<1024, VT>(L, M, S);
     case kClsSpill: return run_masked_global<VT>(L, M, S);

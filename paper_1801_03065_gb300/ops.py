@@ -191,14 +191,19 @@ class SpGEMM:
 
     # ---------------------------------------------------------------- masked / transpose
     def masked(self, X: CsrMatrix, Y: CsrMatrix, S_rowptr: torch.Tensor, S_colidx: torch.Tensor,
-               out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
-        """out(i,l) = sum_j X(i,j) Y(j,l) for (i,l) in the pattern S."""
+               out: Optional[torch.Tensor] = None, x_perm: Optional[torch.Tensor] = None,
+               y_perm: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """out(i,l) = sum_j X(i,j) Y(j,l) for (i,l) in the pattern S.
+
+        x_perm / y_perm: X's (Y's) entry p takes its value from values[perm[p]].
+        """
         n = S_colidx.numel()
         if out is None:
             out = torch.empty(n, dtype=X.dtype, device=S_colidx.device)
         dx, dy = X.desc(), Y.desc()
         B.check(self._lib.spgemm_masked(self._h, C.byref(dx), C.byref(dy), C.c_void_p(S_rowptr.data_ptr()),
-                                        _ptr(S_colidx), n, _ptr(out), _stream(stream)), "spgemm_masked")
+                                        _ptr(S_colidx), n, _ptr(out), _ptr(x_perm), _ptr(y_perm),
+                                        _stream(stream)), "spgemm_masked")
         return out
 
     def transpose(self, A: CsrMatrix, with_values: bool = True, out=None, stream=None):
