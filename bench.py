@@ -49,6 +49,10 @@ def parse_args(argv=None):
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
+    p.add_argument("--workload", choices=["stencil27_100", "batched512"], default="stencil27_100",
+                   help="stencil27_100: the headline step; batched512: batched autotuned vs plain per-matrix")
+    p.add_argument("--count", type=int, default=512, help="batched512: number of products")
+    p.add_argument("--repeats", type=int, default=20, help="batched512: numeric-reuse repeats")
     return p.parse_args(argv)
 
 
@@ -413,10 +417,131 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+# ----------------------------------------------------------------------------- batched
+def run_batched(args):
+    """Batched autotuned plan against the plain per-matrix meta-algorithm.
+
+    NoReuse: symbolic + numeric of all products (batched: one plan, rows of all
+    products binned together, tuned numeric bins; plain: one handle per product
+    with the paper's per-problem rule, called product by product).  Reuse: the
+    numeric phase repeated with values refreshed from pinned host memory; the
+    batched repeats run as one captured CUDA graph (two host-to-device copies
+    plus the numeric launches), the plain ones product by product.
+    """
+    import numpy as np
+    import torch
+    import workloads as w
+    from paper_1801_03065_gb300 import ops
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    pairs = w.batched_pairs(count=args.count, seed=11, dtype=np.float64)
+    va_h = np.concatenate([a.values for a, _ in pairs])
+    vb_h = np.concatenate([b.values for _, b in pairs])
+    va = torch.from_numpy(va_h).to(dev)
+    vb = torch.from_numpy(vb_h).to(dev)
+    As, Bs = [], []
+    oa = ob = 0
+    for a, b in pairs:
+        As.append(ops.CsrMatrix(torch.from_numpy(a.rowptr).to(dev), torch.from_numpy(a.colidx).to(dev),
+                                va[oa:oa + a.nnz], a.shape))
+        Bs.append(ops.CsrMatrix(torch.from_numpy(b.rowptr).to(dev), torch.from_numpy(b.colidx).to(dev),
+                                vb[ob:ob + b.nnz], b.shape))
+        oa += a.nnz
+        ob += b.nnz
+    fresh = w.batched_fresh_values(pairs, repeat=0)
+    hva = torch.from_numpy(np.concatenate([x for x, _ in fresh])).pin_memory()
+    hvb = torch.from_numpy(np.concatenate([y for _, y in fresh])).pin_memory()
+
+    hb = ops.SpGEMM(tune=True)
+    rps, nnzs = hb.batch_symbolic(As, Bs)
+    Cj = [torch.empty(z, dtype=torch.int32, device=dev) for z in nnzs]
+    Cx = [torch.empty(z, dtype=torch.float64, device=dev) for z in nnzs]
+    hb.batch_numeric(As, Bs, rps, nnzs, Cj, Cx)   # tunes the numeric bins
+    hb.sync()
+    st = hb.stats()
+    fm = st["f_m"]
+    hp = [ops.SpGEMM(method=1) for _ in pairs]
+    rpp = [torch.empty(a.nrows + 1, dtype=torch.int64, device=dev) for a in As]
+
+    def batched_step():
+        hb.batch_symbolic(As, Bs)
+        hb.batch_numeric(As, Bs, rps, nnzs, Cj, Cx)
+
+    def plain_step():
+        for i in range(len(pairs)):
+            rp, z = hp[i].symbolic(As[i], Bs[i], C_rowptr=rpp[i])
+            hp[i].numeric(As[i], Bs[i], rp, z, Cj[i], Cx[i])
+
+    for _ in range(max(1, args.warmup)):
+        batched_step()
+        plain_step()
+    torch.cuda.synchronize()
+    t_b = statistics.mean(time_region(torch, batched_step, args.steps))
+    t_p = statistics.mean(time_region(torch, plain_step, max(1, args.steps // 2)))
+
+    # numeric reuse: values refreshed from pinned host memory every repeat
+    def batched_num():
+        hb.batch_numeric(As, Bs, rps, nnzs, Cj, Cx)
+
+    def plain_num():
+        for i in range(len(pairs)):
+            hp[i].numeric(As[i], Bs[i], rpp[i], nnzs[i], Cj[i], Cx[i])
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        batched_num()
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        va.copy_(hva, non_blocking=True)
+        vb.copy_(hvb, non_blocking=True)
+        batched_num()
+    reps = args.repeats
+
+    def batched_reuse():
+        for _ in range(reps):
+            graph.replay()
+
+    def plain_reuse():
+        for _ in range(reps):
+            va.copy_(hva, non_blocking=True)
+            vb.copy_(hvb, non_blocking=True)
+            plain_num()
+
+    batched_reuse()
+    plain_reuse()
+    t_br = statistics.mean(time_region(torch, batched_reuse, 2))
+    t_pr = statistics.mean(time_region(torch, plain_reuse, 1))
+    hb.sync()
+    gf = lambda t, n=1: round(2.0 * fm * n / (t * 1e-3) / 1e9, 3)
+    out = {
+        "metric": METRIC, "value": gf(t_b), "unit": "GFLOP/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t_b, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "batched512: %d independent square products, n_i log-uniform in [1e3, 2e5], "
+                               "geometric rows with means U(3, 40), uniform columns, FP64 U(-1, 1), seed 11"
+                               % len(pairs),
+                   "f_m": fm, "nnzC": st["nnzC"], "rows": sum(a.nrows for a in As),
+                   "l2": "inputs larger than L2"},
+        "batched_vs_plain": {
+            "sym_num": {"batched_autotuned": gf(t_b), "plain_per_matrix": gf(t_p), "speedup": round(t_p / t_b, 3),
+                        "ms": [round(t_b, 3), round(t_p, 3)]},
+            "numeric_reuse_%d" % reps: {"batched_graph": gf(t_br, reps), "plain_per_matrix": gf(t_pr, reps),
+                                        "speedup": round(t_pr / t_br, 3), "ms": [round(t_br, 3), round(t_pr, 3)],
+                                        "h2d_bytes_per_repeat": int((hva.numel() + hvb.numel()) * 8)}},
+        "tuned_bins": st["tuned_bins"], "numeric_bins": st["nbins_numeric"],
+    }
+    print(json.dumps(out), flush=True)
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched512":
+        run_batched(args)
     else:
         run_ours(args)
 

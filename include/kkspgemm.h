@@ -92,7 +92,9 @@ typedef struct {
   int32_t hash_function;         /* 0 = key & (size - 1) (the paper's), 1 = multiplicative (default) */
   int32_t verbose;               /* 1: print device-detected errors to stderr */
   int32_t slots_per_key_log2;    /* hash-table slots per key bound, log2 (0 = default 1: 50 % load) */
-  int32_t reserved[4];
+  int32_t tune;                  /* 1: the first numeric call of a plan times candidate kernel
+                                    configurations per row bin and keeps the fastest (synchronises) */
+  int32_t reserved[3];
 } spgemm_options_t;
 
 /* Statistics of the last symbolic call (Section 4 results-table columns). */
@@ -107,7 +109,7 @@ typedef struct {
   int32_t compressed;     /* 1 if the symbolic phase ran on the compressed B */
   int32_t nbins_symbolic; /* non-empty row bins used by the symbolic phase */
   int32_t nbins_numeric;  /* non-empty row bins used by the numeric phase */
-  int32_t reserved0;
+  int32_t tuned_bins;     /* numeric bins whose configuration the tuner changed */
   int64_t nnzC;
   int64_t maxrs;          /* largest row of C */
   double ars;             /* average row size of C */

@@ -35,7 +35,7 @@ class OptionsT(C.Structure):
                 ("dense", C.c_int32), ("method", C.c_int32),
                 ("workspace_limit_bytes", C.c_int64), ("pool_limit_bytes", C.c_int64),
                 ("device", C.c_int32), ("hash_function", C.c_int32), ("verbose", C.c_int32),
-                ("slots_per_key_log2", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("slots_per_key_log2", C.c_int32), ("tune", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 class StatsT(C.Structure):
@@ -43,7 +43,7 @@ class StatsT(C.Structure):
                 ("nnzB", C.c_int64), ("f_m", C.c_int64), ("maxrf", C.c_int64),
                 ("f_m_compressed", C.c_int64), ("maxrf_compressed", C.c_int64),
                 ("CF", C.c_double), ("CMRF", C.c_double), ("compressed", C.c_int32),
-                ("nbins_symbolic", C.c_int32), ("nbins_numeric", C.c_int32), ("reserved0", C.c_int32),
+                ("nbins_symbolic", C.c_int32), ("nbins_numeric", C.c_int32), ("tuned_bins", C.c_int32),
                 ("nnzC", C.c_int64), ("maxrs", C.c_int64), ("ars", C.c_double),
                 ("workspace_bytes", C.c_int64), ("bin_rows_numeric", C.c_int64 * 8)]
 

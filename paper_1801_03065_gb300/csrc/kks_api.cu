@@ -74,6 +74,7 @@ struct PatternId {
 struct BinRun {
   int cls, logT, compressed;
   long long off, count;
+  int hash;   // LpHash mode used for this bin (the tuner may change it)
 };
 
 constexpr int kRing = 8;
@@ -108,6 +109,15 @@ struct kks_handle {
   spgemm_stats_t stats;
   MaskPlan reuse;
   MaskPlan masked;   // last plan of spgemm_masked (reused while the patterns are unchanged)
+  bool tuned = false;
+  // tuner results by bin (class, log2 table, rows, dtype): a new plan of the
+  // same problem reuses them instead of tuning again
+  struct TuneEntry {
+    int cls, logT, dtype;
+    long long count;
+    BinRun pick;
+  };
+  std::vector<TuneEntry> tune_cache;
 };
 
 namespace {
@@ -118,10 +128,16 @@ spgemm_status_t cuda_status(cudaError_t e) {
   return SPGEMM_ERR_CUDA;
 }
 
-#define KKS_CU(expr)                                        \
-  do {                                                      \
-    cudaError_t _e = (expr);                                \
-    if (_e != cudaSuccess) return cuda_status(_e);          \
+// CUDA failures are rare and otherwise opaque behind SPGEMM_ERR_CUDA: name the
+// failing call on stderr.
+#define KKS_CU(expr)                                                                              \
+  do {                                                                                            \
+    cudaError_t _e = (expr);                                                                      \
+    if (_e != cudaSuccess) {                                                                      \
+      fprintf(stderr, "kkspgemm: %s failed: %s (%s:%d)\n", #expr, cudaGetErrorString(_e), __FILE__, \
+              __LINE__);                                                                          \
+      return cuda_status(_e);                                                                     \
+    }                                                                                             \
   } while (0)
 #define KKS_ST(expr)                                        \
   do {                                                      \
@@ -319,11 +335,29 @@ BinCfg sym_cfg(kks_handle* h, int comp) {
   return c;
 }
 
+// The paper's GPU meta-algorithm restated (Section 3.3): one team class for
+// the whole problem, warp teams (kkmem, Thread-Sequential) when rows average
+// fewer than 256 multiplications, CTA teams (kklp, Thread-Flat-Parallel)
+// otherwise; the L1 table is sized from the average row size `est` (known in
+// the numeric phase; estimated as flops / 8 in the symbolic phase); rows that
+// do not fit L1 spill to an L2 table in global memory.
+void plain_rule(BinCfg& c, double avg_flops, double est) {
+  c.force_cls = avg_flops < 256.0 ? kClsW32 : kClsC256;
+  const int cap = c.force_cls == kClsW32 ? c.w32_max_logT : c.c256_max_logT;
+  int l = ilog2_ceil((long long)std::max(1.0, std::ceil(2.0 * est)));
+  c.force_logT = std::max(c.min_logT, std::min(l, cap));
+  c.dense_ok = 0;
+  c.t1_max_work = 0;
+}
+
 BinCfg num_cfg(kks_handle* h, int dtype, long long kmax) {
   BinCfg c = base_cfg(h);
   c.cta_max_logT = cta_max_logT_num(h, dtype);
   c.dense_max_kwords = ((long long)h->max_smem - 26 * 1024) / 4;
-  c.dense_ratio = 8;
+  // FP64 dense rows add into a global chunk with FP64 atomics, which the GB300
+  // FP64 units make slow: in FP64 the dense accumulator only takes rows too
+  // large for a shared table
+  c.dense_ratio = dtype == 1 ? 0 : 8;
   long long pool_limit = h->opt.pool_limit_bytes > 0 ? h->opt.pool_limit_bytes : (8ll << 30);
   if (kmax * (dtype == 1 ? 8 : 4) > pool_limit) c.dense_ok = 0;
   clamp_cfg(h, c);
@@ -509,6 +543,11 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
 
   // (4) symbolic bins: the compressed and plain rows use separate bin ranges
   BinCfg cfg_c = sym_cfg(h, 1), cfg_u = sym_cfg(h, 0);
+  if (h->opt.method == 1 && totalA > 0) {
+    const double avg = (double)fm_all / (double)totalA;
+    plain_rule(cfg_u, avg, (double)fm_all / 8.0 / (double)totalA);
+    plain_rule(cfg_c, avg, (double)fmc_all / 8.0 / (double)totalA);
+  }
   unsigned long long* d_hist = B<unsigned long long>(h, kBufHist);
   unsigned long long* h_hist = (unsigned long long*)(rd + sizeof(unsigned long long) * (4 * ni + 2 * ni));
   // one launch per compression flag keeps the device bin function simple
@@ -588,6 +627,15 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
   long long kmax = 0;
   for (int b = 0; b < count; ++b) kmax = std::max<long long>(kmax, h->inst[b].k);
   BinCfg ncfg = num_cfg(h, dtype, kmax);
+  if (h->opt.method == 1 && totalA > 0) {
+    // the plain rule sizes L1 from the average row of C: read nnz(C) first
+    unsigned long long* h_o = (unsigned long long*)(rd + sizeof(unsigned long long) * 4 * ni);
+    KKS_CU(cudaMemcpyAsync(h_o, h->buf[kBufInstOut], sizeof(unsigned long long) * 2 * ni, cudaMemcpyDeviceToHost, s));
+    KKS_CU(cudaStreamSynchronize(s));
+    long long nz = 0;
+    for (int b = 0; b < count; ++b) nz += (long long)h_o[2 * b];
+    plain_rule(ncfg, (double)fm_all / (double)totalA, (double)nz / (double)totalA);
+  }
   KKS_CU(cudaMemsetAsync(d_hist, 0, sizeof(unsigned long long) * kNumBins, s));
   KKS_CU(launch_bin_count(L, P, totalA, 1, B<long long>(h, kBufRf), nullptr, B<long long>(h, kBufRowsize), ncfg,
                           d_hist));
@@ -618,7 +666,7 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
     cls_rows[cls] += (long long)h_hist[t];
     const long long cnt = noff[t + 1] - noff[t];
     if (cnt == 0) continue;
-    h->num_bins.push_back(BinRun{cls, bin_logT(t), 0, noff[t], cnt});
+    h->num_bins.push_back(BinRun{cls, bin_logT(t), 0, noff[t], cnt, h->opt.hash_function});
     if (cls == kClsDense) dense_rows += cnt;
     if (cls == kClsSpill) {
       spill_rows += cnt;
@@ -689,7 +737,124 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
   st.ars = totalA > 0 ? (double)nnz_all / (double)totalA : 0.0;
   st.workspace_bytes = (int64_t)h->total;
   for (int c = 0; c < kNumClasses; ++c) st.bin_rows_numeric[c] = cls_rows[c];
+  h->tuned = false;
   h->ready = true;
+  return SPGEMM_OK;
+}
+
+// Launch the numeric kernel of one bin with its (possibly tuned) configuration.
+cudaError_t launch_bin(kks_handle* h, const BinRun& r, cudaStream_t s) {
+  LaunchCtx L = ctx(h, s);
+  ProbD P = prob(h);
+  P.hash_mode = r.hash;
+  NumLaunch S;
+  memset(&S, 0, sizeof(S));
+  S.cls = r.cls;
+  S.logT = r.logT;
+  S.rows = B<int>(h, kBufNumRows) + r.off;
+  S.nrows = r.count;
+  S.dtype = h->dtype;
+  S.kwords_max = h->num_kw_max;
+  S.kmax = h->num_kmax;
+  S.max_occ = h->opt.l1_max_occupancy;
+  if (r.cls == kClsDense) {
+    S.pool = h->buf[kBufNumPool];
+    S.nchunks = h->num_dense_chunks;
+    S.kwords_max = h->num_dense_kw;
+  } else if (r.cls == kClsSpill) {
+    S.pool = h->buf[kBufNumPool2];
+    S.chunk_bytes = h->num_spill_chunk_bytes;
+    S.pool2 = h->buf[kBufNumPool3];
+    S.nchunks = h->num_spill_chunks;
+    S.l1_logT = h->num_l1_logT;
+  }
+  cudaError_t e = launch_numeric(L, P, S);
+  if (e != cudaSuccess)
+    fprintf(stderr, "kkspgemm: numeric bin (class %d, log2 table %d, %lld rows, %d chunks, %lld bitmap words) failed\n",
+            r.cls, r.logT, r.count, S.nchunks, S.kwords_max);
+  return e;
+}
+
+// The autotuner: for every hash-table bin, time the kernel configurations that
+// are valid for its rows (table one size larger, the next team class up or
+// down, the other hash function) on the bin itself and keep the fastest.  Each
+// launch computes the bin's rows of C completely, so tuning runs inside the
+// first numeric call and leaves a correct C behind.
+spgemm_status_t tune_numeric(kks_handle* h, cudaStream_t s) {
+  BinCfg c = num_cfg(h, h->dtype, h->num_kmax);
+  const int cta_max = cta_max_logT_num(h, h->dtype);
+  cudaEvent_t e0, e1;
+  KKS_CU(cudaEventCreate(&e0));
+  KKS_CU(cudaEventCreate(&e1));
+  int changed = 0;
+  for (BinRun& r : h->num_bins) {
+    if (r.cls != kClsW8 && r.cls != kClsW32 && r.cls != kClsC256 && r.cls != kClsC1024) continue;
+    bool cached = false;
+    for (const auto& te : h->tune_cache) {
+      if (te.cls == r.cls && te.logT == r.logT && te.count == r.count && te.dtype == h->dtype) {
+        BinRun p = te.pick;
+        p.off = r.off;
+        p.count = r.count;
+        if (p.cls != r.cls || p.logT != r.logT || p.hash != r.hash) ++changed;
+        r = p;
+        cached = true;
+        break;
+      }
+    }
+    if (cached) continue;
+    const int cls0 = r.cls, logT0 = r.logT;
+    std::vector<BinRun> cand;
+    cand.push_back(r);
+    BinRun x = r;
+    x.hash = 1 - r.hash;
+    cand.push_back(x);
+    auto max_logT = [&](int cls) {
+      return cls == kClsW8 ? 5 : cls == kClsW32 ? 10 : cls == kClsC256 ? std::min(12, cta_max) : cta_max;
+    };
+    if (r.logT + 1 <= max_logT(r.cls)) {
+      x = r;
+      x.logT = r.logT + 1;
+      cand.push_back(x);
+    }
+    const int up = r.cls == kClsW8 ? kClsW32 : r.cls == kClsW32 ? kClsC256 : r.cls == kClsC256 ? kClsC1024 : 0;
+    if (up && r.logT <= max_logT(up)) {
+      x = r;
+      x.cls = up;
+      cand.push_back(x);
+    }
+    const int down = r.cls == kClsW32 ? kClsW8 : r.cls == kClsC256 ? kClsW32 : r.cls == kClsC1024 ? kClsC256 : 0;
+    if (down && r.logT <= max_logT(down)) {
+      x = r;
+      x.cls = down;
+      cand.push_back(x);
+    }
+    float best = 1e30f;
+    BinRun pick = r;
+    for (const BinRun& cd : cand) {
+      float t_min = 1e30f;
+      for (int rep = 0; rep < 3; ++rep) {
+        KKS_CU(cudaEventRecord(e0, s));
+        KKS_CU(launch_bin(h, cd, s));
+        KKS_CU(cudaEventRecord(e1, s));
+        KKS_CU(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        KKS_CU(cudaEventElapsedTime(&ms, e0, e1));
+        t_min = std::min(t_min, ms);
+      }
+      if (t_min < best) {
+        best = t_min;
+        pick = cd;
+      }
+    }
+    if (pick.cls != r.cls || pick.logT != r.logT || pick.hash != r.hash) ++changed;
+    r = pick;
+    h->tune_cache.push_back({cls0, logT0, h->dtype, r.count, pick});
+  }
+  (void)c;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->tuned = true;
+  h->stats.tuned_bins = changed;
   return SPGEMM_OK;
 }
 
@@ -725,32 +890,13 @@ spgemm_status_t do_numeric(kks_handle* h, int count, const spgemm_csr_t* A, cons
     if (cs != cudaStreamCaptureStatusNone) return SPGEMM_ERR_NOT_READY;
     KKS_ST(upload_inst(h, s));
   }
-  LaunchCtx L = ctx(h, s);
-  ProbD P = prob(h);
-  for (const BinRun& r : h->num_bins) {
-    NumLaunch S;
-    memset(&S, 0, sizeof(S));
-    S.cls = r.cls;
-    S.logT = r.logT;
-    S.rows = B<int>(h, kBufNumRows) + r.off;
-    S.nrows = r.count;
-    S.dtype = h->dtype;
-    S.kwords_max = h->num_kw_max;
-    S.kmax = h->num_kmax;
-    S.max_occ = h->opt.l1_max_occupancy;
-    if (r.cls == kClsDense) {
-      S.pool = h->buf[kBufNumPool];
-      S.nchunks = h->num_dense_chunks;
-      S.kwords_max = h->num_dense_kw;
-    } else if (r.cls == kClsSpill) {
-      S.pool = h->buf[kBufNumPool2];
-      S.chunk_bytes = h->num_spill_chunk_bytes;
-      S.pool2 = h->buf[kBufNumPool3];
-      S.nchunks = h->num_spill_chunks;
-      S.l1_logT = h->num_l1_logT;
-    }
-    KKS_CU(launch_numeric(L, P, S));
+  if (h->opt.tune && !h->tuned) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    KKS_CU(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return SPGEMM_ERR_NOT_READY;
+    KKS_ST(tune_numeric(h, s));
   }
+  for (const BinRun& r : h->num_bins) KKS_CU(launch_bin(h, r, s));
   return SPGEMM_OK;
 }
 

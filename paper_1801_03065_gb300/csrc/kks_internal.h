@@ -66,7 +66,12 @@ __host__ __device__ inline int choose_bin(long long u, long long work, long long
   int logT = ilog2_ceil(u) + (c.slots_log2 > 0 ? c.slots_log2 : 1);
   if (logT < c.min_logT) logT = c.min_logT;
   if (logT > 30) logT = 30;   // bin ids hold logT < kBinsPerClass; such rows fail pool sizing
-  if (c.force_cls > 0) return bin_id(c.force_cls, c.force_cls == kClsDense ? 0 : c.force_logT);
+  if (c.force_cls > 0) {
+    // one team class and table size for the whole problem (the paper's
+    // per-problem choice); rows too large for that L1 go to L1 + L2
+    if (logT <= c.force_logT) return bin_id(c.force_cls, c.force_logT);
+    return bin_id(kClsSpill, logT);
+  }
   if (c.t1_max_work > 0 && u <= kT1MaxKeys && work <= c.t1_max_work) return bin_id(kClsT1, 0);
   bool dense_fit = c.dense_ok && kwords <= c.dense_max_kwords;
   if (dense_fit && (logT > c.cta_max_logT || u * c.dense_ratio >= kk)) return bin_id(kClsDense, 0);

@@ -518,7 +518,8 @@ __global__ void k_gather(const VT* src, const long long* perm, VT* dst, long lon
 
 template <class K>
 cudaError_t set_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  // the kernels also hold up to 1 KB of static shared memory: opt in above 47 KB of dynamic
+  if (bytes + 1024 > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   return cudaSuccess;
 }
 

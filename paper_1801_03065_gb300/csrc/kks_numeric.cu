@@ -31,8 +31,13 @@ __host__ __device__ size_t num_team_bytes(int T) {
          al16(sizeof(ChunkScratch<TW, VT>)) + 16;
 }
 
+// kw_cap > 0 (CTA teams): rows whose column range has at most kw_cap 32-bit
+// words are written by rank instead of sorted: a k-bit bitmap of the row's
+// columns, one prefix count per group of 32 words, and for each entry the rank
+// = group prefix + set bits before it in its group.  This replaces a
+// block-wide bitonic sort with O(k / 32 + s) work.
 template <int TW, typename VT>
-__global__ void k_num_hash(ProbD P, const int* __restrict__ rows, long long nrows, int logT) {
+__global__ void k_num_hash(ProbD P, const int* __restrict__ rows, long long nrows, int logT, long long kw_cap) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long scan_scratch[33];
   Team<TW> tm;
@@ -40,6 +45,8 @@ __global__ void k_num_hash(ProbD P, const int* __restrict__ rows, long long nrow
   const LpHash tmask(logT, P.hash_mode);
   const int half = T / 2 > 0 ? T / 2 : 1;
   unsigned char* base = smem + (size_t)tm.id * num_team_bytes<TW, VT>(T);
+  unsigned* bm = reinterpret_cast<unsigned*>(smem + num_team_bytes<TW, VT>(T));
+  unsigned* gp = bm + ((kw_cap + 3) & ~3ll);
   VT* vals = reinterpret_cast<VT*>(base);
   int* keys = reinterpret_cast<int*>(base + al16((size_t)T * sizeof(VT)));
   unsigned long long* sortb =
@@ -78,6 +85,48 @@ __global__ void k_num_hash(ProbD P, const int* __restrict__ rows, long long nrow
       else dev_fail(P.status, kDevTableFull, 10, g);
     };
     for_each_product<TW, VT>(tm, csc, scan_scratch, I.A.cj, a0, a1, range, aval, body);
+    const long long kw = (I.k + 31) >> 5;
+    if (Team<TW>::kCta && kw_cap > 0 && kw <= kw_cap) {
+      VT* __restrict__ Cx = reinterpret_cast<VT*>(I.Cx);
+      int* __restrict__ Cj = I.Cj;
+      for (long long w = tm.lane; w < kw; w += TW) bm[w] = 0u;
+      tm.sync();
+      for (int x = tm.lane; x < T; x += TW) {
+        const int kk = keys[x];
+        if (kk != kEmpty) atomicOr(bm + (kk >> 5), 1u << (kk & 31));
+      }
+      tm.sync();
+      const long long ng = (kw + 31) >> 5;
+      long long run = 0;
+      for (long long gb = 0; gb < ng; gb += TW) {
+        const long long gi = gb + tm.lane;
+        int cg = 0;
+        if (gi < ng) {
+          const long long w1 = (gi + 1) * 32 < kw ? (gi + 1) * 32 : kw;
+          for (long long w = gi * 32; w < w1; ++w) cg += __popc(bm[w]);
+        }
+        long long tot;
+        const long long ex = team_excl_scan<TW>(tm, cg, &tot, scan_scratch);
+        if (gi < ng) gp[gi] = (unsigned)(run + ex);
+        run += tot;
+      }
+      if (tm.lane == 0 && run != s) dev_fail(P.status, kDevRowSizeMismatch, 9, g);
+      tm.sync();
+      for (int x = tm.lane; x < T; x += TW) {
+        const int kk = keys[x];
+        if (kk == kEmpty) continue;
+        const int w = kk >> 5;
+        long long rk = gp[w >> 5];
+        for (int w2 = w & ~31; w2 < w; ++w2) rk += __popc(bm[w2]);
+        rk += __popc(bm[w] & ((1u << (kk & 31)) - 1u));
+        if (rk < s) {
+          Cj[c0 + rk] = kk;
+          Cx[c0 + rk] = vals[x];
+        }
+      }
+      tm.sync();
+      continue;
+    }
     // compaction of the occupied slots into (column << 32 | slot)
     long long cnt = 0;
     for (int xb = 0; xb < T; xb += TW) {
@@ -508,7 +557,8 @@ __global__ void __launch_bounds__(TW) k_num_spill(ProbD P, const int* __restrict
 
 template <class K>
 cudaError_t set_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  // the kernels also hold up to 1 KB of static shared memory: opt in above 47 KB of dynamic
+  if (bytes + 1024 > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   return cudaSuccess;
 }
 
@@ -523,7 +573,17 @@ cudaError_t run_hash(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
     if (teams > tmax) teams = tmax;
     if (teams < 1) teams = 1;
   }
-  const size_t smem = tb * teams;
+  size_t smem = tb * teams;
+  // CTA teams: room for the rank bitmap when the plan's column ranges are small
+  long long kw_cap = 0;
+  if (TW > 32 && S.kwords_max > 0) {
+    const long long kw = S.kwords_max;
+    const size_t extra = al16((size_t)((kw + 3) & ~3ll) * 4) + al16((size_t)((kw + 31) / 32 + 1) * 4);
+    if (kw <= 16384 && smem + extra + 1024 <= (size_t)L.max_smem_optin) {
+      kw_cap = kw;
+      smem += extra;
+    }
+  }
   if (smem > (size_t)L.max_smem_optin) return cudaErrorInvalidConfiguration;
   auto kern = k_num_hash<TW, VT>;
   cudaError_t e = set_smem(kern, smem);
@@ -532,7 +592,7 @@ cudaError_t run_hash(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
   long long cap = (long long)L.num_sms * 64;
   if (grid > cap) grid = cap;
   KKS_LAUNCHED();
-  kern<<<(unsigned)grid, TW * teams, smem, L.stream>>>(P, S.rows, S.nrows, S.logT);
+  kern<<<(unsigned)grid, TW * teams, smem, L.stream>>>(P, S.rows, S.nrows, S.logT, kw_cap);
   return cudaGetLastError();
 }
 

@@ -105,7 +105,7 @@ class SpGEMM:
                  l1_max_occupancy: float = 0.5, l1_max_log2_slots: int = 0, dense: int = -1,
                  method: int = 0, workspace_limit_bytes: int = 0, pool_limit_bytes: int = 0,
                  device: int = 0, hash_function: int = 1, slots_per_key_log2: int = 0,
-                 verbose: bool = False):
+                 tune: bool = False, verbose: bool = False):
         self._lib = B.load()
         opt = B.OptionsT()
         B.check(self._lib.spgemm_options_default(C.byref(opt)), "spgemm_options_default")
@@ -120,6 +120,7 @@ class SpGEMM:
         opt.device = device
         opt.hash_function = hash_function
         opt.slots_per_key_log2 = slots_per_key_log2
+        opt.tune = 1 if tune else 0
         opt.verbose = 1 if verbose else 0
         self.device = torch.device("cuda", device)
         h = C.c_void_p()

@@ -371,3 +371,41 @@ def test_rmat18_full_sampled(ops):
     rows = np.concatenate([hubs, rng.integers(0, A.nrows, 60)])
     assert_rows_match_oracle(A, A, Cd, np.float32, rows)
     assert st["nnzC"] > 2 ** 31   # int64 row pointers
+
+
+# ------------------------------------------------------------------ plain meta-algorithm and tuner
+@pytest.mark.parametrize("seed", range(3))
+def test_plain_meta_algorithm_path(ops, seed):
+    """method=1: one team class and L1 size per problem, overflow rows through L1 + L2."""
+    rng = np.random.default_rng(seed)
+    la = np.concatenate([rng.integers(0, 5, 300), rng.integers(30, 200, 40)])
+    A = w.random_csr(340, 600, lengths=la, seed=seed, dtype=np.float64)
+    B = w.random_csr(600, 5000, 20.0, seed=seed + 9, dtype=np.float64)
+    for dtype in (np.float64, np.float32):
+        h, _, _, Cd = run(ops, A, B, dtype, method=1)
+        assert_matches_oracle(A, B, Cd, dtype)
+
+
+def test_tuned_numeric_and_reuse(ops):
+    A = w.random_csr(2000, 1500, 12.0, seed=5)
+    B = w.random_csr(1500, 30000, 12.0, seed=6)
+    h, Ad, Bd, Cd = run(ops, A, B, tune=True)
+    assert_matches_oracle(A, B, Cd, np.float64)
+    A2 = A.with_values(np.random.default_rng(1).uniform(-1, 1, A.nnz))
+    Ad.values.copy_(torch.as_tensor(A2.values))
+    h.numeric(Ad, Bd, Cd.rowptr, Cd.nnz, Cd.colidx, Cd.values)
+    h.sync()
+    assert_matches_oracle(A2, B, Cd, np.float64)
+    assert h.stats()["tuned_bins"] >= 0
+
+
+def test_batched_tuned_matches(ops):
+    pairs = w.batched_pairs(count=10, nmin=500, nmax=20000, seed=11)
+    h = ops.SpGEMM(tune=True)
+    As = [dev(a) for a, _ in pairs]
+    Bs = [dev(b) for _, b in pairs]
+    rps, nnzs = h.batch_symbolic(As, Bs)
+    Cs = h.batch_numeric(As, Bs, rps, nnzs)
+    h.sync()
+    for (a, b), Cd in zip(pairs, Cs):
+        assert_matches_oracle(a, b, Cd, np.float64)
