@@ -94,7 +94,11 @@ typedef struct {
   int32_t slots_per_key_log2;    /* hash-table slots per key bound, log2 (0 = default 1: 50 % load) */
   int32_t tune;                  /* 1: the first numeric call of a plan times candidate kernel
                                     configurations per row bin and keeps the fastest (synchronises) */
-  int32_t reserved[3];
+  int32_t numeric_positions;     /* 1 (default): when every product of a plan runs on the compressed B,
+                                    warp-team rows of the numeric phase take each product's place in
+                                    C(i,:) from the column sets (Section 3.2) instead of sorting the
+                                    accumulator; 0: always hash and sort */
+  int32_t reserved[2];
 } spgemm_options_t;
 
 /* Statistics of the last symbolic call (Section 4 results-table columns). */
@@ -115,6 +119,7 @@ typedef struct {
   double ars;             /* average row size of C */
   int64_t workspace_bytes;/* device scratch held by the handle */
   int64_t bin_rows_numeric[8]; /* rows per team class: none, w8, w32, c256, c1024, dense, spill, thread */
+  int64_t rows_positions; /* numeric rows that take their output positions from the column sets */
 } spgemm_stats_t;
 
 /* Fills *opt with the defaults.  Returns SPGEMM_ERR_INVALID_ARG for NULL. */

@@ -35,7 +35,8 @@ class OptionsT(C.Structure):
                 ("dense", C.c_int32), ("method", C.c_int32),
                 ("workspace_limit_bytes", C.c_int64), ("pool_limit_bytes", C.c_int64),
                 ("device", C.c_int32), ("hash_function", C.c_int32), ("verbose", C.c_int32),
-                ("slots_per_key_log2", C.c_int32), ("tune", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("slots_per_key_log2", C.c_int32), ("tune", C.c_int32),
+                ("numeric_positions", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class StatsT(C.Structure):
@@ -45,7 +46,8 @@ class StatsT(C.Structure):
                 ("CF", C.c_double), ("CMRF", C.c_double), ("compressed", C.c_int32),
                 ("nbins_symbolic", C.c_int32), ("nbins_numeric", C.c_int32), ("tuned_bins", C.c_int32),
                 ("nnzC", C.c_int64), ("maxrs", C.c_int64), ("ars", C.c_double),
-                ("workspace_bytes", C.c_int64), ("bin_rows_numeric", C.c_int64 * 8)]
+                ("workspace_bytes", C.c_int64), ("bin_rows_numeric", C.c_int64 * 8),
+                ("rows_positions", C.c_int64)]
 
 
 # name -> (restype, argtypes); mirrors include/kkspgemm.h

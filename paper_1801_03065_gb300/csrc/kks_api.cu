@@ -110,10 +110,11 @@ struct kks_handle {
   MaskPlan reuse;
   MaskPlan masked;   // last plan of spgemm_masked (reused while the patterns are unchanged)
   bool tuned = false;
+  bool positions_ok = false;   // every product of the plan runs on the compressed B
   // tuner results by bin (class, log2 table, rows, dtype): a new plan of the
   // same problem reuses them instead of tuning again
   struct TuneEntry {
-    int cls, logT, dtype;
+    int cls, logT, dtype, positions;
     long long count;
     BinRun pick;
   };
@@ -377,6 +378,7 @@ void set_default_options(spgemm_options_t* o) {
   o->device = 0;
   o->hash_function = 1;
   o->verbose = 0;
+  o->numeric_positions = 1;
 }
 
 // Upload the instance table through a pinned ring slot (numeric path).
@@ -408,6 +410,14 @@ spgemm_status_t upload_inst(kks_handle* h, cudaStream_t s) {
   KKS_CU(cudaMemcpyAsync(h->buf[kBufInst], h->ring[r], bytes, cudaMemcpyHostToDevice, s));
   KKS_CU(cudaEventRecord(h->ring_ev[r], s));
   return SPGEMM_OK;
+}
+
+// Numeric rows whose warp-class bin takes output positions from the column sets.
+long long rows_positions(const kks_handle* h) {
+  long long n = 0;
+  for (const BinRun& r : h->num_bins)
+    if (r.compressed && (r.cls == kClsW8 || r.cls == kClsW32)) n += r.count;
+  return n;
 }
 
 // ---------------------------------------------------------------------------
@@ -658,6 +668,8 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
                             B<unsigned long long>(h, kBufCursor), B<int>(h, kBufNumRows)));
 
   h->num_bins.clear();
+  const bool positions_ok = h->opt.numeric_positions != 0 && count > 0 && ncomp == count;
+  h->positions_ok = positions_ok;
   long long dense_rows = 0, spill_rows = 0;
   int spill_logT = 0;
   long long cls_rows[kNumClasses] = {0};
@@ -666,7 +678,10 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
     cls_rows[cls] += (long long)h_hist[t];
     const long long cnt = noff[t + 1] - noff[t];
     if (cnt == 0) continue;
-    h->num_bins.push_back(BinRun{cls, bin_logT(t), 0, noff[t], cnt, h->opt.hash_function});
+    // warp-class rows of a plan whose products all run on the compressed B
+    // take their output positions from the column sets
+    const int pos = (positions_ok && (cls == kClsW8 || cls == kClsW32)) ? 1 : 0;
+    h->num_bins.push_back(BinRun{cls, bin_logT(t), pos, noff[t], cnt, h->opt.hash_function});
     if (cls == kClsDense) dense_rows += cnt;
     if (cls == kClsSpill) {
       spill_rows += cnt;
@@ -737,6 +752,7 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
   st.ars = totalA > 0 ? (double)nnz_all / (double)totalA : 0.0;
   st.workspace_bytes = (int64_t)h->total;
   for (int c = 0; c < kNumClasses; ++c) st.bin_rows_numeric[c] = cls_rows[c];
+  st.rows_positions = rows_positions(h);
   h->tuned = false;
   h->ready = true;
   return SPGEMM_OK;
@@ -757,6 +773,7 @@ cudaError_t launch_bin(kks_handle* h, const BinRun& r, cudaStream_t s) {
   S.kwords_max = h->num_kw_max;
   S.kmax = h->num_kmax;
   S.max_occ = h->opt.l1_max_occupancy;
+  S.positions = (r.compressed && (r.cls == kClsW8 || r.cls == kClsW32)) ? 1 : 0;
   if (r.cls == kClsDense) {
     S.pool = h->buf[kBufNumPool];
     S.nchunks = h->num_dense_chunks;
@@ -791,23 +808,29 @@ spgemm_status_t tune_numeric(kks_handle* h, cudaStream_t s) {
     if (r.cls != kClsW8 && r.cls != kClsW32 && r.cls != kClsC256 && r.cls != kClsC1024) continue;
     bool cached = false;
     for (const auto& te : h->tune_cache) {
-      if (te.cls == r.cls && te.logT == r.logT && te.count == r.count && te.dtype == h->dtype) {
+      if (te.cls == r.cls && te.logT == r.logT && te.count == r.count && te.dtype == h->dtype &&
+          te.positions == r.compressed) {
         BinRun p = te.pick;
         p.off = r.off;
         p.count = r.count;
-        if (p.cls != r.cls || p.logT != r.logT || p.hash != r.hash) ++changed;
+        if (p.cls != r.cls || p.logT != r.logT || p.hash != r.hash || p.compressed != r.compressed) ++changed;
         r = p;
         cached = true;
         break;
       }
     }
     if (cached) continue;
-    const int cls0 = r.cls, logT0 = r.logT;
+    const int cls0 = r.cls, logT0 = r.logT, pos0 = r.compressed;
     std::vector<BinRun> cand;
     cand.push_back(r);
     BinRun x = r;
     x.hash = 1 - r.hash;
     cand.push_back(x);
+    if (h->positions_ok && (r.cls == kClsW8 || r.cls == kClsW32)) {
+      x = r;
+      x.compressed = 1 - r.compressed;   // column-set positions against the hash-and-sort kernel
+      cand.push_back(x);
+    }
     auto max_logT = [&](int cls) {
       return cls == kClsW8 ? 5 : cls == kClsW32 ? 10 : cls == kClsC256 ? std::min(12, cta_max) : cta_max;
     };
@@ -820,12 +843,14 @@ spgemm_status_t tune_numeric(kks_handle* h, cudaStream_t s) {
     if (up && r.logT <= max_logT(up)) {
       x = r;
       x.cls = up;
+      if (up != kClsW32) x.compressed = 0;
       cand.push_back(x);
     }
     const int down = r.cls == kClsW32 ? kClsW8 : r.cls == kClsC256 ? kClsW32 : r.cls == kClsC1024 ? kClsC256 : 0;
     if (down && r.logT <= max_logT(down)) {
       x = r;
       x.cls = down;
+      x.compressed = (h->positions_ok && (down == kClsW8 || down == kClsW32)) ? 1 : 0;
       cand.push_back(x);
     }
     float best = 1e30f;
@@ -846,15 +871,16 @@ spgemm_status_t tune_numeric(kks_handle* h, cudaStream_t s) {
         pick = cd;
       }
     }
-    if (pick.cls != r.cls || pick.logT != r.logT || pick.hash != r.hash) ++changed;
+    if (pick.cls != r.cls || pick.logT != r.logT || pick.hash != r.hash || pick.compressed != r.compressed) ++changed;
     r = pick;
-    h->tune_cache.push_back({cls0, logT0, h->dtype, r.count, pick});
+    h->tune_cache.push_back({cls0, logT0, h->dtype, pos0, r.count, pick});
   }
   (void)c;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   h->tuned = true;
   h->stats.tuned_bins = changed;
+  h->stats.rows_positions = rows_positions(h);
   return SPGEMM_OK;
 }
 
@@ -1042,7 +1068,8 @@ spgemm_status_t spgemm_handle_create(spgemm_handle_t* out, const spgemm_options_
   if (opt) h->opt = *opt; else set_default_options(&h->opt);
   if (!(h->opt.l1_max_occupancy > 0.0 && h->opt.l1_max_occupancy <= 1.0) || h->opt.compress_threshold < 0.0 ||
       h->opt.compression < -1 || h->opt.compression > 1 || h->opt.hash_function < 0 || h->opt.hash_function > 1 ||
-      h->opt.slots_per_key_log2 < 0 || h->opt.slots_per_key_log2 > 4) {
+      h->opt.slots_per_key_log2 < 0 || h->opt.slots_per_key_log2 > 4 || h->opt.numeric_positions < 0 ||
+      h->opt.numeric_positions > 1) {
     delete h;
     return SPGEMM_ERR_INVALID_ARG;
   }

@@ -277,6 +277,127 @@ __device__ __forceinline__ int lp_find(const int* keys, const LpHash& hs, int ke
   return -1;
 }
 
+// --------------------------------------------------------------------------
+// Union of keys over one chunk of A(i,:) for warp teams (Algorithm 3's insert
+// loop).  Lane t holds the range [qs, qs + ql) of keys of the B row of its
+// entry of the chunk.  Every key goes into an LP table whose slots are STRIDE
+// words with the key first; with BITS the key's 32-bit column set (Section
+// 3.2) is ORed into the slot's second word.  Products are spread flat over the
+// lanes, and the loads of kUnionPasses passes are issued before their inserts
+// so that their latencies overlap.  pre holds TW + 1 ints, qsv TW offsets.
+// Returns the number of slots this lane claimed.
+// --------------------------------------------------------------------------
+constexpr int kUnionPasses = 4;
+
+template <int STRIDE>
+__device__ __forceinline__ int slot_insert(int* words, const LpHash& hs, int key, int* fresh) {
+  unsigned h = hs(key);
+  for (unsigned probe = 0; probe <= hs.mask; ++probe) {
+    const int cur = *((volatile int*)(words + STRIDE * h));
+    if (cur == key) return (int)h;
+    if (cur == kEmpty) {
+      const int old = atomicCAS(words + STRIDE * h, kEmpty, key);
+      if (old == kEmpty) {
+        ++*fresh;
+        return (int)h;
+      }
+      if (old == key) return (int)h;
+    }
+    h = (h + 1) & hs.mask;
+  }
+  return -2;
+}
+
+template <int TW, int STRIDE, bool BITS>
+__device__ __forceinline__ int union_chunk(unsigned team_mask, int lane, int* pre, long long* qsv, long long qs,
+                                           int ql, const int* __restrict__ ksrc, const unsigned* __restrict__ bsrc,
+                                           int* words, const LpHash& hs, DevStatus* status, int code, long long g) {
+  int ex = ql;
+#pragma unroll
+  for (int d = 1; d < TW; d <<= 1) {
+    const int y = __shfl_up_sync(team_mask, ex, d, TW);
+    if (lane >= d) ex += y;
+  }
+  const int tot = __shfl_sync(team_mask, ex, TW - 1, TW);
+  pre[lane] = ex - ql;
+  qsv[lane] = qs;
+  if (lane == 0) pre[TW] = tot;
+  __syncwarp(team_mask);
+  int fresh = 0;
+  int t = 0;
+  for (int xb = 0; xb < tot; xb += kUnionPasses * TW) {
+    int key[kUnionPasses];
+    unsigned m[kUnionPasses];
+#pragma unroll
+    for (int u = 0; u < kUnionPasses; ++u) {
+      const int x = xb + u * TW + lane;
+      key[u] = -1;
+      m[u] = 0u;
+      if (x < tot) {
+        while (pre[t + 1] <= x) ++t;
+        const long long q = qsv[t] + (x - pre[t]);
+        key[u] = ksrc[q];
+        if (BITS) m[u] = bsrc[q];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kUnionPasses; ++u) {
+      if (key[u] >= 0) {
+        const int slot = slot_insert<STRIDE>(words, hs, key[u], &fresh);
+        if (slot >= 0) {
+          if (BITS) atomicOr(reinterpret_cast<unsigned*>(words + STRIDE * slot + 1), m[u]);
+        } else {
+          dev_fail(status, kDevTableFull, code, g);
+        }
+      }
+    }
+  }
+  __syncwarp(team_mask);
+  return fresh;
+}
+
+// Ascending bitonic sort of one 32-bit key per lane of a team of TW lanes
+// (register exchanges only).
+template <int TW>
+__device__ __forceinline__ unsigned team_sort1(unsigned team_mask, int lane, unsigned v) {
+#pragma unroll
+  for (int k = 2; k <= TW; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const unsigned o = __shfl_xor_sync(team_mask, v, j, TW);
+      const bool up = (lane & k) == 0;
+      const bool lower = (lane & j) == 0;
+      v = (lower == up) ? min(v, o) : max(v, o);
+    }
+  }
+  return v;
+}
+
+// Ascending bitonic sort of 2 * TW keys, two per lane: v0 is element lane,
+// v1 element lane + TW.
+template <int TW>
+__device__ __forceinline__ void team_sort2(unsigned team_mask, int lane, unsigned& v0, unsigned& v1) {
+#pragma unroll
+  for (int k = 2; k <= 2 * TW; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j == TW) {
+        const unsigned lo = min(v0, v1), hi = max(v0, v1);
+        v0 = lo;
+        v1 = hi;
+      } else {
+        const unsigned o0 = __shfl_xor_sync(team_mask, v0, j, TW);
+        const unsigned o1 = __shfl_xor_sync(team_mask, v1, j, TW);
+        const bool lower = (lane & j) == 0;
+        const bool up0 = (lane & k) == 0;
+        const bool up1 = ((lane + TW) & k) == 0;
+        v0 = (lower == up0) ? min(v0, o0) : max(v0, o0);
+        v1 = (lower == up1) ? min(v1, o1) : max(v1, o1);
+      }
+    }
+  }
+}
+
 template <int TW, typename T>
 __device__ __forceinline__ void team_fill_n(const Team<TW>& tm, T* p, long long n, T v) {
   for (long long x = tm.lane; x < n; x += TW) p[x] = v;

@@ -142,6 +142,7 @@ struct NumLaunch {
   void* pool2;           // spill: bitmap + prefix words
   long long chunk2_words;
   int nchunks;
+  int positions;         // warp classes: compressed-position kernel (every product's B compressed)
 };
 cudaError_t launch_numeric(const LaunchCtx&, const ProbD&, const NumLaunch&);
 

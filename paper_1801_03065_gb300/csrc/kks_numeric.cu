@@ -346,6 +346,322 @@ __global__ void __launch_bounds__(256, 3) k_num_warp(ProbD P, const int* __restr
   }
 }
 
+// ---------------------------------------------------------------------------
+// Compressed-position numeric (warp teams, products whose B was compressed).
+// The compressed B of the symbolic phase (Section 3.2) fixes each row's
+// sorted column list, so every product's output position can be computed
+// instead of sorting the accumulator afterwards:
+//   1. OR the column sets of the compressed B rows over A(i,:) into a table
+//      keyed by column-set index (the symbolic insert, CF times fewer keys)
+//   2. sort the column-set indices, give each the count of set bits before it
+//      (its base) and write C(i,:)'s columns from the sets
+//   3. each product goes to base(col >> 5) + popcount of the lower bits of
+//      its set: one fused multiply-add into a row-local array (positions are
+//      distinct within a pass, as in k_num_warp)
+//   4. the row's values are written in order
+// A table slot holds (column-set index, set bits, base) in 16 bytes, so the
+// lookup of step 3 is one shared-memory load per probe.
+// ---------------------------------------------------------------------------
+template <int TW, typename VT>
+__host__ __device__ size_t cpn_team_bytes(int T) {
+  const int half = T / 2 > 0 ? T / 2 : 1;
+  return al16((size_t)T * 16) + al16((size_t)half * 8) + al16(sizeof(ChunkScratch<TW, VT>)) +
+         al16((size_t)TW * sizeof(VT));
+}
+
+// The slot index of a column-set index once the table is complete (-1: absent).
+__device__ __forceinline__ int cpn_slot(const int4* tab, const LpHash& hs, int key) {
+  unsigned h = hs(key);
+  for (unsigned probe = 0; probe <= hs.mask; ++probe) {
+    const int k = tab[h].x;
+    if (k == key) return (int)h;
+    if (k == kEmpty) return -1;
+    h = (h + 1) & hs.mask;
+  }
+  return -1;
+}
+
+// The slot of a column-set index once the table is complete (x = kEmpty: absent).
+__device__ __forceinline__ int4 cpn_find(const int4* tab, const LpHash& hs, int key) {
+  unsigned h = hs(key);
+  for (unsigned probe = 0; probe <= hs.mask; ++probe) {
+    const int4 e = tab[h];
+    if (e.x == key || e.x == kEmpty) return e;
+    h = (h + 1) & hs.mask;
+  }
+  return make_int4(kEmpty, 0, 0, 0);
+}
+
+template <int TW, typename VT>
+__global__ void __launch_bounds__(256, 4) k_num_cpn(ProbD P, const int* __restrict__ rows, long long nrows, int logT) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Team<TW> tm;
+  const int T = 1 << logT;
+  const LpHash hs(logT, P.hash_mode);
+  const int half = T / 2 > 0 ? T / 2 : 1;
+  unsigned char* base_p = smem + (size_t)tm.id * cpn_team_bytes<TW, VT>(T);
+  int4* tab = reinterpret_cast<int4*>(base_p);
+  // step 2 sorts (set << 32 | slot) and stages C's columns here; steps 3-4 accumulate here
+  unsigned long long* sortb = reinterpret_cast<unsigned long long*>(base_p + al16((size_t)T * 16));
+  int* colst = reinterpret_cast<int*>(sortb);
+  VT* outv = reinterpret_cast<VT*>(sortb);
+  ChunkScratch<TW, VT>* csc =
+      reinterpret_cast<ChunkScratch<TW, VT>*>(base_p + al16((size_t)T * 16) + al16((size_t)half * 8));
+  VT* xchg = reinterpret_cast<VT*>(reinterpret_cast<unsigned char*>(csc) + al16(sizeof(ChunkScratch<TW, VT>)));
+  const unsigned lane_lt = (1u << tm.lane) - 1u;
+  const int lane_base = (threadIdx.x & 31) & ~(TW - 1);
+  const unsigned tbits = (TW == 32) ? 0xffffffffu : ((1u << TW) - 1u);
+
+  const long long team = (long long)blockIdx.x * tm.per_cta + tm.id;
+  const long long nteams = (long long)gridDim.x * tm.per_cta;
+  for (long long r = team; r < nrows; r += nteams) {
+    const long long g = rows[r];
+    const int b = inst_of(P.arow0s, P.ninst, g);
+    const InstD& I = P.inst[b];
+    const long long i = g - I.arow0;
+    const long long c0 = I.Crp[i];
+    const int s = (int)(I.Crp[i + 1] - c0);
+    for (int x = tm.lane; x < T; x += TW) tab[x] = make_int4(kEmpty, 0, 0, 0);
+    __syncwarp(tm.mask);
+    const long long a0 = rp_at(I.A, i), a1 = rp_at(I.A, i + 1);
+    const VT* __restrict__ Ax = reinterpret_cast<const VT*>(I.A.vx);
+    const VT* __restrict__ Bx = reinterpret_cast<const VT*>(I.B.vx);
+    const int* __restrict__ Bj = I.B.cj;
+    const int* __restrict__ Aj = I.A.cj;
+    const long long brow0 = I.brow0;
+    // the operands of one chunk of A(i,:): B row range, compressed B row range, a_ij
+    long long bs = 0, cbs = 0;
+    int len = 0, clen = 0;
+    VT av = VT(0);
+    auto load_chunk = [&](long long c) {
+      const long long p = c + tm.lane;
+      bs = 0;
+      cbs = 0;
+      len = 0;
+      clen = 0;
+      av = VT(0);
+      if (p < a1) {
+        const int j = Aj[p];
+        av = Ax[p];
+        bs = rp_at(I.B, j);
+        len = (int)(rp_at(I.B, j + 1) - bs);
+        cbs = P.Bcp[brow0 + j];
+        clen = (int)(P.Bcp[brow0 + j + 1] - cbs);
+      }
+    };
+    const bool one_chunk = a1 - a0 <= TW;
+    // 1. union of the compressed B rows
+    int* upre = reinterpret_cast<int*>(csc);
+    long long* uqs = reinterpret_cast<long long*>(reinterpret_cast<unsigned char*>(csc) + al16((size_t)(TW + 1) * 4));
+    for (long long c = a0; c < a1; c += TW) {
+      load_chunk(c);
+      union_chunk<TW, 4, true>(tm.mask, tm.lane, upre, uqs, cbs, clen, P.csi, P.cs, reinterpret_cast<int*>(tab), hs,
+                               P.status, 25, g);
+    }
+    // 2. sorted column sets, their bases, and C(i,:)'s columns
+    int cnt = 0;
+    for (int xb = 0; xb < T; xb += TW) {
+      const int x = xb + tm.lane;
+      const bool o = x < T && tab[x].x != kEmpty;
+      const unsigned bal = (__ballot_sync(tm.mask, o) >> lane_base) & tbits;
+      const int pos = cnt + __popc(bal & lane_lt);
+      if (o && pos < half) sortb[pos] = ((unsigned long long)(unsigned)tab[x].x << 32) | (unsigned)x;
+      cnt += __popc(bal);
+    }
+    const int n = cnt < half ? cnt : half;
+    const int sw = s < half ? s : half;
+    __syncwarp(tm.mask);
+    int run = 0;
+    if (n <= 2 * TW) {
+      // up to two sets per lane: sorted in registers, slots found again by key
+      unsigned v0 = tm.lane < n ? (unsigned)(sortb[tm.lane] >> 32) : 0xffffffffu;
+      unsigned v1 = tm.lane + TW < n ? (unsigned)(sortb[tm.lane + TW] >> 32) : 0xffffffffu;
+      if (n <= TW) v0 = team_sort1<TW>(tm.mask, tm.lane, v0);
+      else team_sort2<TW>(tm.mask, tm.lane, v0, v1);
+      int sl[2] = {-1, -1}, bs2[2] = {0, 0};
+      unsigned mk[2] = {0u, 0u};
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const unsigned v = h ? v1 : v0;
+        if (v != 0xffffffffu) {
+          sl[h] = cpn_slot(tab, hs, (int)v);
+          if (sl[h] >= 0) mk[h] = (unsigned)tab[sl[h]].y;
+        }
+        const int c = __popc(mk[h]);
+        int incl = c;
+#pragma unroll
+        for (int d = 1; d < TW; d <<= 1) {
+          const int y = __shfl_up_sync(tm.mask, incl, d, TW);
+          if (tm.lane >= d) incl += y;
+        }
+        bs2[h] = run + incl - c;
+        if (sl[h] >= 0) tab[sl[h]].z = bs2[h];
+        run += __shfl_sync(tm.mask, incl, TW - 1, TW);
+      }
+      __syncwarp(tm.mask);
+      // columns staged in shared memory (over the compaction list, now read)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        unsigned m = mk[h];
+        int o = bs2[h];
+        const int key = (int)(h ? v1 : v0);
+        while (m) {
+          const int bit = __ffs(m) - 1;
+          m &= m - 1u;
+          if (o < sw) colst[o] = key * 32 + bit;
+          ++o;
+        }
+      }
+    } else {
+      int N = 1;
+      while (N < n) N <<= 1;
+      for (int x = n + tm.lane; x < N; x += TW) sortb[x] = ~0ull;
+      __syncwarp(tm.mask);
+      team_bitonic<TW>(tm, sortb, N);
+      for (int xb = 0; xb < n; xb += TW) {
+        const int x = xb + tm.lane;
+        int c = 0, slot = 0;
+        if (x < n) {
+          slot = (int)(sortb[x] & 0xffffffffull);
+          c = __popc((unsigned)tab[slot].y);
+        }
+        int incl = c;
+#pragma unroll
+        for (int d = 1; d < TW; d <<= 1) {
+          const int y = __shfl_up_sync(tm.mask, incl, d, TW);
+          if (tm.lane >= d) incl += y;
+        }
+        if (x < n) tab[slot].z = run + incl - c;
+        run += __shfl_sync(tm.mask, incl, TW - 1, TW);
+      }
+      __syncwarp(tm.mask);
+      // columns staged in shared memory from the table
+      for (int x = tm.lane; x < T; x += TW) {
+        const int4 e = tab[x];
+        if (e.x != kEmpty) {
+          unsigned m = (unsigned)e.y;
+          int o = e.z;
+          while (m) {
+            const int bit = __ffs(m) - 1;
+            m &= m - 1u;
+            if (o < sw) colst[o] = e.x * 32 + bit;
+            ++o;
+          }
+        }
+      }
+    }
+    if (tm.lane == 0 && run != s) dev_fail(P.status, kDevRowSizeMismatch, 26, g);
+    __syncwarp(tm.mask);
+    int* __restrict__ Cj = I.Cj;
+    for (int x = tm.lane; x < sw; x += TW) Cj[c0 + x] = colst[x];
+    __syncwarp(tm.mask);
+    for (int x = tm.lane; x < half; x += TW) outv[x] = VT(0);
+    __syncwarp(tm.mask);
+    // 3. products to their positions
+    auto pos_of = [&](int col) -> int {
+      const int4 e = cpn_find(tab, hs, col >> 5);
+      if (e.x == kEmpty) return -1;
+      return e.z + __popc((unsigned)e.y & ((1u << (col & 31)) - 1u));
+    };
+    for (long long c = a0; c < a1; c += TW) {
+      if (!one_chunk) load_chunk(c);
+      const int nc = (a1 - c) < TW ? (int)(a1 - c) : TW;
+      int tot = len;
+#pragma unroll
+      for (int d = TW / 2; d > 0; d >>= 1) tot += __shfl_xor_sync(tm.mask, tot, d, TW);
+      if (2 * tot >= nc * TW) {
+        // sequential: one B row per pass, distinct positions inside a pass
+        constexpr int kU = 4;
+        for (int t0 = 0; t0 < nc; t0 += kU) {
+          int q[kU], lent[kU];
+          long long bst[kU];
+          VT at[kU], bv[kU];
+#pragma unroll
+          for (int u = 0; u < kU; ++u) {
+            const int t = (t0 + u < nc) ? t0 + u : nc - 1;
+            bst[u] = __shfl_sync(tm.mask, bs, t, TW);
+            const int l = __shfl_sync(tm.mask, len, t, TW);
+            at[u] = __shfl_sync(tm.mask, av, t, TW);
+            lent[u] = (t0 + u < nc) ? l : 0;
+            q[u] = -1;
+            bv[u] = VT(0);
+            if (tm.lane < lent[u]) {
+              q[u] = Bj[bst[u] + tm.lane];
+              bv[u] = Bx[bst[u] + tm.lane];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < kU; ++u) {
+            if (q[u] >= 0) {
+              const int o = pos_of(q[u]);
+              if (o >= 0 && o < half) outv[o] = fma_acc(at[u], bv[u], outv[o]);
+              else dev_fail(P.status, kDevTableFull, 27, g);
+            }
+            for (int x = tm.lane + TW; x < lent[u]; x += TW) {
+              const int o = pos_of(Bj[bst[u] + x]);
+              if (o >= 0 && o < half) outv[o] = fma_acc(at[u], Bx[bst[u] + x], outv[o]);
+              else dev_fail(P.status, kDevTableFull, 27, g);
+            }
+            __syncwarp(tm.mask);
+          }
+        }
+      } else {
+        // flat: the chunk's products over the lanes, equal positions pre-summed
+        int ex = len;
+#pragma unroll
+        for (int d = 1; d < TW; d <<= 1) {
+          const int y = __shfl_up_sync(tm.mask, ex, d, TW);
+          if (tm.lane >= d) ex += y;
+        }
+        ex -= len;
+        csc->pre[tm.lane] = ex;
+        csc->bs[tm.lane] = bs;
+        csc->av[tm.lane] = av;
+        if (tm.lane == 0) csc->pre[TW] = tot;
+        __syncwarp(tm.mask);
+        int t = 0;
+        for (int xb = 0; xb < tot; xb += TW) {
+          const int x = xb + tm.lane;
+          int o = -1 - tm.lane;
+          VT v = VT(0);
+          if (x < tot) {
+            while (csc->pre[t + 1] <= x) ++t;
+            const long long qq = csc->bs[t] + (x - csc->pre[t]);
+            o = pos_of(Bj[qq]);
+            v = csc->av[t] * Bx[qq];
+            if (o < 0 || o >= half) {
+              dev_fail(P.status, kDevTableFull, 28, g);
+              o = -1 - tm.lane;
+            }
+          }
+          const unsigned grp = (__match_any_sync(tm.mask, o) >> lane_base) & tbits;
+          const bool leader = (grp & lane_lt) == 0;
+          if (__any_sync(tm.mask, __popc(grp) > 1)) {
+            xchg[tm.lane] = v;
+            __syncwarp(tm.mask);
+            if (leader) {
+              unsigned rest = grp & ~(1u << tm.lane);
+              while (rest) {
+                const int oo = __ffs(rest) - 1;
+                rest &= rest - 1u;
+                v += xchg[oo];
+              }
+            }
+            __syncwarp(tm.mask);
+          }
+          if (o >= 0 && leader) outv[o] += v;
+          __syncwarp(tm.mask);
+        }
+        __syncwarp(tm.mask);
+      }
+    }
+    // 4. values in order
+    VT* __restrict__ Cx = reinterpret_cast<VT*>(I.Cx);
+    for (int x = tm.lane; x < sw; x += TW) Cx[c0 + x] = outv[x];
+    __syncwarp(tm.mask);
+  }
+}
+
 template <int TW, typename VT>
 __global__ void __launch_bounds__(TW) k_num_dense(ProbD P, const int* __restrict__ rows, long long nrows,
                                                   long long kw_max, VT* pool, long long kmax) {
@@ -617,6 +933,27 @@ cudaError_t run_warp(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
   return cudaGetLastError();
 }
 
+template <int TW, typename VT>
+cudaError_t run_cpn(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
+  const int T = 1 << S.logT;
+  const size_t tb = cpn_team_bytes<TW, VT>(T);
+  int teams = (int)((48 * 1024) / tb);
+  const int tmax = 256 / TW;
+  if (teams > tmax) teams = tmax;
+  if (teams < 1) teams = 1;
+  const size_t smem = tb * teams;
+  if (smem > (size_t)L.max_smem_optin) return cudaErrorInvalidConfiguration;
+  auto kern = k_num_cpn<TW, VT>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  long long grid = (S.nrows + teams - 1) / teams;
+  const long long cap = (long long)L.num_sms * 64;
+  if (grid > cap) grid = cap;
+  KKS_LAUNCHED();
+  kern<<<(unsigned)grid, TW * teams, smem, L.stream>>>(P, S.rows, S.nrows, S.logT);
+  return cudaGetLastError();
+}
+
 template <typename VT>
 cudaError_t run_dense(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
   constexpr int TW = 1024;
@@ -656,8 +993,8 @@ cudaError_t run_spill(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
 template <typename VT>
 cudaError_t dispatch(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
   switch (S.cls) {
-    case kClsW8: return run_warp<8, VT>(L, P, S);
-    case kClsW32: return run_warp<32, VT>(L, P, S);
+    case kClsW8: return S.positions ? run_cpn<8, VT>(L, P, S) : run_warp<8, VT>(L, P, S);
+    case kClsW32: return S.positions ? run_cpn<32, VT>(L, P, S) : run_warp<32, VT>(L, P, S);
     case kClsC256: return run_hash<256, VT>(L, P, S);
     case kClsC1024: return run_hash<1024, VT>(L, P, S);
     case kClsDense: return run_dense<VT>(L, P, S);

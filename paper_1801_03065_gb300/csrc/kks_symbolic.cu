@@ -6,7 +6,9 @@
 // On the compressed B (Section 3.2) the keys are column-set indices and the
 // accumulator ORs the 32-bit column sets, so the row size is the number of
 // set bits of the union.  Variants:
-//   k_sym_hash<TW, COMP, false> : shared LP table sized to hold the row
+//   k_sym_warp<TW, COMP>        : warp teams (8 or 32 lanes), shared LP table
+//                                 sized to hold the row, batched loads
+//   k_sym_hash<TW, COMP, false> : CTA teams, shared LP table sized to hold the row
 //   k_sym_hash<TW, COMP, true>  : shared L1 table with the maximum-occupancy
 //                                 cut-off plus a global L2 table (Algorithm 3
 //                                 lines 7-11); a key may sit in both levels,
@@ -123,6 +125,75 @@ __global__ void k_sym_hash(ProbD P, const int* __restrict__ rows, long long nrow
   }
 }
 
+// Warp teams (W8, W32 rows): slots of one key (or key + column-set word), the
+// union of union_chunk with the loads of several passes in flight; the row
+// size is the number of claimed slots, or the set bits of the union.
+template <int TW, bool COMP>
+__host__ __device__ size_t symw_team_bytes(int T) {
+  return al16((size_t)T * 4 * (COMP ? 2 : 1)) + al16((size_t)(TW + 1) * 4) + al16((size_t)TW * 8);
+}
+
+template <int TW, bool COMP>
+__global__ void __launch_bounds__(256, 4) k_sym_warp(ProbD P, const int* __restrict__ rows, long long nrows,
+                                                     int logT, long long* __restrict__ rowsize) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Team<TW> tm;
+  constexpr int S = COMP ? 2 : 1;
+  const int T = 1 << logT;
+  const LpHash hs(logT, P.hash_mode);
+  unsigned char* base = smem + (size_t)tm.id * symw_team_bytes<TW, COMP>(T);
+  int* words = reinterpret_cast<int*>(base);
+  int* pre = reinterpret_cast<int*>(base + al16((size_t)T * 4 * S));
+  long long* qsv = reinterpret_cast<long long*>(base + al16((size_t)T * 4 * S) + al16((size_t)(TW + 1) * 4));
+  const long long team = (long long)blockIdx.x * tm.per_cta + tm.id;
+  const long long nteams = (long long)gridDim.x * tm.per_cta;
+  for (long long r = team; r < nrows; r += nteams) {
+    const long long g = rows[r];
+    const int b = inst_of(P.arow0s, P.ninst, g);
+    const InstD& I = P.inst[b];
+    const long long i = g - I.arow0;
+    for (int x = tm.lane; x < T; x += TW) {
+      if (COMP) reinterpret_cast<int2*>(words)[x] = make_int2(kEmpty, 0);
+      else words[x] = kEmpty;
+    }
+    __syncwarp(tm.mask);
+    const long long a0 = rp_at(I.A, i), a1 = rp_at(I.A, i + 1);
+    const long long brow0 = I.brow0;
+    const int* __restrict__ Aj = I.A.cj;
+    int fresh = 0;
+    for (long long c = a0; c < a1; c += TW) {
+      const long long p = c + tm.lane;
+      long long qs = 0;
+      int ql = 0;
+      if (p < a1) {
+        const int j = Aj[p];
+        if (COMP) {
+          qs = P.Bcp[brow0 + j];
+          ql = (int)(P.Bcp[brow0 + j + 1] - qs);
+        } else {
+          qs = rp_at(I.B, j);
+          ql = (int)(rp_at(I.B, j + 1) - qs);
+        }
+      }
+      fresh += union_chunk<TW, S, COMP>(tm.mask, tm.lane, pre, qsv, qs, ql, COMP ? P.csi : I.B.cj, P.cs, words,
+                                        hs, P.status, 1, g);
+    }
+    long long cnt = 0;
+    if (COMP) {
+      for (int x = tm.lane; x < T; x += TW) {
+        const int2 e = reinterpret_cast<const int2*>(words)[x];
+        if (e.x != kEmpty) cnt += __popc((unsigned)e.y);
+      }
+    } else {
+      cnt = fresh;
+    }
+#pragma unroll
+    for (int d = TW / 2; d > 0; d >>= 1) cnt += __shfl_xor_sync(tm.mask, cnt, d, TW);
+    if (tm.lane == 0) rowsize[g] = cnt;
+    __syncwarp(tm.mask);
+  }
+}
+
 template <int TW, bool COMP>
 __global__ void __launch_bounds__(TW) k_sym_dense(ProbD P, const int* __restrict__ rows, long long nrows,
                                                   long long kw_max, long long* __restrict__ rowsize) {
@@ -213,6 +284,24 @@ cudaError_t run_hash(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, lon
   return cudaGetLastError();
 }
 
+template <int TW, bool COMP>
+cudaError_t run_warp(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, long long* rowsize) {
+  const int T = 1 << S.logT;
+  const size_t tb = symw_team_bytes<TW, COMP>(T);
+  int teams = (int)((48 * 1024) / tb);
+  const int tmax = 256 / TW;
+  if (teams > tmax) teams = tmax;
+  if (teams < 1) teams = 1;
+  const size_t smem = tb * teams;
+  if (smem > (size_t)L.max_smem_optin) return cudaErrorInvalidConfiguration;
+  auto kern = k_sym_warp<TW, COMP>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  KKS_LAUNCHED();
+  kern<<<hash_grid(S.nrows, teams, L.num_sms), TW * teams, smem, L.stream>>>(P, S.rows, S.nrows, S.logT, rowsize);
+  return cudaGetLastError();
+}
+
 template <bool COMP>
 cudaError_t run_spill(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, long long* rowsize) {
   constexpr int TW = 1024;
@@ -254,8 +343,8 @@ cudaError_t run_dense(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, lo
 template <bool COMP>
 cudaError_t dispatch(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, long long* rowsize) {
   switch (S.cls) {
-    case kClsW8: return run_hash<8, COMP>(L, P, S, rowsize);
-    case kClsW32: return run_hash<32, COMP>(L, P, S, rowsize);
+    case kClsW8: return run_warp<8, COMP>(L, P, S, rowsize);
+    case kClsW32: return run_warp<32, COMP>(L, P, S, rowsize);
     case kClsC256: return run_hash<256, COMP>(L, P, S, rowsize);
     case kClsC1024: return run_hash<1024, COMP>(L, P, S, rowsize);
     case kClsDense: return run_dense<COMP>(L, P, S, rowsize);

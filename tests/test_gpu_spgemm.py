@@ -409,3 +409,79 @@ def test_batched_tuned_matches(ops):
     h.sync()
     for (a, b), Cd in zip(pairs, Cs):
         assert_matches_oracle(a, b, Cd, np.float64)
+
+
+# ------------------------------------------------------------------ compressed-position numeric
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_positions_against_hash_and_sort(ops, dtype):
+    """Warp rows of compressed products take positions from the column sets; the
+    hash-and-sort kernel (numeric_positions=False) and the oracle agree."""
+    cases = [(w.stencil3d_27pt(14, seed=1),) * 2, (w.laplace2d_5pt(40),) * 2,
+             (w.random_csr(300, 200, 9.0, seed=4), w.random_csr(200, 900, 15.0, seed=5))]
+    for A, B in cases:
+        ref = None
+        for pos in (True, False):
+            h, _, _, Cd = run(ops, A, B, dtype, compression=1, numeric_positions=pos)
+            st = h.stats()
+            if pos:
+                assert st["rows_positions"] > 0
+                assert st["rows_positions"] == st["bin_rows_numeric"][1] + st["bin_rows_numeric"][2]
+            else:
+                assert st["rows_positions"] == 0
+            ref = assert_matches_oracle(A, B, Cd, dtype, ref)
+
+
+def test_positions_straddling_and_colliding_sets(ops):
+    rows = np.repeat(np.arange(50), 5)
+    cols = np.tile(np.arange(30, 35), 50)
+    B1 = csr_from_coo(50, 70, rows, cols, np.linspace(-1, 1, 250))
+    A1 = w.random_csr(80, 50, 6.0, seed=9)
+    nb, per = 64, 10
+    k = 32 * 1024 * 16
+    rows = np.repeat(np.arange(nb), per)
+    # column-set indices that are multiples of 1024: with key & (size - 1) every set key collides
+    rng = np.random.default_rng(1)
+    sets = rng.integers(0, 16, nb * per) * 1024
+    cols = sets * 32 + rng.integers(0, 32, sets.size)
+    keep = np.ones(cols.size, bool)
+    for r in range(nb):   # no duplicate (row, column)
+        seg = slice(r * per, (r + 1) * per)
+        _, first = np.unique(cols[seg], return_index=True)
+        m = np.zeros(per, bool)
+        m[first] = True
+        keep[seg] = m
+    B2 = csr_from_coo(nb, k, rows[keep], cols[keep], np.random.default_rng(2).uniform(-1, 1, keep.sum()))
+    A2 = w.random_csr(100, nb, 8.0, seed=3)
+    for A, B in ((A1, B1), (A2, B2)):
+        for hf in (0, 1):
+            h, _, _, Cd = run(ops, A, B, compression=1, hash_function=hf)
+            assert h.stats()["rows_positions"] > 0
+            assert_matches_oracle(A, B, Cd, np.float64)
+
+
+def test_positions_batched_all_or_none(ops):
+    """A plan takes positions only when every product is compressed."""
+    pairs = w.batched_pairs(count=6, nmin=500, nmax=6000, seed=11)
+    for comp, expect in ((1, True), (0, False)):
+        h = ops.SpGEMM(compression=comp)
+        As = [dev(a) for a, _ in pairs]
+        Bs = [dev(b) for _, b in pairs]
+        rps, nnzs = h.batch_symbolic(As, Bs)
+        Cs = h.batch_numeric(As, Bs, rps, nnzs)
+        h.sync()
+        assert (h.stats()["rows_positions"] > 0) == expect
+        for (a, b), Cd in zip(pairs, Cs):
+            assert_matches_oracle(a, b, Cd, np.float64)
+
+
+def test_positions_tuned_and_repeated(ops):
+    A = w.stencil3d_27pt(20, seed=2)
+    h, Ad, Bd, Cd = run(ops, A, A, compression=1, tune=True)
+    assert_matches_oracle(A, A, Cd, np.float64)
+    A2 = A.with_values(np.random.default_rng(5).uniform(-1, 1, A.nnz))
+    Ad.values.copy_(torch.as_tensor(A2.values))
+    Bd.values.copy_(torch.as_tensor(A2.values))
+    for _ in range(2):
+        h.numeric(Ad, Bd, Cd.rowptr, Cd.nnz, Cd.colidx, Cd.values)
+        h.sync()
+        assert_matches_oracle(A2, A2, Cd, np.float64)
