@@ -97,7 +97,9 @@ typedef struct {
   int32_t numeric_positions;     /* 1 (default): when every product of a plan runs on the compressed B,
                                     warp-team rows of the numeric phase take each product's place in
                                     C(i,:) from the column sets (Section 3.2) instead of sorting the
-                                    accumulator; 0: always hash and sort */
+                                    accumulator; masked products and numeric reuse whose pattern rows
+                                    are all sorted key their warp-team tables by the pattern's column
+                                    sets.  0: hash-and-sort numeric, column-keyed masked tables */
   int32_t reserved[2];
 } spgemm_options_t;
 

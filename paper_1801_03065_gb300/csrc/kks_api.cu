@@ -56,6 +56,7 @@ struct MaskPlan {
   std::vector<long long> off, cnt;
   int gchunks = 0;
   long long gslots = 0;
+  bool sorted = false;   // every row of S strictly increasing: warp rows use column-set places
 };
 
 struct PatternId {
@@ -965,9 +966,9 @@ MaskedD maskd(kks_handle* h, const spgemm_csr_t* X, const spgemm_csr_t* Y, const
 spgemm_status_t plan_masked(kks_handle* h, const MaskedD& M, long long nrows, int dtype, int rows_buf, int pool_buf,
                             MaskPlan* plan, cudaStream_t s) {
   KKS_ST(ensure(h, kBufStatus, sizeof(DevStatus)));
-  KKS_ST(ensure(h, kBufMaskHist, sizeof(unsigned long long) * 2 * kNumBins));
+  KKS_ST(ensure(h, kBufMaskHist, sizeof(unsigned long long) * (2 * kNumBins + 2)));
   KKS_ST(ensure(h, rows_buf, sizeof(int) * (nrows + 1)));
-  KKS_ST(ensure_pinned(h, sizeof(unsigned long long) * 2 * kNumBins + sizeof(DevStatus)));
+  KKS_ST(ensure_pinned(h, sizeof(unsigned long long) * (2 * kNumBins + 2) + sizeof(DevStatus)));
   MaskedD Mx = M;
   Mx.status = B<DevStatus>(h, kBufStatus);
   BinCfg c = base_cfg(h);
@@ -978,13 +979,19 @@ spgemm_status_t plan_masked(kks_handle* h, const MaskedD& M, long long nrows, in
   unsigned long long* d_hist = B<unsigned long long>(h, kBufMaskHist);
   unsigned long long* h_hist = (unsigned long long*)h->pinned;
   LaunchCtx L = ctx(h, s);
+  unsigned long long* d_unsorted = d_hist + 2 * kNumBins;
+  unsigned long long* h_unsorted = h_hist + 2 * kNumBins;
   KKS_CU(cudaMemsetAsync(d_hist, 0, sizeof(unsigned long long) * kNumBins, s));
+  KKS_CU(cudaMemsetAsync(d_unsorted, 0, sizeof(unsigned long long), s));
   KKS_CU(launch_masked_bin_count(L, Mx, nrows, c, d_hist));
+  if (h->opt.numeric_positions) KKS_CU(launch_pattern_unsorted(L, Mx, nrows, d_unsorted));
   KKS_CU(cudaMemcpyAsync(h_hist, d_hist, sizeof(unsigned long long) * kNumBins, cudaMemcpyDeviceToHost, s));
-  DevStatus* hs = (DevStatus*)(h->pinned + sizeof(unsigned long long) * 2 * kNumBins);
+  KKS_CU(cudaMemcpyAsync(h_unsorted, d_unsorted, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  DevStatus* hs = (DevStatus*)(h->pinned + sizeof(unsigned long long) * (2 * kNumBins + 2));
   KKS_CU(cudaMemcpyAsync(hs, h->buf[kBufStatus], sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
   KKS_CU(cudaStreamSynchronize(s));
   KKS_ST(consume_status(h, hs, s));
+  plan->sorted = h->opt.numeric_positions != 0 && *h_unsorted == 0;
   plan->cls_logT.clear();
   plan->off.clear();
   plan->cnt.clear();
@@ -1037,6 +1044,7 @@ spgemm_status_t run_masked_plan(kks_handle* h, const MaskedD& M, int dtype, int 
     S.rows = B<int>(h, rows_buf) + plan.off[b];
     S.nrows = plan.cnt[b];
     S.dtype = dtype;
+    S.positions = (plan.sorted && (S.cls == kClsW8 || S.cls == kClsW32)) ? 1 : 0;
     if (S.cls == kClsSpill) {
       S.pool = h->buf[pool_buf];
       S.chunk_slots = plan.gslots;

@@ -356,6 +356,30 @@ __device__ __forceinline__ int union_chunk(unsigned team_mask, int lane, int* pr
   return fresh;
 }
 
+// Tables of 16-byte slots (column-set index, set bits, base, unused): the
+// place of column c in a sorted row is base(c >> 5) + the number of set bits
+// below bit c & 31.  Lookups once the table is complete.
+__device__ __forceinline__ int4 set_find(const int4* tab, const LpHash& hs, int key) {
+  unsigned h = hs(key);
+  for (unsigned probe = 0; probe <= hs.mask; ++probe) {
+    const int4 e = tab[h];
+    if (e.x == key || e.x == kEmpty) return e;
+    h = (h + 1) & hs.mask;
+  }
+  return make_int4(kEmpty, 0, 0, 0);
+}
+
+__device__ __forceinline__ int set_slot(const int4* tab, const LpHash& hs, int key) {
+  unsigned h = hs(key);
+  for (unsigned probe = 0; probe <= hs.mask; ++probe) {
+    const int k = tab[h].x;
+    if (k == key) return (int)h;
+    if (k == kEmpty) return -1;
+    h = (h + 1) & hs.mask;
+  }
+  return -1;
+}
+
 // Ascending bitonic sort of one 32-bit key per lane of a team of TW lanes
 // (register exchanges only).
 template <int TW>

@@ -166,7 +166,9 @@ struct MaskedLaunch {
   void* pool;            // big rows: global tables
   long long chunk_slots;
   int nchunks;
+  int positions;         // warp classes: S's rows are sorted, places from its column sets
 };
+cudaError_t launch_pattern_unsorted(const LaunchCtx&, const MaskedD&, long long nrows, unsigned long long* count);
 cudaError_t launch_masked_bin_count(const LaunchCtx&, const MaskedD&, long long nrows, BinCfg cfg,
                                     unsigned long long* hist);
 cudaError_t launch_masked_bin_scatter(const LaunchCtx&, const MaskedD&, long long nrows, BinCfg cfg,

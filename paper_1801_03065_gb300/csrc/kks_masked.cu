@@ -9,7 +9,9 @@
 //     dA = G * B^T on A's pattern (X = G, Y = B^T), dB = A^T * G on B's
 //     pattern (X = A^T, Y = G).
 // Rows of S larger than the shared table use the same code with the table in
-// a global pool chunk.
+// a global pool chunk.  When every row of S is sorted, warp-team rows key the
+// table by S's column sets instead and compute each column's place in S(i,:)
+// from the set bits (k_masked_pos).
 //
 // Transpose: column counts, their scan, an atomic scatter of (row, position)
 // and a per-row bitonic sort by row, which also yields the permutation that
@@ -276,6 +278,221 @@ __global__ void __launch_bounds__(256) k_masked_warp(MaskedD M, const int* __res
     const long long sw = s < half ? s : half;
     for (long long p = tm.lane; p < sw; p += TW) out[s0 + p] = acc[p];
     __syncwarp(tm.mask);
+  }
+}
+
+// Warp / sub-warp teams on a pattern whose rows are sorted (strictly
+// increasing columns, as every C of this library): the table is keyed by the
+// column sets of S(i,:) (Section 3.2's 32-column sets), each slot holding the
+// set bits and the position of the set's first column in S(i,:), so the place
+// of a product's column is base + popcount of the bits below it and a column
+// outside the pattern is a missing key or a clear bit.  Products are added as
+// in k_masked_warp.
+template <int TW, typename VT>
+__host__ __device__ size_t mskp_team_bytes(int T) {
+  const int half = T / 2 > 0 ? T / 2 : 1;
+  return al16((size_t)T * 16) + al16((size_t)half * sizeof(VT)) + al16(sizeof(ChunkScratch<TW, VT>)) +
+         al16((size_t)TW * sizeof(VT));
+}
+
+template <int TW, typename VT>
+__global__ void __launch_bounds__(256, 4) k_masked_pos(MaskedD M, const int* __restrict__ rows, long long nrows,
+                                                       int logT) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Team<TW> tm;
+  const int T = 1 << logT;
+  const LpHash hs(logT, M.hash_mode);
+  const int half = T / 2 > 0 ? T / 2 : 1;
+  unsigned char* base = smem + (size_t)tm.id * mskp_team_bytes<TW, VT>(T);
+  int4* tab = reinterpret_cast<int4*>(base);
+  VT* acc = reinterpret_cast<VT*>(base + al16((size_t)T * 16));
+  ChunkScratch<TW, VT>* csc =
+      reinterpret_cast<ChunkScratch<TW, VT>*>(base + al16((size_t)T * 16) + al16((size_t)half * sizeof(VT)));
+  VT* xchg = reinterpret_cast<VT*>(reinterpret_cast<unsigned char*>(csc) + al16(sizeof(ChunkScratch<TW, VT>)));
+  const VT* __restrict__ Xx = reinterpret_cast<const VT*>(M.X.vx);
+  const VT* __restrict__ Yx = reinterpret_cast<const VT*>(M.Y.vx);
+  auto XV = [&](long long p) -> VT { return Xx[M.xperm ? M.xperm[p] : p]; };
+  auto YV = [&](long long q) -> VT { return Yx[M.yperm ? M.yperm[q] : q]; };
+  const int* __restrict__ Yj = M.Y.cj;
+  const int* __restrict__ Xj = M.X.cj;
+  VT* __restrict__ out = reinterpret_cast<VT*>(M.out);
+  const unsigned lane_lt = (1u << tm.lane) - 1u;
+  const int lane_base = (threadIdx.x & 31) & ~(TW - 1);
+  const unsigned tbits = (TW == 32) ? 0xffffffffu : ((1u << TW) - 1u);
+
+  const long long team = (long long)blockIdx.x * tm.per_cta + tm.id;
+  const long long nteams = (long long)gridDim.x * tm.per_cta;
+  for (long long r = team; r < nrows; r += nteams) {
+    const long long i = rows[r];
+    const long long s0 = M.Sp[i];
+    const int s = (int)(M.Sp[i + 1] - s0);
+    const long long a0 = rp_at(M.X, i), a1 = rp_at(M.X, i + 1);
+    // the first chunk of X(i,:) is fetched before the pattern is keyed
+    long long bs = 0;
+    int len = 0;
+    VT av = VT(0);
+    if (a0 + tm.lane < a1) {
+      const int j = Xj[a0 + tm.lane];
+      bs = rp_at(M.Y, j);
+      len = (int)(rp_at(M.Y, j + 1) - bs);
+      av = XV(a0 + tm.lane);
+    }
+    for (int x = tm.lane; x < T; x += TW) tab[x] = make_int4(kEmpty, 0, 0, 0);
+    const int sw = s < half ? s : half;
+    for (int x = tm.lane; x < sw; x += TW) acc[x] = VT(0);
+    __syncwarp(tm.mask);
+    // the pattern's column sets: the lane holding a set's first column claims
+    // its slot and records the position; the last lane of each run of one set
+    // inside a pass ORs in the run's bits (a segmented OR over the lanes)
+    for (int pb = 0; pb < s; pb += TW) {
+      const int p = pb + tm.lane;
+      const int col = p < s ? M.Sj[s0 + p] : -1;
+      int prev = __shfl_up_sync(tm.mask, col, 1, TW);
+      if (tm.lane == 0) prev = pb > 0 ? M.Sj[s0 + pb - 1] : -1;
+      const int set = col >= 0 ? (col >> 5) : -1 - tm.lane;
+      if (col >= 0 && p > 0 && prev >= col) dev_fail(M.status, kDevBadIndex, 29, i);   // not sorted
+      unsigned bits = col >= 0 ? (1u << (col & 31)) : 0u;
+#pragma unroll
+      for (int d = 1; d < TW; d <<= 1) {
+        const unsigned y = __shfl_up_sync(tm.mask, bits, d, TW);
+        const int ys = __shfl_up_sync(tm.mask, set, d, TW);
+        if (tm.lane >= d && ys == set) bits |= y;
+      }
+      const int next_set = __shfl_down_sync(tm.mask, set, 1, TW);
+      const bool last = col >= 0 && (tm.lane == TW - 1 || p + 1 >= s || next_set != set);
+      const bool head = col >= 0 && (p == 0 || (prev >> 5) != set);
+      if (head) {
+        int fresh = 0;
+        const int slot = slot_insert<4>(reinterpret_cast<int*>(tab), hs, set, &fresh);
+        if (slot >= 0) tab[slot].z = p;
+        else dev_fail(M.status, kDevTableFull, 30, i);
+      }
+      __syncwarp(tm.mask);
+      if (last) {
+        const int slot = set_slot(tab, hs, set);
+        if (slot >= 0) tab[slot].y |= (int)bits;
+      }
+      __syncwarp(tm.mask);
+    }
+    auto pos_of = [&](int c) -> int {
+      const int4 e = set_find(tab, hs, c >> 5);
+      const unsigned m = (unsigned)e.y;
+      if (e.x == kEmpty || !((m >> (c & 31)) & 1u)) return -1;
+      return e.z + __popc(m & ((1u << (c & 31)) - 1u));
+    };
+    for (long long c = a0; c < a1; c += TW) {
+      if (c != a0) {
+        const long long p = c + tm.lane;
+        bs = 0;
+        len = 0;
+        av = VT(0);
+        if (p < a1) {
+          const int j = Xj[p];
+          bs = rp_at(M.Y, j);
+          len = (int)(rp_at(M.Y, j + 1) - bs);
+          av = XV(p);
+        }
+      }
+      const int nc = (a1 - c) < TW ? (int)(a1 - c) : TW;
+      int tot = len;
+#pragma unroll
+      for (int d = TW / 2; d > 0; d >>= 1) tot += __shfl_xor_sync(tm.mask, tot, d, TW);
+      if (2 * tot >= nc * TW) {
+        constexpr int kU = 4;
+        for (int t0 = 0; t0 < nc; t0 += kU) {
+          int key[kU], lent[kU];
+          long long bst[kU];
+          VT at[kU], yv[kU];
+#pragma unroll
+          for (int u = 0; u < kU; ++u) {
+            const int t = (t0 + u < nc) ? t0 + u : nc - 1;
+            bst[u] = __shfl_sync(tm.mask, bs, t, TW);
+            const int l = __shfl_sync(tm.mask, len, t, TW);
+            at[u] = __shfl_sync(tm.mask, av, t, TW);
+            lent[u] = (t0 + u < nc) ? l : 0;
+            key[u] = -1;
+            yv[u] = VT(0);
+            if (tm.lane < lent[u]) {
+              key[u] = Yj[bst[u] + tm.lane];
+              yv[u] = YV(bst[u] + tm.lane);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < kU; ++u) {
+            if (key[u] >= 0) {
+              const int o = pos_of(key[u]);
+              if (o >= 0 && o < half) acc[o] = fma_acc(at[u], yv[u], acc[o]);
+            }
+            for (int x = tm.lane + TW; x < lent[u]; x += TW) {
+              const int o = pos_of(Yj[bst[u] + x]);
+              if (o >= 0 && o < half) acc[o] = fma_acc(at[u], YV(bst[u] + x), acc[o]);
+            }
+            __syncwarp(tm.mask);
+          }
+        }
+      } else {
+        int ex = len;
+#pragma unroll
+        for (int d = 1; d < TW; d <<= 1) {
+          const int y = __shfl_up_sync(tm.mask, ex, d, TW);
+          if (tm.lane >= d) ex += y;
+        }
+        ex -= len;
+        csc->pre[tm.lane] = ex;
+        csc->bs[tm.lane] = bs;
+        csc->av[tm.lane] = av;
+        if (tm.lane == 0) csc->pre[TW] = tot;
+        __syncwarp(tm.mask);
+        int t = 0;
+        for (int xb = 0; xb < tot; xb += TW) {
+          const int x = xb + tm.lane;
+          int q = -1 - tm.lane;   // inactive or masked-out lanes: a distinct negative id
+          VT v = VT(0);
+          if (x < tot) {
+            while (csc->pre[t + 1] <= x) ++t;
+            const long long yq = csc->bs[t] + (x - csc->pre[t]);
+            const int o = pos_of(Yj[yq]);
+            if (o >= 0 && o < half) {
+              q = o;
+              v = csc->av[t] * YV(yq);
+            }
+          }
+          const unsigned grp = (__match_any_sync(tm.mask, q) >> lane_base) & tbits;
+          const bool leader = (grp & lane_lt) == 0;
+          if (__any_sync(tm.mask, __popc(grp) > 1)) {
+            xchg[tm.lane] = v;
+            __syncwarp(tm.mask);
+            if (leader) {
+              unsigned rest = grp & ~(1u << tm.lane);
+              while (rest) {
+                const int o = __ffs(rest) - 1;
+                rest &= rest - 1u;
+                v += xchg[o];
+              }
+            }
+            __syncwarp(tm.mask);
+          }
+          if (q >= 0 && leader) acc[q] += v;
+          __syncwarp(tm.mask);
+        }
+        __syncwarp(tm.mask);
+      }
+    }
+    for (int p = tm.lane; p < sw; p += TW) out[s0 + p] = acc[p];
+    __syncwarp(tm.mask);
+  }
+}
+
+// Rows of S whose columns are not strictly increasing (one warp per row).
+__global__ void k_pattern_unsorted(MaskedD M, long long nrows, unsigned long long* count) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long i = warp; i < nrows; i += nwarps) {
+    const long long s0 = M.Sp[i], s1 = M.Sp[i + 1];
+    bool bad = false;
+    for (long long p = s0 + 1 + lane; p < s1; p += 32) bad |= M.Sj[p] <= M.Sj[p - 1];
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicAdd(count, 1ull);
   }
 }
 
@@ -570,6 +787,24 @@ cudaError_t run_masked_warp(const LaunchCtx& L, const MaskedD& M, const MaskedLa
   return cudaGetLastError();
 }
 
+template <int TW, typename VT>
+cudaError_t run_masked_pos(const LaunchCtx& L, const MaskedD& M, const MaskedLaunch& S) {
+  const int T = 1 << S.logT;
+  const size_t tb = mskp_team_bytes<TW, VT>(T);
+  int teams = (int)((48 * 1024) / tb);
+  const int tmax = 256 / TW;
+  if (teams > tmax) teams = tmax;
+  if (teams < 1) teams = 1;
+  const size_t smem = tb * teams;
+  if (smem > (size_t)L.max_smem_optin) return cudaErrorInvalidConfiguration;
+  auto kern = k_masked_pos<TW, VT>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  KKS_LAUNCHED();
+  kern<<<grid_cap(S.nrows, teams, L.num_sms, 64), TW * teams, smem, L.stream>>>(M, S.rows, S.nrows, S.logT);
+  return cudaGetLastError();
+}
+
 template <typename VT>
 cudaError_t run_masked_global(const LaunchCtx& L, const MaskedD& M, const MaskedLaunch& S) {
   constexpr int TW = 1024;
@@ -597,8 +832,8 @@ cudaError_t masked_dispatch(const LaunchCtx& L, const MaskedD& M, const MaskedLa
         k_masked_thread<VT, true><<<grid_cap(S.nrows, 256, L.num_sms, 32), 256, 0, L.stream>>>(M, S.rows, S.nrows);
       return cudaGetLastError();
     }
-    case kClsW8: return run_masked_warp<8, VT>(L, M, S);
-    case kClsW32: return run_masked_warp<32, VT>(L, M, S);
+    case kClsW8: return S.positions ? run_masked_pos<8, VT>(L, M, S) : run_masked_warp<8, VT>(L, M, S);
+    case kClsW32: return S.positions ? run_masked_pos<32, VT>(L, M, S) : run_masked_warp<32, VT>(L, M, S);
     case kClsC256: return run_masked_hash<256, VT>(L, M, S);
     case kClsC1024: return run_masked_hash<1024, VT>(L, M, S);
     case kClsSpill: return run_masked_global<VT>(L, M, S);
@@ -645,6 +880,14 @@ cudaError_t launch_masked_bin_scatter(const LaunchCtx& L, const MaskedD& M, long
 cudaError_t launch_masked(const LaunchCtx& L, const MaskedD& M, const MaskedLaunch& S) {
   if (S.nrows <= 0) return cudaSuccess;
   return S.dtype == 1 ? masked_dispatch<double>(L, M, S) : masked_dispatch<float>(L, M, S);
+}
+
+cudaError_t launch_pattern_unsorted(const LaunchCtx& L, const MaskedD& M, long long nrows,
+                                    unsigned long long* count) {
+  if (nrows <= 0) return cudaSuccess;
+  KKS_LAUNCHED();
+  k_pattern_unsorted<<<grid_cap(nrows, 8, L.num_sms, 8), 256, 0, L.stream>>>(M, nrows, count);
+  return cudaGetLastError();
 }
 
 size_t masked_global_chunk_bytes(long long slots, int dtype) {

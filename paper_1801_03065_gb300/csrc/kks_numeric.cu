@@ -369,29 +369,6 @@ __host__ __device__ size_t cpn_team_bytes(int T) {
          al16((size_t)TW * sizeof(VT));
 }
 
-// The slot index of a column-set index once the table is complete (-1: absent).
-__device__ __forceinline__ int cpn_slot(const int4* tab, const LpHash& hs, int key) {
-  unsigned h = hs(key);
-  for (unsigned probe = 0; probe <= hs.mask; ++probe) {
-    const int k = tab[h].x;
-    if (k == key) return (int)h;
-    if (k == kEmpty) return -1;
-    h = (h + 1) & hs.mask;
-  }
-  return -1;
-}
-
-// The slot of a column-set index once the table is complete (x = kEmpty: absent).
-__device__ __forceinline__ int4 cpn_find(const int4* tab, const LpHash& hs, int key) {
-  unsigned h = hs(key);
-  for (unsigned probe = 0; probe <= hs.mask; ++probe) {
-    const int4 e = tab[h];
-    if (e.x == key || e.x == kEmpty) return e;
-    h = (h + 1) & hs.mask;
-  }
-  return make_int4(kEmpty, 0, 0, 0);
-}
-
 template <int TW, typename VT>
 __global__ void __launch_bounds__(256, 4) k_num_cpn(ProbD P, const int* __restrict__ rows, long long nrows, int logT) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -484,7 +461,7 @@ __global__ void __launch_bounds__(256, 4) k_num_cpn(ProbD P, const int* __restri
       for (int h = 0; h < 2; ++h) {
         const unsigned v = h ? v1 : v0;
         if (v != 0xffffffffu) {
-          sl[h] = cpn_slot(tab, hs, (int)v);
+          sl[h] = set_slot(tab, hs, (int)v);
           if (sl[h] >= 0) mk[h] = (unsigned)tab[sl[h]].y;
         }
         const int c = __popc(mk[h]);
@@ -559,7 +536,7 @@ __global__ void __launch_bounds__(256, 4) k_num_cpn(ProbD P, const int* __restri
     __syncwarp(tm.mask);
     // 3. products to their positions
     auto pos_of = [&](int col) -> int {
-      const int4 e = cpn_find(tab, hs, col >> 5);
+      const int4 e = set_find(tab, hs, col >> 5);
       if (e.x == kEmpty) return -1;
       return e.z + __popc((unsigned)e.y & ((1u << (col & 31)) - 1u));
     };

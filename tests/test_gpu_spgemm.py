@@ -485,3 +485,59 @@ def test_positions_tuned_and_repeated(ops):
         h.numeric(Ad, Bd, Cd.rowptr, Cd.nnz, Cd.colidx, Cd.values)
         h.sync()
         assert_matches_oracle(A2, A2, Cd, np.float64)
+
+
+# ------------------------------------------------------------------ masked products keyed by column sets
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("shuffled", [False, True])
+@pytest.mark.parametrize("pos", [True, False])
+def test_masked_sorted_and_unsorted_patterns(ops, dtype, shuffled, pos):
+    """Sorted patterns take places from their column sets (pos=True); a pattern
+    with unsorted rows keeps the column-keyed tables; all agree with the oracle."""
+    rng = np.random.default_rng(6)
+    A = w.random_csr(300, 200, 8.0, seed=12)
+    if shuffled:
+        A = w.shuffle_rows(A, 3)
+    B = w.random_csr(200, 400, 8.0, seed=13)
+    Ah, Bh = host_inputs(A, dtype), host_inputs(B, dtype)
+    C, _ = oracle.spgemm(Ah, Bh)
+    G = C.with_values(rng.uniform(-1, 1, C.nnz).astype(dtype))
+    h = ops.SpGEMM(numeric_positions=pos)
+    Ad, Bd, Gd = dev(A, dtype), dev(B, dtype), dev(G, dtype)
+    Bt, _ = h.transpose(Bd)
+    At, _ = h.transpose(Ad)
+    dA = h.masked(Gd, Bt, Ad.rowptr, Ad.colidx)
+    dB = h.masked(At, Gd, Bd.rowptr, Bd.colidx)
+    h.sync()
+    ref_a, sa = oracle.masked_dA(Ah, Bh, G)
+    ref_b, sb = oracle.masked_dB(Ah, Bh, G)
+    t = tol_of(dtype)
+    assert np.all(np.abs(dA.cpu().numpy() - ref_a) <= t * sa)
+    assert np.all(np.abs(dB.cpu().numpy() - ref_b) <= t * sb)
+
+
+@pytest.mark.parametrize("pos", [True, False])
+def test_masked_stencil_sets_and_reuse(ops, pos):
+    """Stencil patterns: runs of columns inside and across 32-column sets, pattern
+    rows longer than one warp pass (C's rows), numeric reuse on C's pattern."""
+    A = w.stencil3d_27pt(12, seed=3)
+    C, _ = oracle.spgemm(A, A)
+    G = C.with_values(np.random.default_rng(2).uniform(-1, 1, C.nnz))
+    h = ops.SpGEMM(numeric_positions=pos)
+    Ad, Gd = dev(A), dev(G)
+    At, _ = h.transpose(Ad)
+    dA = h.masked(Gd, At, Ad.rowptr, Ad.colidx)
+    dB = h.masked(At, Gd, Ad.rowptr, Ad.colidx)
+    h.sync()
+    ref_a, sa = oracle.masked_dA(A, A, G)
+    ref_b, sb = oracle.masked_dB(A, A, G)
+    assert np.all(np.abs(dA.cpu().numpy() - ref_a) <= 1e-13 * sa)
+    assert np.all(np.abs(dB.cpu().numpy() - ref_b) <= 1e-13 * sb)
+    rp, nnz = h.symbolic(Ad, Ad)
+    Cd = h.numeric(Ad, Ad, rp, nnz)
+    A2 = A.with_values(np.random.default_rng(4).uniform(-1, 1, A.nnz))
+    Ad.values.copy_(torch.as_tensor(A2.values))
+    for _ in range(2):
+        h.numeric_reuse(Ad, Ad, Cd)
+        h.sync()
+        assert_matches_oracle(A2, A2, Cd, np.float64)
