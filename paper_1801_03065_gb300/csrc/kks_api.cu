@@ -38,7 +38,7 @@ enum BufId {
   kBufInst, kBufArow0, kBufBrow0, kBufCnt, kBufBcp, kBufCsi, kBufCs, kBufRf, kBufRfc, kBufRowsize, kBufOffs,
   kBufScanTmp, kBufInstStats, kBufInstOut, kBufHist, kBufCursor, kBufSymRows, kBufNumRows, kBufSymPool,
   kBufNumPool, kBufNumPool2, kBufNumPool3, kBufStatus, kBufMaskRows, kBufMaskHist, kBufMaskPool, kBufTrTmp,
-  kBufTrPool, kBufReuseRows, kBufReusePool, kNumBufs
+  kBufTrPool, kBufReuseRows, kBufReusePool, kBufBinCnt, kBufBinOfs, kNumBufs
 };
 
 // Row bins of a masked product, cached for numeric reuse on one pattern.
@@ -473,7 +473,11 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
   KKS_ST(ensure(h, kBufRfc, sizeof(long long) * (totalA + 1)));
   KKS_ST(ensure(h, kBufRowsize, sizeof(long long) * (totalA + 1)));
   KKS_ST(ensure(h, kBufOffs, sizeof(long long) * (totalA + 1)));
-  KKS_ST(ensure(h, kBufScanTmp, scan_tmp_bytes(std::max(totalA, totalB) + 1)));
+  // stable binning: per-block bin counts of up to two passes and their scans
+  const long long nbc = (long long)kNumBins * bin_blocks(totalA);
+  KKS_ST(ensure(h, kBufBinCnt, sizeof(long long) * 2 * (nbc + 1)));
+  KKS_ST(ensure(h, kBufBinOfs, sizeof(long long) * 2 * (nbc + 1)));
+  KKS_ST(ensure(h, kBufScanTmp, scan_tmp_bytes(std::max(std::max(totalA, totalB), nbc) + 1)));
   KKS_ST(ensure(h, kBufInstStats, sizeof(unsigned long long) * 4 * ni));
   KKS_ST(ensure(h, kBufInstOut, sizeof(unsigned long long) * 2 * ni));
   KKS_ST(ensure(h, kBufHist, sizeof(unsigned long long) * 2 * kNumBins));
@@ -570,7 +574,9 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
     KKS_CU(cudaMemsetAsync(d_hist, 0, sizeof(unsigned long long) * kNumBins, s));
     BinCfg c = pass ? cfg_c : cfg_u;
     KKS_CU(launch_bin_count(L, P, totalA, pass ? 2 : 3, B<long long>(h, kBufRf), B<long long>(h, kBufRfc), nullptr, c,
-                            d_hist));
+                            d_hist, B<long long>(h, kBufBinCnt) + pass * (nbc + 1)));
+    KKS_CU(launch_scan(L, B<long long>(h, kBufBinCnt) + pass * (nbc + 1), B<long long>(h, kBufBinOfs) + pass * (nbc + 1),
+                       nbc, h->buf[kBufScanTmp]));
     KKS_CU(cudaMemcpyAsync(h_hist, d_hist, sizeof(unsigned long long) * kNumBins, cudaMemcpyDeviceToHost, s));
     KKS_CU(cudaStreamSynchronize(s));
     for (int t = 0; t < kNumBins; ++t) hist[pass * kNumBins + t] = h_hist[t];
@@ -590,8 +596,8 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
     if (pass == 0 && ncomp == count && count > 0) continue;
     BinCfg c = pass ? cfg_c : cfg_u;
     KKS_CU(launch_bin_scatter(L, P, totalA, pass ? 2 : 3, B<long long>(h, kBufRf), B<long long>(h, kBufRfc),
-                              B<long long>(h, kBufRowsize), c,
-                              B<unsigned long long>(h, kBufCursor) + pass * kNumBins, B<int>(h, kBufSymRows)));
+                              B<long long>(h, kBufRowsize), c, B<unsigned long long>(h, kBufCursor) + pass * kNumBins,
+                              B<long long>(h, kBufBinOfs) + pass * (nbc + 1), B<int>(h, kBufSymRows)));
   }
 
   // (5) symbolic kernels, bin by bin
@@ -649,7 +655,8 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
   }
   KKS_CU(cudaMemsetAsync(d_hist, 0, sizeof(unsigned long long) * kNumBins, s));
   KKS_CU(launch_bin_count(L, P, totalA, 1, B<long long>(h, kBufRf), nullptr, B<long long>(h, kBufRowsize), ncfg,
-                          d_hist));
+                          d_hist, B<long long>(h, kBufBinCnt)));
+  KKS_CU(launch_scan(L, B<long long>(h, kBufBinCnt), B<long long>(h, kBufBinOfs), nbc, h->buf[kBufScanTmp]));
   unsigned long long* h_out = (unsigned long long*)(rd + sizeof(unsigned long long) * 4 * ni);
   KKS_CU(cudaMemcpyAsync(h_hist, d_hist, sizeof(unsigned long long) * kNumBins, cudaMemcpyDeviceToHost, s));
   KKS_CU(cudaMemcpyAsync(h_out, h->buf[kBufInstOut], sizeof(unsigned long long) * 2 * ni, cudaMemcpyDeviceToHost, s));
@@ -666,7 +673,7 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
   KKS_CU(cudaMemcpyAsync(h->buf[kBufCursor], h_cur, sizeof(unsigned long long) * kNumBins, cudaMemcpyHostToDevice,
                          s));
   KKS_CU(launch_bin_scatter(L, P, totalA, 1, B<long long>(h, kBufRf), nullptr, B<long long>(h, kBufRowsize), ncfg,
-                            B<unsigned long long>(h, kBufCursor), B<int>(h, kBufNumRows)));
+                            B<unsigned long long>(h, kBufCursor), B<long long>(h, kBufBinOfs), B<int>(h, kBufNumRows)));
 
   h->num_bins.clear();
   const bool positions_ok = h->opt.numeric_positions != 0 && count > 0 && ncomp == count;
@@ -969,6 +976,10 @@ spgemm_status_t plan_masked(kks_handle* h, const MaskedD& M, long long nrows, in
   KKS_ST(ensure(h, kBufMaskHist, sizeof(unsigned long long) * (2 * kNumBins + 2)));
   KKS_ST(ensure(h, rows_buf, sizeof(int) * (nrows + 1)));
   KKS_ST(ensure_pinned(h, sizeof(unsigned long long) * (2 * kNumBins + 2) + sizeof(DevStatus)));
+  const long long nbc = (long long)kNumBins * bin_blocks(nrows);
+  KKS_ST(ensure(h, kBufBinCnt, sizeof(long long) * (nbc + 1)));
+  KKS_ST(ensure(h, kBufBinOfs, sizeof(long long) * (nbc + 1)));
+  KKS_ST(ensure(h, kBufScanTmp, scan_tmp_bytes(nbc + 1)));
   MaskedD Mx = M;
   Mx.status = B<DevStatus>(h, kBufStatus);
   BinCfg c = base_cfg(h);
@@ -983,7 +994,8 @@ spgemm_status_t plan_masked(kks_handle* h, const MaskedD& M, long long nrows, in
   unsigned long long* h_unsorted = h_hist + 2 * kNumBins;
   KKS_CU(cudaMemsetAsync(d_hist, 0, sizeof(unsigned long long) * kNumBins, s));
   KKS_CU(cudaMemsetAsync(d_unsorted, 0, sizeof(unsigned long long), s));
-  KKS_CU(launch_masked_bin_count(L, Mx, nrows, c, d_hist));
+  KKS_CU(launch_masked_bin_count(L, Mx, nrows, c, d_hist, B<long long>(h, kBufBinCnt)));
+  if (nrows > 0) KKS_CU(launch_scan(L, B<long long>(h, kBufBinCnt), B<long long>(h, kBufBinOfs), nbc, h->buf[kBufScanTmp]));
   if (h->opt.numeric_positions) KKS_CU(launch_pattern_unsorted(L, Mx, nrows, d_unsorted));
   KKS_CU(cudaMemcpyAsync(h_hist, d_hist, sizeof(unsigned long long) * kNumBins, cudaMemcpyDeviceToHost, s));
   KKS_CU(cudaMemcpyAsync(h_unsorted, d_unsorted, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
@@ -1015,7 +1027,7 @@ spgemm_status_t plan_masked(kks_handle* h, const MaskedD& M, long long nrows, in
   memcpy(h_hist + kNumBins, cur.data(), sizeof(unsigned long long) * kNumBins);
   KKS_CU(cudaMemcpyAsync(d_hist + kNumBins, h_hist + kNumBins, sizeof(unsigned long long) * kNumBins,
                          cudaMemcpyHostToDevice, s));
-  KKS_CU(launch_masked_bin_scatter(L, Mx, nrows, c, d_hist + kNumBins, B<int>(h, rows_buf)));
+  KKS_CU(launch_masked_bin_scatter(L, Mx, nrows, c, d_hist + kNumBins, B<long long>(h, kBufBinOfs), B<int>(h, rows_buf)));
   plan->gchunks = 0;
   plan->gslots = 0;
   if (grows > 0) {

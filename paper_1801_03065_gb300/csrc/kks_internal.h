@@ -92,6 +92,25 @@ struct LaunchCtx {
   int max_smem_optin;   // bytes of dynamic shared memory a CTA may use
 };
 
+// Shared memory per CTA of the team kernels: up to 8 warp teams of a 256-slot
+// FP64 table, so that four such CTAs (32 warps) share one SM's 228 KB.
+constexpr size_t kTeamSmemBudget = 56 * 1024;
+
+// CTAs of `kernel` (threads, dynamic shared memory smem) that fit on one SM,
+// remembered per configuration (a host-side query, no device work).
+int resident_per_sm(const void* kernel, int threads, size_t smem);
+
+// Grid of a persistent team kernel: enough CTAs for the rows, at most the
+// CTAs that are resident at once, so the rows in flight are one contiguous
+// window of the (row-ordered) bin list and its B rows stay in L2.
+template <class K>
+inline unsigned resident_grid(K kernel, int threads, size_t smem, int num_sms, long long need) {
+  const long long cap = (long long)num_sms * resident_per_sm(reinterpret_cast<const void*>(kernel), threads, smem);
+  long long g = need < cap ? need : cap;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
 // prep: statistics, compression, scans, binning
 cudaError_t launch_compress_count(const LaunchCtx&, const ProbD&, long long totalB, long long* cnt);
 cudaError_t launch_compress_fill(const LaunchCtx&, const ProbD&, long long totalB, int* csi, unsigned* cs);
@@ -101,13 +120,66 @@ cudaError_t launch_row_stats(const LaunchCtx&, const ProbD&, long long totalA, i
 size_t scan_tmp_bytes(long long n);
 cudaError_t launch_scan(const LaunchCtx&, const long long* in, long long* out, long long n, void* tmp);
 // phase 1 = numeric (u = row size); phase 2 / 3 = symbolic rows of compressed /
-// uncompressed products (u from rfc / rf); rows of the other kind are skipped
+// uncompressed products (u from rfc / rf); rows of the other kind are skipped.
+// Stable binning: the count adds the bin histogram into hist and writes the
+// per-block counts bcnt[bin * bin_blocks + block] (kNumBins * bin_blocks
+// entries); the scatter takes their exclusive scan bofs and the first slot of
+// every bin (cursor) and lists each bin's rows in increasing row order.
+constexpr int kBinRows = 1024;
+constexpr int kBinThreads = 256;
+inline long long bin_blocks(long long totalA) { return totalA > 0 ? (totalA + kBinRows - 1) / kBinRows : 1; }
+
+// Device halves of the stable binning, for a block of kBinThreads threads over
+// the rows [r0, r1).  key(g): the bin of row g, or -1 for a row not listed.
+// Count: the block's histogram h (kNumBins, zeroed by the caller).
+template <class Key>
+__device__ __forceinline__ void bin_block_count(long long r0, long long r1, Key key, unsigned long long* h) {
+  for (long long base = r0; base < r1; base += kBinThreads) {
+    const long long g = base + threadIdx.x;
+    const int bin = (g < r1) ? key(g) : -1;
+    const unsigned grp = __match_any_sync(0xffffffffu, bin);
+    if (bin >= 0 && (__ffs(grp) - 1) == (int)(threadIdx.x & 31)) atomicAdd(&h[bin], (unsigned long long)__popc(grp));
+  }
+}
+
+// List: run[bin] holds the block's first slot in each bin's list; rows are
+// written in increasing order.  wcnt: kBinThreads / 32 x kNumBins zeroed ints.
+template <class Key>
+__device__ __forceinline__ void bin_block_list(long long r0, long long r1, Key key, long long* run,
+                                               int (*wcnt)[kNumBins], int* rows) {
+  constexpr int kWarps = kBinThreads / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned lt;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+  for (long long base = r0; base < r1; base += kBinThreads) {
+    const long long g = base + threadIdx.x;
+    const int bin = (g < r1) ? key(g) : -1;
+    const unsigned grp = __match_any_sync(0xffffffffu, bin);
+    if (bin >= 0 && lane == __ffs(grp) - 1) wcnt[warp][bin] = __popc(grp);
+    __syncthreads();
+    if (bin >= 0) {
+      long long pos = run[bin];
+      for (int w = 0; w < warp; ++w) pos += wcnt[w][bin];
+      rows[pos + __popc(grp & lt)] = (int)g;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < kNumBins; t += kBinThreads) {
+      long long add = 0;
+      for (int w = 0; w < kWarps; ++w) {
+        add += wcnt[w][t];
+        wcnt[w][t] = 0;
+      }
+      run[t] += add;
+    }
+    __syncthreads();
+  }
+}
 cudaError_t launch_bin_count(const LaunchCtx&, const ProbD&, long long totalA, int phase,
                              const long long* rf, const long long* rfc, const long long* rowsize,
-                             BinCfg cfg, unsigned long long* hist);
+                             BinCfg cfg, unsigned long long* hist, long long* bcnt);
 cudaError_t launch_bin_scatter(const LaunchCtx&, const ProbD&, long long totalA, int phase,
                                const long long* rf, const long long* rfc, const long long* rowsize,
-                               BinCfg cfg, unsigned long long* cursor, int* rows);
+                               BinCfg cfg, const unsigned long long* cursor, const long long* bofs, int* rows);
 // C row pointers per instance from the global scan; per-instance nnz and max row size
 cudaError_t launch_write_rowptr(const LaunchCtx&, const ProbD&, long long totalA, const long long* offs,
                                 const long long* rowsize, unsigned long long* inst_out);
@@ -169,10 +241,11 @@ struct MaskedLaunch {
   int positions;         // warp classes: S's rows are sorted, places from its column sets
 };
 cudaError_t launch_pattern_unsorted(const LaunchCtx&, const MaskedD&, long long nrows, unsigned long long* count);
+// stable binning of the pattern's rows (bcnt / bofs as launch_bin_count / launch_bin_scatter)
 cudaError_t launch_masked_bin_count(const LaunchCtx&, const MaskedD&, long long nrows, BinCfg cfg,
-                                    unsigned long long* hist);
+                                    unsigned long long* hist, long long* bcnt);
 cudaError_t launch_masked_bin_scatter(const LaunchCtx&, const MaskedD&, long long nrows, BinCfg cfg,
-                                      unsigned long long* cursor, int* rows);
+                                      const unsigned long long* cursor, const long long* bofs, int* rows);
 cudaError_t launch_masked(const LaunchCtx&, const MaskedD&, const MaskedLaunch&);
 
 size_t masked_global_chunk_bytes(long long slots, int dtype);

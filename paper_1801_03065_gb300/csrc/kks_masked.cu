@@ -584,65 +584,68 @@ __global__ void __launch_bounds__(256, 4) k_masked_thread(MaskedD M, const int* 
   }
 }
 
-// work_i = sum over j in X(i,:) of |Y(j,:)|, then bins from (|S(i,:)|, work_i)
-__global__ void k_masked_bins(MaskedD M, long long nrows, int phase, BinCfg cfg, unsigned long long* hist,
-                              unsigned long long* cursor, int* rows) {
+// work_i = sum over j in X(i,:) of |Y(j,:)|, then the bin from (|S(i,:)|,
+// work_i); -1 for rows without work and for invalid rows (reported when
+// `report`, which turns the call's status into SPGEMM_ERR_BAD_INDEX).
+__device__ __forceinline__ int masked_row_bin(const MaskedD& M, long long i, const BinCfg& cfg, bool report) {
+  long long w = 0;
+  const long long a0 = rp_at(M.X, i), a1 = rp_at(M.X, i + 1);
+  bool ok = a0 >= 0 && a0 <= a1 && a1 <= M.X.nnz;
+  for (long long p = a0; ok && p < a1; ++p) {
+    const int j = M.X.cj[p];
+    if ((unsigned long long)(unsigned)j >= (unsigned long long)M.X.ncols) {
+      ok = false;
+      break;
+    }
+    const long long bs = rp_at(M.Y, j), be = rp_at(M.Y, j + 1);
+    if (bs < 0 || bs > be || be > M.Y.nnz) {
+      ok = false;
+      break;
+    }
+    w += be - bs;
+  }
+  if (!ok) {
+    if (report) dev_fail(M.status, kDevBadIndex, 21, i);
+    return -1;
+  }
+  const long long s = M.Sp[i + 1] - M.Sp[i];
+  int bin = choose_bin(s, w > 0 ? w : (s > 0 ? 1 : 0), M.Y.ncols, (M.Y.ncols + 31) >> 5, cfg);
+  if (bin_cls(bin) == kClsNone) return -1;
+  // thread-per-row rows: staged loads once Y rows average more than 2 entries
+  if (bin_cls(bin) == kClsT1 && w > 2 * (a1 - a0)) bin = bin_id(kClsT1, 1);
+  return bin;
+}
+
+// Stable binning of the pattern's rows (as the product's row binning).
+__global__ void __launch_bounds__(kBinThreads) k_masked_bin_count(MaskedD M, long long nrows, BinCfg cfg,
+                                                                  unsigned long long* hist, long long* bcnt,
+                                                                  long long nblk) {
   __shared__ unsigned long long h[kNumBins];
-  if (phase == 0) {
-    for (int t = threadIdx.x; t < kNumBins; t += blockDim.x) h[t] = 0ull;
-    __syncthreads();
+  for (int t = threadIdx.x; t < kNumBins; t += blockDim.x) h[t] = 0ull;
+  __syncthreads();
+  const long long r0 = (long long)blockIdx.x * kBinRows;
+  const long long r1 = r0 + kBinRows < nrows ? r0 + kBinRows : nrows;
+  bin_block_count(r0, r1, [&](long long i) { return masked_row_bin(M, i, cfg, true); }, h);
+  __syncthreads();
+  for (int t = threadIdx.x; t < kNumBins; t += blockDim.x) {
+    bcnt[(long long)t * nblk + blockIdx.x] = (long long)h[t];
+    if (h[t]) atomicAdd(&hist[t], h[t]);
   }
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  const int lane = threadIdx.x & 31;
-  for (long long base = (long long)blockIdx.x * blockDim.x; base < nrows; base += stride) {
-    const long long i = base + threadIdx.x;
-    int bin = -1;
-    if (i < nrows) {
-      long long w = 0;
-      const long long a0 = rp_at(M.X, i), a1 = rp_at(M.X, i + 1);
-      bool ok = a0 >= 0 && a0 <= a1 && a1 <= M.X.nnz;
-      for (long long p = a0; ok && p < a1; ++p) {
-        const int j = M.X.cj[p];
-        if ((unsigned long long)(unsigned)j >= (unsigned long long)M.X.ncols) {
-          ok = false;
-          break;
-        }
-        const long long bs = rp_at(M.Y, j), be = rp_at(M.Y, j + 1);
-        if (bs < 0 || bs > be || be > M.Y.nnz) {
-          ok = false;
-          break;
-        }
-        w += be - bs;
-      }
-      const long long s = M.Sp[i + 1] - M.Sp[i];
-      if (!ok) {
-        // the row is not computed; the status word turns into SPGEMM_ERR_BAD_INDEX
-        if (phase == 0) dev_fail(M.status, kDevBadIndex, 21, i);
-      } else {
-        bin = choose_bin(s, w > 0 ? w : (s > 0 ? 1 : 0), M.Y.ncols, (M.Y.ncols + 31) >> 5, cfg);
-        if (bin_cls(bin) == kClsNone) bin = -1;
-        // thread-per-row rows: staged loads once Y rows average more than 2 entries
-        if (bin >= 0 && bin_cls(bin) == kClsT1 && w > 2 * (a1 - a0)) bin = bin_id(kClsT1, 1);
-      }
-    }
-    const unsigned grp = __match_any_sync(0xffffffffu, bin);
-    const int leader = __ffs(grp) - 1;
-    if (phase == 0) {
-      if (bin >= 0 && lane == leader) atomicAdd(&h[bin], (unsigned long long)__popc(grp));
-    } else {
-      unsigned long long p = 0;
-      if (bin >= 0 && lane == leader) p = atomicAdd(&cursor[bin], (unsigned long long)__popc(grp));
-      p = __shfl_sync(0xffffffffu, p, leader);
-      unsigned lt;
-      asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
-      if (bin >= 0) rows[p + __popc(grp & lt)] = (int)i;
-    }
+}
+
+__global__ void __launch_bounds__(kBinThreads) k_masked_bin_list(MaskedD M, long long nrows, BinCfg cfg,
+                                                                 const unsigned long long* cursor,
+                                                                 const long long* bofs, long long nblk, int* rows) {
+  __shared__ long long run[kNumBins];
+  __shared__ int wcnt[kBinThreads / 32][kNumBins];
+  for (int t = threadIdx.x; t < kNumBins; t += blockDim.x) {
+    run[t] = (long long)cursor[t] + bofs[(long long)t * nblk + blockIdx.x] - bofs[(long long)t * nblk];
+    for (int w = 0; w < kBinThreads / 32; ++w) wcnt[w][t] = 0;
   }
-  if (phase == 0) {
-    __syncthreads();
-    for (int t = threadIdx.x; t < kNumBins; t += blockDim.x)
-      if (h[t]) atomicAdd(&hist[t], h[t]);
-  }
+  __syncthreads();
+  const long long r0 = (long long)blockIdx.x * kBinRows;
+  const long long r1 = r0 + kBinRows < nrows ? r0 + kBinRows : nrows;
+  bin_block_list(r0, r1, [&](long long i) { return masked_row_bin(M, i, cfg, false); }, run, wcnt, rows);
 }
 
 // ---------------------------------------------------------------- transpose
@@ -754,7 +757,7 @@ cudaError_t run_masked_hash(const LaunchCtx& L, const MaskedD& M, const MaskedLa
   const size_t tb = msk_team_bytes<TW, VT>(T);
   int teams = 1;
   if (TW <= 32) {
-    teams = (int)((48 * 1024) / tb);
+    teams = (int)(kTeamSmemBudget / tb);
     int tmax = 256 / TW;
     if (teams > tmax) teams = tmax;
     if (teams < 1) teams = 1;
@@ -765,7 +768,8 @@ cudaError_t run_masked_hash(const LaunchCtx& L, const MaskedD& M, const MaskedLa
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   KKS_LAUNCHED();
-  kern<<<grid_cap(S.nrows, teams, L.num_sms, 64), TW * teams, smem, L.stream>>>(M, S.rows, S.nrows, S.logT, nullptr, 0);
+  kern<<<resident_grid(kern, TW * teams, smem, L.num_sms, (S.nrows + teams - 1) / teams), TW * teams, smem,
+         L.stream>>>(M, S.rows, S.nrows, S.logT, nullptr, 0);
   return cudaGetLastError();
 }
 
@@ -773,7 +777,7 @@ template <int TW, typename VT>
 cudaError_t run_masked_warp(const LaunchCtx& L, const MaskedD& M, const MaskedLaunch& S) {
   const int T = 1 << S.logT;
   const size_t tb = mskw_team_bytes<TW, VT>(T);
-  int teams = (int)((48 * 1024) / tb);
+  int teams = (int)(kTeamSmemBudget / tb);
   const int tmax = 256 / TW;
   if (teams > tmax) teams = tmax;
   if (teams < 1) teams = 1;
@@ -783,7 +787,8 @@ cudaError_t run_masked_warp(const LaunchCtx& L, const MaskedD& M, const MaskedLa
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   KKS_LAUNCHED();
-  kern<<<grid_cap(S.nrows, teams, L.num_sms, 64), TW * teams, smem, L.stream>>>(M, S.rows, S.nrows, S.logT);
+  kern<<<resident_grid(kern, TW * teams, smem, L.num_sms, (S.nrows + teams - 1) / teams), TW * teams, smem,
+         L.stream>>>(M, S.rows, S.nrows, S.logT);
   return cudaGetLastError();
 }
 
@@ -791,7 +796,7 @@ template <int TW, typename VT>
 cudaError_t run_masked_pos(const LaunchCtx& L, const MaskedD& M, const MaskedLaunch& S) {
   const int T = 1 << S.logT;
   const size_t tb = mskp_team_bytes<TW, VT>(T);
-  int teams = (int)((48 * 1024) / tb);
+  int teams = (int)(kTeamSmemBudget / tb);
   const int tmax = 256 / TW;
   if (teams > tmax) teams = tmax;
   if (teams < 1) teams = 1;
@@ -801,7 +806,8 @@ cudaError_t run_masked_pos(const LaunchCtx& L, const MaskedD& M, const MaskedLau
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   KKS_LAUNCHED();
-  kern<<<grid_cap(S.nrows, teams, L.num_sms, 64), TW * teams, smem, L.stream>>>(M, S.rows, S.nrows, S.logT);
+  kern<<<resident_grid(kern, TW * teams, smem, L.num_sms, (S.nrows + teams - 1) / teams), TW * teams, smem,
+         L.stream>>>(M, S.rows, S.nrows, S.logT);
   return cudaGetLastError();
 }
 
@@ -862,18 +868,20 @@ size_t masked_team_bytes(int cls, int logT, int dtype) {
 }
 
 cudaError_t launch_masked_bin_count(const LaunchCtx& L, const MaskedD& M, long long nrows, BinCfg cfg,
-                                    unsigned long long* hist) {
+                                    unsigned long long* hist, long long* bcnt) {
   if (nrows <= 0) return cudaSuccess;
+  const long long nblk = bin_blocks(nrows);
   KKS_LAUNCHED();
-  k_masked_bins<<<grid_cap(nrows, 256, L.num_sms, 8), 256, 0, L.stream>>>(M, nrows, 0, cfg, hist, nullptr, nullptr);
+  k_masked_bin_count<<<(unsigned)nblk, kBinThreads, 0, L.stream>>>(M, nrows, cfg, hist, bcnt, nblk);
   return cudaGetLastError();
 }
 
 cudaError_t launch_masked_bin_scatter(const LaunchCtx& L, const MaskedD& M, long long nrows, BinCfg cfg,
-                                      unsigned long long* cursor, int* rows) {
+                                      const unsigned long long* cursor, const long long* bofs, int* rows) {
   if (nrows <= 0) return cudaSuccess;
+  const long long nblk = bin_blocks(nrows);
   KKS_LAUNCHED();
-  k_masked_bins<<<grid_cap(nrows, 256, L.num_sms, 8), 256, 0, L.stream>>>(M, nrows, 1, cfg, nullptr, cursor, rows);
+  k_masked_bin_list<<<(unsigned)nblk, kBinThreads, 0, L.stream>>>(M, nrows, cfg, cursor, bofs, nblk, rows);
   return cudaGetLastError();
 }
 

@@ -861,7 +861,7 @@ cudaError_t run_hash(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
   const size_t tb = num_team_bytes<TW, VT>(T);
   int teams = 1;
   if (TW <= 32) {
-    teams = (int)((48 * 1024) / tb);
+    teams = (int)(kTeamSmemBudget / tb);
     int tmax = 256 / TW;
     if (teams > tmax) teams = tmax;
     if (teams < 1) teams = 1;
@@ -881,11 +881,9 @@ cudaError_t run_hash(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
   auto kern = k_num_hash<TW, VT>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
-  long long grid = (S.nrows + teams - 1) / teams;
-  long long cap = (long long)L.num_sms * 64;
-  if (grid > cap) grid = cap;
+  const unsigned grid = resident_grid(kern, TW * teams, smem, L.num_sms, (S.nrows + teams - 1) / teams);
   KKS_LAUNCHED();
-  kern<<<(unsigned)grid, TW * teams, smem, L.stream>>>(P, S.rows, S.nrows, S.logT, kw_cap);
+  kern<<<grid, TW * teams, smem, L.stream>>>(P, S.rows, S.nrows, S.logT, kw_cap);
   return cudaGetLastError();
 }
 
@@ -893,7 +891,7 @@ template <int TW, typename VT>
 cudaError_t run_warp(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
   const int T = 1 << S.logT;
   const size_t tb = warp_team_bytes<TW, VT>(T);
-  int teams = (int)((48 * 1024) / tb);
+  int teams = (int)(kTeamSmemBudget / tb);
   const int tmax = 256 / TW;
   if (teams > tmax) teams = tmax;
   if (teams < 1) teams = 1;
@@ -902,11 +900,9 @@ cudaError_t run_warp(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
   auto kern = k_num_warp<TW, VT>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
-  long long grid = (S.nrows + teams - 1) / teams;
-  const long long cap = (long long)L.num_sms * 64;
-  if (grid > cap) grid = cap;
+  const unsigned grid = resident_grid(kern, TW * teams, smem, L.num_sms, (S.nrows + teams - 1) / teams);
   KKS_LAUNCHED();
-  kern<<<(unsigned)grid, TW * teams, smem, L.stream>>>(P, S.rows, S.nrows, S.logT);
+  kern<<<grid, TW * teams, smem, L.stream>>>(P, S.rows, S.nrows, S.logT);
   return cudaGetLastError();
 }
 
@@ -914,7 +910,7 @@ template <int TW, typename VT>
 cudaError_t run_cpn(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
   const int T = 1 << S.logT;
   const size_t tb = cpn_team_bytes<TW, VT>(T);
-  int teams = (int)((48 * 1024) / tb);
+  int teams = (int)(kTeamSmemBudget / tb);
   const int tmax = 256 / TW;
   if (teams > tmax) teams = tmax;
   if (teams < 1) teams = 1;
@@ -923,11 +919,9 @@ cudaError_t run_cpn(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
   auto kern = k_num_cpn<TW, VT>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
-  long long grid = (S.nrows + teams - 1) / teams;
-  const long long cap = (long long)L.num_sms * 64;
-  if (grid > cap) grid = cap;
+  const unsigned grid = resident_grid(kern, TW * teams, smem, L.num_sms, (S.nrows + teams - 1) / teams);
   KKS_LAUNCHED();
-  kern<<<(unsigned)grid, TW * teams, smem, L.stream>>>(P, S.rows, S.nrows, S.logT);
+  kern<<<grid, TW * teams, smem, L.stream>>>(P, S.rows, S.nrows, S.logT);
   return cudaGetLastError();
 }
 

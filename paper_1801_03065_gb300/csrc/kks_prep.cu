@@ -7,6 +7,9 @@
 // into column-set indices CSI = col >> 5 with a 32-bit set CS; a first pass
 // counts the compressed row lengths so the compressed product count can decide
 // whether compressing pays (more than a 15 % reduction), a second pass fills.
+#include <mutex>
+#include <vector>
+
 #include "kks_internal.h"
 
 namespace kks {
@@ -290,41 +293,50 @@ struct RowBin {
   }
 };
 
-__global__ void __launch_bounds__(kBlock) k_bin_count(ProbD P, long long totalA, int phase, const long long* rf,
-                                                      const long long* rfc, const long long* rowsize, BinCfg cfg,
-                                                      unsigned long long* hist) {
+// Binning is stable: block b takes the contiguous rows [b * kBinRows,
+// (b + 1) * kBinRows), counts them per bin into bcnt[bin * nblk + b], and the
+// scatter places them in row order after the rows of earlier blocks, so each
+// bin's list keeps the order of A's rows and concurrently running teams touch
+// neighbouring rows of B.
+__global__ void __launch_bounds__(kBinThreads) k_bin_count(ProbD P, long long totalA, int phase, const long long* rf,
+                                                           const long long* rfc, const long long* rowsize,
+                                                           BinCfg cfg, unsigned long long* hist, long long* bcnt,
+                                                           long long nblk) {
   __shared__ unsigned long long h[kNumBins];
   for (int t = threadIdx.x; t < kNumBins; t += blockDim.x) h[t] = 0ull;
   __syncthreads();
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long base = (long long)blockIdx.x * blockDim.x; base < totalA; base += stride) {
-    const long long g = base + threadIdx.x;
-    const int bin = (g < totalA) ? RowBin::get(P, g, phase, rf, rfc, rowsize, cfg) : -1;
-    const unsigned grp = __match_any_sync(0xffffffffu, bin);
-    if (bin >= 0 && (__ffs(grp) - 1) == (threadIdx.x & 31)) atomicAdd(&h[bin], (unsigned long long)__popc(grp));
-  }
+  const long long r0 = (long long)blockIdx.x * kBinRows;
+  const long long r1 = r0 + kBinRows < totalA ? r0 + kBinRows : totalA;
+  bin_block_count(r0, r1, [&](long long g) { return RowBin::get(P, g, phase, rf, rfc, rowsize, cfg); }, h);
   __syncthreads();
-  for (int t = threadIdx.x; t < kNumBins; t += blockDim.x)
+  for (int t = threadIdx.x; t < kNumBins; t += blockDim.x) {
+    bcnt[(long long)t * nblk + blockIdx.x] = (long long)h[t];
     if (h[t]) atomicAdd(&hist[t], h[t]);
+  }
 }
 
-__global__ void __launch_bounds__(kBlock) k_bin_scatter(ProbD P, long long totalA, int phase, const long long* rf,
-                                                        const long long* rfc, long long* rowsize, BinCfg cfg,
-                                                        unsigned long long* cursor, int* rows) {
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  const int lane = threadIdx.x & 31;
-  for (long long base = (long long)blockIdx.x * blockDim.x; base < totalA; base += stride) {
-    const long long g = base + threadIdx.x;
-    const int bin = (g < totalA) ? RowBin::get(P, g, phase, rf, rfc, rowsize, cfg) : -1;
-    if (bin >= 0 && bin_cls(bin) == kClsNone && phase != 1) rowsize[g] = 0;
-    const int key = (bin >= 0 && bin_cls(bin) != kClsNone) ? bin : -1;
-    const unsigned grp = __match_any_sync(0xffffffffu, key);
-    const int leader = __ffs(grp) - 1;
-    unsigned long long pos = 0;
-    if (key >= 0 && lane == leader) pos = atomicAdd(&cursor[key], (unsigned long long)__popc(grp));
-    pos = __shfl_sync(0xffffffffu, pos, leader);
-    if (key >= 0) rows[pos + __popc(grp & (unsigned)lanemask_lt())] = (int)g;
+// cursor[bin]: first slot of the bin's list; bofs: exclusive scan of bcnt.
+// Rows of the class-none bin are not listed (symbolic: their size is 0).
+__global__ void __launch_bounds__(kBinThreads) k_bin_scatter(ProbD P, long long totalA, int phase,
+                                                             const long long* rf, const long long* rfc,
+                                                             long long* rowsize, BinCfg cfg,
+                                                             const unsigned long long* cursor, const long long* bofs,
+                                                             long long nblk, int* rows) {
+  __shared__ long long run[kNumBins];
+  __shared__ int wcnt[kBinThreads / 32][kNumBins];
+  for (int t = threadIdx.x; t < kNumBins; t += blockDim.x) {
+    run[t] = (long long)cursor[t] + bofs[(long long)t * nblk + blockIdx.x] - bofs[(long long)t * nblk];
+    for (int w = 0; w < kBinThreads / 32; ++w) wcnt[w][t] = 0;
   }
+  __syncthreads();
+  const long long r0 = (long long)blockIdx.x * kBinRows;
+  const long long r1 = r0 + kBinRows < totalA ? r0 + kBinRows : totalA;
+  auto key = [&](long long g) {
+    const int bin = RowBin::get(P, g, phase, rf, rfc, rowsize, cfg);
+    if (bin >= 0 && bin_cls(bin) == kClsNone && phase != 1) rowsize[g] = 0;
+    return (bin >= 0 && bin_cls(bin) != kClsNone) ? bin : -1;
+  };
+  bin_block_list(r0, r1, key, run, wcnt, rows);
 }
 
 // -------------------------------------------------------------- C row pointers
@@ -371,6 +383,29 @@ __global__ void k_empty_instances(ProbD P, unsigned long long* inst_out) {
 }  // namespace
 
 // ============================================================== launchers
+int resident_per_sm(const void* kernel, int threads, size_t smem) {
+  struct Entry {
+    const void* k;
+    int dev, threads;
+    size_t smem;
+    int per_sm;
+  };
+  static std::mutex mu;
+  static std::vector<Entry> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  for (const Entry& e : cache)
+    if (e.k == kernel && e.dev == dev && e.threads == threads && e.smem == smem) return e.per_sm;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess || n < 1) {
+    cudaGetLastError();
+    n = 1;
+  }
+  cache.push_back({kernel, dev, threads, smem, n});
+  return n;
+}
+
 cudaError_t launch_compress_count(const LaunchCtx& L, const ProbD& P, long long totalB, long long* cnt) {
   if (totalB <= 0) return cudaSuccess;
   int grid = grid_for(totalB, kBlock / 8, L.num_sms);
@@ -421,22 +456,23 @@ cudaError_t launch_scan(const LaunchCtx& L, const long long* in, long long* out,
 }
 
 cudaError_t launch_bin_count(const LaunchCtx& L, const ProbD& P, long long totalA, int phase, const long long* rf,
-                             const long long* rfc, const long long* rowsize, BinCfg cfg, unsigned long long* hist) {
+                             const long long* rfc, const long long* rowsize, BinCfg cfg, unsigned long long* hist,
+                             long long* bcnt) {
   if (totalA <= 0) return cudaSuccess;
-  int grid = grid_for(totalA, kBlock, L.num_sms, 8);
+  const long long nblk = bin_blocks(totalA);
   KKS_LAUNCHED();
-  k_bin_count<<<grid, kBlock, 0, L.stream>>>(P, totalA, phase, rf, rfc, rowsize, cfg, hist);
+  k_bin_count<<<(unsigned)nblk, kBinThreads, 0, L.stream>>>(P, totalA, phase, rf, rfc, rowsize, cfg, hist, bcnt, nblk);
   return cudaGetLastError();
 }
 
 cudaError_t launch_bin_scatter(const LaunchCtx& L, const ProbD& P, long long totalA, int phase, const long long* rf,
                                const long long* rfc, const long long* rowsize, BinCfg cfg,
-                               unsigned long long* cursor, int* rows) {
+                               const unsigned long long* cursor, const long long* bofs, int* rows) {
   if (totalA <= 0) return cudaSuccess;
-  int grid = grid_for(totalA, kBlock, L.num_sms, 8);
+  const long long nblk = bin_blocks(totalA);
   KKS_LAUNCHED();
-  k_bin_scatter<<<grid, kBlock, 0, L.stream>>>(P, totalA, phase, rf, rfc, const_cast<long long*>(rowsize), cfg,
-                                               cursor, rows);
+  k_bin_scatter<<<(unsigned)nblk, kBinThreads, 0, L.stream>>>(P, totalA, phase, rf, rfc, const_cast<long long*>(rowsize),
+                                                         cfg, cursor, bofs, nblk, rows);
   return cudaGetLastError();
 }
 

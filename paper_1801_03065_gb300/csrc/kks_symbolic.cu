@@ -254,21 +254,13 @@ cudaError_t set_smem(K kernel, size_t bytes) {
   return cudaSuccess;
 }
 
-inline unsigned hash_grid(long long nrows, int teams_per_cta, int num_sms) {
-  long long g = (nrows + teams_per_cta - 1) / teams_per_cta;
-  long long cap = (long long)num_sms * 64;
-  if (g > cap) g = cap;
-  if (g < 1) g = 1;
-  return (unsigned)g;
-}
-
 template <int TW, bool COMP>
 cudaError_t run_hash(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, long long* rowsize) {
   const int T = 1 << S.logT;
   const size_t tb = sym_team_bytes<TW, COMP>(T);
   int teams = 1;
   if (TW <= 32) {
-    teams = (int)((48 * 1024) / tb);
+    teams = (int)(kTeamSmemBudget / tb);
     int tmax = 256 / TW;
     if (teams > tmax) teams = tmax;
     if (teams < 1) teams = 1;
@@ -279,8 +271,8 @@ cudaError_t run_hash(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, lon
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   KKS_LAUNCHED();
-  kern<<<hash_grid(S.nrows, teams, L.num_sms), TW * teams, smem, L.stream>>>(P, S.rows, S.nrows, S.logT, -1,
-                                                                            nullptr, 0, rowsize);
+  kern<<<resident_grid(kern, TW * teams, smem, L.num_sms, (S.nrows + teams - 1) / teams), TW * teams, smem,
+         L.stream>>>(P, S.rows, S.nrows, S.logT, -1, nullptr, 0, rowsize);
   return cudaGetLastError();
 }
 
@@ -288,7 +280,7 @@ template <int TW, bool COMP>
 cudaError_t run_warp(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, long long* rowsize) {
   const int T = 1 << S.logT;
   const size_t tb = symw_team_bytes<TW, COMP>(T);
-  int teams = (int)((48 * 1024) / tb);
+  int teams = (int)(kTeamSmemBudget / tb);
   const int tmax = 256 / TW;
   if (teams > tmax) teams = tmax;
   if (teams < 1) teams = 1;
@@ -298,7 +290,8 @@ cudaError_t run_warp(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, lon
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   KKS_LAUNCHED();
-  kern<<<hash_grid(S.nrows, teams, L.num_sms), TW * teams, smem, L.stream>>>(P, S.rows, S.nrows, S.logT, rowsize);
+  kern<<<resident_grid(kern, TW * teams, smem, L.num_sms, (S.nrows + teams - 1) / teams), TW * teams, smem,
+         L.stream>>>(P, S.rows, S.nrows, S.logT, rowsize);
   return cudaGetLastError();
 }
 
