@@ -176,6 +176,7 @@ class StencilStep:
         rp, nnz = self.hAP.symbolic(Ad, Pd, C_rowptr=self.rpAP)
         self.CAP = self._out(self.CAP, rp, nnz, t.float64)
         AP = self.hAP.numeric(Ad, Pd, rp, nnz, self.CAP.colidx, self.CAP.values)
+        self.AP = AP
         Pt = self.Pt[0]
         rp, nnz = self.hRAP.symbolic(Pt, AP, C_rowptr=self.rpRAP)
         self.CRAP = self._out(self.CRAP, rp, nnz, t.float64)
@@ -274,6 +275,20 @@ def run_ours(args):
     sym = lambda: S.hAA.symbolic(Ad, Ad, C_rowptr=S.rpAA)
     t_sym = statistics.mean(time_region(torch, sym, max(args.steps, 5)))
     S.hAA.sync()
+    # the other products of the step, one phase at a time (each on its own handle)
+    Pd, Pt, AP = S.Pd, S.Pt[0], S.AP
+    others = {
+        "Pt_transpose": lambda: S.hT.transpose(Pd, out=S.Pt),
+        "AP_symbolic": lambda: S.hAP.symbolic(Ad, Pd, C_rowptr=S.rpAP),
+        "AP_numeric": lambda: S.hAP.numeric(Ad, Pd, S.CAP.rowptr, S.CAP.nnz, S.CAP.colidx, S.CAP.values),
+        "RAP_symbolic": lambda: S.hRAP.symbolic(Pt, AP, C_rowptr=S.rpRAP),
+        "RAP_numeric": lambda: S.hRAP.numeric(Pt, AP, S.CRAP.rowptr, S.CRAP.nnz, S.CRAP.colidx, S.CRAP.values),
+    }
+    t_other = {}
+    for name, fn in others.items():
+        fn()
+        t_other[name] = round(statistics.mean(time_region(torch, fn, max(args.steps, 5))), 4)
+    S.hAA.sync()
 
     nnzC = stAA["nnzC"]
     bytes_num = 2 * csr_bytes(A.nrows, A.nnz, 8) + csr_bytes(A.nrows, nnzC, 8)
@@ -295,8 +310,8 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (A = %.0f MB, C = %.0f MB)" % (
                        csr_bytes(A.nrows, A.nnz, 8) / 1e6, csr_bytes(A.nrows, nnzC, 8) / 1e6),
                    "parallelism": "one independent problem per GPU (row blocks), no data-path collective"},
-        "phases_ms": {"AA_symbolic": round(t_sym, 4), "AA_numeric": round(t_num, 4),
-                      "AA_numeric_reuse_probe": round(t_reuse, 4)},
+        "phases_ms": dict({"AA_symbolic": round(t_sym, 4), "AA_numeric": round(t_num, 4),
+                           "AA_numeric_reuse_probe": round(t_reuse, 4)}, **t_other),
         "numeric_reuse": {"value": round(2.0 * stAA["f_m"] / (t_num * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
                           "probe_only_value": round(2.0 * stAA["f_m"] / (t_reuse * 1e-3) / 1e9, 3),
                           "product": "A*A"},

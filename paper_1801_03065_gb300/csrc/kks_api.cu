@@ -333,6 +333,9 @@ BinCfg sym_cfg(kks_handle* h, int comp) {
   c.dense_max_kwords = ((long long)h->max_smem - 12 * 1024) / 4;
   // the bitmap (kw words) is preferred once the hash table would be as large
   c.dense_ratio = comp ? 4 : 64;
+  // one thread per row when the row has at most kT1SymKeys products
+  c.t1_max_keys = kT1SymKeys;
+  c.t1_max_work = kT1SymKeys;
   clamp_cfg(h, c);
   return c;
 }
@@ -362,6 +365,9 @@ BinCfg num_cfg(kks_handle* h, int dtype, long long kmax) {
   c.dense_ratio = dtype == 1 ? 0 : 8;
   long long pool_limit = h->opt.pool_limit_bytes > 0 ? h->opt.pool_limit_bytes : (8ll << 30);
   if (kmax * (dtype == 1 ? 8 : 4) > pool_limit) c.dense_ok = 0;
+  // one thread per row: at most kT1MaxKeys columns of C and 64 products
+  c.t1_max_keys = kT1MaxKeys;
+  c.t1_max_work = 64;
   clamp_cfg(h, c);
   return c;
 }
@@ -698,7 +704,9 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
   }
   // heaviest classes first so the long rows start early
   std::stable_sort(h->num_bins.begin(), h->num_bins.end(), [](const BinRun& a, const BinRun& b) {
-    auto key = [](const BinRun& r) { return r.cls == kClsSpill ? 7 : r.cls == kClsDense ? 6 : r.cls; };
+    auto key = [](const BinRun& r) {
+      return r.cls == kClsSpill ? 7 : r.cls == kClsDense ? 6 : r.cls == kClsT1 ? 0 : r.cls;
+    };
     return key(a) * 64 + a.logT > key(b) * 64 + b.logT;
   });
   const int vt = dtype == 1 ? 8 : 4;

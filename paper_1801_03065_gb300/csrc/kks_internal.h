@@ -31,7 +31,8 @@ enum TeamClass : int {
   kClsT1 = 7,      // one thread per row, keys and accumulators in registers
   kNumClasses = 8,
 };
-constexpr int kT1MaxKeys = 8;   // rows of class T1 have at most this many keys
+constexpr int kT1MaxKeys = 8;   // rows of class T1 have at most this many keys (numeric, masked)
+constexpr int kT1SymKeys = 32;  // symbolic T1 rows: at most this many products, hence keys
 constexpr int kBinsPerClass = 32;
 constexpr int kNumBins = kNumClasses * kBinsPerClass;
 
@@ -55,7 +56,8 @@ struct BinCfg {
   int force_cls;           // >0: every non-empty row goes to this class
   int force_logT;          // with force_cls: table size used for every row
   int slots_log2;          // table slots per key bound, log2 (1: at most 50 % load)
-  long long t1_max_work;   // > 0: rows with u <= kT1MaxKeys and work <= this go to class T1
+  long long t1_max_work;   // > 0: rows with u <= t1_max_keys and work <= this go to class T1
+  int t1_max_keys;         // 0: kT1MaxKeys
 };
 
 // kk: the key range the dense test compares against (k, or k/32 compressed);
@@ -72,7 +74,8 @@ __host__ __device__ inline int choose_bin(long long u, long long work, long long
     if (logT <= c.force_logT) return bin_id(c.force_cls, c.force_logT);
     return bin_id(kClsSpill, logT);
   }
-  if (c.t1_max_work > 0 && u <= kT1MaxKeys && work <= c.t1_max_work) return bin_id(kClsT1, 0);
+  if (c.t1_max_work > 0 && u <= (c.t1_max_keys > 0 ? c.t1_max_keys : kT1MaxKeys) && work <= c.t1_max_work)
+    return bin_id(kClsT1, 0);
   bool dense_fit = c.dense_ok && kwords <= c.dense_max_kwords;
   if (dense_fit && (logT > c.cta_max_logT || u * c.dense_ratio >= kk)) return bin_id(kClsDense, 0);
   if (logT <= c.w8_max_logT && work <= c.w8_max_work) return bin_id(kClsW8, logT);

@@ -639,6 +639,98 @@ __global__ void __launch_bounds__(256, 4) k_num_cpn(ProbD P, const int* __restri
   }
 }
 
+// One thread per row for rows of C with at most kT1MaxKeys columns and few
+// products (Thread-Sequential with a team of one, Section 3.1.1): the keys
+// stay in registers, a product is matched with integer compares and goes to
+// one accumulator in the thread's column of shared memory (one FP64
+// instruction per product), and the row is written in column order from the
+// ranks of its keys.
+template <typename VT>
+__global__ void __launch_bounds__(256, 3) k_num_thread(ProbD P, const int* __restrict__ rows, long long nrows) {
+  __shared__ VT accs[kT1MaxKeys][256];
+  const int tid = threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long r = (long long)blockIdx.x * blockDim.x + tid; r < nrows; r += stride) {
+    const long long g = rows[r];
+    const int b = inst_of(P.arow0s, P.ninst, g);
+    const InstD& I = P.inst[b];
+    const long long i = g - I.arow0;
+    const long long c0 = I.Crp[i];
+    const int s = (int)(I.Crp[i + 1] - c0);
+    const long long a0 = rp_at(I.A, i), a1 = rp_at(I.A, i + 1);
+    const VT* __restrict__ Ax = reinterpret_cast<const VT*>(I.A.vx);
+    const VT* __restrict__ Bx = reinterpret_cast<const VT*>(I.B.vx);
+    const int* __restrict__ Bj = I.B.cj;
+    int key[kT1MaxKeys];
+#pragma unroll
+    for (int t = 0; t < kT1MaxKeys; ++t) {
+      key[t] = -1;
+      accs[t][tid] = VT(0);
+    }
+    int n = 0;
+    bool over = false;
+    auto add = [&](int c, VT a, VT y) {
+      int hit = -1;
+#pragma unroll
+      for (int t = 0; t < kT1MaxKeys; ++t) hit = (key[t] == c) ? t : hit;
+      if (hit < 0) {
+        if (n < kT1MaxKeys) {
+#pragma unroll
+          for (int t = 0; t < kT1MaxKeys; ++t) key[t] = (t == n) ? c : key[t];
+          hit = n++;
+        } else {
+          over = true;
+        }
+      }
+      if (hit >= 0) accs[hit][tid] = fma_acc(a, y, accs[hit][tid]);
+    };
+    constexpr int kX = 4, kQ = 4;
+    for (long long c = a0; c < a1; c += kX) {
+      long long qs[kX], qe[kX];
+      VT a[kX];
+#pragma unroll
+      for (int u = 0; u < kX; ++u) {
+        const bool ok = c + u < a1;
+        const int j = ok ? I.A.cj[c + u] : -1;
+        a[u] = ok ? Ax[c + u] : VT(0);
+        qs[u] = j >= 0 ? rp_at(I.B, j) : 0;
+        qe[u] = j >= 0 ? rp_at(I.B, j + 1) : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < kX; ++u) {
+        for (long long q = qs[u]; q < qe[u]; q += kQ) {
+          int cc[kQ];
+          VT y[kQ];
+#pragma unroll
+          for (int v = 0; v < kQ; ++v) {
+            const bool ok = q + v < qe[u];
+            cc[v] = ok ? Bj[q + v] : -1;
+            y[v] = ok ? Bx[q + v] : VT(0);
+          }
+#pragma unroll
+          for (int v = 0; v < kQ; ++v)
+            if (cc[v] >= 0) add(cc[v], a[u], y[v]);
+        }
+      }
+    }
+    if (over || n != s) dev_fail(P.status, over ? kDevTableFull : kDevRowSizeMismatch, 29, g);
+    int* __restrict__ Cj = I.Cj;
+    VT* __restrict__ Cx = reinterpret_cast<VT*>(I.Cx);
+#pragma unroll
+    for (int t = 0; t < kT1MaxKeys; ++t) {
+      if (t < n) {
+        int rk = 0;
+#pragma unroll
+        for (int t2 = 0; t2 < kT1MaxKeys; ++t2) rk += (t2 < n && key[t2] < key[t]) ? 1 : 0;
+        if (rk < s) {
+          Cj[c0 + rk] = key[t];
+          Cx[c0 + rk] = accs[t][tid];
+        }
+      }
+    }
+  }
+}
+
 template <int TW, typename VT>
 __global__ void __launch_bounds__(TW) k_num_dense(ProbD P, const int* __restrict__ rows, long long nrows,
                                                   long long kw_max, VT* pool, long long kmax) {
@@ -962,8 +1054,17 @@ cudaError_t run_spill(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
 }
 
 template <typename VT>
+cudaError_t run_thread(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
+  auto kern = k_num_thread<VT>;
+  KKS_LAUNCHED();
+  kern<<<resident_grid(kern, 256, 0, L.num_sms, (S.nrows + 255) / 256), 256, 0, L.stream>>>(P, S.rows, S.nrows);
+  return cudaGetLastError();
+}
+
+template <typename VT>
 cudaError_t dispatch(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
   switch (S.cls) {
+    case kClsT1: return run_thread<VT>(L, P, S);
     case kClsW8: return S.positions ? run_cpn<8, VT>(L, P, S) : run_warp<8, VT>(L, P, S);
     case kClsW32: return S.positions ? run_cpn<32, VT>(L, P, S) : run_warp<32, VT>(L, P, S);
     case kClsC256: return run_hash<256, VT>(L, P, S);

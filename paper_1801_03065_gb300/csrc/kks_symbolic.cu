@@ -6,6 +6,7 @@
 // On the compressed B (Section 3.2) the keys are column-set indices and the
 // accumulator ORs the 32-bit column sets, so the row size is the number of
 // set bits of the union.  Variants:
+//   k_sym_thread<COMP>          : one thread per row of at most 32 products
 //   k_sym_warp<TW, COMP>        : warp teams (8 or 32 lanes), shared LP table
 //                                 sized to hold the row, batched loads
 //   k_sym_hash<TW, COMP, false> : CTA teams, shared LP table sized to hold the row
@@ -194,6 +195,90 @@ __global__ void __launch_bounds__(256, 4) k_sym_warp(ProbD P, const int* __restr
   }
 }
 
+// One thread per row for rows with at most kT1SymKeys products
+// (Thread-Sequential with a team of one, Section 3.1.1): the row's distinct
+// keys (and, compressed, their column sets) go to a short list in the
+// thread's own column of shared memory, searched linearly.  Whole bins of
+// short rows are in flight at once, which hides their chains of dependent
+// loads; the loads of 4 entries of A(i,:) and of 4 keys at a time are issued
+// together.
+constexpr int kSymThreads = 128;
+
+template <bool COMP>
+__global__ void __launch_bounds__(kSymThreads) k_sym_thread(ProbD P, const int* __restrict__ rows, long long nrows,
+                                                            long long* __restrict__ rowsize) {
+  __shared__ int lk[kT1SymKeys][kSymThreads];
+  __shared__ unsigned lm[COMP ? kT1SymKeys : 1][kSymThreads];
+  const int tid = threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long r = (long long)blockIdx.x * blockDim.x + tid; r < nrows; r += stride) {
+    const long long g = rows[r];
+    const int b = inst_of(P.arow0s, P.ninst, g);
+    const InstD& I = P.inst[b];
+    const long long i = g - I.arow0;
+    const long long a0 = rp_at(I.A, i), a1 = rp_at(I.A, i + 1);
+    const long long brow0 = I.brow0;
+    const int* __restrict__ ksrc = COMP ? P.csi : I.B.cj;
+    int n = 0;
+    bool over = false;
+    auto add = [&](int key, unsigned m) {
+      int t = 0;
+      while (t < n && lk[t][tid] != key) ++t;
+      if (t < n) {
+        if (COMP) lm[t][tid] |= m;
+      } else if (n < kT1SymKeys) {
+        lk[n][tid] = key;
+        if (COMP) lm[n][tid] = m;
+        ++n;
+      } else {
+        over = true;
+      }
+    };
+    constexpr int kX = 4, kQ = 4;
+    for (long long c = a0; c < a1; c += kX) {
+      long long qs[kX], qe[kX];
+#pragma unroll
+      for (int u = 0; u < kX; ++u) {
+        const int j = c + u < a1 ? I.A.cj[c + u] : -1;
+        qs[u] = 0;
+        qe[u] = 0;
+        if (j >= 0) {
+          if (COMP) {
+            qs[u] = P.Bcp[brow0 + j];
+            qe[u] = P.Bcp[brow0 + j + 1];
+          } else {
+            qs[u] = rp_at(I.B, j);
+            qe[u] = rp_at(I.B, j + 1);
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kX; ++u) {
+        for (long long q = qs[u]; q < qe[u]; q += kQ) {
+          int kk[kQ];
+          unsigned mm[kQ];
+#pragma unroll
+          for (int v = 0; v < kQ; ++v) {
+            const bool ok = q + v < qe[u];
+            kk[v] = ok ? ksrc[q + v] : -1;
+            mm[v] = (COMP && ok) ? P.cs[q + v] : 0u;
+          }
+#pragma unroll
+          for (int v = 0; v < kQ; ++v)
+            if (kk[v] >= 0) add(kk[v], mm[v]);
+        }
+      }
+    }
+    if (over) dev_fail(P.status, kDevTableFull, 3, g);
+    long long cnt = n;
+    if (COMP) {
+      cnt = 0;
+      for (int t = 0; t < n; ++t) cnt += __popc(lm[t][tid]);
+    }
+    rowsize[g] = cnt;
+  }
+}
+
 template <int TW, bool COMP>
 __global__ void __launch_bounds__(TW) k_sym_dense(ProbD P, const int* __restrict__ rows, long long nrows,
                                                   long long kw_max, long long* __restrict__ rowsize) {
@@ -296,6 +381,15 @@ cudaError_t run_warp(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, lon
 }
 
 template <bool COMP>
+cudaError_t run_thread(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, long long* rowsize) {
+  auto kern = k_sym_thread<COMP>;
+  KKS_LAUNCHED();
+  kern<<<resident_grid(kern, kSymThreads, 0, L.num_sms, (S.nrows + kSymThreads - 1) / kSymThreads), kSymThreads, 0,
+         L.stream>>>(P, S.rows, S.nrows, rowsize);
+  return cudaGetLastError();
+}
+
+template <bool COMP>
 cudaError_t run_spill(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, long long* rowsize) {
   constexpr int TW = 1024;
   const int T = 1 << S.l1_logT;
@@ -336,6 +430,7 @@ cudaError_t run_dense(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, lo
 template <bool COMP>
 cudaError_t dispatch(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, long long* rowsize) {
   switch (S.cls) {
+    case kClsT1: return run_thread<COMP>(L, P, S, rowsize);
     case kClsW8: return run_warp<8, COMP>(L, P, S, rowsize);
     case kClsW32: return run_warp<32, COMP>(L, P, S, rowsize);
     case kClsC256: return run_hash<256, COMP>(L, P, S, rowsize);

@@ -541,3 +541,29 @@ def test_masked_stencil_sets_and_reuse(ops, pos):
         h.numeric_reuse(Ad, Ad, Cd)
         h.sync()
         assert_matches_oracle(A2, A2, Cd, np.float64)
+
+
+# ------------------------------------------------------------------ thread-per-row rows
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("comp", [0, 1])
+def test_thread_per_row_classes(ops, dtype, comp):
+    """Rows with at most 32 products (symbolic) and at most 8 columns of C
+    (numeric) run one thread per row; rows beyond either limit share the plan."""
+    rng = np.random.default_rng(21)
+    la = np.concatenate([rng.integers(0, 4, 1500), rng.integers(8, 40, 300)])
+    A = w.random_csr(1800, 700, lengths=la, seed=22, dtype=np.float64)
+    B = w.random_csr(700, 2500, 2.5, seed=23)
+    h, _, _, Cd = run(ops, A, B, dtype, compression=comp)
+    st = h.stats()
+    assert st["bin_rows_numeric"][7] > 0, "no row took the thread-per-row numeric kernel"
+    assert st["bin_rows_numeric"][1] + st["bin_rows_numeric"][2] > 0
+    assert_matches_oracle(A, B, Cd, dtype)
+
+
+def test_aggregation_product_thread_rows(ops):
+    """A * P with P a 3x3x3 aggregation: every B row holds one entry."""
+    A = w.stencil3d_27pt(15, seed=4)
+    P = w.aggregation(15, 3)
+    h, _, _, Cd = run(ops, A, P)
+    assert h.stats()["bin_rows_numeric"][7] == A.nrows
+    assert_matches_oracle(A, P, Cd, np.float64)
