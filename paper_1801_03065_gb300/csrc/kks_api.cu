@@ -558,7 +558,6 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
     P = prob(h);
     memcpy(up, h->inst.data(), sizeof(InstD) * count);
     KKS_CU(cudaMemcpyAsync(h->buf[kBufInst], up, sizeof(InstD) * count, cudaMemcpyHostToDevice, s));
-    KKS_CU(cudaMemsetAsync(h->buf[kBufCs], 0, sizeof(unsigned) * (nbc + 1), s));
     KKS_CU(launch_compress_fill(L, P, totalB, B<int>(h, kBufCsi), B<unsigned>(h, kBufCs)));
   }
 

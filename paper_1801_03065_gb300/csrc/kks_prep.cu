@@ -69,7 +69,9 @@ __global__ void __launch_bounds__(kBlock) k_compress_count(ProbD P, long long to
 }
 
 // Runs of equal CSI in row order become one compressed entry; rows with sorted
-// columns therefore get exactly one entry per distinct CSI.  cs must be zero.
+// columns therefore get exactly one entry per distinct CSI.  The chunk where a
+// run starts stores its bits and later chunks of the same run OR in theirs
+// (cs needs no clearing).
 template <int TW>
 __global__ void __launch_bounds__(kBlock) k_compress_fill(ProbD P, long long totalB, int* csi, unsigned* cs) {
   Team<TW> tm;
@@ -106,7 +108,10 @@ __global__ void __launch_bounds__(kBlock) k_compress_fill(ProbD P, long long tot
       }
       const bool next_head = (tm.lane + 1 < TW) && ((hb >> (tm.lane + 1)) & 1u);
       const bool tail = valid && (tm.lane == TW - 1 || p + 1 >= e || next_head);
-      if (tail) atomicOr(cs + ridx, v);
+      if (tail) {
+        if (hb & le) cs[ridx] = v;     // the run starts in this chunk
+        else atomicOr(cs + ridx, v);   // continuation of the previous chunk's last run
+      }
       run += __popc(hb);
       tm.sync();
     }
@@ -133,6 +138,8 @@ __global__ void __launch_bounds__(kBlock) k_row_stats(ProbD P, long long totalA,
   }
   __syncthreads();
   const bool single = (b_first == b_last);
+  // single-instance blocks: per-team totals in registers, one shared update per team
+  unsigned long long t_sum = 0, t_max = 0, t_csum = 0, t_cmax = 0;
   for (long long g = g0 + tm.id; g < g1; g += tm.per_cta) {
     const int b = single ? b_first : inst_of(P.arow0s, P.ninst, g);
     const InstD& I = P.inst[b];
@@ -163,10 +170,10 @@ __global__ void __launch_bounds__(kBlock) k_row_stats(ProbD P, long long totalA,
       rf[g] = f;
       if (rfc) rfc[g] = fc;
       if (single) {
-        atomicAdd(&acc[0], (unsigned long long)f);
-        atomicMax(&acc[1], (unsigned long long)f);
-        atomicAdd(&acc[2], (unsigned long long)fc);
-        atomicMax(&acc[3], (unsigned long long)fc);
+        t_sum += (unsigned long long)f;
+        t_max = t_max > (unsigned long long)f ? t_max : (unsigned long long)f;
+        t_csum += (unsigned long long)fc;
+        t_cmax = t_cmax > (unsigned long long)fc ? t_cmax : (unsigned long long)fc;
       } else {
         unsigned long long* st = inst_stats + 4ll * b;
         atomicAdd(st + 0, (unsigned long long)f);
@@ -175,6 +182,12 @@ __global__ void __launch_bounds__(kBlock) k_row_stats(ProbD P, long long totalA,
         atomicMax(st + 3, (unsigned long long)fc);
       }
     }
+  }
+  if (single && tm.lane == 0) {
+    atomicAdd(&acc[0], t_sum);
+    atomicMax(&acc[1], t_max);
+    atomicAdd(&acc[2], t_csum);
+    atomicMax(&acc[3], t_cmax);
   }
   __syncthreads();
   if (single && threadIdx.x == 0) {
