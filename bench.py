@@ -62,6 +62,19 @@ def parse_args(argv=None):
 
 
 # ----------------------------------------------------------------------------- helpers
+def reduce_over_ranks(t_step_ms, flops_step, world, device=None):
+    """Whole-job figures of a weak-scaling run: the slowest rank's step time and
+    the products of all ranks.  Every rank calls it (a collective when world > 1)."""
+    import torch
+    t = torch.tensor([float(t_step_ms)], dtype=torch.float64, device=device)
+    f = torch.tensor([float(flops_step)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(f, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(f.item())
+
+
 def dist_env():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
@@ -256,11 +269,8 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     t_step = sum(times) / len(times)
-    t_tensor = torch.tensor([t_step], dtype=torch.float64, device=device)
-    if world > 1:
-        dist.all_reduce(t_tensor, op=dist.ReduceOp.MAX)
-    t_step = float(t_tensor.item())
-    value = world * flops_step * 2.0 / (t_step * 1e-3) / 1e9
+    t_step, flops_all = reduce_over_ranks(t_step, flops_step, world, device)
+    value = flops_all * 2.0 / (t_step * 1e-3) / 1e9
 
     # numeric reuse (Reuse case: numeric phase only) and the roofline of the numeric phase
     Ad = S.Ad
@@ -369,8 +379,8 @@ def run_e2e(torch, S, A, P, args, world, flops_step):
 
     e2e_step()
     times = time_region(torch, e2e_step, max(3, args.steps // 2))
-    t = sum(times) / len(times)
-    return {"value": round(world * 2.0 * flops_step / (t * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
+    t, flops_all = reduce_over_ranks(sum(times) / len(times), flops_step, world, S.Ad.rowptr.device)
+    return {"value": round(2.0 * flops_all / (t * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": round(t, 4)}
 
 
