@@ -380,6 +380,20 @@ __device__ __forceinline__ int set_slot(const int4* tab, const LpHash& hs, int k
   return -1;
 }
 
+// Probe-only lookup over a plain key array once the table is complete (-1:
+// absent); the sorted-pattern masked kernel keeps its (set bits, base) pairs
+// beside the keys.
+__device__ __forceinline__ int key_slot(const int* keys, const LpHash& hs, int key) {
+  unsigned h = hs(key);
+  for (unsigned probe = 0; probe <= hs.mask; ++probe) {
+    const int k = keys[h];
+    if (k == key) return (int)h;
+    if (k == kEmpty) return -1;
+    h = (h + 1) & hs.mask;
+  }
+  return -1;
+}
+
 // Ascending bitonic sort of one 32-bit key per lane of a team of TW lanes
 // (register exchanges only).
 template <int TW>

@@ -291,8 +291,8 @@ __global__ void __launch_bounds__(256) k_masked_warp(MaskedD M, const int* __res
 template <int TW, typename VT>
 __host__ __device__ size_t mskp_team_bytes(int T) {
   const int half = T / 2 > 0 ? T / 2 : 1;
-  return al16((size_t)T * 16) + al16((size_t)half * sizeof(VT)) + al16(sizeof(ChunkScratch<TW, VT>)) +
-         al16((size_t)TW * sizeof(VT));
+  return al16((size_t)T * 4) + al16((size_t)T * 8) + al16((size_t)half * sizeof(VT)) +
+         al16(sizeof(ChunkScratch<TW, VT>)) + al16((size_t)TW * sizeof(VT));
 }
 
 template <int TW, typename VT>
@@ -304,10 +304,11 @@ __global__ void __launch_bounds__(256, 4) k_masked_pos(MaskedD M, const int* __r
   const LpHash hs(logT, M.hash_mode);
   const int half = T / 2 > 0 ? T / 2 : 1;
   unsigned char* base = smem + (size_t)tm.id * mskp_team_bytes<TW, VT>(T);
-  int4* tab = reinterpret_cast<int4*>(base);
-  VT* acc = reinterpret_cast<VT*>(base + al16((size_t)T * 16));
-  ChunkScratch<TW, VT>* csc =
-      reinterpret_cast<ChunkScratch<TW, VT>*>(base + al16((size_t)T * 16) + al16((size_t)half * sizeof(VT)));
+  int* keys = reinterpret_cast<int*>(base);
+  int2* mb = reinterpret_cast<int2*>(base + al16((size_t)T * 4));   // (set bits, position of the set's first column)
+  const size_t tabb = al16((size_t)T * 4) + al16((size_t)T * 8);
+  VT* acc = reinterpret_cast<VT*>(base + tabb);
+  ChunkScratch<TW, VT>* csc = reinterpret_cast<ChunkScratch<TW, VT>*>(base + tabb + al16((size_t)half * sizeof(VT)));
   VT* xchg = reinterpret_cast<VT*>(reinterpret_cast<unsigned char*>(csc) + al16(sizeof(ChunkScratch<TW, VT>)));
   const VT* __restrict__ Xx = reinterpret_cast<const VT*>(M.X.vx);
   const VT* __restrict__ Yx = reinterpret_cast<const VT*>(M.Y.vx);
@@ -337,7 +338,10 @@ __global__ void __launch_bounds__(256, 4) k_masked_pos(MaskedD M, const int* __r
       len = (int)(rp_at(M.Y, j + 1) - bs);
       av = XV(a0 + tm.lane);
     }
-    for (int x = tm.lane; x < T; x += TW) tab[x] = make_int4(kEmpty, 0, 0, 0);
+    for (int x = tm.lane; x < T; x += TW) {
+      keys[x] = kEmpty;
+      mb[x] = make_int2(0, 0);
+    }
     const int sw = s < half ? s : half;
     for (int x = tm.lane; x < sw; x += TW) acc[x] = VT(0);
     __syncwarp(tm.mask);
@@ -363,22 +367,24 @@ __global__ void __launch_bounds__(256, 4) k_masked_pos(MaskedD M, const int* __r
       const bool head = col >= 0 && (p == 0 || (prev >> 5) != set);
       if (head) {
         int fresh = 0;
-        const int slot = slot_insert<4>(reinterpret_cast<int*>(tab), hs, set, &fresh);
-        if (slot >= 0) tab[slot].z = p;
+        const int slot = slot_insert<1>(keys, hs, set, &fresh);
+        if (slot >= 0) mb[slot].y = p;
         else dev_fail(M.status, kDevTableFull, 30, i);
       }
       __syncwarp(tm.mask);
       if (last) {
-        const int slot = set_slot(tab, hs, set);
-        if (slot >= 0) tab[slot].y |= (int)bits;
+        const int slot = key_slot(keys, hs, set);
+        if (slot >= 0) mb[slot].x |= (int)bits;
       }
       __syncwarp(tm.mask);
     }
     auto pos_of = [&](int c) -> int {
-      const int4 e = set_find(tab, hs, c >> 5);
-      const unsigned m = (unsigned)e.y;
-      if (e.x == kEmpty || !((m >> (c & 31)) & 1u)) return -1;
-      return e.z + __popc(m & ((1u << (c & 31)) - 1u));
+      const int slot = key_slot(keys, hs, c >> 5);
+      if (slot < 0) return -1;
+      const int2 e = mb[slot];
+      const unsigned m = (unsigned)e.x;
+      if (!((m >> (c & 31)) & 1u)) return -1;
+      return e.y + __popc(m & ((1u << (c & 31)) - 1u));
     };
     for (long long c = a0; c < a1; c += TW) {
       if (c != a0) {
