@@ -22,7 +22,7 @@
 
 namespace kks {
 size_t symbolic_team_bytes(int cls, int logT, int compressed);
-size_t numeric_team_bytes(int cls, int logT, int dtype);
+size_t numeric_cta_bytes(int logT, int dtype, long long kwords);
 size_t numeric_spill_l1_bytes(int logT, int dtype);
 size_t numeric_l2_chunk_bytes(long long slots, int dtype);
 size_t masked_team_bytes(int cls, int logT, int dtype);
@@ -289,10 +289,10 @@ int cta_max_logT_sym(kks_handle* h, int comp) {
     if (symbolic_team_bytes(kClsC1024, l, comp) + 1024 <= (size_t)h->max_smem) best = l;
   return best;
 }
-int cta_max_logT_num(kks_handle* h, int dtype) {
+int cta_max_logT_num(kks_handle* h, int dtype, long long kmax) {
   int best = 4;
   for (int l = 4; l <= 20; ++l)
-    if (numeric_team_bytes(kClsC1024, l, dtype) + 1024 <= (size_t)h->max_smem) best = l;
+    if (numeric_cta_bytes(l, dtype, kwords_of(kmax)) + 1024 <= (size_t)h->max_smem) best = l;
   return best;
 }
 
@@ -357,14 +357,17 @@ void plain_rule(BinCfg& c, double avg_flops, double est) {
 
 BinCfg num_cfg(kks_handle* h, int dtype, long long kmax) {
   BinCfg c = base_cfg(h);
-  c.cta_max_logT = cta_max_logT_num(h, dtype);
+  c.cta_max_logT = cta_max_logT_num(h, dtype, kmax);
   c.dense_max_kwords = ((long long)h->max_smem - 26 * 1024) / 4;
-  // FP64 dense rows add into a global chunk with FP64 atomics, which the GB300
-  // FP64 units make slow: in FP64 the dense accumulator only takes rows too
-  // large for a shared table
+  // FP64 dense rows add into a global chunk with FP64 atomics: in FP64 the
+  // dense accumulator is not chosen by size ratio
   c.dense_ratio = dtype == 1 ? 0 : 8;
   long long pool_limit = h->opt.pool_limit_bytes > 0 ? h->opt.pool_limit_bytes : (8ll << 30);
   if (kmax * (dtype == 1 ? 8 : 4) > pool_limit) c.dense_ok = 0;
+  // FP64 rows too large for a shared table also go to L1 + L2 rather than to a
+  // k-wide dense chunk (the chunks outgrow L2 and every product is a global
+  // FP64 atomic); option dense = 1 still forces the dense accumulator
+  if (dtype == 1 && h->opt.dense != 1) c.dense_ok = 0;
   // one thread per row: at most kT1MaxKeys columns of C and 64 products
   c.t1_max_keys = kT1MaxKeys;
   c.t1_max_work = 64;
@@ -814,7 +817,7 @@ cudaError_t launch_bin(kks_handle* h, const BinRun& r, cudaStream_t s) {
 // first numeric call and leaves a correct C behind.
 spgemm_status_t tune_numeric(kks_handle* h, cudaStream_t s) {
   BinCfg c = num_cfg(h, h->dtype, h->num_kmax);
-  const int cta_max = cta_max_logT_num(h, h->dtype);
+  const int cta_max = cta_max_logT_num(h, h->dtype, h->num_kmax);
   cudaEvent_t e0, e1;
   KKS_CU(cudaEventCreate(&e0));
   KKS_CU(cudaEventCreate(&e1));

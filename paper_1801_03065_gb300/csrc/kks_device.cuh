@@ -474,12 +474,21 @@ struct ChunkScratch {
 
 // Calls body(q, t) for every product of row i: q indexes B's entry, t the
 // chunk slot holding the A entry.  range(j, &bs, &be) gives the B range of
-// A column j; aval(p) the value of A entry p (or 0 when unused).
-template <int TW, typename VT, class Range, class AVal, class Body>
+// A column j; aval(p) the value of A entry p (or 0 when unused).  The entries
+// of kStagedPasses passes are located first and handed to prefetch(q), which
+// may pull their B data into L1, so the body's loads of a whole group are in
+// flight together instead of one dependent miss per pass.
+constexpr int kStagedPasses = 4;
+
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+template <int TW, typename VT, class Range, class AVal, class Body, class Prefetch>
 __device__ __forceinline__ void for_each_product(const Team<TW>& tm, ChunkScratch<TW, VT>* cs,
                                                  long long* scan_scratch, const int* Aj,
                                                  long long a_beg, long long a_end, Range range,
-                                                 AVal aval, Body body) {
+                                                 AVal aval, Body body, Prefetch prefetch) {
   for (long long c = a_beg; c < a_end; c += TW) {
     long long p = c + tm.lane;
     long long bs = 0, be = 0;
@@ -506,14 +515,37 @@ __device__ __forceinline__ void for_each_product(const Team<TW>& tm, ChunkScratc
           if (cs->pre[mid] <= x) lo = mid; else hi = mid - 1;
         }
         int t = lo;
-        for (; x < total; x += TW) {
-          while (cs->pre[t + 1] <= x) ++t;
-          body(cs->bs[t] + (x - cs->pre[t]), t);
+        for (; x < total; x += (long long)kStagedPasses * TW) {
+          long long q[kStagedPasses];
+          int tt[kStagedPasses];
+#pragma unroll
+          for (int u = 0; u < kStagedPasses; ++u) {
+            const long long xu = x + (long long)u * TW;
+            q[u] = -1;
+            tt[u] = t;
+            if (xu < total) {
+              while (cs->pre[t + 1] <= xu) ++t;
+              q[u] = cs->bs[t] + (xu - cs->pre[t]);
+              tt[u] = t;
+              prefetch(q[u]);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < kStagedPasses; ++u)
+            if (q[u] >= 0) body(q[u], tt[u]);
         }
       }
     }
     tm.sync();
   }
+}
+
+template <int TW, typename VT, class Range, class AVal, class Body>
+__device__ __forceinline__ void for_each_product(const Team<TW>& tm, ChunkScratch<TW, VT>* cs,
+                                                 long long* scan_scratch, const int* Aj,
+                                                 long long a_beg, long long a_end, Range range,
+                                                 AVal aval, Body body) {
+  for_each_product<TW, VT>(tm, cs, scan_scratch, Aj, a_beg, a_end, range, aval, body, [](long long) {});
 }
 
 }  // namespace kks

@@ -89,7 +89,11 @@ __global__ void k_masked(MaskedD M, const int* __restrict__ rows, long long nrow
       const int slot = lp_find(keys, tmask, Yj[q]);
       if (slot >= 0) atomicAdd(acc + pos[slot], csc->av[t] * YV(q));
     };
-    for_each_product<TW, VT>(tm, csc, scan_scratch, M.X.cj, a0, a1, range, aval, body);
+    auto pf = [&](long long q) {
+      prefetch_l1(Yj + q);
+      prefetch_l1(Yx + (M.yperm ? M.yperm[q] : q));
+    };
+    for_each_product<TW, VT>(tm, csc, scan_scratch, M.X.cj, a0, a1, range, aval, body, pf);
     if (GTAB) {
       __threadfence_block();
       tm.sync();

@@ -24,35 +24,40 @@ namespace {
 
 __host__ __device__ constexpr size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
 
+// CTA teams (one row per CTA).  kw_cap > 0: every row of the plan has a
+// column range of at most kw_cap 32-bit words and is written by rank instead
+// of sorted: a k-bit bitmap of the row's columns, the count of set bits before
+// every word (16 bits: a row holds at most T / 2 < 65 536 columns), and for
+// each entry the rank = that count + set bits below it in its word.  This
+// replaces a block-wide bitonic sort with O(k / 32 + s) work, and the table
+// needs no sort buffer.
+constexpr long long kRankMaxWords = 16384;   // rank bitmaps cover k <= 524 288 columns
+
 template <int TW, typename VT>
-__host__ __device__ size_t num_team_bytes(int T) {
+__host__ __device__ size_t num_cta_bytes(int T, long long kw_cap) {
   const int half = T / 2 > 0 ? T / 2 : 1;
-  return al16((size_t)T * sizeof(VT)) + al16((size_t)T * 4) + al16((size_t)half * 8) +
-         al16(sizeof(ChunkScratch<TW, VT>)) + 16;
+  size_t b = al16((size_t)T * sizeof(VT)) + al16((size_t)T * 4) + al16(sizeof(ChunkScratch<TW, VT>)) + 16;
+  if (kw_cap > 0) return b + al16((size_t)((kw_cap + 3) & ~3ll) * 4) + al16((size_t)(kw_cap + 1) * 2);
+  return b + al16((size_t)half * 8);
 }
 
-// kw_cap > 0 (CTA teams): rows whose column range has at most kw_cap 32-bit
-// words are written by rank instead of sorted: a k-bit bitmap of the row's
-// columns, one prefix count per group of 32 words, and for each entry the rank
-// = group prefix + set bits before it in its group.  This replaces a
-// block-wide bitonic sort with O(k / 32 + s) work.
 template <int TW, typename VT>
 __global__ void k_num_hash(ProbD P, const int* __restrict__ rows, long long nrows, int logT, long long kw_cap) {
+  static_assert(TW > 32, "CTA teams only");
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long scan_scratch[33];
   Team<TW> tm;
   const int T = 1 << logT;
   const LpHash tmask(logT, P.hash_mode);
   const int half = T / 2 > 0 ? T / 2 : 1;
-  unsigned char* base = smem + (size_t)tm.id * num_team_bytes<TW, VT>(T);
-  unsigned* bm = reinterpret_cast<unsigned*>(smem + num_team_bytes<TW, VT>(T));
-  unsigned* gp = bm + ((kw_cap + 3) & ~3ll);
-  VT* vals = reinterpret_cast<VT*>(base);
-  int* keys = reinterpret_cast<int*>(base + al16((size_t)T * sizeof(VT)));
-  unsigned long long* sortb =
-      reinterpret_cast<unsigned long long*>(base + al16((size_t)T * sizeof(VT)) + al16((size_t)T * 4));
-  ChunkScratch<TW, VT>* csc = reinterpret_cast<ChunkScratch<TW, VT>*>(
-      base + al16((size_t)T * sizeof(VT)) + al16((size_t)T * 4) + al16((size_t)half * 8));
+  VT* vals = reinterpret_cast<VT*>(smem);
+  int* keys = reinterpret_cast<int*>(smem + al16((size_t)T * sizeof(VT)));
+  ChunkScratch<TW, VT>* csc =
+      reinterpret_cast<ChunkScratch<TW, VT>*>(smem + al16((size_t)T * sizeof(VT)) + al16((size_t)T * 4));
+  unsigned char* tail = reinterpret_cast<unsigned char*>(csc) + al16(sizeof(ChunkScratch<TW, VT>)) + 16;
+  unsigned long long* sortb = reinterpret_cast<unsigned long long*>(tail);   // kw_cap == 0
+  unsigned* bm = reinterpret_cast<unsigned*>(tail);                          // kw_cap > 0
+  unsigned short* gp = reinterpret_cast<unsigned short*>(bm + ((kw_cap + 3) & ~3ll));
 
   const long long team = (long long)blockIdx.x * tm.per_cta + tm.id;
   const long long nteams = (long long)gridDim.x * tm.per_cta;
@@ -84,9 +89,13 @@ __global__ void k_num_hash(ProbD P, const int* __restrict__ rows, long long nrow
       if (slot >= 0) atomicAdd(vals + slot, v);
       else dev_fail(P.status, kDevTableFull, 10, g);
     };
-    for_each_product<TW, VT>(tm, csc, scan_scratch, I.A.cj, a0, a1, range, aval, body);
+    auto pf = [&](long long q) {
+      prefetch_l1(Bj + q);
+      prefetch_l1(Bx + q);
+    };
+    for_each_product<TW, VT>(tm, csc, scan_scratch, I.A.cj, a0, a1, range, aval, body, pf);
     const long long kw = (I.k + 31) >> 5;
-    if (Team<TW>::kCta && kw_cap > 0 && kw <= kw_cap) {
+    if (kw_cap > 0 && kw <= kw_cap) {
       VT* __restrict__ Cx = reinterpret_cast<VT*>(I.Cx);
       int* __restrict__ Cj = I.Cj;
       for (long long w = tm.lane; w < kw; w += TW) bm[w] = 0u;
@@ -96,19 +105,17 @@ __global__ void k_num_hash(ProbD P, const int* __restrict__ rows, long long nrow
         if (kk != kEmpty) atomicOr(bm + (kk >> 5), 1u << (kk & 31));
       }
       tm.sync();
-      const long long ng = (kw + 31) >> 5;
-      long long run = 0;
-      for (long long gb = 0; gb < ng; gb += TW) {
-        const long long gi = gb + tm.lane;
-        int cg = 0;
-        if (gi < ng) {
-          const long long w1 = (gi + 1) * 32 < kw ? (gi + 1) * 32 : kw;
-          for (long long w = gi * 32; w < w1; ++w) cg += __popc(bm[w]);
-        }
-        long long tot;
-        const long long ex = team_excl_scan<TW>(tm, cg, &tot, scan_scratch);
-        if (gi < ng) gp[gi] = (unsigned)(run + ex);
-        run += tot;
+      // set bits before every word: each thread sums a contiguous run of words,
+      // the runs are scanned across the team, then each word gets its prefix
+      const long long seg = (kw + TW - 1) / TW;
+      const long long w0 = tm.lane * seg, w1 = w0 + seg < kw ? w0 + seg : kw;
+      int cseg = 0;
+      for (long long w = w0; w < w1; ++w) cseg += __popc(bm[w]);
+      long long run;
+      long long pre = team_excl_scan<TW>(tm, cseg, &run, scan_scratch);
+      for (long long w = w0; w < w1; ++w) {
+        gp[w] = (unsigned short)pre;
+        pre += __popc(bm[w]);
       }
       if (tm.lane == 0 && run != s) dev_fail(P.status, kDevRowSizeMismatch, 9, g);
       tm.sync();
@@ -116,9 +123,7 @@ __global__ void k_num_hash(ProbD P, const int* __restrict__ rows, long long nrow
         const int kk = keys[x];
         if (kk == kEmpty) continue;
         const int w = kk >> 5;
-        long long rk = gp[w >> 5];
-        for (int w2 = w & ~31; w2 < w; ++w2) rk += __popc(bm[w2]);
-        rk += __popc(bm[w] & ((1u << (kk & 31)) - 1u));
+        const long long rk = (long long)gp[w] + __popc(bm[w] & ((1u << (kk & 31)) - 1u));
         if (rk < s) {
           Cj[c0 + rk] = kk;
           Cx[c0 + rk] = vals[x];
@@ -769,7 +774,11 @@ __global__ void __launch_bounds__(TW) k_num_dense(ProbD P, const int* __restrict
         dev_fail(P.status, kDevBadIndex, 12, g);
       }
     };
-    for_each_product<TW, VT>(tm, csc, scan_scratch, I.A.cj, a0, a1, range, aval, body);
+    auto pf = [&](long long q) {
+      prefetch_l1(Bj + q);
+      prefetch_l1(Bx + q);
+    };
+    for_each_product<TW, VT>(tm, csc, scan_scratch, I.A.cj, a0, a1, range, aval, body, pf);
     __threadfence_block();
     __syncthreads();
     VT* __restrict__ Cx = reinterpret_cast<VT*>(I.Cx);
@@ -871,7 +880,11 @@ __global__ void __launch_bounds__(TW) k_num_spill(ProbD P, const int* __restrict
         else dev_fail(P.status, kDevTableFull, 15, g);
       }
     };
-    for_each_product<TW, VT>(tm, csc, scan_scratch, I.A.cj, a0, a1, range, aval, body);
+    auto pf = [&](long long q) {
+      prefetch_l1(Bj + q);
+      prefetch_l1(Bx + q);
+    };
+    for_each_product<TW, VT>(tm, csc, scan_scratch, I.A.cj, a0, a1, range, aval, body, pf);
     __threadfence_block();
     __syncthreads();
     // fold L2 entries whose key also reached L1 into L1
@@ -950,32 +963,19 @@ cudaError_t set_smem(K kernel, size_t bytes) {
 template <int TW, typename VT>
 cudaError_t run_hash(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
   const int T = 1 << S.logT;
-  const size_t tb = num_team_bytes<TW, VT>(T);
-  int teams = 1;
-  if (TW <= 32) {
-    teams = (int)(kTeamSmemBudget / tb);
-    int tmax = 256 / TW;
-    if (teams > tmax) teams = tmax;
-    if (teams < 1) teams = 1;
-  }
-  size_t smem = tb * teams;
-  // CTA teams: room for the rank bitmap when the plan's column ranges are small
+  // the rank bitmap when every row's column range fits it, else the sort buffer
   long long kw_cap = 0;
-  if (TW > 32 && S.kwords_max > 0) {
-    const long long kw = S.kwords_max;
-    const size_t extra = al16((size_t)((kw + 3) & ~3ll) * 4) + al16((size_t)((kw + 31) / 32 + 1) * 4);
-    if (kw <= 16384 && smem + extra + 1024 <= (size_t)L.max_smem_optin) {
-      kw_cap = kw;
-      smem += extra;
-    }
-  }
+  if (S.kwords_max > 0 && S.kwords_max <= kRankMaxWords &&
+      num_cta_bytes<TW, VT>(T, S.kwords_max) + 1024 <= (size_t)L.max_smem_optin)
+    kw_cap = S.kwords_max;
+  const size_t smem = num_cta_bytes<TW, VT>(T, kw_cap);
   if (smem > (size_t)L.max_smem_optin) return cudaErrorInvalidConfiguration;
   auto kern = k_num_hash<TW, VT>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
-  const unsigned grid = resident_grid(kern, TW * teams, smem, L.num_sms, (S.nrows + teams - 1) / teams);
+  const unsigned grid = resident_grid(kern, TW, smem, L.num_sms, S.nrows);
   KKS_LAUNCHED();
-  kern<<<grid, TW * teams, smem, L.stream>>>(P, S.rows, S.nrows, S.logT, kw_cap);
+  kern<<<grid, TW, smem, L.stream>>>(P, S.rows, S.nrows, S.logT, kw_cap);
   return cudaGetLastError();
 }
 
@@ -1077,22 +1077,16 @@ cudaError_t dispatch(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
 
 }  // namespace
 
-size_t numeric_team_bytes(int cls, int logT, int dtype) {
+size_t numeric_cta_bytes(int logT, int dtype, long long kwords) {
+  // the launcher takes the rank layout when it fits, else the sort buffer
   const int T = 1 << logT;
+  const long long kw = (kwords > 0 && kwords <= kRankMaxWords) ? kwords : 0;
   if (dtype == 1) {
-    switch (cls) {
-      case kClsW8: return num_team_bytes<8, double>(T);
-      case kClsW32: return num_team_bytes<32, double>(T);
-      case kClsC256: return num_team_bytes<256, double>(T);
-      default: return num_team_bytes<1024, double>(T);
-    }
+    const size_t a = num_cta_bytes<1024, double>(T, kw), b = num_cta_bytes<1024, double>(T, 0);
+    return a < b ? a : b;
   }
-  switch (cls) {
-    case kClsW8: return num_team_bytes<8, float>(T);
-    case kClsW32: return num_team_bytes<32, float>(T);
-    case kClsC256: return num_team_bytes<256, float>(T);
-    default: return num_team_bytes<1024, float>(T);
-  }
+  const size_t a = num_cta_bytes<1024, float>(T, kw), b = num_cta_bytes<1024, float>(T, 0);
+  return a < b ? a : b;
 }
 
 size_t numeric_spill_l1_bytes(int logT, int dtype) {

@@ -102,7 +102,15 @@ __global__ void k_sym_hash(ProbD P, const int* __restrict__ rows, long long nrow
         dev_fail(P.status, kDevTableFull, 1, g);
       }
     };
-    for_each_product<TW, int>(tm, csc, scan_scratch, I.A.cj, a0, a1, range, aval, body);
+    auto pf = [&](long long q) {
+      if (COMP) {
+        prefetch_l1(P.csi + q);
+        prefetch_l1(P.cs + q);
+      } else {
+        prefetch_l1(Bj + q);
+      }
+    };
+    for_each_product<TW, int>(tm, csc, scan_scratch, I.A.cj, a0, a1, range, aval, body, pf);
     if (SPILL) {
       __threadfence_block();
       tm.sync();
@@ -320,7 +328,15 @@ __global__ void __launch_bounds__(TW) k_sym_dense(ProbD P, const int* __restrict
         else dev_fail(P.status, kDevBadIndex, 4, g);
       }
     };
-    for_each_product<TW, int>(tm, csc, scan_scratch, I.A.cj, a0, a1, range, aval, body);
+    auto pf = [&](long long q) {
+      if (COMP) {
+        prefetch_l1(P.csi + q);
+        prefetch_l1(P.cs + q);
+      } else {
+        prefetch_l1(Bj + q);
+      }
+    };
+    for_each_product<TW, int>(tm, csc, scan_scratch, I.A.cj, a0, a1, range, aval, body, pf);
     long long c = 0;
     for (long long w = tm.lane; w < kw; w += TW) {
       c += __popc(bm[w]);
