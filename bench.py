@@ -49,7 +49,8 @@ def parse_args(argv=None):
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
-    p.add_argument("--workload", choices=["stencil27_100", "batched512"], default="stencil27_100",
+    p.add_argument("--workload", choices=["stencil27_100", "batched512", "rmat18", "laplace5_64", "laplace7_64"],
+                   default="stencil27_100",
                    help="stencil27_100: the headline step; batched512: batched autotuned vs plain per-matrix")
     p.add_argument("--count", type=int, default=512, help="batched512: number of products")
     p.add_argument("--repeats", type=int, default=20, help="batched512: numeric-reuse repeats")
@@ -598,6 +599,115 @@ def run_numeric_only(args):
     print(json.dumps({"grid": args.grid, "nnzC": nnz}))
 
 
+def _base_line(args, value, t_ms, workload, dtype, extra):
+    out = {"metric": METRIC, "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(t_ms, 4), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": {"workload": workload}}
+    out.update(extra)
+    return out
+
+
+def run_single(args):
+    """One product C = A·A: NoReuse (symbolic + numeric), numeric reuse, and the
+    pattern-only symbolic phase; R-MAT (FP32, skewed rows, nnz(C) > 2^31) or the
+    5-point Laplacian (FP64, launch-bound: reported in microseconds too)."""
+    import numpy as np
+    import torch
+    import workloads as w
+    from paper_1801_03065_gb300 import ops
+    torch.cuda.set_device(0)
+    wl = w.config_workload(args.workload)
+    A = wl["A"]
+    vdt = np.float32 if wl["dtype"] == "f32" else np.float64
+    tdt = torch.float32 if vdt == np.float32 else torch.float64
+    Ad = ops.CsrMatrix.from_host(A.rowptr, A.colidx, A.values.astype(vdt), A.shape, device="cuda:0")
+    h = ops.SpGEMM()
+    rp = torch.empty(A.nrows + 1, dtype=torch.int64, device="cuda:0")
+    rp, nnz = h.symbolic(Ad, Ad, C_rowptr=rp)
+    Cj = torch.empty(nnz, dtype=torch.int32, device="cuda:0")
+    Cx = torch.empty(nnz, dtype=tdt, device="cuda:0")
+    h.numeric(Ad, Ad, rp, nnz, Cj, Cx)
+    h.sync()
+    st = h.stats()
+
+    def step():
+        h.symbolic(Ad, Ad, C_rowptr=rp)
+        h.numeric(Ad, Ad, rp, nnz, Cj, Cx)
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0).start()
+    times = time_region(torch, step, args.steps)
+    clk = clocks.stop()
+    t = sum(times) / len(times)
+    num = lambda: h.numeric(Ad, Ad, rp, nnz, Cj, Cx)
+    t_num = statistics.mean(time_region(torch, num, max(args.steps, 5)))
+    sym = lambda: h.symbolic(Ad, Ad, C_rowptr=rp)
+    t_sym = statistics.mean(time_region(torch, sym, max(args.steps, 5)))
+    h.sync()
+    fm = st["f_m"]
+    vb = 4 if vdt == np.float32 else 8
+    bytes_num = 2 * csr_bytes(A.nrows, A.nnz, vb, 8) + csr_bytes(A.nrows, nnz, vb, 8)
+    peak, peak_kind = measured_peaks()
+    if args.workload == "rmat18":
+        desc = ("rmat18: C = A*A, A = symmetrised R-MAT scale 18, edge factor 16 (.57,.19,.19,.05), seed 7, "
+                "%d nnz, FP32 U(0,1]" % A.nnz)
+    else:
+        desc = "laplace5_64: C = A*A, A = 5-point Laplacian on a 64^2 grid (4096 rows, %d nnz, FP64 4/-1)" % A.nnz
+    h.close()
+    print(json.dumps(_base_line(args, 2.0 * fm / (t * 1e-3) / 1e9, t, desc, wl["dtype"], {
+        "phases_ms": {"symbolic": round(t_sym, 4), "numeric": round(t_num, 4),
+                      "sym_num_us": round(1e3 * t, 2)},
+        "numeric_reuse": {"value": round(2.0 * fm / (t_num * 1e-3) / 1e9, 3), "unit": "GFLOP/s"},
+        "roofline_hbm": {"bound": "hbm", "achieved": round(bytes_num / (t_num * 1e-3) / 1e9, 2), "peak": peak,
+                         "unit": "GB/s", "frac": round(bytes_num / (t_num * 1e-3) / 1e9 / peak, 4),
+                         "peak_kind": peak_kind, "algorithmic_bytes": bytes_num, "kernel": "numeric phase"},
+        "stats": {k: st[k] for k in ("f_m", "maxrf", "nnzC", "maxrs", "CF", "compressed", "bin_rows_numeric")},
+        "clocks": clk})), flush=True)
+
+
+def run_differentiation(args):
+    """loss = sum W * (A·P) on fixed patterns (7-point Laplacian 64^3, 2^3
+    aggregation P): forward (numeric reuse on C's pattern) and backward (dA and dB
+    masked products), each captured in a CUDA graph and replayed."""
+    import numpy as np
+    import torch
+    import workloads as w
+    from paper_1801_03065_gb300 import autograd as ag
+    from paper_1801_03065_gb300 import ops
+    torch.cuda.set_device(0)
+    wl = w.config_workload("laplace7_64")
+    A, P = wl["A"], wl["B"]
+    Ad = ops.CsrMatrix.from_host(A.rowptr, A.colidx, A.values, A.shape, device="cuda:0")
+    Pd = ops.CsrMatrix.from_host(P.rowptr, P.colidx, P.values, P.shape, device="cuda:0")
+    pat = ag.SpGEMMPattern(Ad, Pd)
+    W = torch.as_tensor(wl["rng"].uniform(-1.0, 1.0, pat.C.nnz), device="cuda:0")
+    a0, b0 = Ad.values, Pd.values
+    out = torch.empty(pat.C.nnz, dtype=torch.float64, device="cuda:0")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(max(args.warmup, 1)):
+            pat.forward_values(a0, b0, out=out)
+            pat.grads(W, a0, b0)
+    torch.cuda.current_stream().wait_stream(side)
+    gf, gb = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gf):
+        pat.forward_values(a0, b0, out=out)
+    with torch.cuda.graph(gb):
+        pat.grads(W, a0, b0)
+    t_f = statistics.mean(time_region(torch, gf.replay, max(args.steps, 5)))
+    t_b = statistics.mean(time_region(torch, gb.replay, max(args.steps, 5)))
+    fm = pat.h_fwd.stats()["f_m"]
+    desc = ("laplace7_64: loss = sum W * (A*P), A = 7-point Laplacian on a 64^3 grid (FP64 6/-1 + U(+-0.1), "
+            "seed 3), P = 2x2x2 aggregation U(0.5,1.5); forward and backward on fixed patterns, graph replay")
+    pat.close()
+    print(json.dumps(_base_line(args, 2.0 * fm / (t_f * 1e-3) / 1e9, t_f + t_b, desc, "f64", {
+        "phases_ms": {"forward": round(t_f, 4), "backward_dA_dB": round(t_b, 4)},
+        "backward_over_forward": round(t_b / t_f, 3)})), flush=True)
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.numeric_only:
@@ -607,6 +717,10 @@ def main(argv=None):
         run_reference(args)
     elif args.workload == "batched512":
         run_batched(args)
+    elif args.workload in ("rmat18", "laplace5_64"):
+        run_single(args)
+    elif args.workload == "laplace7_64":
+        run_differentiation(args)
     else:
         run_ours(args)
 

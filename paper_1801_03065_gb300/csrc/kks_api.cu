@@ -37,7 +37,7 @@ namespace {
 enum BufId {
   kBufInst, kBufArow0, kBufBrow0, kBufCnt, kBufBcp, kBufCsi, kBufCs, kBufRf, kBufRfc, kBufRowsize, kBufOffs,
   kBufScanTmp, kBufInstStats, kBufInstOut, kBufHist, kBufCursor, kBufSymRows, kBufNumRows, kBufSymPool,
-  kBufNumPool, kBufNumPool2, kBufNumPool3, kBufStatus, kBufMaskRows, kBufMaskHist, kBufMaskPool, kBufTrTmp,
+  kBufNumPool2, kBufNumPool3, kBufStatus, kBufMaskRows, kBufMaskHist, kBufMaskPool, kBufTrTmp,
   kBufTrPool, kBufReuseRows, kBufReusePool, kBufBinCnt, kBufBinOfs, kNumBufs
 };
 
@@ -104,7 +104,7 @@ struct kks_handle {
   std::vector<PatternId> pat;
   std::vector<BinRun> num_bins;
   long long num_kw_max = 0, num_kmax = 0;
-  int num_dense_chunks = 0, num_spill_chunks = 0;
+  int num_spill_chunks = 0;
   long long num_spill_chunk_bytes = 0, num_spill_kw = 0, num_dense_kw = 0;
   int num_l1_logT = 0;
   spgemm_stats_t stats;
@@ -112,6 +112,7 @@ struct kks_handle {
   MaskPlan masked;   // last plan of spgemm_masked (reused while the patterns are unchanged)
   bool tuned = false;
   bool positions_ok = false;   // every product of the plan runs on the compressed B
+  bool b_sorted = false;       // every B row of the plan has increasing columns
   // tuner results by bin (class, log2 table, rows, dtype): a new plan of the
   // same problem reuses them instead of tuning again
   struct TuneEntry {
@@ -358,16 +359,12 @@ void plain_rule(BinCfg& c, double avg_flops, double est) {
 BinCfg num_cfg(kks_handle* h, int dtype, long long kmax) {
   BinCfg c = base_cfg(h);
   c.cta_max_logT = cta_max_logT_num(h, dtype, kmax);
-  c.dense_max_kwords = ((long long)h->max_smem - 26 * 1024) / 4;
-  // FP64 dense rows add into a global chunk with FP64 atomics: in FP64 the
-  // dense accumulator is not chosen by size ratio
+  // the dense accumulator works through shared-memory windows of the column
+  // range, so any k fits; rows too large for a shared table always qualify,
+  // and FP32 rows also once their size reaches k / 8 (FP64 rows of that size
+  // stay in hash tables, which take fewer passes over their products)
+  c.dense_max_kwords = 1ll << 40;
   c.dense_ratio = dtype == 1 ? 0 : 8;
-  long long pool_limit = h->opt.pool_limit_bytes > 0 ? h->opt.pool_limit_bytes : (8ll << 30);
-  if (kmax * (dtype == 1 ? 8 : 4) > pool_limit) c.dense_ok = 0;
-  // FP64 rows too large for a shared table also go to L1 + L2 rather than to a
-  // k-wide dense chunk (the chunks outgrow L2 and every product is a global
-  // FP64 atomic); option dense = 1 still forces the dense accumulator
-  if (dtype == 1 && h->opt.dense != 1) c.dense_ok = 0;
   // one thread per row: at most kT1MaxKeys columns of C and 64 products
   c.t1_max_keys = kT1MaxKeys;
   c.t1_max_work = 64;
@@ -487,7 +484,7 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
   KKS_ST(ensure(h, kBufBinCnt, sizeof(long long) * 2 * (nbc + 1)));
   KKS_ST(ensure(h, kBufBinOfs, sizeof(long long) * 2 * (nbc + 1)));
   KKS_ST(ensure(h, kBufScanTmp, scan_tmp_bytes(std::max(std::max(totalA, totalB), nbc) + 1)));
-  KKS_ST(ensure(h, kBufInstStats, sizeof(unsigned long long) * 4 * ni));
+  KKS_ST(ensure(h, kBufInstStats, sizeof(unsigned long long) * (4 * ni + 1)));
   KKS_ST(ensure(h, kBufInstOut, sizeof(unsigned long long) * 2 * ni));
   KKS_ST(ensure(h, kBufHist, sizeof(unsigned long long) * 2 * kNumBins));
   KKS_ST(ensure(h, kBufCursor, sizeof(unsigned long long) * 2 * kNumBins));
@@ -510,7 +507,7 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
                          cudaMemcpyHostToDevice, s));
   KKS_CU(cudaMemcpyAsync(h->buf[kBufBrow0], up + sizeof(InstD) * ni + sizeof(long long) * (ni + 1),
                          sizeof(long long) * (count + 1), cudaMemcpyHostToDevice, s));
-  KKS_CU(cudaMemsetAsync(h->buf[kBufInstStats], 0, sizeof(unsigned long long) * 4 * ni, s));
+  KKS_CU(cudaMemsetAsync(h->buf[kBufInstStats], 0, sizeof(unsigned long long) * (4 * ni + 1), s));
   KKS_CU(cudaMemsetAsync(h->buf[kBufInstOut], 0, sizeof(unsigned long long) * 2 * ni, s));
   KKS_CU(cudaMemsetAsync(h->buf[kBufHist], 0, sizeof(unsigned long long) * 2 * kNumBins, s));
   KKS_CU(cudaMemsetAsync(h->buf[kBufStatus], 0, sizeof(DevStatus), s));
@@ -521,7 +518,8 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
 
   // (1) compression pass 1 and (2) row statistics
   if (comp_on) {
-    KKS_CU(launch_compress_count(L, P, totalB, B<long long>(h, kBufCnt)));
+    KKS_CU(launch_compress_count(L, P, totalB, B<long long>(h, kBufCnt),
+                                 B<unsigned long long>(h, kBufInstStats) + 4 * ni));
     KKS_CU(launch_scan(L, B<long long>(h, kBufCnt), B<long long>(h, kBufBcp), totalB, h->buf[kBufScanTmp]));
   }
   KKS_CU(launch_row_stats(L, P, totalA, comp_on ? 1 : 0, B<long long>(h, kBufRf),
@@ -529,14 +527,20 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
   unsigned long long* h_stats = (unsigned long long*)rd;
   long long* h_nbc = (long long*)(rd + sizeof(unsigned long long) * 4 * ni);
   DevStatus* h_status = (DevStatus*)(rd + sizeof(unsigned long long) * (4 * ni + 2 * ni + 2 * kNumBins + 8));
+  unsigned long long* h_unsorted = (unsigned long long*)(rd + sizeof(unsigned long long) * (4 * ni + 2 * ni + 2 * kNumBins));
   *h_nbc = 0;
+  *h_unsorted = 1;
   KKS_CU(cudaMemcpyAsync(h_stats, h->buf[kBufInstStats], sizeof(unsigned long long) * 4 * ni,
                          cudaMemcpyDeviceToHost, s));
-  if (comp_on)
+  if (comp_on) {
     KKS_CU(cudaMemcpyAsync(h_nbc, B<long long>(h, kBufBcp) + totalB, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    KKS_CU(cudaMemcpyAsync(h_unsorted, B<unsigned long long>(h, kBufInstStats) + 4 * ni, sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, s));
+  }
   KKS_CU(cudaMemcpyAsync(h_status, h->buf[kBufStatus], sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
   KKS_CU(cudaStreamSynchronize(s));
   KKS_ST(consume_status(h, h_status, s));
+  h->b_sorted = comp_on && *h_unsorted == 0;
 
   // (3) the 15 % rule, per product
   long long fm_all = 0, fmc_all = 0, maxrf_all = 0, maxrfc_all = 0;
@@ -686,7 +690,7 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
   h->num_bins.clear();
   const bool positions_ok = h->opt.numeric_positions != 0 && count > 0 && ncomp == count;
   h->positions_ok = positions_ok;
-  long long dense_rows = 0, spill_rows = 0;
+  long long spill_rows = 0;
   int spill_logT = 0;
   long long cls_rows[kNumClasses] = {0};
   for (int t = 0; t < kNumBins; ++t) {
@@ -698,7 +702,6 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
     // take their output positions from the column sets
     const int pos = (positions_ok && (cls == kClsW8 || cls == kClsW32)) ? 1 : 0;
     h->num_bins.push_back(BinRun{cls, bin_logT(t), pos, noff[t], cnt, h->opt.hash_function});
-    if (cls == kClsDense) dense_rows += cnt;
     if (cls == kClsSpill) {
       spill_rows += cnt;
       spill_logT = std::max(spill_logT, bin_logT(t));
@@ -716,16 +719,7 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
   h->num_kmax = kmax;
   h->num_kw_max = kwords_of(kmax);
   h->num_dense_kw = std::min(kwords_of(kmax), ncfg.dense_max_kwords);
-  h->num_dense_chunks = 0;
   h->num_spill_chunks = 0;
-  if (dense_rows > 0) {
-    const long long chunk = kmax * vt;
-    long long nch = std::min<long long>(std::min<long long>(2ll * h->num_sms, dense_rows), pool_limit / std::max(chunk, 1ll));
-    if (nch < 1) return SPGEMM_ERR_OOM;
-    KKS_ST(ensure(h, kBufNumPool, (size_t)(nch * chunk)));
-    KKS_CU(cudaMemsetAsync(h->buf[kBufNumPool], 0, (size_t)(nch * chunk), s));
-    h->num_dense_chunks = (int)nch;
-  }
   if (spill_rows > 0) {
     const long long slots = 1ll << spill_logT;
     const long long chunk = (long long)numeric_l2_chunk_bytes(slots, dtype);
@@ -792,9 +786,8 @@ cudaError_t launch_bin(kks_handle* h, const BinRun& r, cudaStream_t s) {
   S.kmax = h->num_kmax;
   S.max_occ = h->opt.l1_max_occupancy;
   S.positions = (r.compressed && (r.cls == kClsW8 || r.cls == kClsW32)) ? 1 : 0;
+  S.b_sorted = h->b_sorted ? 1 : 0;
   if (r.cls == kClsDense) {
-    S.pool = h->buf[kBufNumPool];
-    S.nchunks = h->num_dense_chunks;
     S.kwords_max = h->num_dense_kw;
   } else if (r.cls == kClsSpill) {
     S.pool = h->buf[kBufNumPool2];

@@ -524,7 +524,17 @@ __device__ __forceinline__ void for_each_product(const Team<TW>& tm, ChunkScratc
             q[u] = -1;
             tt[u] = t;
             if (xu < total) {
-              while (cs->pre[t + 1] <= xu) ++t;
+              // the A entry of product xu: a few linear steps (long B ranges),
+              // then a binary search (many short or empty ranges per pass)
+              for (int st = 0; st < 8 && cs->pre[t + 1] <= xu; ++st) ++t;
+              if (cs->pre[t + 1] <= xu) {
+                int lo = t + 1, hi = TW - 1;
+                while (lo < hi) {
+                  const int mid = (lo + hi + 1) >> 1;
+                  if (cs->pre[mid] <= xu) lo = mid; else hi = mid - 1;
+                }
+                t = lo;
+              }
               q[u] = cs->bs[t] + (xu - cs->pre[t]);
               tt[u] = t;
               prefetch(q[u]);

@@ -115,7 +115,9 @@ inline unsigned resident_grid(K kernel, int threads, size_t smem, int num_sms, l
 }
 
 // prep: statistics, compression, scans, binning
-cudaError_t launch_compress_count(const LaunchCtx&, const ProbD&, long long totalB, long long* cnt);
+// per-row compressed lengths; *unsorted += rows of B whose columns do not increase
+cudaError_t launch_compress_count(const LaunchCtx&, const ProbD&, long long totalB, long long* cnt,
+                                  unsigned long long* unsorted);
 cudaError_t launch_compress_fill(const LaunchCtx&, const ProbD&, long long totalB, int* csi, unsigned* cs);
 cudaError_t launch_row_stats(const LaunchCtx&, const ProbD&, long long totalA, int use_bc,
                              long long* rf, long long* rfc, unsigned long long* inst_stats);
@@ -218,6 +220,7 @@ struct NumLaunch {
   long long chunk2_words;
   int nchunks;
   int positions;         // warp classes: compressed-position kernel (every product's B compressed)
+  int b_sorted;          // dense class: every B row has increasing columns
 };
 cudaError_t launch_numeric(const LaunchCtx&, const ProbD&, const NumLaunch&);
 

@@ -736,16 +736,44 @@ __global__ void __launch_bounds__(256, 3) k_num_thread(ProbD P, const int* __res
   }
 }
 
+// Dense accumulator (Section 3.1.2) for rows whose column count is a large
+// fraction of k or too large for a shared table, kept in shared memory: the
+// column range is cut into windows of W = 2^win_log2 columns and the row is
+// accumulated window by window (products outside the window are skipped), so
+// every add is a shared-memory atomic and a window's columns come out in
+// order from its bitmap.  Values of emitted columns are cleared as they are
+// read, so each window starts from zero without a sweep.  When every B row
+// has increasing columns (sorted_b), the part of a B row inside the window is
+// found by binary search, so each product is visited in one window only.
+__device__ __forceinline__ long long lower_col(const int* __restrict__ cj, long long lo, long long hi, long long c) {
+  while (lo < hi) {
+    const long long mid = (lo + hi) >> 1;
+    if ((long long)cj[mid] < c) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+template <int TW, typename VT>
+__host__ __device__ size_t dense_win_bytes(int win_log2) {
+  const size_t W = (size_t)1 << win_log2;
+  return al16(W * sizeof(VT)) + al16((W / 32) * 4) + al16(sizeof(ChunkScratch<TW, VT>));
+}
+
 template <int TW, typename VT>
 __global__ void __launch_bounds__(TW) k_num_dense(ProbD P, const int* __restrict__ rows, long long nrows,
-                                                  long long kw_max, VT* pool, long long kmax) {
+                                                  int win_log2, int sorted_b) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long scan_scratch[33];
   Team<TW> tm;
-  unsigned* bm = reinterpret_cast<unsigned*>(smem);
-  ChunkScratch<TW, VT>* csc = reinterpret_cast<ChunkScratch<TW, VT>*>(smem + al16((size_t)kw_max * 4));
-  VT* dense = pool + (long long)blockIdx.x * kmax;
-  for (long long w = tm.lane; w < kw_max; w += TW) bm[w] = 0u;
+  const long long W = 1ll << win_log2;
+  const long long ww = W / 32;
+  VT* acc = reinterpret_cast<VT*>(smem);
+  unsigned* bm = reinterpret_cast<unsigned*>(smem + al16((size_t)W * sizeof(VT)));
+  ChunkScratch<TW, VT>* csc =
+      reinterpret_cast<ChunkScratch<TW, VT>*>(smem + al16((size_t)W * sizeof(VT)) + al16((size_t)ww * 4));
+  for (long long x = tm.lane; x < W; x += TW) acc[x] = VT(0);
+  for (long long x = tm.lane; x < ww; x += TW) bm[x] = 0u;
   __syncthreads();
   for (long long r = blockIdx.x; r < nrows; r += gridDim.x) {
     const long long g = rows[r];
@@ -755,58 +783,66 @@ __global__ void __launch_bounds__(TW) k_num_dense(ProbD P, const int* __restrict
     const long long c0 = I.Crp[i];
     const long long s = I.Crp[i + 1] - c0;
     const long long k = I.k;
-    const long long kw = (k + 31) >> 5;
     const long long a0 = rp_at(I.A, i), a1 = rp_at(I.A, i + 1);
     const VT* __restrict__ Ax = reinterpret_cast<const VT*>(I.A.vx);
     const VT* __restrict__ Bx = reinterpret_cast<const VT*>(I.B.vx);
     const int* __restrict__ Bj = I.B.cj;
-    auto range = [&](int j, long long* bs, long long* be) {
-      *bs = rp_at(I.B, j);
-      *be = rp_at(I.B, j + 1);
-    };
+    VT* __restrict__ Cx = reinterpret_cast<VT*>(I.Cx);
+    int* __restrict__ Cj = I.Cj;
     auto aval = [&](long long p) { return Ax[p]; };
-    auto body = [&](long long q, int t) {
-      const int col = Bj[q];
-      if ((unsigned long long)(unsigned)col < (unsigned long long)k) {
-        atomicAdd(dense + col, csc->av[t] * Bx[q]);
-        atomicOr(bm + (col >> 5), 1u << (col & 31));
-      } else {
-        dev_fail(P.status, kDevBadIndex, 12, g);
-      }
-    };
     auto pf = [&](long long q) {
       prefetch_l1(Bj + q);
       prefetch_l1(Bx + q);
     };
-    for_each_product<TW, VT>(tm, csc, scan_scratch, I.A.cj, a0, a1, range, aval, body, pf);
-    __threadfence_block();
-    __syncthreads();
-    VT* __restrict__ Cx = reinterpret_cast<VT*>(I.Cx);
-    int* __restrict__ Cj = I.Cj;
     long long run = 0;
-    for (long long wb = 0; wb < kw; wb += TW) {
-      const long long w = wb + tm.lane;
-      unsigned word = (w < kw) ? bm[w] : 0u;
-      long long tot;
-      long long pos = run + team_excl_scan<TW>(tm, __popc(word), &tot, scan_scratch);
-      while (word) {
-        const int bit = __ffs(word) - 1;
-        word &= word - 1u;
-        const long long col = w * 32 + bit;
-        const VT v = dense[col];
-        dense[col] = VT(0);
-        if (pos < s) {
-          Cj[c0 + pos] = (int)col;
-          Cx[c0 + pos] = v;
+    for (long long w0 = 0; w0 < k; w0 += W) {
+      auto range = [&](int j, long long* bs, long long* be) {
+        *bs = rp_at(I.B, j);
+        *be = rp_at(I.B, j + 1);
+        if (sorted_b && *be > *bs) {
+          *bs = lower_col(Bj, *bs, *be, w0);
+          *be = lower_col(Bj, *bs, *be, w0 + W);
         }
-        ++pos;
+      };
+      auto body = [&](long long q, int t) {
+        const int col = Bj[q];
+        if ((unsigned long long)(unsigned)col >= (unsigned long long)k) {
+          if (w0 == 0) dev_fail(P.status, kDevBadIndex, 12, g);
+          return;
+        }
+        const long long x = (long long)col - w0;
+        if ((unsigned long long)x < (unsigned long long)W) {
+          atomicAdd(acc + x, csc->av[t] * Bx[q]);
+          atomicOr(bm + (x >> 5), 1u << (x & 31));
+        }
+      };
+      for_each_product<TW, VT>(tm, csc, scan_scratch, I.A.cj, a0, a1, range, aval, body, pf);
+      __syncthreads();
+      // the window's columns in order: word-wise prefix of set bits, then emit
+      const long long nw = ((k - w0 + 31) >> 5) < ww ? ((k - w0 + 31) >> 5) : ww;
+      for (long long wb = 0; wb < nw; wb += TW) {
+        const long long wi = wb + tm.lane;
+        unsigned word = (wi < nw) ? bm[wi] : 0u;
+        long long tot;
+        long long pos = run + team_excl_scan<TW>(tm, __popc(word), &tot, scan_scratch);
+        while (word) {
+          const int bit = __ffs(word) - 1;
+          word &= word - 1u;
+          const long long x = wi * 32 + bit;
+          const VT v = acc[x];
+          acc[x] = VT(0);
+          if (pos < s) {
+            Cj[c0 + pos] = (int)(w0 + x);
+            Cx[c0 + pos] = v;
+          }
+          ++pos;
+        }
+        if (wi < nw) bm[wi] = 0u;
+        run += tot;
       }
-      if (w < kw) bm[w] = 0u;
-      run += tot;
+      __syncthreads();
     }
     if (tm.lane == 0 && run != s) dev_fail(P.status, kDevRowSizeMismatch, 13, g);
-    __threadfence_block();
-    __syncthreads();
   }
 }
 
@@ -1020,15 +1056,18 @@ cudaError_t run_cpn(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
 template <typename VT>
 cudaError_t run_dense(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
   constexpr int TW = 1024;
-  const size_t smem = al16((size_t)S.kwords_max * 4) + al16(sizeof(ChunkScratch<TW, VT>));
+  // the widest window that fits one CTA's shared memory (a 1024-thread CTA
+  // of this kernel holds a whole SM's registers, so one CTA runs per SM)
+  int wl = 17;
+  while (wl > 10 && dense_win_bytes<TW, VT>(wl) + 1024 > (size_t)L.max_smem_optin) --wl;
+  const size_t smem = dense_win_bytes<TW, VT>(wl);
   if (smem > (size_t)L.max_smem_optin) return cudaErrorInvalidConfiguration;
   auto kern = k_num_dense<TW, VT>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
-  long long grid = S.nchunks;
-  if (grid > S.nrows) grid = S.nrows;
+  const unsigned grid = resident_grid(kern, TW, smem, L.num_sms, S.nrows);
   KKS_LAUNCHED();
-  kern<<<(unsigned)grid, TW, smem, L.stream>>>(P, S.rows, S.nrows, S.kwords_max, (VT*)S.pool, S.kmax);
+  kern<<<grid, TW, smem, L.stream>>>(P, S.rows, S.nrows, wl, S.b_sorted);
   return cudaGetLastError();
 }
 

@@ -41,7 +41,10 @@ inline int grid_for(long long items, int per_block, int num_sms, int cap_per_sm 
 
 // -------------------------------------------------------------- compression
 template <int TW>
-__global__ void __launch_bounds__(kBlock) k_compress_count(ProbD P, long long totalB, long long* cnt) {
+// Also counts the B rows whose columns are not strictly increasing (the dense
+// numeric windows look up column ranges by binary search only when none is).
+__global__ void __launch_bounds__(kBlock) k_compress_count(ProbD P, long long totalB, long long* cnt,
+                                                           unsigned long long* unsorted) {
   Team<TW> tm;
   const long long nteams = (long long)gridDim.x * tm.per_cta;
   for (long long gb = (long long)blockIdx.x * tm.per_cta + tm.id; gb < totalB; gb += nteams) {
@@ -58,13 +61,17 @@ __global__ void __launch_bounds__(kBlock) k_compress_count(ProbD P, long long to
       }
       continue;
     }
+    bool bad = false;
     for (long long p = s + tm.lane; p < e; p += TW) {
       int col = cj[p];
       if ((unsigned long long)(unsigned)col >= (unsigned long long)I.k) dev_fail(P.status, kDevBadIndex, 41, gb);
-      if (p == s || (col >> 5) != (cj[p - 1] >> 5)) ++c;
+      const int prev = p > s ? cj[p - 1] : -1;
+      if (p == s || (col >> 5) != (prev >> 5)) ++c;
+      bad |= p > s && col <= prev;
     }
     c = warp_team_sum<TW>(tm, c);
     if (tm.lane == 0) cnt[gb] = c;
+    if (__any_sync(tm.mask, bad) && tm.lane == 0) atomicAdd(unsorted, 1ull);
   }
 }
 
@@ -419,11 +426,12 @@ int resident_per_sm(const void* kernel, int threads, size_t smem) {
   return n;
 }
 
-cudaError_t launch_compress_count(const LaunchCtx& L, const ProbD& P, long long totalB, long long* cnt) {
+cudaError_t launch_compress_count(const LaunchCtx& L, const ProbD& P, long long totalB, long long* cnt,
+                                  unsigned long long* unsorted) {
   if (totalB <= 0) return cudaSuccess;
   int grid = grid_for(totalB, kBlock / 8, L.num_sms);
   KKS_LAUNCHED();
-  k_compress_count<8><<<grid, kBlock, 0, L.stream>>>(P, totalB, cnt);
+  k_compress_count<8><<<grid, kBlock, 0, L.stream>>>(P, totalB, cnt, unsorted);
   return cudaGetLastError();
 }
 

@@ -567,3 +567,18 @@ def test_aggregation_product_thread_rows(ops):
     h, _, _, Cd = run(ops, A, P)
     assert h.stats()["bin_rows_numeric"][7] == A.nrows
     assert_matches_oracle(A, P, Cd, np.float64)
+
+
+# ------------------------------------------------------------------ dense windows
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("shuffled", [False, True])
+def test_dense_windows_wide_k(ops, dtype, shuffled):
+    """Dense rows over a column range of several shared-memory windows; sorted B
+    rows take the binary-searched window ranges, shuffled ones the full scan."""
+    A = w.random_csr(200, 500, 20.0, seed=31)
+    B = w.random_csr(500, 70000, 30.0, seed=32)
+    if shuffled:
+        B = w.shuffle_rows(B, 5)
+    h, _, _, Cd = run(ops, A, B, dtype, dense=1)
+    assert h.stats()["bin_rows_numeric"][5] > 0
+    assert_matches_oracle(A, B, Cd, dtype)
