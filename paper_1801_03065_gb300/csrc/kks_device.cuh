@@ -484,11 +484,153 @@ __device__ __forceinline__ void prefetch_l1(const void* p) {
   asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
+// Exclusive max-scan over a CTA team (int values, -1 before the first thread).
+template <int TW>
+__device__ __forceinline__ int team_excl_max(const Team<TW>& tm, int v, long long* scratch) {
+  static_assert(Team<TW>::kCta, "CTA teams only");
+  const int l = threadIdx.x & 31, w = threadIdx.x >> 5, nw = TW / 32;
+  int x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, d);
+    if (l >= d) x = max(x, y);
+  }
+  int within = __shfl_up_sync(0xffffffffu, x, 1);
+  if (l == 0) within = -1;
+  if (l == 31) scratch[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int s = (l < nw) ? (int)scratch[l] : -1;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, s, d);
+      if (l >= d) s = max(s, y);
+    }
+    if (l < nw) scratch[l] = s;
+  }
+  __syncthreads();
+  const int before = w > 0 ? (int)scratch[w - 1] : -1;
+  __syncthreads();
+  return max(before, within);
+}
+
+// With seg (CTA teams, kStagedPasses * TW ints of shared memory) the A entry
+// of each product is not searched for: per block of kStagedPasses * TW
+// products, every non-empty B range marks where it starts and a forward fill
+// (max-scan) gives every product its range, one shared load per product.
+// This pays off when the chunk holds many short or empty B ranges (dense
+// windows, short B rows), where the search below needs many steps.
+// One chunk of A(i,:): lane t holds the B range [bs, be) and the value av of
+// its A entry.  Returns the chunk's product count (the same in every lane).
+template <int TW, typename VT, class Body, class Prefetch>
+__device__ __forceinline__ long long for_each_product_chunk(const Team<TW>& tm, ChunkScratch<TW, VT>* cs,
+                                                            long long* scan_scratch, long long bs, long long be,
+                                                            VT av, Body body, Prefetch prefetch, int* seg) {
+  long long total;
+  long long ex = team_excl_scan<TW>(tm, be - bs, &total, scan_scratch);
+  cs->pre[tm.lane] = ex;
+  cs->bs[tm.lane] = bs;
+  cs->av[tm.lane] = av;
+  if (tm.lane == 0) cs->pre[TW] = total;
+  tm.sync();
+  if constexpr (Team<TW>::kCta) {
+    if (seg != nullptr) {
+      constexpr int E = kStagedPasses;
+      constexpr long long S = (long long)kStagedPasses * TW;
+      int carry = -1;
+      for (long long x0 = 0; x0 < total; x0 += S) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) seg[tm.lane * E + e] = -1;
+        tm.sync();
+        if (be > bs && ex >= x0 && ex < x0 + S) seg[ex - x0] = tm.lane;
+        tm.sync();
+        int v[E];
+        int m = -1;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          v[e] = seg[tm.lane * E + e];
+          m = max(m, v[e]);
+        }
+        int run = max(carry, team_excl_max<TW>(tm, m, scan_scratch));
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          run = max(run, v[e]);
+          seg[tm.lane * E + e] = run;
+        }
+        tm.sync();
+        carry = seg[S - 1];
+        long long q[kStagedPasses];
+        int tt[kStagedPasses];
+#pragma unroll
+        for (int u = 0; u < kStagedPasses; ++u) {
+          const long long xu = x0 + (long long)u * TW + tm.lane;
+          q[u] = -1;
+          tt[u] = 0;
+          if (xu < total) {
+            const int t = seg[xu - x0];
+            q[u] = cs->bs[t] + (xu - cs->pre[t]);
+            tt[u] = t;
+            prefetch(q[u]);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kStagedPasses; ++u)
+          if (q[u] >= 0) body(q[u], tt[u]);
+        tm.sync();
+      }
+      return total;
+    }
+  }
+  if (total > 0) {
+    long long x = tm.lane;
+    if (x < total) {
+      // first product: binary search for the last t with pre[t] <= x
+      int lo = 0, hi = TW - 1;
+      while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (cs->pre[mid] <= x) lo = mid; else hi = mid - 1;
+      }
+      int t = lo;
+      for (; x < total; x += (long long)kStagedPasses * TW) {
+        long long q[kStagedPasses];
+        int tt[kStagedPasses];
+#pragma unroll
+        for (int u = 0; u < kStagedPasses; ++u) {
+          const long long xu = x + (long long)u * TW;
+          q[u] = -1;
+          tt[u] = t;
+          if (xu < total) {
+            // the A entry of product xu: a few linear steps (long B ranges),
+            // then a binary search (many short or empty ranges per pass)
+            for (int st = 0; st < 8 && cs->pre[t + 1] <= xu; ++st) ++t;
+            if (cs->pre[t + 1] <= xu) {
+              int lo2 = t + 1, hi2 = TW - 1;
+              while (lo2 < hi2) {
+                const int mid = (lo2 + hi2 + 1) >> 1;
+                if (cs->pre[mid] <= xu) lo2 = mid; else hi2 = mid - 1;
+              }
+              t = lo2;
+            }
+            q[u] = cs->bs[t] + (xu - cs->pre[t]);
+            tt[u] = t;
+            prefetch(q[u]);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kStagedPasses; ++u)
+          if (q[u] >= 0) body(q[u], tt[u]);
+      }
+    }
+  }
+  tm.sync();
+  return total;
+}
+
 template <int TW, typename VT, class Range, class AVal, class Body, class Prefetch>
 __device__ __forceinline__ void for_each_product(const Team<TW>& tm, ChunkScratch<TW, VT>* cs,
                                                  long long* scan_scratch, const int* Aj,
                                                  long long a_beg, long long a_end, Range range,
-                                                 AVal aval, Body body, Prefetch prefetch) {
+                                                 AVal aval, Body body, Prefetch prefetch, int* seg) {
   for (long long c = a_beg; c < a_end; c += TW) {
     long long p = c + tm.lane;
     long long bs = 0, be = 0;
@@ -498,55 +640,7 @@ __device__ __forceinline__ void for_each_product(const Team<TW>& tm, ChunkScratc
       range(j, &bs, &be);
       av = aval(p);
     }
-    long long total;
-    long long ex = team_excl_scan<TW>(tm, be - bs, &total, scan_scratch);
-    cs->pre[tm.lane] = ex;
-    cs->bs[tm.lane] = bs;
-    cs->av[tm.lane] = av;
-    if (tm.lane == 0) cs->pre[TW] = total;
-    tm.sync();
-    if (total > 0) {
-      long long x = tm.lane;
-      if (x < total) {
-        // first product: binary search for the last t with pre[t] <= x
-        int lo = 0, hi = TW - 1;
-        while (lo < hi) {
-          int mid = (lo + hi + 1) >> 1;
-          if (cs->pre[mid] <= x) lo = mid; else hi = mid - 1;
-        }
-        int t = lo;
-        for (; x < total; x += (long long)kStagedPasses * TW) {
-          long long q[kStagedPasses];
-          int tt[kStagedPasses];
-#pragma unroll
-          for (int u = 0; u < kStagedPasses; ++u) {
-            const long long xu = x + (long long)u * TW;
-            q[u] = -1;
-            tt[u] = t;
-            if (xu < total) {
-              // the A entry of product xu: a few linear steps (long B ranges),
-              // then a binary search (many short or empty ranges per pass)
-              for (int st = 0; st < 8 && cs->pre[t + 1] <= xu; ++st) ++t;
-              if (cs->pre[t + 1] <= xu) {
-                int lo = t + 1, hi = TW - 1;
-                while (lo < hi) {
-                  const int mid = (lo + hi + 1) >> 1;
-                  if (cs->pre[mid] <= xu) lo = mid; else hi = mid - 1;
-                }
-                t = lo;
-              }
-              q[u] = cs->bs[t] + (xu - cs->pre[t]);
-              tt[u] = t;
-              prefetch(q[u]);
-            }
-          }
-#pragma unroll
-          for (int u = 0; u < kStagedPasses; ++u)
-            if (q[u] >= 0) body(q[u], tt[u]);
-        }
-      }
-    }
-    tm.sync();
+    for_each_product_chunk<TW, VT>(tm, cs, scan_scratch, bs, be, av, body, prefetch, seg);
   }
 }
 
@@ -555,7 +649,15 @@ __device__ __forceinline__ void for_each_product(const Team<TW>& tm, ChunkScratc
                                                  long long* scan_scratch, const int* Aj,
                                                  long long a_beg, long long a_end, Range range,
                                                  AVal aval, Body body) {
-  for_each_product<TW, VT>(tm, cs, scan_scratch, Aj, a_beg, a_end, range, aval, body, [](long long) {});
+  for_each_product<TW, VT>(tm, cs, scan_scratch, Aj, a_beg, a_end, range, aval, body, [](long long) {}, nullptr);
+}
+
+template <int TW, typename VT, class Range, class AVal, class Body, class Prefetch>
+__device__ __forceinline__ void for_each_product(const Team<TW>& tm, ChunkScratch<TW, VT>* cs,
+                                                 long long* scan_scratch, const int* Aj,
+                                                 long long a_beg, long long a_end, Range range,
+                                                 AVal aval, Body body, Prefetch prefetch) {
+  for_each_product<TW, VT>(tm, cs, scan_scratch, Aj, a_beg, a_end, range, aval, body, prefetch, nullptr);
 }
 
 }  // namespace kks

@@ -36,7 +36,8 @@ constexpr long long kRankMaxWords = 16384;   // rank bitmaps cover k <= 524 288 
 template <int TW, typename VT>
 __host__ __device__ size_t num_cta_bytes(int T, long long kw_cap) {
   const int half = T / 2 > 0 ? T / 2 : 1;
-  size_t b = al16((size_t)T * sizeof(VT)) + al16((size_t)T * 4) + al16(sizeof(ChunkScratch<TW, VT>)) + 16;
+  size_t b = al16((size_t)T * sizeof(VT)) + al16((size_t)T * 4) + al16(sizeof(ChunkScratch<TW, VT>)) +
+             al16((size_t)kStagedPasses * TW * 4) + 16;
   if (kw_cap > 0) return b + al16((size_t)((kw_cap + 3) & ~3ll) * 4) + al16((size_t)(kw_cap + 1) * 2);
   return b + al16((size_t)half * 8);
 }
@@ -54,7 +55,9 @@ __global__ void k_num_hash(ProbD P, const int* __restrict__ rows, long long nrow
   int* keys = reinterpret_cast<int*>(smem + al16((size_t)T * sizeof(VT)));
   ChunkScratch<TW, VT>* csc =
       reinterpret_cast<ChunkScratch<TW, VT>*>(smem + al16((size_t)T * sizeof(VT)) + al16((size_t)T * 4));
-  unsigned char* tail = reinterpret_cast<unsigned char*>(csc) + al16(sizeof(ChunkScratch<TW, VT>)) + 16;
+  int* seg = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(csc) + al16(sizeof(ChunkScratch<TW, VT>)));
+  unsigned char* tail =
+      reinterpret_cast<unsigned char*>(seg) + al16((size_t)kStagedPasses * TW * 4) + 16;
   unsigned long long* sortb = reinterpret_cast<unsigned long long*>(tail);   // kw_cap == 0
   unsigned* bm = reinterpret_cast<unsigned*>(tail);                          // kw_cap > 0
   unsigned short* gp = reinterpret_cast<unsigned short*>(bm + ((kw_cap + 3) & ~3ll));
@@ -93,7 +96,7 @@ __global__ void k_num_hash(ProbD P, const int* __restrict__ rows, long long nrow
       prefetch_l1(Bj + q);
       prefetch_l1(Bx + q);
     };
-    for_each_product<TW, VT>(tm, csc, scan_scratch, I.A.cj, a0, a1, range, aval, body, pf);
+    for_each_product<TW, VT>(tm, csc, scan_scratch, I.A.cj, a0, a1, range, aval, body, pf, seg);
     const long long kw = (I.k + 31) >> 5;
     if (kw_cap > 0 && kw <= kw_cap) {
       VT* __restrict__ Cx = reinterpret_cast<VT*>(I.Cx);
@@ -795,6 +798,17 @@ __global__ void __launch_bounds__(TW) k_num_dense(ProbD P, const int* __restrict
       prefetch_l1(Bx + q);
     };
     long long run = 0;
+    // rows of one chunk on sorted B rows keep each A entry's cursor across
+    // windows: one binary search per window, and empty windows are skipped
+    const bool one_chunk = sorted_b && a1 - a0 <= TW;
+    long long cur = 0, end = 0;
+    VT av1 = VT(0);
+    if (one_chunk && a0 + tm.lane < a1) {
+      const int j = I.A.cj[a0 + tm.lane];
+      cur = rp_at(I.B, j);
+      end = rp_at(I.B, j + 1);
+      av1 = Ax[a0 + tm.lane];
+    }
     for (long long w0 = 0; w0 < k; w0 += W) {
       auto range = [&](int j, long long* bs, long long* be) {
         *bs = rp_at(I.B, j);
@@ -816,8 +830,17 @@ __global__ void __launch_bounds__(TW) k_num_dense(ProbD P, const int* __restrict
           atomicOr(bm + (x >> 5), 1u << (x & 31));
         }
       };
-      for_each_product<TW, VT>(tm, csc, scan_scratch, I.A.cj, a0, a1, range, aval, body, pf);
-      __syncthreads();
+      if (one_chunk) {
+        long long ub = cur;
+        if (cur < end && (long long)Bj[cur] < w0 + W) ub = lower_col(Bj, cur, end, w0 + W);
+        const long long tot = for_each_product_chunk<TW, VT>(tm, csc, scan_scratch, cur, ub, av1, body, pf, nullptr);
+        cur = ub;
+        __syncthreads();
+        if (tot == 0) continue;
+      } else {
+        for_each_product<TW, VT>(tm, csc, scan_scratch, I.A.cj, a0, a1, range, aval, body, pf);
+        __syncthreads();
+      }
       // the window's columns in order: word-wise prefix of set bits, then emit
       const long long nw = ((k - w0 + 31) >> 5) < ww ? ((k - w0 + 31) >> 5) : ww;
       for (long long wb = 0; wb < nw; wb += TW) {
