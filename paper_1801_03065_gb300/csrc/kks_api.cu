@@ -90,6 +90,7 @@ struct kks_handle {
   size_t cap[kNumBufs] = {};
   size_t total = 0;
   unsigned char* pinned = nullptr;   // readbacks and uploads
+  unsigned char* pinned_dev = nullptr;   // its device alias (mapped memory)
   size_t pinned_bytes = 0;
   unsigned char* ring[kRing] = {};   // numeric table uploads
   size_t ring_bytes = 0;
@@ -189,11 +190,18 @@ spgemm_status_t ensure_pinned(kks_handle* h, size_t bytes) {
   h->pinned_bytes = 0;
   size_t want = std::max<size_t>(bytes, 1 << 16);
   void* p = nullptr;
-  if (cudaHostAlloc(&p, want, cudaHostAllocDefault) != cudaSuccess) {
+  if (cudaHostAlloc(&p, want, cudaHostAllocMapped) != cudaSuccess) {
     cudaGetLastError();
     return SPGEMM_ERR_OOM;
   }
+  void* pd = nullptr;
+  if (cudaHostGetDevicePointer(&pd, p, 0) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFreeHost(p);
+    return SPGEMM_ERR_CUDA;
+  }
   h->pinned = (unsigned char*)p;
+  h->pinned_dev = (unsigned char*)pd;
   h->pinned_bytes = want;
   return SPGEMM_OK;
 }
@@ -419,6 +427,13 @@ spgemm_status_t upload_inst(kks_handle* h, cudaStream_t s) {
   return SPGEMM_OK;
 }
 
+// Read-back of `bytes` from device memory into the handle's pinned buffer
+// (dst points into it) by a kernel writing the mapped alias.
+cudaError_t to_host(kks_handle* h, void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  LaunchCtx L = ctx(h, s);
+  return launch_copy_to_host(L, h->pinned_dev + ((unsigned char*)dst - h->pinned), src, bytes);
+}
+
 // Numeric rows whose warp-class bin takes output positions from the column sets.
 long long rows_positions(const kks_handle* h) {
   long long n = 0;
@@ -530,14 +545,12 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
   unsigned long long* h_unsorted = (unsigned long long*)(rd + sizeof(unsigned long long) * (4 * ni + 2 * ni + 2 * kNumBins));
   *h_nbc = 0;
   *h_unsorted = 1;
-  KKS_CU(cudaMemcpyAsync(h_stats, h->buf[kBufInstStats], sizeof(unsigned long long) * 4 * ni,
-                         cudaMemcpyDeviceToHost, s));
+  KKS_CU(to_host(h, h_stats, h->buf[kBufInstStats], sizeof(unsigned long long) * 4 * ni, s));
   if (comp_on) {
-    KKS_CU(cudaMemcpyAsync(h_nbc, B<long long>(h, kBufBcp) + totalB, sizeof(long long), cudaMemcpyDeviceToHost, s));
-    KKS_CU(cudaMemcpyAsync(h_unsorted, B<unsigned long long>(h, kBufInstStats) + 4 * ni, sizeof(unsigned long long),
-                           cudaMemcpyDeviceToHost, s));
+    KKS_CU(to_host(h, h_nbc, B<long long>(h, kBufBcp) + totalB, sizeof(long long), s));
+    KKS_CU(to_host(h, h_unsorted, B<unsigned long long>(h, kBufInstStats) + 4 * ni, sizeof(unsigned long long), s));
   }
-  KKS_CU(cudaMemcpyAsync(h_status, h->buf[kBufStatus], sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+  KKS_CU(to_host(h, h_status, h->buf[kBufStatus], sizeof(DevStatus), s));
   KKS_CU(cudaStreamSynchronize(s));
   KKS_ST(consume_status(h, h_status, s));
   h->b_sorted = comp_on && *h_unsorted == 0;
@@ -589,7 +602,7 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
                             d_hist, B<long long>(h, kBufBinCnt) + pass * (nbc + 1)));
     KKS_CU(launch_scan(L, B<long long>(h, kBufBinCnt) + pass * (nbc + 1), B<long long>(h, kBufBinOfs) + pass * (nbc + 1),
                        nbc, h->buf[kBufScanTmp]));
-    KKS_CU(cudaMemcpyAsync(h_hist, d_hist, sizeof(unsigned long long) * kNumBins, cudaMemcpyDeviceToHost, s));
+    KKS_CU(to_host(h, h_hist, d_hist, sizeof(unsigned long long) * kNumBins, s));
     KKS_CU(cudaStreamSynchronize(s));
     for (int t = 0; t < kNumBins; ++t) hist[pass * kNumBins + t] = h_hist[t];
   }
@@ -659,7 +672,7 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
   if (h->opt.method == 1 && totalA > 0) {
     // the plain rule sizes L1 from the average row of C: read nnz(C) first
     unsigned long long* h_o = (unsigned long long*)(rd + sizeof(unsigned long long) * 4 * ni);
-    KKS_CU(cudaMemcpyAsync(h_o, h->buf[kBufInstOut], sizeof(unsigned long long) * 2 * ni, cudaMemcpyDeviceToHost, s));
+    KKS_CU(to_host(h, h_o, h->buf[kBufInstOut], sizeof(unsigned long long) * 2 * ni, s));
     KKS_CU(cudaStreamSynchronize(s));
     long long nz = 0;
     for (int b = 0; b < count; ++b) nz += (long long)h_o[2 * b];
@@ -670,9 +683,9 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
                           d_hist, B<long long>(h, kBufBinCnt)));
   KKS_CU(launch_scan(L, B<long long>(h, kBufBinCnt), B<long long>(h, kBufBinOfs), nbc, h->buf[kBufScanTmp]));
   unsigned long long* h_out = (unsigned long long*)(rd + sizeof(unsigned long long) * 4 * ni);
-  KKS_CU(cudaMemcpyAsync(h_hist, d_hist, sizeof(unsigned long long) * kNumBins, cudaMemcpyDeviceToHost, s));
-  KKS_CU(cudaMemcpyAsync(h_out, h->buf[kBufInstOut], sizeof(unsigned long long) * 2 * ni, cudaMemcpyDeviceToHost, s));
-  KKS_CU(cudaMemcpyAsync(h_status, h->buf[kBufStatus], sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+  KKS_CU(to_host(h, h_hist, d_hist, sizeof(unsigned long long) * kNumBins, s));
+  KKS_CU(to_host(h, h_out, h->buf[kBufInstOut], sizeof(unsigned long long) * 2 * ni, s));
+  KKS_CU(to_host(h, h_status, h->buf[kBufStatus], sizeof(DevStatus), s));
   KKS_CU(cudaStreamSynchronize(s));
   KKS_ST(consume_status(h, h_status, s));
 
@@ -1000,10 +1013,10 @@ spgemm_status_t plan_masked(kks_handle* h, const MaskedD& M, long long nrows, in
   KKS_CU(launch_masked_bin_count(L, Mx, nrows, c, d_hist, B<long long>(h, kBufBinCnt)));
   if (nrows > 0) KKS_CU(launch_scan(L, B<long long>(h, kBufBinCnt), B<long long>(h, kBufBinOfs), nbc, h->buf[kBufScanTmp]));
   if (h->opt.numeric_positions) KKS_CU(launch_pattern_unsorted(L, Mx, nrows, d_unsorted));
-  KKS_CU(cudaMemcpyAsync(h_hist, d_hist, sizeof(unsigned long long) * kNumBins, cudaMemcpyDeviceToHost, s));
-  KKS_CU(cudaMemcpyAsync(h_unsorted, d_unsorted, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  KKS_CU(to_host(h, h_hist, d_hist, sizeof(unsigned long long) * kNumBins, s));
+  KKS_CU(to_host(h, h_unsorted, d_unsorted, sizeof(unsigned long long), s));
   DevStatus* hs = (DevStatus*)(h->pinned + sizeof(unsigned long long) * (2 * kNumBins + 2));
-  KKS_CU(cudaMemcpyAsync(hs, h->buf[kBufStatus], sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+  KKS_CU(to_host(h, hs, h->buf[kBufStatus], sizeof(DevStatus), s));
   KKS_CU(cudaStreamSynchronize(s));
   KKS_ST(consume_status(h, hs, s));
   plan->sorted = h->opt.numeric_positions != 0 && *h_unsorted == 0;
@@ -1168,7 +1181,7 @@ spgemm_status_t spgemm_handle_sync(spgemm_handle_t h, spgemm_stream_t stream) {
   }
   KKS_ST(ensure_pinned(h, sizeof(DevStatus)));
   DevStatus* hs = (DevStatus*)h->pinned;
-  KKS_CU(cudaMemcpyAsync(hs, h->buf[kBufStatus], sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+  KKS_CU(to_host(h, hs, h->buf[kBufStatus], sizeof(DevStatus), s));
   KKS_CU(cudaStreamSynchronize(s));
   return consume_status(h, hs, s);
 }
@@ -1286,7 +1299,7 @@ spgemm_status_t spgemm_transpose(spgemm_handle_t h, const spgemm_csr_t* A, int64
   DevStatus* hs = (DevStatus*)(h->pinned + 64);
   KKS_CU(launch_transpose_count(L, M, reinterpret_cast<long long*>(At_rowptr), h->buf[kBufTrTmp], hmax,
                                 B<DevStatus>(h, kBufStatus)));
-  KKS_CU(cudaMemcpyAsync(hs, h->buf[kBufStatus], sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+  KKS_CU(to_host(h, hs, h->buf[kBufStatus], sizeof(DevStatus), s));
   KKS_CU(cudaStreamSynchronize(s));
   KKS_ST(consume_status(h, hs, s));
   const long long max_len = (long long)*hmax;

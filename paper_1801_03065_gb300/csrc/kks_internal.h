@@ -114,6 +114,10 @@ inline unsigned resident_grid(K kernel, int threads, size_t smem, int num_sms, l
   return (unsigned)g;
 }
 
+// device -> mapped pinned host memory through a kernel (4-byte aligned; bytes
+// rounded up to whole words)
+cudaError_t launch_copy_to_host(const LaunchCtx&, void* dst_mapped, const void* src, size_t bytes);
+
 // prep: statistics, compression, scans, binning
 // per-row compressed lengths; *unsorted += rows of B whose columns do not increase
 cudaError_t launch_compress_count(const LaunchCtx&, const ProbD&, long long totalB, long long* cnt,

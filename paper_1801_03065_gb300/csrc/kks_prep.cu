@@ -157,19 +157,41 @@ __global__ void __launch_bounds__(kBlock) k_row_stats(ProbD P, long long totalA,
     // here so malformed input stops the symbolic phase at its first sync
     const bool rows_ok = (s >= 0 && s <= e && e <= I.A.nnz);
     if (!rows_ok && tm.lane == 0) dev_fail(P.status, kDevBadIndex, 42, g);
-    for (long long p = s + tm.lane; rows_ok && p < e; p += TW) {
-      const int j = I.A.cj[p];
-      if ((unsigned long long)(unsigned)j >= (unsigned long long)I.A.ncols) {
-        dev_fail(P.status, kDevBadIndex, 43, g);
-        continue;
+    // four entries per lane in flight: their column loads, then their row-pointer loads
+    constexpr int kU = 4;
+    for (long long p0 = s + tm.lane; rows_ok && p0 < e; p0 += (long long)kU * TW) {
+      int jj[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const long long p = p0 + (long long)u * TW;
+        jj[u] = p < e ? I.A.cj[p] : -1;
+        if (p < e && (unsigned long long)(unsigned)jj[u] >= (unsigned long long)I.A.ncols) {
+          dev_fail(P.status, kDevBadIndex, 43, g);
+          jj[u] = -1;
+        }
       }
-      const long long bs = rp_at(I.B, j), be = rp_at(I.B, j + 1);
-      if (bs < 0 || bs > be || be > I.B.nnz) {
-        dev_fail(P.status, kDevBadIndex, 44, g);
-        continue;
+      long long bs[kU], be[kU], cs[kU], ce[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        bs[u] = be[u] = cs[u] = ce[u] = 0;
+        if (jj[u] >= 0) {
+          bs[u] = rp_at(I.B, jj[u]);
+          be[u] = rp_at(I.B, jj[u] + 1);
+          if (use_bc) {
+            cs[u] = P.Bcp[I.brow0 + jj[u]];
+            ce[u] = P.Bcp[I.brow0 + jj[u] + 1];
+          }
+        }
       }
-      f += be - bs;
-      if (use_bc) fc += P.Bcp[I.brow0 + j + 1] - P.Bcp[I.brow0 + j];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        if (bs[u] < 0 || bs[u] > be[u] || be[u] > I.B.nnz) {
+          dev_fail(P.status, kDevBadIndex, 44, g);
+          continue;
+        }
+        f += be[u] - bs[u];
+        fc += ce[u] - cs[u];
+      }
     }
     f = warp_team_sum<TW>(tm, f);
     fc = warp_team_sum<TW>(tm, fc);
@@ -402,7 +424,25 @@ __global__ void k_empty_instances(ProbD P, unsigned long long* inst_out) {
 
 }  // namespace
 
+// A few words from device memory into mapped pinned host memory.  The
+// planning calls read their statistics back this way rather than with a copy
+// engine, so the read-backs never queue behind large copies that the caller
+// runs on other streams.
+__global__ void k_copy_to_host(const unsigned* __restrict__ src, unsigned* dst, long long words) {
+  for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < words; x += (long long)gridDim.x * blockDim.x)
+    dst[x] = src[x];
+}
+
 // ============================================================== launchers
+cudaError_t launch_copy_to_host(const LaunchCtx& L, void* dst_mapped, const void* src, size_t bytes) {
+  if (bytes == 0) return cudaSuccess;
+  const long long words = (long long)((bytes + 3) / 4);
+  KKS_LAUNCHED();
+  k_copy_to_host<<<(unsigned)std::min<long long>((words + 255) / 256, 64), 256, 0, L.stream>>>(
+      reinterpret_cast<const unsigned*>(src), reinterpret_cast<unsigned*>(dst_mapped), words);
+  return cudaGetLastError();
+}
+
 int resident_per_sm(const void* kernel, int threads, size_t smem) {
   struct Entry {
     const void* k;
