@@ -285,7 +285,8 @@ __device__ __forceinline__ int lp_find(const int* keys, const LpHash& hs, int ke
 // 3.2) is ORed into the slot's second word.  Products are spread flat over the
 // lanes, and the loads of kUnionPasses passes are issued before their inserts
 // so that their latencies overlap.  pre holds TW + 1 ints, qsv TW offsets.
-// Returns the number of slots this lane claimed.
+// Returns the number of slots this lane claimed, or with BITS the number of
+// column bits this lane was first to set (their team sum is the row size).
 // --------------------------------------------------------------------------
 constexpr int kUnionPasses = 4;
 
@@ -323,7 +324,7 @@ __device__ __forceinline__ int union_chunk(unsigned team_mask, int lane, int* pr
   qsv[lane] = qs;
   if (lane == 0) pre[TW] = tot;
   __syncwarp(team_mask);
-  int fresh = 0;
+  int fresh = 0, nbits = 0;
   int t = 0;
   for (int xb = 0; xb < tot; xb += kUnionPasses * TW) {
     int key[kUnionPasses];
@@ -345,7 +346,10 @@ __device__ __forceinline__ int union_chunk(unsigned team_mask, int lane, int* pr
       if (key[u] >= 0) {
         const int slot = slot_insert<STRIDE>(words, hs, key[u], &fresh);
         if (slot >= 0) {
-          if (BITS) atomicOr(reinterpret_cast<unsigned*>(words + STRIDE * slot + 1), m[u]);
+          if (BITS) {
+            const unsigned old = atomicOr(reinterpret_cast<unsigned*>(words + STRIDE * slot + 1), m[u]);
+            nbits += __popc(m[u] & ~old);
+          }
         } else {
           dev_fail(status, kDevTableFull, code, g);
         }
@@ -353,7 +357,7 @@ __device__ __forceinline__ int union_chunk(unsigned team_mask, int lane, int* pr
     }
   }
   __syncwarp(team_mask);
-  return fresh;
+  return BITS ? nbits : fresh;
 }
 
 // Tables of 16-byte slots (column-set index, set bits, base, unused): the

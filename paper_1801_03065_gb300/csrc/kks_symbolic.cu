@@ -136,7 +136,8 @@ __global__ void k_sym_hash(ProbD P, const int* __restrict__ rows, long long nrow
 
 // Warp teams (W8, W32 rows): slots of one key (or key + column-set word), the
 // union of union_chunk with the loads of several passes in flight; the row
-// size is the number of claimed slots, or the set bits of the union.
+// size is the number of claimed slots, or of the column bits set first by an
+// insert (counted as they are ORed in, so no sweep of the table is needed).
 template <int TW, bool COMP>
 __host__ __device__ size_t symw_team_bytes(int T) {
   return al16((size_t)T * 4 * (COMP ? 2 : 1)) + al16((size_t)(TW + 1) * 4) + al16((size_t)TW * 8);
@@ -187,15 +188,8 @@ __global__ void __launch_bounds__(256, 4) k_sym_warp(ProbD P, const int* __restr
       fresh += union_chunk<TW, S, COMP>(tm.mask, tm.lane, pre, qsv, qs, ql, COMP ? P.csi : I.B.cj, P.cs, words,
                                         hs, P.status, 1, g);
     }
-    long long cnt = 0;
-    if (COMP) {
-      for (int x = tm.lane; x < T; x += TW) {
-        const int2 e = reinterpret_cast<const int2*>(words)[x];
-        if (e.x != kEmpty) cnt += __popc((unsigned)e.y);
-      }
-    } else {
-      cnt = fresh;
-    }
+    // claimed slots, or (compressed) newly set column bits, summed over the team
+    long long cnt = fresh;
 #pragma unroll
     for (int d = TW / 2; d > 0; d >>= 1) cnt += __shfl_xor_sync(tm.mask, cnt, d, TW);
     if (tm.lane == 0) rowsize[g] = cnt;
