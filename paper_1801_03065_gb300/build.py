@@ -46,7 +46,9 @@ def _digest() -> str:
                 h.update(n.encode())
                 with open(p, "rb") as f:
                     h.update(f.read())
-    h.update(" ".join(ARCH + FLAGS).encode())
+    # flags without the include directories, whose absolute paths depend on
+    # where the repository sits
+    h.update(" ".join(ARCH + [f for f in FLAGS if not f.startswith("-I")]).encode())
     return h.hexdigest()
 
 

@@ -345,6 +345,11 @@ BinCfg sym_cfg(kks_handle* h, int comp) {
   // one thread per row when the row has at most kT1SymKeys products
   c.t1_max_keys = kT1SymKeys;
   c.t1_max_work = kT1SymKeys;
+  // on the compressed B the key bound min(rfc, k/32) counts compressed
+  // products, of which many share a column set (that is why B was
+  // compressed): a table of the next power of two >= the bound holds every key
+  // and runs at low load, with half the sweep and twice the teams per SM
+  if (comp && h->opt.slots_per_key_log2 == 0) c.slots_log2 = -1;
   clamp_cfg(h, c);
   return c;
 }

@@ -55,7 +55,7 @@ struct BinCfg {
   int spill_ok;            // L1 + L2 hash allowed
   int force_cls;           // >0: every non-empty row goes to this class
   int force_logT;          // with force_cls: table size used for every row
-  int slots_log2;          // table slots per key bound, log2 (1: at most 50 % load)
+  int slots_log2;          // table slots per key bound, log2 (0 = 1: at most 50 % load; -1: next power of two)
   long long t1_max_work;   // > 0: rows with u <= t1_max_keys and work <= this go to class T1
   int t1_max_keys;         // 0: kT1MaxKeys
 };
@@ -65,7 +65,7 @@ struct BinCfg {
 __host__ __device__ inline int choose_bin(long long u, long long work, long long kk, long long kwords,
                                           const BinCfg& c) {
   if (u <= 0 || work <= 0) return bin_id(kClsNone, 0);
-  int logT = ilog2_ceil(u) + (c.slots_log2 > 0 ? c.slots_log2 : 1);
+  int logT = ilog2_ceil(u) + (c.slots_log2 > 0 ? c.slots_log2 : (c.slots_log2 < 0 ? 0 : 1));
   if (logT < c.min_logT) logT = c.min_logT;
   if (logT > 30) logT = 30;   // bin ids hold logT < kBinsPerClass; such rows fail pool sizing
   if (c.force_cls > 0) {
