@@ -49,7 +49,8 @@ def parse_args(argv=None):
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
-    p.add_argument("--workload", choices=["stencil27_100", "batched512", "rmat18", "laplace5_64", "laplace7_64"],
+    p.add_argument("--workload", choices=["stencil27_100", "batched512", "rmat18", "laplace5_64", "laplace7_64",
+                                          "rmat18_triangles"],
                    default="stencil27_100",
                    help="stencil27_100: the headline step; batched512: batched autotuned vs plain per-matrix")
     p.add_argument("--count", type=int, default=512, help="batched512: number of products")
@@ -701,6 +702,39 @@ def run_single(args):
         "clocks": clk})), flush=True)
 
 
+def run_triangles(args):
+    """Triangle counts of the R-MAT scale-18 graph: the masked count of (L·L) on
+    L (L its strictly lower triangle), symbolic only on the compressed L; the
+    rate is in structural products of L·L per second."""
+    import numpy as np
+    import torch
+    import workloads as w
+    import oracle
+    from paper_1801_03065_gb300 import ops
+    torch.cuda.set_device(0)
+    G = w.rmat_symmetric(scale=18, seed=7)
+    L = oracle.lower_triangle(G)
+    Ld = ops.CsrMatrix.from_host(L.rowptr, L.colidx, None, L.shape, device="cuda:0")
+    h = ops.SpGEMM()
+    out = torch.empty(L.nrows, dtype=torch.int64, device="cuda:0")
+    fn = lambda: h.masked_count(Ld, Ld, Ld.rowptr, Ld.colidx, out=out)
+    for _ in range(max(args.warmup, 1)):
+        fn()
+    torch.cuda.synchronize()
+    t = statistics.mean(time_region(torch, fn, args.steps))
+    tri = int(out.sum().item())
+    lens = np.diff(L.rowptr)
+    products = int(lens[L.colidx].sum())          # |L(j,:)| summed over the entries of L
+    desc = ("rmat18_triangles: per-vertex triangle counts of the symmetrised R-MAT scale-18 graph "
+            "(%d edges), masked count of L*L on L with L compressed" % (L.nnz))
+    h.close()
+    out_line = _base_line(args, products / (t * 1e-3) / 1e9, t, desc, "int64", {
+        "unit": "G structural products/s", "triangles": tri, "products": products})
+    out_line["metric"] = "masked count (triangles) throughput"
+    out_line["higher_is_better"] = True
+    print(json.dumps(out_line), flush=True)
+
+
 def run_differentiation(args):
     """loss = sum W * (A·P) on fixed patterns (7-point Laplacian 64^3, 2^3
     aggregation P): forward (numeric reuse on C's pattern) and backward (dA and dB
@@ -755,6 +789,8 @@ def main(argv=None):
         run_single(args)
     elif args.workload == "laplace7_64":
         run_differentiation(args)
+    elif args.workload == "rmat18_triangles":
+        run_triangles(args)
     else:
         run_ours(args)
 

@@ -6,10 +6,10 @@
  * Multiplication for Many-Core and GPU Architectures" (Section 2).  The calls
  * follow the paper's two-phase structure (Algorithm 2):
  *
- *   spgemm_symbolic   lines 1-3: row statistics, compression of B, and the
- *                     size of every row of C -> C row pointers and nnz(C)
- *   (caller)          line 4: allocate C column indices and values
- *   spgemm_numeric    line 5: C's columns and values
+ *   spgemm_symbolic   the symbolic phase: row statistics, compression of B,
+ *                     and the size of every row of C -> C row pointers, nnz(C)
+ *   (caller)          allocation of C's column indices and values
+ *   spgemm_numeric    the numeric phase: C's columns and values
  *
  * Numeric reuse (Section 2, two-phase methods; Section 4 "Reuse"): after one
  * symbolic call, spgemm_numeric may be called any number of times with new
@@ -134,7 +134,7 @@ spgemm_status_t spgemm_handle_create(spgemm_handle_t *out, const spgemm_options_
 spgemm_status_t spgemm_handle_destroy(spgemm_handle_t h);
 
 /*
- * Symbolic phase (Algorithm 2 lines 1-3).  Computes the row pointers of C into
+ * Symbolic phase (Algorithm 2).  Computes the row pointers of C into
  * C_rowptr (device, int64[m + 1], caller-allocated) and writes nnz(C) to
  * *nnzC (HOST pointer).  Values of A and B are not read.  Synchronises the
  * stream once to return nnz(C), and plans the numeric phase.
@@ -143,7 +143,7 @@ spgemm_status_t spgemm_symbolic(spgemm_handle_t h, const spgemm_csr_t *A, const 
                                 int64_t *C_rowptr, int64_t *nnzC, spgemm_stream_t stream);
 
 /*
- * Numeric phase (Algorithm 2 line 5).  A and B must be the operands of the
+ * Numeric phase (Algorithm 2).  A and B must be the operands of the
  * last symbolic call on h (same patterns, same device pointers for the
  * patterns; the value pointers may change).  Writes C_colidx (int32[nnzC])
  * and C_values (nnzC values of A's dtype), rows sorted by column.  Fully
@@ -187,6 +187,28 @@ spgemm_status_t spgemm_masked(spgemm_handle_t h, const spgemm_csr_t *X, const sp
                               const int64_t *S_rowptr, const int32_t *S_colidx, int64_t S_nnz,
                               void *out, const int64_t *X_perm, const int64_t *Y_perm,
                               spgemm_stream_t stream);
+
+/*
+ * Structural masked count on the compressed Y (the symbolic-only use of the
+ * two-phase method for graph analytics, Section 2, with the compression of
+ * Section 3.2):
+ *     row_counts[i] = sum over l in S(i,:) of |{ j : (i,j) in X and (j,l) in Y }|,
+ * the row sums of (X*Y) sampled on S over the counting semiring; values are
+ * never read (X.values and Y.values may be NULL).  With X = Y = S = L, the
+ * strictly lower triangle of an undirected graph, the sum of row_counts is the
+ * number of triangles.  Y's rows are compressed into 32-column sets inside
+ * the call, and every compressed product adds the popcount of its set bits
+ * that S(i,:) also holds.  S: int64 row pointers [X.nrows + 1] and S_nnz
+ * int32 columns, distinct within a row, any order.  row_counts: int64
+ * [X.nrows], device.  Synchronises the stream twice.  A row of S with more
+ * than 1024 entries is counted against a bitmap of ceil(Y.ncols / 32) words
+ * in shared memory: when that does not fit (Y.ncols above about 1.6 M) the
+ * call returns SPGEMM_ERR_DEVICE_LIMIT.  Out-of-range indices give
+ * SPGEMM_ERR_BAD_INDEX.
+ */
+spgemm_status_t spgemm_masked_count(spgemm_handle_t h, const spgemm_csr_t *X, const spgemm_csr_t *Y,
+                                    const int64_t *S_rowptr, const int32_t *S_colidx, int64_t S_nnz,
+                                    int64_t *row_counts, spgemm_stream_t stream);
 
 /*
  * Transpose: At = A^T (A.ncols x A.nrows) with At_rowptr int64[A.ncols + 1],

@@ -10,7 +10,7 @@ brackets):
 * ``row_flops``        – rf_i = Σ_{j∈A(i,:)} |B(j,:)|, f_m = Σ rf_i, maxrf
                          [§2, multiplication count of Algorithm 1; §3.1.2]
 * ``compress``         – CSI = col >> 5, CS = OR of 1 << (col & 31) per distinct CSI [§3.2]
-* ``symbolic_plain``   – |C(i,:)| = #distinct l reachable through A(i,:) [Alg. 2 line 3]
+* ``symbolic_plain``   – |C(i,:)| = #distinct l reachable through A(i,:) [Algorithm 2, symbolic phase]
 * ``symbolic_compressed`` – Σ popcount of the OR-union of B_c rows [§3.2, Alg. 3]
 * ``spgemm``           – C = A·B by gather / stable sort / in-order sum [Alg. 1]
 * ``transpose``        – counting transpose with value permutation
@@ -49,9 +49,10 @@ def lib():
         L.oracle_transpose.argtypes = [i64, i64, p, p, p, p, p, p, p]
         L.oracle_masked_dA.argtypes = [i64, i64, p, p, p, p, p, p, p, p, p, p]
         L.oracle_masked_dB.argtypes = [i64, i64, i64, p, p, p, p, p, p, p, p, p, p]
+        L.oracle_masked_count.argtypes = [i64, i64, p, p, p, p, p, p, p]
         for f in ("oracle_row_flops", "oracle_compress_count", "oracle_compress_fill",
                   "oracle_symbolic_plain", "oracle_symbolic_compressed", "oracle_numeric",
-                  "oracle_transpose", "oracle_masked_dA", "oracle_masked_dB",
+                  "oracle_transpose", "oracle_masked_dA", "oracle_masked_dB", "oracle_masked_count",
                   "oracle_num_threads"):
             getattr(L, f).restype = C.c_int
         _lib = L
@@ -189,3 +190,22 @@ def stats(A: Csr, B: Csr):
     out["CMRF"] = out["maxrf_compressed"] / maxrf if maxrf else 1.0
     out["rowsizes_match"] = bool(np.array_equal(cp, cpc))
     return out
+
+
+def masked_count(X: Csr, Y: Csr, S: Csr):
+    """counts[i] = sum over l in S(i,:) of |{j : (i,j) in X, (j,l) in Y}| (int64[X.nrows])."""
+    assert X.ncols == Y.nrows and S.nrows == X.nrows
+    out = np.zeros(X.nrows, dtype=np.int64)
+    _check(lib().oracle_masked_count(X.nrows, Y.ncols, _ptr(X.rowptr), _ptr(X.colidx), _ptr(Y.rowptr),
+                                     _ptr(Y.colidx), _ptr(S.rowptr), _ptr(S.colidx), _ptr(out)),
+           "masked_count")
+    return out
+
+
+def lower_triangle(A: Csr) -> Csr:
+    """The strictly lower triangle of A's pattern (values dropped)."""
+    rid = np.repeat(np.arange(A.nrows), np.diff(A.rowptr))
+    keep = A.colidx < rid
+    rp = np.zeros(A.nrows + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rid[keep], minlength=A.nrows), out=rp[1:])
+    return Csr(A.nrows, A.ncols, rp, A.colidx[keep].astype(np.int32), None)

@@ -18,15 +18,18 @@
  *                                 CS = OR of (1 << (col & 31)) (Section 3.2)
  *   oracle_symbolic_plain ....... |C(i,:)| by its definition, the number of
  *                                 distinct l with A(i,j) != 0 and B(j,l) != 0
- *                                 (Algorithm 2, line 3)
+ *                                 (Algorithm 2, symbolic phase)
  *   oracle_symbolic_compressed .. |C(i,:)| the way the symbolic phase computes it
  *                                 on the compressed B: OR-union of column sets,
  *                                 then the number of set bits (Section 3.2,
- *                                 Algorithm 3 line 14)
+ *                                 Algorithm 3)
  *   oracle_numeric .............. C(i,:) = sum_j A(i,j) * B(j,:) (Algorithm 1),
  *                                 as a gather of all products of the row, a
  *                                 stable sort by column, and an in-order sum
  *   oracle_transpose ............ counting transpose with its value permutation
+ *   oracle_masked_count ......... row sums of (X*Y) on a pattern S over the
+ *                                 counting semiring (symbolic-only graph use,
+ *                                 Section 2): triangle counts when X = Y = S = L
  *   oracle_masked_dA / _dB ...... gradients of a loss sum(W o (A*B)) on fixed
  *                                 patterns, by their definition:
  *                                 dA(i,j) = sum_l G(i,l) B(j,l) on A's pattern,
@@ -384,5 +387,35 @@ int oracle_masked_dB(int64_t m, int64_t n, int64_t k, const int64_t *Ap, const i
         }
     }
     free(Atp); free(Atj); free(Atx); free(acc); free(acca);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* counts[i] = sum over l in S(i,:) of |{ j : (i,j) in X and (j,l) in Y }|:  */
+/* the row sums of (X*Y) sampled on S over the counting semiring (the        */
+/* symbolic-only product of graph analytics, Section 2), by definition: mark  */
+/* S(i,:), then walk every product of row i and count those that land on a   */
+/* mark.  Values are not read.                                               */
+/* ------------------------------------------------------------------------ */
+int oracle_masked_count(int64_t m, int64_t k, const int64_t *Xp, const int32_t *Xj, const int64_t *Yp,
+                        const int32_t *Yj, const int64_t *Sp, const int32_t *Sj, int64_t *counts) {
+    int nt = oracle_threads();
+    size_t stride = (size_t)(k > 0 ? k : 1);
+    int64_t *mark = (int64_t *)malloc(stride * nt * sizeof(int64_t));
+    if (!mark) return -1;
+    for (size_t x = 0; x < stride * nt; ++x) mark[x] = -1;
+    #pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < m; ++i) {
+        int64_t *mk = mark + (size_t)oracle_tid() * stride;
+        for (int64_t p = Sp[i]; p < Sp[i + 1]; ++p) mk[Sj[p]] = i;
+        int64_t c = 0;
+        for (int64_t p = Xp[i]; p < Xp[i + 1]; ++p) {
+            int64_t j = Xj[p];
+            for (int64_t q = Yp[j]; q < Yp[j + 1]; ++q)
+                if (mk[Yj[q]] == i) ++c;
+        }
+        counts[i] = c;
+    }
+    free(mark);
     return 0;
 }

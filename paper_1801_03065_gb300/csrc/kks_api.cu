@@ -1,6 +1,6 @@
 // kks_api.cu -- the C ABI: handle, workspace, planning of the two phases.
 //
-// spgemm_symbolic runs Algorithm 2 lines 1-3 on the GPU:
+// spgemm_symbolic runs the symbolic phase of Algorithm 2 on the GPU:
 //   (1) compression pass 1: compressed row lengths of B, their scan
 //   (2) row statistics rf_i (and rfc_i on the compressed B), per problem f_m,
 //       maxrf and the compressed counterparts                      -> sync 1
@@ -8,7 +8,7 @@
 //   (4) row bins for the symbolic kernels                           -> sync 2
 //   (5) symbolic kernels, scan of the row sizes, C row pointers
 //   (6) row bins and accumulator pools for the numeric phase        -> sync 3
-// spgemm_numeric (line 5) then only launches the numeric kernels of the
+// spgemm_numeric (the numeric phase) then only launches the kernels of the
 // planned bins: no synchronisation and no allocation.
 #include <algorithm>
 #include <cmath>
@@ -38,7 +38,8 @@ enum BufId {
   kBufInst, kBufArow0, kBufBrow0, kBufCnt, kBufBcp, kBufCsi, kBufCs, kBufRf, kBufRfc, kBufRowsize, kBufOffs,
   kBufScanTmp, kBufInstStats, kBufInstOut, kBufHist, kBufCursor, kBufSymRows, kBufNumRows, kBufSymPool,
   kBufNumPool2, kBufNumPool3, kBufStatus, kBufMaskRows, kBufMaskHist, kBufMaskPool, kBufTrTmp,
-  kBufTrPool, kBufReuseRows, kBufReusePool, kBufBinCnt, kBufBinOfs, kNumBufs
+  kBufTrPool, kBufReuseRows, kBufReusePool, kBufBinCnt, kBufBinOfs, kBufMcCnt, kBufMcYcp, kBufMcCsi, kBufMcCs,
+  kBufMcMax, kNumBufs
 };
 
 // Row bins of a masked product, cached for numeric reuse on one pattern.
@@ -1282,6 +1283,56 @@ spgemm_status_t spgemm_numeric_reuse(spgemm_handle_t h, const spgemm_csr_t* A, c
     P.dtype = (int)A->dtype;
   }
   return run_masked_plan(h, M, (int)A->dtype, kBufReuseRows, kBufReusePool, P, s);
+}
+
+spgemm_status_t spgemm_masked_count(spgemm_handle_t h, const spgemm_csr_t* X, const spgemm_csr_t* Y,
+                                    const int64_t* S_rowptr, const int32_t* S_colidx, int64_t S_nnz,
+                                    int64_t* row_counts, spgemm_stream_t stream) {
+  if (!h || !X || !Y || !S_rowptr || !row_counts) return SPGEMM_ERR_INVALID_ARG;
+  KKS_ST(check_csr(X, false));
+  KKS_ST(check_csr(Y, false));
+  if (X->ncols != Y->nrows || S_nnz < 0 || (S_nnz > 0 && !S_colidx)) return SPGEMM_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  KKS_CU(cudaSetDevice(h->opt.device));
+  if (X->nrows == 0) return SPGEMM_OK;
+  MaskedD M = maskd(h, X, Y, S_rowptr, S_colidx, nullptr);
+  const long long ny = Y->nrows;
+  KKS_ST(ensure(h, kBufStatus, sizeof(DevStatus)));
+  KKS_ST(ensure(h, kBufMcCnt, sizeof(long long) * (ny + 1)));
+  KKS_ST(ensure(h, kBufMcYcp, sizeof(long long) * (ny + 1)));
+  KKS_ST(ensure(h, kBufMcMax, 16));
+  KKS_ST(ensure(h, kBufScanTmp, scan_tmp_bytes(ny + 1)));
+  KKS_ST(ensure_pinned(h, 64 + sizeof(DevStatus)));
+  M.status = B<DevStatus>(h, kBufStatus);
+  LaunchCtx L = ctx(h, s);
+  KKS_CU(cudaMemsetAsync(h->buf[kBufStatus], 0, sizeof(DevStatus), s));
+  // (1) Y's compressed row lengths and their scan; the longest row of S
+  KKS_CU(launch_mc_compress(L, M, 0, nullptr, B<long long>(h, kBufMcCnt), nullptr, nullptr));
+  KKS_CU(launch_scan(L, B<long long>(h, kBufMcCnt), B<long long>(h, kBufMcYcp), ny, h->buf[kBufScanTmp]));
+  KKS_CU(launch_row_len_max(L, reinterpret_cast<const long long*>(S_rowptr), X->nrows,
+                            B<unsigned long long>(h, kBufMcMax)));
+  long long* h_nc = (long long*)h->pinned;
+  unsigned long long* h_max = (unsigned long long*)(h->pinned + 16);
+  DevStatus* hs = (DevStatus*)(h->pinned + 64);
+  KKS_CU(to_host(h, h_nc, B<long long>(h, kBufMcYcp) + ny, sizeof(long long), s));
+  KKS_CU(to_host(h, h_max, h->buf[kBufMcMax], sizeof(unsigned long long), s));
+  KKS_CU(to_host(h, hs, h->buf[kBufStatus], sizeof(DevStatus), s));
+  KKS_CU(cudaStreamSynchronize(s));
+  KKS_ST(consume_status(h, hs, s));
+  const long long nc = *h_nc;
+  const bool big = *h_max > (unsigned long long)kMcBigRow;
+  // (2) the compressed Y, (3) the counts
+  KKS_ST(ensure(h, kBufMcCsi, sizeof(int) * (nc + 1)));
+  KKS_ST(ensure(h, kBufMcCs, sizeof(unsigned) * (nc + 1)));
+  KKS_CU(launch_mc_compress(L, M, 1, B<long long>(h, kBufMcYcp), nullptr, B<int>(h, kBufMcCsi),
+                            B<unsigned>(h, kBufMcCs)));
+  cudaError_t e = launch_masked_count(L, M, B<long long>(h, kBufMcYcp), B<int>(h, kBufMcCsi),
+                                      B<unsigned>(h, kBufMcCs), reinterpret_cast<long long*>(row_counts), big);
+  if (e == cudaErrorInvalidConfiguration) return SPGEMM_ERR_DEVICE_LIMIT;
+  KKS_CU(e);
+  KKS_CU(to_host(h, hs, h->buf[kBufStatus], sizeof(DevStatus), s));
+  KKS_CU(cudaStreamSynchronize(s));
+  return consume_status(h, hs, s);
 }
 
 spgemm_status_t spgemm_transpose(spgemm_handle_t h, const spgemm_csr_t* A, int64_t* At_rowptr, int32_t* At_colidx,

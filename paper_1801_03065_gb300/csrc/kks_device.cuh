@@ -184,6 +184,14 @@ __device__ __forceinline__ long long team_sum(const Team<TW>& tm, long long v, l
   return tot;
 }
 
+// Sum over a warp or sub-warp team (register shuffles only).
+template <int TW>
+__device__ __forceinline__ long long warp_team_sum(const Team<TW>& tm, long long v) {
+#pragma unroll
+  for (int d = TW / 2; d > 0; d >>= 1) v += __shfl_xor_sync(tm.mask, v, d, TW);
+  return v;
+}
+
 // acc + a * b with one rounding (fused multiply-add)
 __device__ __forceinline__ double fma_acc(double a, double b, double acc) { return fma(a, b, acc); }
 __device__ __forceinline__ float fma_acc(float a, float b, float acc) { return fmaf(a, b, acc); }

@@ -257,6 +257,17 @@ cudaError_t launch_masked_bin_count(const LaunchCtx&, const MaskedD&, long long 
 cudaError_t launch_masked_bin_scatter(const LaunchCtx&, const MaskedD&, long long nrows, BinCfg cfg,
                                       const unsigned long long* cursor, const long long* bofs, int* rows);
 cudaError_t launch_masked(const LaunchCtx&, const MaskedD&, const MaskedLaunch&);
+// masked count: Y's compression (pass 0: run counts into cnt; pass 1: fill csi / cs
+// from the scanned counts), then the per-row counts (warp rows of S up to 1024
+// entries, CTA rows above when has_big_rows; those need ceil(k/32) words of
+// shared memory)
+constexpr int kMcBigRow = 1024;
+cudaError_t launch_mc_compress(const LaunchCtx&, const MaskedD&, int pass, const long long* ycp, long long* cnt,
+                               int* csi, unsigned* cs);
+cudaError_t launch_masked_count(const LaunchCtx&, const MaskedD&, const long long* Ycp, const int* csi,
+                                const unsigned* cs, long long* counts, bool has_big_rows);
+// *out = the longest row of a pattern with int64 row pointers (device)
+cudaError_t launch_row_len_max(const LaunchCtx&, const long long* Sp, long long nrows, unsigned long long* out);
 
 size_t masked_global_chunk_bytes(long long slots, int dtype);
 

@@ -658,6 +658,246 @@ __global__ void __launch_bounds__(kBinThreads) k_masked_bin_list(MaskedD M, long
   bin_block_list(r0, r1, [&](long long i) { return masked_row_bin(M, i, cfg, false); }, run, wcnt, rows);
 }
 
+// ---------------------------------------------------------------- masked count
+// Structural counts on the compressed Y (symbolic-only use of the two-phase
+// method for graph analytics, Section 2; compression, Section 3.2):
+// count_i = sum over l in S(i,:) of |{ j : (i,j) in X, (j,l) in Y }|.  Y's
+// rows become runs of (column-set index, bits); S(i,:) becomes a table of
+// (set index, bits); each compressed product adds popcount(Y bits & S bits).
+
+// Runs of equal column-set index per row of Y (cnt[j] = compressed length).
+__global__ void __launch_bounds__(256) k_mc_compress_count(MatD Y, long long* cnt, DevStatus* st) {
+  Team<8> tm;
+  const long long nteams = (long long)gridDim.x * tm.per_cta;
+  for (long long j = (long long)blockIdx.x * tm.per_cta + tm.id; j < Y.nrows; j += nteams) {
+    const long long s = rp_at(Y, j), e = rp_at(Y, j + 1);
+    long long c = 0;
+    if (s < 0 || s > e || e > Y.nnz) {
+      if (tm.lane == 0) {
+        dev_fail(st, kDevBadIndex, 50, j);
+        cnt[j] = 0;
+      }
+      continue;
+    }
+    for (long long p = s + tm.lane; p < e; p += 8) {
+      const int col = Y.cj[p];
+      if ((unsigned long long)(unsigned)col >= (unsigned long long)Y.ncols) dev_fail(st, kDevBadIndex, 51, j);
+      if (p == s || (col >> 5) != (Y.cj[p - 1] >> 5)) ++c;
+    }
+    c = warp_team_sum<8>(tm, c);
+    if (tm.lane == 0) cnt[j] = c;
+  }
+}
+
+// The runs themselves: csi and the OR of their bits (a run is stored by the
+// chunk where it starts and ORed by later chunks, so cs needs no clearing).
+__global__ void __launch_bounds__(256) k_mc_compress_fill(MatD Y, const long long* __restrict__ Ycp, int* csi,
+                                                          unsigned* cs) {
+  Team<8> tm;
+  const long long nteams = (long long)gridDim.x * tm.per_cta;
+  const int base_lane = (threadIdx.x & 31) & ~7;
+  for (long long j = (long long)blockIdx.x * tm.per_cta + tm.id; j < Y.nrows; j += nteams) {
+    const long long s = rp_at(Y, j), e = rp_at(Y, j + 1);
+    if (s < 0 || s > e || e > Y.nnz) continue;
+    long long run = Ycp[j] - 1;
+    for (long long c0 = s; c0 < e; c0 += 8) {
+      const long long p = c0 + tm.lane;
+      const bool valid = p < e;
+      const int col = valid ? Y.cj[p] : 0;
+      const bool head = valid && (p == s || (col >> 5) != (Y.cj[p - 1] >> 5));
+      const unsigned hb = (__ballot_sync(tm.mask, head) >> base_lane) & 0xffu;
+      const unsigned le = (2u << tm.lane) - 1u;
+      const long long ridx = run + __popc(hb & le);
+      if (head) csi[ridx] = col >> 5;
+      unsigned v = valid ? (1u << (col & 31)) : 0u;
+      int f = (head || tm.lane == 0) ? 1 : 0;
+#pragma unroll
+      for (int d = 1; d < 8; d <<= 1) {
+        const unsigned vu = __shfl_up_sync(tm.mask, v, d, 8);
+        const int fu = __shfl_up_sync(tm.mask, f, d, 8);
+        if (tm.lane >= d && !f) {
+          v |= vu;
+          f = fu;
+        }
+      }
+      const bool next_head = (tm.lane + 1 < 8) && ((hb >> (tm.lane + 1)) & 1u);
+      const bool tail = valid && (tm.lane == 7 || p + 1 >= e || next_head);
+      if (tail) {
+        if (hb & le) cs[ridx] = v;
+        else atomicOr(cs + ridx, v);
+      }
+      run += __popc(hb);
+      __syncwarp(tm.mask);
+    }
+  }
+}
+
+constexpr int kMcWarpMaxRow = kMcBigRow;   // S rows up to this size: warp teams with a hash table
+constexpr int kMcWarpSlots = 2048;    // table slots per warp (keys + bits: 16 KB)
+
+// Longest row of S (int64 row pointers).
+__global__ void k_row_len_max(const long long* __restrict__ Sp, long long n, unsigned long long* out) {
+  unsigned long long m = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long l = Sp[i + 1] - Sp[i];
+    m = l > (long long)m ? (unsigned long long)l : m;
+  }
+  m = __reduce_max_sync(0xffffffffu, (unsigned)(m > 0xffffffffull ? 0xffffffffull : m));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+// Warp per row of S with at most kMcWarpMaxRow entries.
+__global__ void __launch_bounds__(128) k_masked_count_warp(MaskedD M, const long long* __restrict__ Ycp,
+                                                           const int* __restrict__ csi,
+                                                           const unsigned* __restrict__ cs,
+                                                           long long* __restrict__ counts) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Team<32> tm;
+  int* keys = reinterpret_cast<int*>(smem) + (size_t)tm.id * 2 * kMcWarpSlots;
+  unsigned* bits = reinterpret_cast<unsigned*>(keys + kMcWarpSlots);
+  __shared__ int pre_s[4][33];
+  __shared__ long long qs_s[4][32];
+  int* pre = pre_s[tm.id];
+  long long* qsv = qs_s[tm.id];
+  const long long nteams = (long long)gridDim.x * tm.per_cta;
+  for (long long i = (long long)blockIdx.x * tm.per_cta + tm.id; i < M.X.nrows; i += nteams) {
+    const long long s0 = M.Sp[i], s1 = M.Sp[i + 1];
+    const long long ns = s1 - s0;
+    if (ns > kMcWarpMaxRow) continue;          // the CTA kernel takes it
+    if (ns <= 0) {
+      if (tm.lane == 0) counts[i] = 0;
+      continue;
+    }
+    int logT = 1;
+    while ((1ll << logT) < 2 * ns) ++logT;
+    const int T = 1 << logT;
+    const LpHash hs(logT, M.hash_mode);
+    for (int x = tm.lane; x < T; x += 32) {
+      keys[x] = kEmpty;
+      bits[x] = 0u;
+    }
+    __syncwarp();
+    int fresh = 0;
+    for (long long p = s0 + tm.lane; p < s1; p += 32) {
+      const int l = M.Sj[p];
+      if ((unsigned long long)(unsigned)l >= (unsigned long long)M.Y.ncols) {
+        dev_fail(M.status, kDevBadIndex, 52, i);
+        continue;
+      }
+      const int slot = slot_insert<1>(keys, hs, l >> 5, &fresh);
+      if (slot >= 0) atomicOr(bits + slot, 1u << (l & 31));
+      else dev_fail(M.status, kDevTableFull, 53, i);
+    }
+    __syncwarp();
+    long long cnt = 0;
+    const long long a0 = rp_at(M.X, i), a1 = rp_at(M.X, i + 1);
+    for (long long c = a0; c < a1; c += 32) {
+      const long long p = c + tm.lane;
+      long long q0 = 0;
+      int ql = 0;
+      if (p < a1) {
+        const int j = M.X.cj[p];
+        if ((unsigned long long)(unsigned)j < (unsigned long long)M.Y.nrows) {
+          q0 = Ycp[j];
+          ql = (int)(Ycp[j + 1] - q0);
+        } else {
+          dev_fail(M.status, kDevBadIndex, 54, i);
+        }
+      }
+      int ex = ql;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, ex, d);
+        if (tm.lane >= d) ex += y;
+      }
+      const int tot = __shfl_sync(0xffffffffu, ex, 31);
+      pre[tm.lane] = ex - ql;
+      qsv[tm.lane] = q0;
+      if (tm.lane == 0) pre[32] = tot;
+      __syncwarp();
+      int t = 0;
+      for (int xb = 0; xb < tot; xb += 4 * 32) {
+        int key[4];
+        unsigned m[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int x = xb + u * 32 + tm.lane;
+          key[u] = -1;
+          m[u] = 0u;
+          if (x < tot) {
+            while (pre[t + 1] <= x) ++t;
+            const long long q = qsv[t] + (x - pre[t]);
+            key[u] = csi[q];
+            m[u] = cs[q];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (key[u] >= 0) {
+            const int slot = key_slot(keys, hs, key[u]);
+            if (slot >= 0) cnt += __popc(m[u] & bits[slot]);
+          }
+        }
+      }
+      __syncwarp();
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
+    if (tm.lane == 0) counts[i] = cnt;
+    __syncwarp();
+  }
+}
+
+// CTA per row of S with more than kMcWarpMaxRow entries: S(i,:) as a bitmap of
+// ceil(k / 32) words in shared memory, set and cleared by its own entries.
+__global__ void __launch_bounds__(256) k_masked_count_cta(MaskedD M, const long long* __restrict__ Ycp,
+                                                          const int* __restrict__ csi,
+                                                          const unsigned* __restrict__ cs,
+                                                          long long* __restrict__ counts, long long kw) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long scan_scratch[33];
+  __shared__ ChunkScratch<256, int> csc;
+  Team<256> tm;
+  unsigned* bm = reinterpret_cast<unsigned*>(smem);
+  for (long long w = tm.lane; w < kw; w += 256) bm[w] = 0u;
+  __syncthreads();
+  for (long long i = blockIdx.x; i < M.X.nrows; i += gridDim.x) {
+    const long long s0 = M.Sp[i], s1 = M.Sp[i + 1];
+    if (s1 - s0 <= kMcWarpMaxRow) continue;
+    for (long long p = s0 + tm.lane; p < s1; p += 256) {
+      const int l = M.Sj[p];
+      if ((unsigned long long)(unsigned)l < (unsigned long long)M.Y.ncols) atomicOr(bm + (l >> 5), 1u << (l & 31));
+      else dev_fail(M.status, kDevBadIndex, 55, i);
+    }
+    __syncthreads();
+    long long cnt = 0;
+    const long long a0 = rp_at(M.X, i), a1 = rp_at(M.X, i + 1);
+    auto range = [&](int j, long long* bs, long long* be) {
+      if ((unsigned long long)(unsigned)j < (unsigned long long)M.Y.nrows) {
+        *bs = Ycp[j];
+        *be = Ycp[j + 1];
+      } else {
+        dev_fail(M.status, kDevBadIndex, 56, i);
+        *bs = *be = 0;
+      }
+    };
+    auto aval = [&](long long) { return 0; };
+    auto body = [&](long long q, int) { cnt += __popc(cs[q] & bm[csi[q]]); };
+    auto pf = [&](long long q) {
+      prefetch_l1(csi + q);
+      prefetch_l1(cs + q);
+    };
+    for_each_product<256, int>(tm, &csc, scan_scratch, M.X.cj, a0, a1, range, aval, body, pf);
+    long long tot = team_sum<256>(tm, cnt, scan_scratch);
+    if (tm.lane == 0) counts[i] = tot;
+    for (long long p = s0 + tm.lane; p < s1; p += 256) {
+      const int l = M.Sj[p];
+      if ((unsigned long long)(unsigned)l < (unsigned long long)M.Y.ncols) bm[l >> 5] = 0u;
+    }
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------- transpose
 __global__ void k_tr_count(MatD A, unsigned long long* cnt, DevStatus* st) {
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -893,6 +1133,52 @@ cudaError_t launch_masked_bin_scatter(const LaunchCtx& L, const MaskedD& M, long
   KKS_LAUNCHED();
   k_masked_bin_list<<<(unsigned)nblk, kBinThreads, 0, L.stream>>>(M, nrows, cfg, cursor, bofs, nblk, rows);
   return cudaGetLastError();
+}
+
+cudaError_t launch_mc_compress(const LaunchCtx& L, const MaskedD& M, int pass, const long long* cnt_or_ycp,
+                               long long* cnt, int* csi, unsigned* cs) {
+  if (M.Y.nrows <= 0) return cudaSuccess;
+  const unsigned grid = grid_cap(M.Y.nrows, 32, L.num_sms, 16);
+  KKS_LAUNCHED();
+  if (pass == 0) k_mc_compress_count<<<grid, 256, 0, L.stream>>>(M.Y, cnt, M.status);
+  else k_mc_compress_fill<<<grid, 256, 0, L.stream>>>(M.Y, cnt_or_ycp, csi, cs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_row_len_max(const LaunchCtx& L, const long long* Sp, long long nrows, unsigned long long* out) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), L.stream);
+  if (e != cudaSuccess || nrows <= 0) return e;
+  KKS_LAUNCHED();
+  k_row_len_max<<<grid_cap(nrows, 256, L.num_sms, 4), 256, 0, L.stream>>>(Sp, nrows, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_masked_count(const LaunchCtx& L, const MaskedD& M, const long long* Ycp, const int* csi,
+                                const unsigned* cs, long long* counts, bool has_big_rows) {
+  if (M.X.nrows <= 0) return cudaSuccess;
+  {
+    auto kern = k_masked_count_warp;
+    const size_t smem = (size_t)4 * 2 * kMcWarpSlots * 4;
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    KKS_LAUNCHED();
+    kern<<<resident_grid(kern, 128, smem, L.num_sms, (M.X.nrows + 3) / 4), 128, smem, L.stream>>>(M, Ycp, csi, cs,
+                                                                                                  counts);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (has_big_rows) {
+    const long long kw = (M.Y.ncols + 31) >> 5;
+    const size_t smem = (size_t)kw * 4;
+    if (smem + 16 * 1024 > (size_t)L.max_smem_optin) return cudaErrorInvalidConfiguration;
+    auto kern = k_masked_count_cta;
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    KKS_LAUNCHED();
+    kern<<<resident_grid(kern, 256, smem, L.num_sms, M.X.nrows), 256, smem, L.stream>>>(M, Ycp, csi, cs, counts, kw);
+    return cudaGetLastError();
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_masked(const LaunchCtx& L, const MaskedD& M, const MaskedLaunch& S) {

@@ -11,7 +11,7 @@
 //                         global k-wide pool chunk, column marker as a bitmap
 //                         in shared memory; emission walks the bitmap, so the
 //                         row comes out sorted and the chunk is reset to zero
-//   k_num_spill<TW, VT> : two-level LP accumulator (Algorithm 3 lines 7-11):
+//   k_num_spill<TW, VT> : two-level LP accumulator (Algorithm 3, Section 3.1.2):
 //                         L1 in shared memory with the maximum-occupancy
 //                         cut-off, L2 in a global pool chunk; L2 entries whose
 //                         key also reached L1 are folded into L1, then each

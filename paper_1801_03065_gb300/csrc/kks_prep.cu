@@ -24,13 +24,6 @@ __device__ __forceinline__ int lanemask_lt() {
   return (int)r;
 }
 
-template <int TW>
-__device__ __forceinline__ long long warp_team_sum(const Team<TW>& tm, long long v) {
-#pragma unroll
-  for (int d = TW / 2; d > 0; d >>= 1) v += __shfl_xor_sync(tm.mask, v, d, TW);
-  return v;
-}
-
 inline int grid_for(long long items, int per_block, int num_sms, int cap_per_sm = 32) {
   long long g = (items + per_block - 1) / per_block;
   long long cap = (long long)num_sms * cap_per_sm;

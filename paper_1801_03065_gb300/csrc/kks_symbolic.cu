@@ -11,8 +11,8 @@
 //                                 sized to hold the row, batched loads
 //   k_sym_hash<TW, COMP, false> : CTA teams, shared LP table sized to hold the row
 //   k_sym_hash<TW, COMP, true>  : shared L1 table with the maximum-occupancy
-//                                 cut-off plus a global L2 table (Algorithm 3
-//                                 lines 7-11); a key may sit in both levels,
+//                                 cut-off plus a global L2 table (Algorithm 3's
+//                                 two-level accumulator); a key may sit in both levels,
 //                                 so the count merges them (union)
 //   k_sym_dense<COMP>           : a k-bit bitmap in shared memory (the dense
 //                                 accumulator of Section 3.1.2 in bit form)

@@ -142,7 +142,7 @@ class SpGEMM:
 
     # ---------------------------------------------------------------- phases
     def symbolic(self, A: CsrMatrix, Bm: CsrMatrix, C_rowptr: Optional[torch.Tensor] = None, stream=None):
-        """Algorithm 2 lines 1-3: returns (C_rowptr int64 tensor, nnz(C))."""
+        """The symbolic phase of Algorithm 2: returns (C_rowptr int64 tensor, nnz(C))."""
         if C_rowptr is None:
             C_rowptr = torch.empty(A.nrows + 1, dtype=torch.int64, device=A.rowptr.device)
         hint = A.dtype or Bm.dtype
@@ -156,7 +156,7 @@ class SpGEMM:
     def numeric(self, A: CsrMatrix, Bm: CsrMatrix, C_rowptr: torch.Tensor, nnz: Optional[int] = None,
                 C_colidx: Optional[torch.Tensor] = None, C_values: Optional[torch.Tensor] = None,
                 stream=None) -> CsrMatrix:
-        """Algorithm 2 line 5: C's columns and values (rows sorted)."""
+        """The numeric phase of Algorithm 2: C's columns and values (rows sorted)."""
         if nnz is None:
             nnz = int(C_rowptr[-1].item()) if C_colidx is None else C_colidx.numel()
         dev = C_rowptr.device
@@ -206,6 +206,20 @@ class SpGEMM:
         B.check(self._lib.spgemm_masked(self._h, C.byref(dx), C.byref(dy), C.c_void_p(S_rowptr.data_ptr()),
                                         _ptr(S_colidx), n, _ptr(out), _ptr(x_perm), _ptr(y_perm),
                                         _stream(stream)), "spgemm_masked")
+        return out
+
+    def masked_count(self, X: CsrMatrix, Y: CsrMatrix, S_rowptr: torch.Tensor, S_colidx: torch.Tensor,
+                     out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """Per-row structural counts of (X·Y) on the pattern S (int64[X.nrows]):
+        out[i] = sum over l in S(i,:) of |{j : (i,j) in X, (j,l) in Y}|; values
+        are not read.  S_rowptr must be int64."""
+        if out is None:
+            out = torch.empty(X.nrows, dtype=torch.int64, device=S_colidx.device)
+        assert S_rowptr.dtype == torch.int64
+        dx, dy = X.desc(torch.float64), Y.desc(torch.float64)
+        B.check(self._lib.spgemm_masked_count(self._h, C.byref(dx), C.byref(dy), C.c_void_p(S_rowptr.data_ptr()),
+                                              _ptr(S_colidx), S_colidx.numel(), _ptr(out), _stream(stream)),
+                "spgemm_masked_count")
         return out
 
     def transpose(self, A: CsrMatrix, with_values: bool = True, out=None, stream=None):

@@ -582,3 +582,54 @@ def test_dense_windows_wide_k(ops, dtype, shuffled):
     h, _, _, Cd = run(ops, A, B, dtype, dense=1)
     assert h.stats()["bin_rows_numeric"][5] > 0
     assert_matches_oracle(A, B, Cd, dtype)
+
+
+# ------------------------------------------------------------------ masked counts (symbolic only)
+def _count(ops, X, Y, S):
+    h = ops.SpGEMM()
+    Xd, Yd, Sd = dev(X, with_values=False), dev(Y, with_values=False), dev(S, with_values=False)
+    out = h.masked_count(Xd, Yd, Sd.rowptr, Sd.colidx)
+    h.sync()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("shuffled", [False, True])
+def test_masked_count_random_patterns(ops, seed, shuffled):
+    X = w.random_csr(700, 500, 6.0, seed=40 + seed)
+    Y = w.random_csr(500, 3000, 9.0, seed=50 + seed)
+    S = w.random_csr(700, 3000, 12.0, seed=60 + seed)
+    if shuffled:
+        X, Y, S = w.shuffle_rows(X, 1), w.shuffle_rows(Y, 2), w.shuffle_rows(S, 3)
+    assert np.array_equal(_count(ops, X, Y, S), oracle.masked_count(X, Y, S))
+
+
+def test_triangle_counts_rmat_and_hub(ops):
+    """Per-vertex triangle counts (X = Y = S = L) on a small R-MAT graph and on
+    a graph with a hub row of S beyond the warp path (shared bitmap path)."""
+    G = w.rmat_symmetric(scale=12, seed=7)
+    L = oracle.lower_triangle(G)
+    assert np.array_equal(_count(ops, L, L, L), oracle.masked_count(L, L, L))
+    n = 6000
+    rng = np.random.default_rng(9)
+    hub = [(n - 1, v) for v in range(0, n - 1, 2)]                 # hub row of 3000 lower neighbours
+    rest = [tuple(e) for e in rng.integers(0, n - 1, size=(20000, 2)) if e[0] != e[1]]
+    e = np.array(sorted({(min(a, b), max(a, b)) for a, b in hub + rest}), dtype=np.int64)
+    H = csr_from_coo(n, n, np.concatenate([e[:, 0], e[:, 1]]), np.concatenate([e[:, 1], e[:, 0]]))
+    LH = oracle.lower_triangle(H)
+    assert np.diff(LH.rowptr).max() > 1024
+    got = _count(ops, LH, LH, LH)
+    ref = oracle.masked_count(LH, LH, LH)
+    assert np.array_equal(got, ref) and ref.sum() > 0
+
+
+def test_masked_count_empty_and_bad_index(ops):
+    from paper_1801_03065_gb300._binding import SpGEMMError
+    X = w.random_csr(50, 40, 3.0, seed=1)
+    Y = w.random_csr(40, 60, 3.0, seed=2)
+    S = Csr(50, 60, np.zeros(51, dtype=np.int64), np.zeros(0, dtype=np.int32), None)
+    assert not _count(ops, X, Y, S).any()
+    bad = Csr(S.nrows, S.ncols, np.arange(51, dtype=np.int64), np.full(50, 60, dtype=np.int32), None)
+    with pytest.raises(SpGEMMError) as e:
+        _count(ops, X, Y, bad)
+    assert e.value.status == 8

@@ -341,3 +341,62 @@ def test_planted_mistakes_are_caught():
     # wrong index: row j+1 of B used for A(i,j)
     Ash = Csr(8, 8, A.rowptr, ((A.colidx + 1) % 8).astype(np.int32), A.values)
     assert not passes(oracle.spgemm(Ash, B)[0].to_dense())
+
+
+# ------------------------------------------------------------------ masked counts (triangles)
+def _graph(n, edges):
+    """Undirected simple graph as a symmetric CSR pattern."""
+    e = np.array(sorted({(min(a, b), max(a, b)) for a, b in edges if a != b}), dtype=np.int64).reshape(-1, 2)
+    rows = np.concatenate([e[:, 0], e[:, 1]])
+    cols = np.concatenate([e[:, 1], e[:, 0]])
+    return csr_from_coo(n, n, rows, cols, np.ones(rows.size))
+
+
+def _triangles(G):
+    L = oracle.lower_triangle(G)
+    return int(oracle.masked_count(L, L, L).sum())
+
+
+@pytest.mark.parametrize("n", [3, 4, 5, 10, 17])
+def test_masked_count_complete_graph(n):
+    G = _graph(n, itertools.combinations(range(n), 2))
+    assert _triangles(G) == n * (n - 1) * (n - 2) // 6
+
+
+@pytest.mark.parametrize("n", [4, 7, 30])
+def test_masked_count_cycle_and_wheel(n):
+    cycle = [(i, (i + 1) % n) for i in range(n)]
+    assert _triangles(_graph(n, cycle)) == 0
+    wheel = cycle + [(n, i) for i in range(n)]   # hub n joined to every cycle vertex
+    assert _triangles(_graph(n + 1, wheel)) == n
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_masked_count_against_dense(seed):
+    rng = np.random.default_rng(seed)
+    # general patterns: counts are the row sums of (X @ Y) * S over 0/1 matrices
+    m, n, k = rng.integers(1, 40, size=3)
+    X = w.random_csr(int(m), int(n), float(rng.uniform(0.5, 6)), seed=seed)
+    Y = w.random_csr(int(n), int(k), float(rng.uniform(0.5, 6)), seed=seed + 100)
+    S = w.random_csr(int(m), int(k), float(rng.uniform(0.5, 8)), seed=seed + 200)
+    Xd, Yd, Sd = _dense_pattern(X), _dense_pattern(Y), _dense_pattern(S)
+    ref = ((Xd.astype(np.int64) @ Yd.astype(np.int64)) * Sd).sum(axis=1)
+    assert np.array_equal(oracle.masked_count(X, Y, S), ref)
+    # triangles of a random graph: trace(A^3) / 6
+    nv = 30
+    edges = [tuple(e) for e in rng.integers(0, nv, size=(120, 2))]
+    G = _graph(nv, edges)
+    Gd = _dense_pattern(G).astype(np.int64)
+    assert _triangles(G) == int(np.trace(Gd @ Gd @ Gd)) // 6
+
+
+def test_masked_count_planted_mistake_is_caught():
+    """Counting every product of the row (dropping the mask) breaks the dense pin."""
+    X = w.random_csr(20, 15, 4.0, seed=1)
+    Y = w.random_csr(15, 25, 4.0, seed=2)
+    S = w.random_csr(20, 25, 3.0, seed=3)
+    Xd, Yd, Sd = _dense_pattern(X), _dense_pattern(Y), _dense_pattern(S)
+    ref = ((Xd.astype(np.int64) @ Yd.astype(np.int64)) * Sd).sum(axis=1)
+    unmasked = (Xd.astype(np.int64) @ Yd.astype(np.int64)).sum(axis=1)
+    assert not np.array_equal(unmasked, ref)
+    assert np.array_equal(oracle.masked_count(X, Y, S), ref)
