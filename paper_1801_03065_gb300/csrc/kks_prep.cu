@@ -33,27 +33,64 @@ inline int grid_for(long long items, int per_block, int num_sms, int cap_per_sm 
 }
 
 // -------------------------------------------------------------- compression
+// Both passes take kBlock consecutive rows of B per block: a thread handles
+// its own row when it has at most kShortRow entries (every row of the block in
+// flight at once), and 8-lane teams share the longer rows afterwards.
+constexpr int kShortRowB = 32;
+
+// Compressed row lengths: runs of equal CSI in row order.  Also counts the B
+// rows whose columns are not strictly increasing (the dense numeric windows
+// look up column ranges by binary search only when none is).
 template <int TW>
-// Also counts the B rows whose columns are not strictly increasing (the dense
-// numeric windows look up column ranges by binary search only when none is).
 __global__ void __launch_bounds__(kBlock) k_compress_count(ProbD P, long long totalB, long long* cnt,
                                                            unsigned long long* unsorted) {
   Team<TW> tm;
-  const long long nteams = (long long)gridDim.x * tm.per_cta;
-  for (long long gb = (long long)blockIdx.x * tm.per_cta + tm.id; gb < totalB; gb += nteams) {
+  __shared__ int nlong;
+  __shared__ int longrows[kBlock];
+  const long long g0 = (long long)blockIdx.x * kBlock;
+  if (g0 >= totalB) return;
+  const long long g1 = g0 + kBlock < totalB ? g0 + kBlock : totalB;
+  if (threadIdx.x == 0) nlong = 0;
+  __syncthreads();
+  {
+    const long long gb = g0 + threadIdx.x;
+    if (gb < g1) {
+      const int b = inst_of(P.brow0s, P.ninst, gb);
+      const InstD& I = P.inst[b];
+      const long long j = gb - I.brow0;
+      const long long s = rp_at(I.B, j), e = rp_at(I.B, j + 1);
+      if (s < 0 || s > e || e > I.B.nnz) {   // malformed row pointers: report, read nothing
+        dev_fail(P.status, kDevBadIndex, 40, gb);
+        cnt[gb] = 0;
+      } else if (e - s <= kShortRowB) {
+        const int* cj = I.B.cj;
+        long long c = 0;
+        int prev = -1;
+        bool bad = false;
+#pragma unroll 4
+        for (long long p = s; p < e; ++p) {
+          const int col = cj[p];
+          if ((unsigned long long)(unsigned)col >= (unsigned long long)I.k) dev_fail(P.status, kDevBadIndex, 41, gb);
+          if (p == s || (col >> 5) != (prev >> 5)) ++c;
+          bad |= p > s && col <= prev;
+          prev = col;
+        }
+        cnt[gb] = c;
+        if (bad) atomicAdd(unsorted, 1ull);
+      } else {
+        longrows[atomicAdd(&nlong, 1)] = (int)(gb - g0);
+      }
+    }
+  }
+  __syncthreads();
+  for (int x = tm.id; x < nlong; x += tm.per_cta) {
+    const long long gb = g0 + longrows[x];
     const int b = inst_of(P.brow0s, P.ninst, gb);
     const InstD& I = P.inst[b];
     const long long j = gb - I.brow0;
     const long long s = rp_at(I.B, j), e = rp_at(I.B, j + 1);
     const int* cj = I.B.cj;
     long long c = 0;
-    if (s < 0 || s > e || e > I.B.nnz) {   // malformed row pointers: report, read nothing
-      if (tm.lane == 0) {
-        dev_fail(P.status, kDevBadIndex, 40, gb);
-        cnt[gb] = 0;
-      }
-      continue;
-    }
     bool bad = false;
     for (long long p = s + tm.lane; p < e; p += TW) {
       int col = cj[p];
@@ -69,18 +106,58 @@ __global__ void __launch_bounds__(kBlock) k_compress_count(ProbD P, long long to
 }
 
 // Runs of equal CSI in row order become one compressed entry; rows with sorted
-// columns therefore get exactly one entry per distinct CSI.  The chunk where a
-// run starts stores its bits and later chunks of the same run OR in theirs
-// (cs needs no clearing).
+// columns therefore get exactly one entry per distinct CSI.  Short rows are
+// written by their thread run by run.  In the team loop of long rows the
+// chunk where a run starts stores its bits and later chunks of the same run
+// OR in theirs (cs needs no clearing).
 template <int TW>
 __global__ void __launch_bounds__(kBlock) k_compress_fill(ProbD P, long long totalB, int* csi, unsigned* cs) {
   Team<TW> tm;
-  const long long nteams = (long long)gridDim.x * tm.per_cta;
+  __shared__ int nlong;
+  __shared__ int longrows[kBlock];
+  const long long g0 = (long long)blockIdx.x * kBlock;
+  if (g0 >= totalB) return;
+  const long long g1 = g0 + kBlock < totalB ? g0 + kBlock : totalB;
+  if (threadIdx.x == 0) nlong = 0;
+  __syncthreads();
   const int base_lane = (threadIdx.x & 31) & ~(TW - 1);
-  for (long long gb = (long long)blockIdx.x * tm.per_cta + tm.id; gb < totalB; gb += nteams) {
+  {
+    const long long gb = g0 + threadIdx.x;
+    if (gb < g1) {
+      const int b = inst_of(P.brow0s, P.ninst, gb);
+      const InstD& I = P.inst[b];
+      if (I.compressed) {
+        const long long j = gb - I.brow0;
+        const long long s = rp_at(I.B, j), e = rp_at(I.B, j + 1);
+        if (e - s <= kShortRowB) {
+          const int* cj = I.B.cj;
+          long long run = P.Bcp[gb] - 1;
+          int set = -1;
+          unsigned bits = 0u;
+#pragma unroll 4
+          for (long long p = s; p < e; ++p) {
+            const int col = cj[p];
+            if (p == s || (col >> 5) != set) {
+              if (p > s) cs[run] = bits;
+              ++run;
+              set = col >> 5;
+              csi[run] = set;
+              bits = 0u;
+            }
+            bits |= 1u << (col & 31);
+          }
+          if (e > s) cs[run] = bits;
+        } else {
+          longrows[atomicAdd(&nlong, 1)] = (int)(gb - g0);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int x = tm.id; x < nlong; x += tm.per_cta) {
+    const long long gb = g0 + longrows[x];
     const int b = inst_of(P.brow0s, P.ninst, gb);
     const InstD& I = P.inst[b];
-    if (!I.compressed) continue;
     const long long j = gb - I.brow0;
     const long long s = rp_at(I.B, j), e = rp_at(I.B, j + 1);
     const int* cj = I.B.cj;
@@ -120,43 +197,58 @@ __global__ void __launch_bounds__(kBlock) k_compress_fill(ProbD P, long long tot
 
 // -------------------------------------------------------------- row statistics
 // inst_stats per instance: [f_m, maxrf, f_m compressed, maxrf compressed]
+// Row statistics: rf_i = sum over j in A(i,:) of |B(j,:)| (and rfc_i on the
+// compressed B), per instance f_m, maxrf and the compressed counterparts.  A
+// block takes kBlock consecutive rows: each thread counts its own row when it
+// has at most kShortRow entries (every row of the block in flight at once),
+// and 8-lane teams share the longer rows afterwards.  This is also the first
+// kernel that follows A's indices into B, so it validates them.
+constexpr int kShortRow = 32;
+
 template <int TW>
-__global__ void __launch_bounds__(kBlock) k_row_stats(ProbD P, long long totalA, int use_bc, long long rows_per_block,
-                                                      long long* rf, long long* rfc,
-                                                      unsigned long long* inst_stats) {
+__global__ void __launch_bounds__(kBlock) k_row_stats(ProbD P, long long totalA, int use_bc, long long* rf,
+                                                      long long* rfc, unsigned long long* inst_stats) {
   Team<TW> tm;
   __shared__ unsigned long long acc[4];
-  __shared__ int b_first, b_last;
-  const long long g0 = (long long)blockIdx.x * rows_per_block;
+  __shared__ int b_first, b_last, nlong;
+  __shared__ int longrows[kBlock];
+  const long long g0 = (long long)blockIdx.x * kBlock;
   if (g0 >= totalA) return;
-  long long g1 = g0 + rows_per_block;
-  if (g1 > totalA) g1 = totalA;
+  const long long g1 = g0 + kBlock < totalA ? g0 + kBlock : totalA;
   if (threadIdx.x == 0) {
     acc[0] = acc[1] = acc[2] = acc[3] = 0ull;
+    nlong = 0;
     b_first = inst_of(P.arow0s, P.ninst, g0);
     b_last = inst_of(P.arow0s, P.ninst, g1 - 1);
   }
   __syncthreads();
   const bool single = (b_first == b_last);
-  // single-instance blocks: per-team totals in registers, one shared update per team
   unsigned long long t_sum = 0, t_max = 0, t_csum = 0, t_cmax = 0;
-  for (long long g = g0 + tm.id; g < g1; g += tm.per_cta) {
-    const int b = single ? b_first : inst_of(P.arow0s, P.ninst, g);
-    const InstD& I = P.inst[b];
-    const long long i = g - I.arow0;
-    const long long s = rp_at(I.A, i), e = rp_at(I.A, i + 1);
-    long long f = 0, fc = 0;
-    // this is the first kernel that follows A's indices into B: validate them
-    // here so malformed input stops the symbolic phase at its first sync
-    const bool rows_ok = (s >= 0 && s <= e && e <= I.A.nnz);
-    if (!rows_ok && tm.lane == 0) dev_fail(P.status, kDevBadIndex, 42, g);
-    // four entries per lane in flight: their column loads, then their row-pointer loads
-    constexpr int kU = 4;
-    for (long long p0 = s + tm.lane; rows_ok && p0 < e; p0 += (long long)kU * TW) {
+  auto record = [&](long long g, int b, long long f, long long fc) {
+    rf[g] = f;
+    if (rfc) rfc[g] = fc;
+    if (single) {
+      t_sum += (unsigned long long)f;
+      t_max = t_max > (unsigned long long)f ? t_max : (unsigned long long)f;
+      t_csum += (unsigned long long)fc;
+      t_cmax = t_cmax > (unsigned long long)fc ? t_cmax : (unsigned long long)fc;
+    } else {
+      unsigned long long* st = inst_stats + 4ll * b;
+      atomicAdd(st + 0, (unsigned long long)f);
+      atomicMax(st + 1, (unsigned long long)f);
+      atomicAdd(st + 2, (unsigned long long)fc);
+      atomicMax(st + 3, (unsigned long long)fc);
+    }
+  };
+  // the B (and compressed B) ranges of up to four entries of A at a time
+  constexpr int kU = 4;
+  auto entries = [&](const InstD& I, long long g, long long p0, long long e, long long step, long long* f,
+                     long long* fc) {
+    for (; p0 < e; p0 += (long long)kU * step) {
       int jj[kU];
 #pragma unroll
       for (int u = 0; u < kU; ++u) {
-        const long long p = p0 + (long long)u * TW;
+        const long long p = p0 + (long long)u * step;
         jj[u] = p < e ? I.A.cj[p] : -1;
         if (p < e && (unsigned long long)(unsigned)jj[u] >= (unsigned long long)I.A.ncols) {
           dev_fail(P.status, kDevBadIndex, 43, g);
@@ -182,34 +274,59 @@ __global__ void __launch_bounds__(kBlock) k_row_stats(ProbD P, long long totalA,
           dev_fail(P.status, kDevBadIndex, 44, g);
           continue;
         }
-        f += be[u] - bs[u];
-        fc += ce[u] - cs[u];
+        *f += be[u] - bs[u];
+        *fc += ce[u] - cs[u];
       }
     }
-    f = warp_team_sum<TW>(tm, f);
-    fc = warp_team_sum<TW>(tm, fc);
-    if (tm.lane == 0) {
-      rf[g] = f;
-      if (rfc) rfc[g] = fc;
-      if (single) {
-        t_sum += (unsigned long long)f;
-        t_max = t_max > (unsigned long long)f ? t_max : (unsigned long long)f;
-        t_csum += (unsigned long long)fc;
-        t_cmax = t_cmax > (unsigned long long)fc ? t_cmax : (unsigned long long)fc;
+  };
+  // (1) short rows, one thread each
+  {
+    const long long g = g0 + threadIdx.x;
+    if (g < g1) {
+      const int b = single ? b_first : inst_of(P.arow0s, P.ninst, g);
+      const InstD& I = P.inst[b];
+      const long long i = g - I.arow0;
+      const long long s = rp_at(I.A, i), e = rp_at(I.A, i + 1);
+      if (!(s >= 0 && s <= e && e <= I.A.nnz)) {
+        dev_fail(P.status, kDevBadIndex, 42, g);
+      } else if (e - s <= kShortRow) {
+        long long f = 0, fc = 0;
+        entries(I, g, s, e, 1, &f, &fc);
+        record(g, b, f, fc);
       } else {
-        unsigned long long* st = inst_stats + 4ll * b;
-        atomicAdd(st + 0, (unsigned long long)f);
-        atomicMax(st + 1, (unsigned long long)f);
-        atomicAdd(st + 2, (unsigned long long)fc);
-        atomicMax(st + 3, (unsigned long long)fc);
+        longrows[atomicAdd(&nlong, 1)] = (int)(g - g0);
       }
     }
   }
-  if (single && tm.lane == 0) {
-    atomicAdd(&acc[0], t_sum);
-    atomicMax(&acc[1], t_max);
-    atomicAdd(&acc[2], t_csum);
-    atomicMax(&acc[3], t_cmax);
+  __syncthreads();
+  // (2) long rows, one 8-lane team each
+  for (int x = tm.id; x < nlong; x += tm.per_cta) {
+    const long long g = g0 + longrows[x];
+    const int b = single ? b_first : inst_of(P.arow0s, P.ninst, g);
+    const InstD& I = P.inst[b];
+    const long long i = g - I.arow0;
+    const long long s = rp_at(I.A, i), e = rp_at(I.A, i + 1);
+    long long f = 0, fc = 0;
+    entries(I, g, s + tm.lane, e, TW, &f, &fc);
+    f = warp_team_sum<TW>(tm, f);
+    fc = warp_team_sum<TW>(tm, fc);
+    if (tm.lane == 0) record(g, b, f, fc);
+  }
+  // per-block totals: a warp reduction, then one shared update per warp
+  if (single) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      t_sum += __shfl_xor_sync(0xffffffffu, t_sum, d);
+      t_csum += __shfl_xor_sync(0xffffffffu, t_csum, d);
+      t_max = max(t_max, __shfl_xor_sync(0xffffffffu, t_max, d));
+      t_cmax = max(t_cmax, __shfl_xor_sync(0xffffffffu, t_cmax, d));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&acc[0], t_sum);
+      atomicMax(&acc[1], t_max);
+      atomicAdd(&acc[2], t_csum);
+      atomicMax(&acc[3], t_cmax);
+    }
   }
   __syncthreads();
   if (single && threadIdx.x == 0) {
@@ -462,27 +579,26 @@ int resident_per_sm(const void* kernel, int threads, size_t smem) {
 cudaError_t launch_compress_count(const LaunchCtx& L, const ProbD& P, long long totalB, long long* cnt,
                                   unsigned long long* unsorted) {
   if (totalB <= 0) return cudaSuccess;
-  int grid = grid_for(totalB, kBlock / 8, L.num_sms);
+  const long long grid = (totalB + kBlock - 1) / kBlock;
   KKS_LAUNCHED();
-  k_compress_count<8><<<grid, kBlock, 0, L.stream>>>(P, totalB, cnt, unsorted);
+  k_compress_count<8><<<(unsigned)grid, kBlock, 0, L.stream>>>(P, totalB, cnt, unsorted);
   return cudaGetLastError();
 }
 
 cudaError_t launch_compress_fill(const LaunchCtx& L, const ProbD& P, long long totalB, int* csi, unsigned* cs) {
   if (totalB <= 0) return cudaSuccess;
-  int grid = grid_for(totalB, kBlock / 8, L.num_sms);
+  const long long grid = (totalB + kBlock - 1) / kBlock;
   KKS_LAUNCHED();
-  k_compress_fill<8><<<grid, kBlock, 0, L.stream>>>(P, totalB, csi, cs);
+  k_compress_fill<8><<<(unsigned)grid, kBlock, 0, L.stream>>>(P, totalB, csi, cs);
   return cudaGetLastError();
 }
 
 cudaError_t launch_row_stats(const LaunchCtx& L, const ProbD& P, long long totalA, int use_bc, long long* rf,
                              long long* rfc, unsigned long long* inst_stats) {
   if (totalA <= 0) return cudaSuccess;
-  const long long rpb = 1024;
-  long long grid = (totalA + rpb - 1) / rpb;
+  const long long grid = (totalA + kBlock - 1) / kBlock;
   KKS_LAUNCHED();
-  k_row_stats<8><<<(unsigned)grid, kBlock, 0, L.stream>>>(P, totalA, use_bc, rpb, rf, rfc, inst_stats);
+  k_row_stats<8><<<(unsigned)grid, kBlock, 0, L.stream>>>(P, totalA, use_bc, rf, rfc, inst_stats);
   return cudaGetLastError();
 }
 
