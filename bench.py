@@ -57,6 +57,8 @@ def parse_args(argv=None):
     p.add_argument("--repeats", type=int, default=20, help="batched512: numeric-reuse repeats")
     p.add_argument("--numeric-only", action="store_true",
                    help="profiling aid: one symbolic and two numeric calls of A*A on --grid, no timing")
+    p.add_argument("--rap", choices=["fused", "two"], default="fused",
+                   help="stencil27_100: the triple product in one plan, or as transpose + two products")
     p.add_argument("--numeric-positions", type=int, default=1, choices=(0, 1),
                    help="1: warp rows of compressed products take positions from the column sets; "
                         "0: hash-and-sort numeric kernel")
@@ -154,9 +156,12 @@ def csr_bytes(nrows, nnz, vbytes, rp_bytes=8):
 
 # ----------------------------------------------------------------------------- GPU arm
 class StencilStep:
-    """Device buffers and library handles of one step (NoReuse A·A and Pᵀ·(A·P))."""
+    """Device buffers and library handles of one step (NoReuse A·A and Pᵀ·A·P).
 
-    def __init__(self, A, P, device, positions=True):
+    rap="fused": the triple product in one plan (spgemm_rap_symbolic / _numeric);
+    rap="two": Pᵀ by transpose, then A·P and Pᵀ·(A·P) as two products."""
+
+    def __init__(self, A, P, device, positions=True, rap="fused"):
         import torch
         from paper_1801_03065_gb300 import ops
         self.torch, self.ops = torch, ops
@@ -165,9 +170,11 @@ class StencilStep:
         self.Pd = ops.CsrMatrix.from_host(P.rowptr, P.colidx, P.values, P.shape, device=device)
         pos = bool(positions)
         self.positions = pos
+        self.rap = rap
         self.hAA, self.hAP, self.hRAP = (ops.SpGEMM(numeric_positions=pos), ops.SpGEMM(numeric_positions=pos),
                                          ops.SpGEMM(numeric_positions=pos))
         self.hT = ops.SpGEMM()
+        self._fm_two = None
         dev = self.Ad.rowptr.device
         self.rpAA = torch.empty(A.nrows + 1, dtype=torch.int64, device=dev)
         self.rpAP = torch.empty(A.nrows + 1, dtype=torch.int64, device=dev)
@@ -188,6 +195,11 @@ class StencilStep:
         rp, nnz = self.hAA.symbolic(Ad, Ad, C_rowptr=self.rpAA)
         self.CAA = self._out(self.CAA, rp, nnz, t.float64)
         self.hAA.numeric(Ad, Ad, rp, nnz, self.CAA.colidx, self.CAA.values)
+        if self.rap == "fused":
+            rp, nnz = self.hRAP.rap_symbolic(Ad, Pd, C_rowptr=self.rpRAP)
+            self.CRAP = self._out(self.CRAP, rp, nnz, t.float64)
+            self.hRAP.rap_numeric(Ad, Pd, rp, nnz, self.CRAP.colidx, self.CRAP.values)
+            return
         self.Pt = self.hT.transpose(Pd, out=self.Pt)
         rp, nnz = self.hAP.symbolic(Ad, Pd, C_rowptr=self.rpAP)
         self.CAP = self._out(self.CAP, rp, nnz, t.float64)
@@ -198,8 +210,24 @@ class StencilStep:
         self.CRAP = self._out(self.CRAP, rp, nnz, t.float64)
         self.hRAP.numeric(Pt, AP, rp, nnz, self.CRAP.colidx, self.CRAP.values)
 
+    def two_step_flops(self):
+        """f_m of A·P plus f_m of Pᵀ·(A·P): the triple product's work as the paper
+        counts it (two SpGEMMs), whichever way it is computed."""
+        if self.rap == "two":
+            return self.hAP.stats()["f_m"] + self.hRAP.stats()["f_m"]
+        if self._fm_two is None:
+            ops = self.ops
+            hT, hAP, hRAP = ops.SpGEMM(), ops.SpGEMM(), ops.SpGEMM()
+            Pt = hT.transpose(self.Pd)[0]
+            AP = hAP.multiply(self.Ad, self.Pd)
+            hRAP.symbolic(Pt, AP)
+            self._fm_two = hAP.stats()["f_m"] + hRAP.stats()["f_m"]
+            for h in (hT, hAP, hRAP):
+                h.close()
+        return self._fm_two
+
     def flops(self):
-        return sum(h.stats()["f_m"] for h in (self.hAA, self.hAP, self.hRAP))
+        return self.hAA.stats()["f_m"] + self.two_step_flops()
 
     def close(self):
         for h in (self.hAA, self.hAP, self.hRAP, self.hT):
@@ -255,7 +283,7 @@ def run_ours(args):
 
     A = w.stencil3d_27pt(args.grid, seed=1)
     P = w.aggregation(args.grid, 3)
-    S = StencilStep(A, P, device, positions=bool(args.numeric_positions))
+    S = StencilStep(A, P, device, positions=bool(args.numeric_positions), rap=args.rap)
     for _ in range(max(args.warmup, 1)):
         S.step()
     torch.cuda.synchronize()
@@ -289,19 +317,39 @@ def run_ours(args):
     t_sym = statistics.mean(time_region(torch, sym, max(args.steps, 5)))
     S.hAA.sync()
     # the other products of the step, one phase at a time (each on its own handle)
-    Pd, Pt, AP = S.Pd, S.Pt[0], S.AP
-    others = {
-        "Pt_transpose": lambda: S.hT.transpose(Pd, out=S.Pt),
-        "AP_symbolic": lambda: S.hAP.symbolic(Ad, Pd, C_rowptr=S.rpAP),
-        "AP_numeric": lambda: S.hAP.numeric(Ad, Pd, S.CAP.rowptr, S.CAP.nnz, S.CAP.colidx, S.CAP.values),
-        "RAP_symbolic": lambda: S.hRAP.symbolic(Pt, AP, C_rowptr=S.rpRAP),
-        "RAP_numeric": lambda: S.hRAP.numeric(Pt, AP, S.CRAP.rowptr, S.CRAP.nnz, S.CRAP.colidx, S.CRAP.values),
-    }
+    Pd = S.Pd
+    if S.rap == "fused":
+        T2 = StencilStep(A, P, device, positions=S.positions, rap="two")
+        T2.step()
+        two_step = lambda: (T2.hT.transpose(Pd, out=T2.Pt),
+                            T2.hAP.symbolic(Ad, Pd, C_rowptr=T2.rpAP),
+                            T2.hAP.numeric(Ad, Pd, T2.CAP.rowptr, T2.CAP.nnz, T2.CAP.colidx, T2.CAP.values),
+                            T2.hRAP.symbolic(T2.Pt[0], T2.AP, C_rowptr=T2.rpRAP),
+                            T2.hRAP.numeric(T2.Pt[0], T2.AP, T2.CRAP.rowptr, T2.CRAP.nnz, T2.CRAP.colidx,
+                                            T2.CRAP.values))
+        others = {
+            "RAP_fused_symbolic": lambda: S.hRAP.rap_symbolic(Ad, Pd, C_rowptr=S.rpRAP),
+            "RAP_fused_numeric": lambda: S.hRAP.rap_numeric(Ad, Pd, S.CRAP.rowptr, S.CRAP.nnz, S.CRAP.colidx,
+                                                            S.CRAP.values),
+            "RAP_as_two_products": two_step,
+        }
+    else:
+        Pt, AP = S.Pt[0], S.AP
+        others = {
+            "Pt_transpose": lambda: S.hT.transpose(Pd, out=S.Pt),
+            "AP_symbolic": lambda: S.hAP.symbolic(Ad, Pd, C_rowptr=S.rpAP),
+            "AP_numeric": lambda: S.hAP.numeric(Ad, Pd, S.CAP.rowptr, S.CAP.nnz, S.CAP.colidx, S.CAP.values),
+            "RAP_symbolic": lambda: S.hRAP.symbolic(Pt, AP, C_rowptr=S.rpRAP),
+            "RAP_numeric": lambda: S.hRAP.numeric(Pt, AP, S.CRAP.rowptr, S.CRAP.nnz, S.CRAP.colidx,
+                                                  S.CRAP.values),
+        }
     t_other = {}
     for name, fn in others.items():
         fn()
         t_other[name] = round(statistics.mean(time_region(torch, fn, max(args.steps, 5))), 4)
     S.hAA.sync()
+    if S.rap == "fused":
+        T2.close()
 
     nnzC = stAA["nnzC"]
     bytes_num = 2 * csr_bytes(A.nrows, A.nnz, 8) + csr_bytes(A.nrows, nnzC, 8)
@@ -320,6 +368,8 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD if args.grid == 100 else WORKLOAD.replace("100^3", "%d^3" % args.grid),
                    "global_batch": world, "flops_per_step": 2 * flops_step,
+                   "triple_product": ("one plan (spgemm_rap_symbolic / spgemm_rap_numeric); flops counted as "
+                                      "A*P and P^T*(A*P)") if S.rap == "fused" else "transpose, A*P, P^T*(A*P)",
                    "l2": "inputs larger than L2 (A = %.0f MB, C = %.0f MB)" % (
                        csr_bytes(A.nrows, A.nnz, 8) / 1e6, csr_bytes(A.nrows, nnzC, 8) / 1e6),
                    "parallelism": "one independent problem per GPU (row blocks), no data-path collective"},
@@ -361,7 +411,7 @@ def run_e2e(torch, S, A, P, args, world, flops_step):
     step's C (on a copy stream) overlaps the next step's upload and kernels; the
     region ends when the last read-back has landed in host memory."""
     pin = lambda x: torch.from_numpy(x).pin_memory()
-    S2 = StencilStep(A, P, S.Ad.rowptr.device, positions=S.positions)
+    S2 = StencilStep(A, P, S.Ad.rowptr.device, positions=S.positions, rap=S.rap)
     S2.step()
     sets = [S, S2]
     hA = [pin(A.rowptr), pin(A.colidx), pin(A.values)]

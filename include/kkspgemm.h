@@ -211,6 +211,50 @@ spgemm_status_t spgemm_masked_count(spgemm_handle_t h, const spgemm_csr_t *X, co
                                     int64_t *row_counts, spgemm_stream_t stream);
 
 /*
+ * Galerkin triple product C = P^T * A * P in one plan (the R x A x P products
+ * of multigrid setup, Section 4, with R = P^T): A is n x n, P is n x K, C is
+ * K x K with int64 row pointers C_rowptr[K + 1], int32 columns sorted within
+ * each row and values in A's dtype.  A and P share one dtype.  C's pattern is
+ * the structural product (every (I, J) with some i, j such that P(i, I),
+ * A(i, j) and P(j, J) are stored; numerical zeros kept).
+ *
+ * Unlike two calls of spgemm_symbolic / spgemm_numeric, A*P is never formed:
+ * row I of C is accumulated directly from the rows A(i,:) of the entries
+ * P(i, I) of column I of P.  The symbolic call builds the pattern of P^T
+ * (which entry of P holds each value of R) and keeps it in the handle; the
+ * numeric call reads R's values from P through it, so new values of A and P
+ * on the same patterns need no transpose or gather.  Each row of C is one
+ * warp (or, for large rows, one 256-thread CTA) with its accumulator in
+ * shared memory: a bitmap of ceil(K / 32) words or an LP table (Section
+ * 3.1.2), whichever is smaller, in the symbolic call; an LP table sized from
+ * the row's known size in the numeric call.
+ *
+ * spgemm_rap_symbolic writes C_rowptr (device, caller-owned, K + 1 entries)
+ * and *nnzC (host); it synchronises the stream twice.  Values of A and P may
+ * be NULL (their dtype fields still select the numeric plan).  Afterwards
+ * spgemm_get_stats describes this product (f_m = the number of products
+ * r * a * p).  Errors: SPGEMM_ERR_INVALID_ARG for mismatched shapes or dtypes,
+ * SPGEMM_ERR_INDEX_OVERFLOW when n or K exceeds 2^31 - 1,
+ * SPGEMM_ERR_BAD_INDEX for malformed row pointers or out-of-range columns,
+ * SPGEMM_ERR_DEVICE_LIMIT when a row of C needs more shared memory than one
+ * CTA has (symbolic: more than about 50 K keys with K above about 1.6 M;
+ * numeric: rows of more than 4096 entries in FP64, 6144 in FP32): multiply in
+ * two steps (spgemm_transpose, spgemm_symbolic / spgemm_numeric) instead.
+ *
+ * spgemm_rap_numeric fills C_colidx and C_values (device, caller-owned, nnzC
+ * entries each) on the pattern of the last spgemm_rap_symbolic call of this
+ * handle.  It returns SPGEMM_ERR_NOT_READY unless A and P have that call's
+ * patterns (the same row-pointer and column pointers and sizes), allocates
+ * nothing and does not synchronise (it can be captured in a CUDA graph);
+ * device-detected problems are returned by spgemm_handle_sync.
+ */
+spgemm_status_t spgemm_rap_symbolic(spgemm_handle_t h, const spgemm_csr_t *A, const spgemm_csr_t *P,
+                                    int64_t *C_rowptr, int64_t *nnzC, spgemm_stream_t stream);
+spgemm_status_t spgemm_rap_numeric(spgemm_handle_t h, const spgemm_csr_t *A, const spgemm_csr_t *P,
+                                   const int64_t *C_rowptr, int32_t *C_colidx, void *C_values,
+                                   spgemm_stream_t stream);
+
+/*
  * Transpose: At = A^T (A.ncols x A.nrows) with At_rowptr int64[A.ncols + 1],
  * At_colidx int32[nnz] (rows sorted), At_values (A's dtype, may be NULL when
  * A.values is NULL) and perm int64[nnz] (may be NULL): At_values[q] =

@@ -16,6 +16,8 @@ brackets):
 * ``transpose``        – counting transpose with value permutation
 * ``masked_dA/dB``     – dA = (G·Bᵀ) on A's pattern, dB = (Aᵀ·G) on B's pattern
 * ``stats``            – f_m, maxrf, nnz(C), maxrs, CF, CMRF [§4 table columns]
+* ``galerkin``         – C = Pᵀ·A·P (the R×A×P products of §4 with R = Pᵀ) as
+                         Pᵀ·(A·P) and its bound |P|ᵀ|A||P|
 
 All values are computed in FP64 (FP32 inputs are widened first).
 """
@@ -209,3 +211,27 @@ def lower_triangle(A: Csr) -> Csr:
     rp = np.zeros(A.nrows + 1, dtype=np.int64)
     np.cumsum(np.bincount(rid[keep], minlength=A.nrows), out=rp[1:])
     return Csr(A.nrows, A.ncols, rp, A.colidx[keep].astype(np.int32), None)
+
+
+def _abs(M: Csr) -> Csr:
+    return Csr(M.nrows, M.ncols, M.rowptr, M.colidx, np.abs(np.asarray(M.values, dtype=np.float64)))
+
+
+def galerkin(A: Csr, P: Csr):
+    """C = Pᵀ·A·P and the entrywise bound S = Σ_{i,j} |p_iI||a_ij||p_jJ|.
+
+    The R×A×P product of multigrid setup (§4) with R = Pᵀ, written out as its
+    definition by two products: C = Pᵀ·(A·P) with the counting transpose and
+    the Gustavson product above (Algorithm 1), and S the same products of the
+    absolute values.  The pattern is the structural product (every (I, J) with
+    some stored P(i,I), A(i,j), P(j,J)), which both factorisations give.
+    """
+    assert A.nrows == A.ncols == P.nrows
+    Pt, _ = transpose(P)
+    AP, _ = spgemm(A, P, with_bounds=False)
+    C, _ = spgemm(Pt, AP, with_bounds=False)
+    Pta, _ = transpose(_abs(P))
+    APa, _ = spgemm(_abs(A), _abs(P), with_bounds=False)
+    S, _ = spgemm(Pta, APa, with_bounds=False)
+    assert np.array_equal(S.rowptr, C.rowptr) and np.array_equal(S.colidx, C.colidx)
+    return C, np.asarray(S.values, dtype=np.float64)

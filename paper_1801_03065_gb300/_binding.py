@@ -63,6 +63,8 @@ SIGNATURES = {
     "spgemm_get_stats": (C.c_int, [_P, C.POINTER(StatsT)]),
     "spgemm_masked": (C.c_int, [_P, C.POINTER(CsrT), C.POINTER(CsrT), _P, _P, C.c_int64, _P, _P, _P, _P]),
     "spgemm_masked_count": (C.c_int, [_P, C.POINTER(CsrT), C.POINTER(CsrT), _P, _P, C.c_int64, _P, _P]),
+    "spgemm_rap_symbolic": (C.c_int, [_P, C.POINTER(CsrT), C.POINTER(CsrT), _P, C.POINTER(C.c_int64), _P]),
+    "spgemm_rap_numeric": (C.c_int, [_P, C.POINTER(CsrT), C.POINTER(CsrT), _P, _P, _P, _P]),
     "spgemm_transpose": (C.c_int, [_P, C.POINTER(CsrT), _P, _P, _P, _P, _P]),
     "spgemm_gather": (C.c_int, [_P, C.c_int, _P, _P, _P, C.c_int64, _P]),
     "spgemm_transpose_noalloc": (C.c_int, [C.POINTER(CsrT), _P, _P, _P, _P, _P]),

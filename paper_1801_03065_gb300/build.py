@@ -21,7 +21,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libkkspgemm.so")
 
-SOURCES = ["kks_prep.cu", "kks_symbolic.cu", "kks_numeric.cu", "kks_masked.cu", "kks_api.cu", "kks_noalloc.cu"]
+SOURCES = ["kks_prep.cu", "kks_symbolic.cu", "kks_numeric.cu", "kks_masked.cu", "kks_api.cu", "kks_noalloc.cu", "kks_rap.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "--extended-lambda", "-lineinfo", "-Xcompiler", "-fPIC",
          "-I" + INCLUDE, "-I" + CSRC]

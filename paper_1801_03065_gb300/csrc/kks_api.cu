@@ -39,7 +39,8 @@ enum BufId {
   kBufScanTmp, kBufInstStats, kBufInstOut, kBufHist, kBufCursor, kBufSymRows, kBufNumRows, kBufSymPool,
   kBufNumPool2, kBufNumPool3, kBufStatus, kBufMaskRows, kBufMaskHist, kBufMaskPool, kBufTrTmp,
   kBufTrPool, kBufReuseRows, kBufReusePool, kBufBinCnt, kBufBinOfs, kBufMcCnt, kBufMcYcp, kBufMcCsi, kBufMcCs,
-  kBufMcMax, kNumBufs
+  kBufMcMax, kBufRapRf, kBufRapRtp, kBufRapRti, kBufRapRpe, kBufRapW, kBufRapCnt, kBufRapSymRows,
+  kBufRapNumRows, kBufRapMeta, kBufRapTmp, kNumBufs
 };
 
 // Row bins of a masked product, cached for numeric reuse on one pattern.
@@ -71,6 +72,17 @@ struct PatternId {
     return arp == o.arp && acj == o.acj && brp == o.brp && bcj == o.bcj && m == o.m && n == o.n && k == o.k &&
            nnza == o.nnza && nnzb == o.nnzb && arp64 == o.arp64 && brp64 == o.brp64;
   }
+};
+
+// Plan of a Galerkin triple product (spgemm_rap_symbolic): the pattern it was
+// made for and its numeric row classes.
+struct RapPlan {
+  bool ready = false;
+  const void *arp = nullptr, *acj = nullptr, *prp = nullptr, *pcj = nullptr;
+  long long n = 0, K = 0, nnza = 0, nnzp = 0, nnzc = 0;
+  int arp64 = 0, prp64 = 0, dtype = 1, punit = 0;
+  long long n_w = 0, n_c = 0;
+  int logT_w = 1, logT_c = 1;
 };
 
 struct BinRun {
@@ -123,6 +135,7 @@ struct kks_handle {
     BinRun pick;
   };
   std::vector<TuneEntry> tune_cache;
+  RapPlan rap;
 };
 
 namespace {
@@ -1194,7 +1207,7 @@ spgemm_status_t spgemm_handle_sync(spgemm_handle_t h, spgemm_stream_t stream) {
 
 spgemm_status_t spgemm_get_stats(spgemm_handle_t h, spgemm_stats_t* out) {
   if (!h || !out) return SPGEMM_ERR_INVALID_ARG;
-  if (!h->ready) return SPGEMM_ERR_NOT_READY;
+  if (!h->ready && !h->rap.ready) return SPGEMM_ERR_NOT_READY;
   *out = h->stats;
   return SPGEMM_OK;
 }
@@ -1333,6 +1346,161 @@ spgemm_status_t spgemm_masked_count(spgemm_handle_t h, const spgemm_csr_t* X, co
   KKS_CU(to_host(h, hs, h->buf[kBufStatus], sizeof(DevStatus), s));
   KKS_CU(cudaStreamSynchronize(s));
   return consume_status(h, hs, s);
+}
+
+namespace {
+
+RapD rapd(kks_handle* h, const spgemm_csr_t* A, const spgemm_csr_t* P) {
+  RapD R;
+  R.A = matd(A);
+  R.P = matd(P);
+  R.Rtp = B<long long>(h, kBufRapRtp);
+  R.Rti = B<int>(h, kBufRapRti);
+  R.Rpe = B<long long>(h, kBufRapRpe);
+  R.status = B<DevStatus>(h, kBufStatus);
+  R.punit = 0;
+  R.pad = 0;
+  return R;
+}
+
+bool rap_same_pattern(const RapPlan& p, const spgemm_csr_t* A, const spgemm_csr_t* P) {
+  return p.arp == A->rowptr && p.acj == (const void*)A->colidx && p.prp == P->rowptr &&
+         p.pcj == (const void*)P->colidx && p.n == A->nrows && p.K == P->ncols && p.nnza == A->nnz &&
+         p.nnzp == P->nnz && p.arp64 == A->rowptr_is_64 && p.prp64 == P->rowptr_is_64;
+}
+
+}  // namespace
+
+spgemm_status_t spgemm_rap_symbolic(spgemm_handle_t h, const spgemm_csr_t* A, const spgemm_csr_t* P,
+                                    int64_t* C_rowptr, int64_t* nnzC, spgemm_stream_t stream) {
+  if (!h || !A || !P || !C_rowptr || !nnzC) return SPGEMM_ERR_INVALID_ARG;
+  KKS_ST(check_csr(A, false));
+  KKS_ST(check_csr(P, false));
+  if (A->nrows != A->ncols || A->ncols != P->nrows) return SPGEMM_ERR_INVALID_ARG;
+  if (A->dtype != P->dtype) return SPGEMM_ERR_INVALID_ARG;
+  if (P->nrows > 2147483647ll || P->ncols > 2147483647ll) return SPGEMM_ERR_INDEX_OVERFLOW;
+  cudaStream_t s = (cudaStream_t)stream;
+  KKS_CU(cudaSetDevice(h->opt.device));
+  RapPlan& pl = h->rap;
+  pl.ready = false;
+  const long long n = A->nrows, K = P->ncols, nnzp = P->nnz;
+  const int dtype = (int)A->dtype;
+  KKS_ST(ensure(h, kBufStatus, sizeof(DevStatus)));
+  KKS_ST(ensure(h, kBufRapRf, sizeof(long long) * (n + 1)));
+  KKS_ST(ensure(h, kBufRapRtp, sizeof(long long) * (K + 1)));
+  KKS_ST(ensure(h, kBufRapRti, sizeof(int) * (nnzp + 1)));
+  KKS_ST(ensure(h, kBufRapRpe, sizeof(long long) * (nnzp + 1)));
+  KKS_ST(ensure(h, kBufRapW, sizeof(long long) * (K + 1)));
+  KKS_ST(ensure(h, kBufRapCnt, sizeof(long long) * (K + 1)));
+  KKS_ST(ensure(h, kBufRapSymRows, sizeof(int) * 2 * (K + 1)));
+  KKS_ST(ensure(h, kBufRapNumRows, sizeof(int) * 2 * (K + 1)));
+  KKS_ST(ensure(h, kBufRapMeta, sizeof(unsigned long long) * 16));
+  KKS_ST(ensure(h, kBufRapTmp, std::max(transpose_pattern_tmp_bytes(K), scan_tmp_bytes(K + 1))));
+  KKS_ST(ensure_pinned(h, 256 + sizeof(DevStatus)));
+  KKS_CU(cudaMemsetAsync(h->buf[kBufStatus], 0, sizeof(DevStatus), s));
+  KKS_CU(cudaMemsetAsync(h->buf[kBufRapMeta], 0, sizeof(unsigned long long) * 16, s));
+  RapD R = rapd(h, A, P);
+  LaunchCtx L = ctx(h, s);
+  unsigned long long* meta = B<unsigned long long>(h, kBufRapMeta);
+  int* sym_w = B<int>(h, kBufRapSymRows);
+  int* sym_c = sym_w + (K + 1);
+  int* num_w = B<int>(h, kBufRapNumRows);
+  int* num_c = num_w + (K + 1);
+  // tables: up to 8 KB per warp team (8 teams per CTA); a CTA team takes what
+  // its shared memory holds beside its scratch
+  const size_t warp_table = 8192;
+  const size_t cta_table = (size_t)h->max_smem - rap_sym_team_bytes_host(1, 0) - 1024;
+  unsigned long long* h_meta = (unsigned long long*)h->pinned;
+  DevStatus* hs = (DevStatus*)(h->pinned + 256);
+  // (1) products per row of A*P, the pattern of P^T, row bounds and classes
+  KKS_CU(launch_rap_prepare(L, R, B<long long>(h, kBufRapRf), B<long long>(h, kBufRapW),
+                            B<long long>(h, kBufRapCnt), sym_w, sym_c, meta, warp_table, cta_table,
+                            h->buf[kBufRapTmp]));
+  KKS_CU(to_host(h, h_meta, meta, sizeof(unsigned long long) * 16, s));
+  KKS_CU(to_host(h, hs, h->buf[kBufStatus], sizeof(DevStatus), s));
+  KKS_CU(cudaStreamSynchronize(s));
+  KKS_ST(consume_status(h, hs, s));
+  const long long fm = (long long)h_meta[4];
+  R.punit = h_meta[10] == 0 ? 1 : 0;
+  // (2) row sizes of C and their scan into C's row pointers
+  KKS_CU(launch_rap_symbolic(L, R, B<long long>(h, kBufRapW), B<long long>(h, kBufRapCnt), sym_w,
+                             (long long)h_meta[0], (size_t)h_meta[2], sym_c, (long long)h_meta[1],
+                             (size_t)h_meta[3], h->opt.hash_function));
+  KKS_CU(launch_scan(L, B<long long>(h, kBufRapCnt), reinterpret_cast<long long*>(C_rowptr), K,
+                     h->buf[kBufRapTmp]));
+  // (3) numeric classes by row size
+  int warp_logT = 1, cta_logT = 1;
+  for (int l = 1; l <= 24; ++l) {
+    if (rap_num_team_bytes_host(0, dtype, l) * 8 <= kTeamSmemBudget) warp_logT = l;
+    if (rap_num_team_bytes_host(1, dtype, l) + 1024 <= (size_t)h->max_smem) cta_logT = l;
+  }
+  KKS_CU(launch_rap_num_bin(L, reinterpret_cast<const long long*>(C_rowptr), K, num_w, num_c, meta, warp_logT,
+                            cta_logT, B<DevStatus>(h, kBufStatus)));
+  long long* h_nnz = (long long*)(h->pinned + 128);
+  *h_nnz = 0;
+  KKS_CU(to_host(h, h_meta, meta, sizeof(unsigned long long) * 16, s));
+  KKS_CU(to_host(h, h_nnz, reinterpret_cast<const long long*>(C_rowptr) + K, sizeof(long long), s));
+  KKS_CU(to_host(h, hs, h->buf[kBufStatus], sizeof(DevStatus), s));
+  KKS_CU(cudaStreamSynchronize(s));
+  KKS_ST(consume_status(h, hs, s));
+  pl.arp = A->rowptr;
+  pl.acj = A->colidx;
+  pl.prp = P->rowptr;
+  pl.pcj = P->colidx;
+  pl.n = n;
+  pl.K = K;
+  pl.nnza = A->nnz;
+  pl.nnzp = nnzp;
+  pl.nnzc = *h_nnz;
+  pl.arp64 = A->rowptr_is_64;
+  pl.prp64 = P->rowptr_is_64;
+  pl.dtype = dtype;
+  pl.punit = R.punit;
+  pl.n_w = (long long)h_meta[5];
+  pl.n_c = (long long)h_meta[6];
+  pl.logT_w = std::max(1, (int)h_meta[7]);
+  pl.logT_c = std::max(1, (int)h_meta[8]);
+  spgemm_stats_t& st = h->stats;
+  memset(&st, 0, sizeof(st));
+  st.m = K;
+  st.n = n;
+  st.k = K;
+  st.nnzA = A->nnz;
+  st.nnzB = nnzp;
+  st.f_m = fm;
+  st.f_m_compressed = fm;
+  st.CF = 1.0;
+  st.CMRF = 1.0;
+  st.nnzC = *h_nnz;
+  st.maxrs = (long long)h_meta[9];
+  st.ars = K > 0 ? (double)*h_nnz / (double)K : 0.0;
+  st.workspace_bytes = (int64_t)h->total;
+  st.bin_rows_numeric[kClsW32] = pl.n_w;
+  st.bin_rows_numeric[kClsC256] = pl.n_c;
+  *nnzC = *h_nnz;
+  pl.ready = true;
+  return SPGEMM_OK;
+}
+
+spgemm_status_t spgemm_rap_numeric(spgemm_handle_t h, const spgemm_csr_t* A, const spgemm_csr_t* P,
+                                   const int64_t* C_rowptr, int32_t* C_colidx, void* C_values,
+                                   spgemm_stream_t stream) {
+  if (!h || !A || !P || !C_rowptr) return SPGEMM_ERR_INVALID_ARG;
+  KKS_ST(check_csr(A, true));
+  KKS_ST(check_csr(P, true));
+  const RapPlan& pl = h->rap;
+  if (!pl.ready || !rap_same_pattern(pl, A, P)) return SPGEMM_ERR_NOT_READY;
+  if ((int)A->dtype != pl.dtype || (int)P->dtype != pl.dtype) return SPGEMM_ERR_INVALID_ARG;
+  if (pl.nnzc > 0 && (!C_colidx || !C_values)) return SPGEMM_ERR_INVALID_ARG;
+  KKS_CU(cudaSetDevice(h->opt.device));
+  cudaStream_t s = (cudaStream_t)stream;
+  RapD R = rapd(h, A, P);
+  R.punit = pl.punit;
+  LaunchCtx L = ctx(h, s);
+  int* num_w = B<int>(h, kBufRapNumRows);
+  KKS_CU(launch_rap_numeric(L, R, pl.dtype, reinterpret_cast<const long long*>(C_rowptr), C_colidx, C_values, num_w,
+                            pl.n_w, pl.logT_w, num_w + (pl.K + 1), pl.n_c, pl.logT_c, h->opt.hash_function));
+  return SPGEMM_OK;
 }
 
 spgemm_status_t spgemm_transpose(spgemm_handle_t h, const spgemm_csr_t* A, int64_t* At_rowptr, int32_t* At_colidx,

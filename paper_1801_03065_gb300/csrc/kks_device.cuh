@@ -31,6 +31,7 @@ enum DevCode : int {
   kDevRowSizeMismatch = 2,  // numeric produced a row size != symbolic's
   kDevBadIndex = 3,         // a column index outside [0, k)
   kDevSortOverflow = 4,     // a row larger than its sort buffer
+  kDevRowTooLarge = 5,      // a row whose table fits no team's shared memory
 };
 
 struct DevStatus {

@@ -283,5 +283,52 @@ cudaError_t launch_transpose_fill(const LaunchCtx&, const MatD& A, int dtype, co
                                   unsigned long long* gbuf, long long gbuf_len, int gbuf_chunks, DevStatus* st);
 cudaError_t launch_gather_values(const LaunchCtx&, int dtype, const void* src, const long long* perm,
                                  void* dst, long long n);
+// pattern of A^T only: column counts, their scan into Atp (m + 1 = ncols + 1
+// entries), and per entry of A^T its row of A (trow) and its entry of A
+// (tperm), rows of A^T in no particular order.  tmp >= transpose_pattern_tmp_bytes.
+size_t transpose_pattern_tmp_bytes(long long ncols);
+cudaError_t launch_transpose_pattern(const LaunchCtx&, const MatD& A, long long* Atp, int* trow, long long* tperm,
+                                     void* tmp, DevStatus* st);
+
+// ---------------------------------------------------------------------------
+// Galerkin triple product C = P^T * A * P (A n x n, P n x K, C K x K)
+// ---------------------------------------------------------------------------
+constexpr int kRapCtaThreads = 256;
+
+struct RapD {
+  MatD A;
+  MatD P;
+  const long long* Rtp;   // K + 1: row pointers of P^T
+  const int* Rti;         // per entry of P^T: its column (the row i of P)
+  const long long* Rpe;   // per entry of P^T: the entry of P holding its value
+  DevStatus* status;
+  int punit;              // every row i of P holds one entry, at position i
+  int pad;
+};
+
+__host__ __device__ int rap_sym_logT(long long w, long long K);
+__host__ __device__ bool rap_sym_bitmap(long long w, long long K);
+__host__ __device__ size_t rap_sym_table_bytes(long long w, long long K);
+__host__ __device__ int rap_num_logT(long long s);
+size_t rap_sym_team_bytes_host(int cta, size_t table);
+size_t rap_num_team_bytes_host(int cta, int dtype, int logT);
+// products per row of A*P (rf), the pattern of P^T (into R's Rtp / Rti / Rpe),
+// per row of C its product count (w) and symbolic class; rows without
+// products get cnt 0.  meta (16 zeroed words): [0] / [1] warp / CTA rows,
+// [2] / [3] their largest table bytes, [4] total products, [10] nonzero
+// unless every row i of P holds exactly one entry at position i.
+cudaError_t launch_rap_prepare(const LaunchCtx&, const RapD& R, long long* rf, long long* w, long long* cnt,
+                               int* rows_w, int* rows_c, unsigned long long* meta, size_t warp_table,
+                               size_t cta_table, void* tmp);
+cudaError_t launch_rap_symbolic(const LaunchCtx&, const RapD& R, const long long* w, long long* cnt,
+                                const int* rows_w, long long n_w, size_t table_w, const int* rows_c, long long n_c,
+                                size_t table_c, int hash_mode);
+// numeric classes from C's row pointers: meta [5] / [6] warp / CTA rows, [7] /
+// [8] their largest log2 table, [9] the longest row
+cudaError_t launch_rap_num_bin(const LaunchCtx&, const long long* Crp, long long K, int* rows_w, int* rows_c,
+                               unsigned long long* meta, int warp_logT, int cta_logT, DevStatus* st);
+cudaError_t launch_rap_numeric(const LaunchCtx&, const RapD& R, int dtype, const long long* Crp, int* Cj, void* Cx,
+                               const int* rows_w, long long n_w, int logT_w, const int* rows_c, long long n_c,
+                               int logT_c, int hash_mode);
 
 }  // namespace kks

@@ -1275,6 +1275,32 @@ cudaError_t launch_transpose_fill(const LaunchCtx& L, const MatD& A, int dtype, 
   return cudaGetLastError();
 }
 
+size_t transpose_pattern_tmp_bytes(long long ncols) {
+  return al16((size_t)(ncols + 1) * 8) * 2 + scan_tmp_bytes(ncols + 1);
+}
+
+cudaError_t launch_transpose_pattern(const LaunchCtx& L, const MatD& A, long long* Atp, int* trow, long long* tperm,
+                                     void* tmp, DevStatus* st) {
+  unsigned char* t = (unsigned char*)tmp;
+  const long long n = A.ncols;
+  unsigned long long* cnt = (unsigned long long*)t;
+  unsigned long long* cursor = (unsigned long long*)(t + al16((size_t)(n + 1) * 8));
+  void* stmp = t + al16((size_t)(n + 1) * 8) * 2;
+  cudaError_t e = cudaMemsetAsync(cnt, 0, al16((size_t)(n + 1) * 8) * 2, L.stream);
+  if (e != cudaSuccess) return e;
+  if (A.nnz > 0) {
+    KKS_LAUNCHED();
+    k_tr_count<<<grid_cap(A.nnz, 256, L.num_sms, 16), 256, 0, L.stream>>>(A, cnt, st);
+  }
+  e = launch_scan(L, (const long long*)cnt, Atp, n, stmp);
+  if (e != cudaSuccess) return e;
+  if (A.nnz > 0 && A.nrows > 0) {
+    KKS_LAUNCHED();
+    k_tr_scatter<<<grid_cap(A.nrows, 256, L.num_sms, 16), 256, 0, L.stream>>>(A, Atp, cursor, trow, tperm, st);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gather_values(const LaunchCtx& L, int dtype, const void* src, const long long* perm, void* dst,
                                  long long n) {
   if (n <= 0) return cudaSuccess;

@@ -181,6 +181,41 @@ class SpGEMM:
         rp, nnz = self.symbolic(A, Bm, stream=stream)
         return self.numeric(A, Bm, rp, nnz, stream=stream)
 
+    # ---------------------------------------------------------------- Galerkin triple product
+    def rap_symbolic(self, A: CsrMatrix, P: CsrMatrix, C_rowptr: Optional[torch.Tensor] = None, stream=None):
+        """Row pointers and nnz of C = P^T A P, planned in one pass (A*P is never formed)."""
+        if C_rowptr is None:
+            C_rowptr = torch.empty(P.ncols + 1, dtype=torch.int64, device=A.rowptr.device)
+        hint = A.dtype or P.dtype
+        da, dp = A.desc(hint), P.desc(hint)
+        nnz = C.c_int64(0)
+        self._keep = (A, P, C_rowptr)
+        B.check(self._lib.spgemm_rap_symbolic(self._h, C.byref(da), C.byref(dp), C.c_void_p(C_rowptr.data_ptr()),
+                                              C.byref(nnz), _stream(stream)), "spgemm_rap_symbolic")
+        return C_rowptr, int(nnz.value)
+
+    def rap_numeric(self, A: CsrMatrix, P: CsrMatrix, C_rowptr: torch.Tensor, nnz: Optional[int] = None,
+                    C_colidx: Optional[torch.Tensor] = None, C_values: Optional[torch.Tensor] = None,
+                    stream=None) -> CsrMatrix:
+        """Columns (sorted per row) and values of C = P^T A P on the last rap_symbolic plan."""
+        if nnz is None:
+            nnz = int(C_rowptr[-1].item()) if C_colidx is None else C_colidx.numel()
+        dev = C_rowptr.device
+        if C_colidx is None:
+            C_colidx = torch.empty(nnz, dtype=torch.int32, device=dev)
+        if C_values is None:
+            C_values = torch.empty(nnz, dtype=A.dtype, device=dev)
+        da, dp = A.desc(), P.desc()
+        B.check(self._lib.spgemm_rap_numeric(self._h, C.byref(da), C.byref(dp), C.c_void_p(C_rowptr.data_ptr()),
+                                             _ptr(C_colidx), _ptr(C_values), _stream(stream)),
+                "spgemm_rap_numeric")
+        return CsrMatrix(C_rowptr, C_colidx, C_values, (P.ncols, P.ncols))
+
+    def rap(self, A: CsrMatrix, P: CsrMatrix, stream=None) -> CsrMatrix:
+        """C = P^T A P (both phases)."""
+        rp, nnz = self.rap_symbolic(A, P, stream=stream)
+        return self.rap_numeric(A, P, rp, nnz, stream=stream)
+
     def sync(self, stream=None):
         B.check(self._lib.spgemm_handle_sync(self._h, _stream(stream)), "spgemm_handle_sync")
 

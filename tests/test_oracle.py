@@ -218,6 +218,64 @@ def test_galerkin_triple_product_invariants():
     assert np.allclose(rs_ap, rs_a, rtol=1e-13, atol=1e-12)
 
 
+@pytest.mark.parametrize("seed", range(24))
+def test_galerkin_matches_dense_triple_product(seed):
+    """oracle.galerkin equals the dense Pᵀ·A·P (values, structural pattern, bound) on tiny inputs."""
+    rng = np.random.default_rng(500 + seed)
+    n, K = int(rng.integers(0, 12)), int(rng.integers(0, 8))
+    da, dp = rng.choice([0.0, 0.15, 0.4, 1.0], size=2)
+    A = _rand(n, n, da, 600 + seed, shuffle=bool(seed % 2))
+    P = _rand(n, K, dp, 700 + seed, shuffle=bool(seed % 3 == 0))
+    C, S = oracle.galerkin(A, P)
+    assert C.shape == (K, K)
+    pa, pp = _dense_pattern(A), _dense_pattern(P)
+    pat = (pp.T @ pa @ pp) > 0
+    assert np.array_equal(_dense_pattern(C) > 0, pat)
+    Ad, Pd = A.to_dense(), P.to_dense()
+    sabs = np.abs(Pd).T @ np.abs(Ad) @ np.abs(Pd)
+    assert np.all(np.abs(C.to_dense() - Pd.T @ Ad @ Pd) <= 1e-13 * sabs + 1e-300)
+    assert np.allclose(_scatter(C, S), np.where(pat, sabs, 0), rtol=1e-14, atol=0)
+    _assert_sorted_rows(C)
+
+
+def test_galerkin_aggregation_closed_form_and_sum():
+    """Aggregation P with unit values: C_IJ = Σ_{i∈I, j∈J} a_ij (every entry); with
+    general values Σ_IJ C_IJ = uᵀ A u for u = P·1."""
+    g = 6
+    A = w.stencil3d_27pt(g, seed=2)
+    P = w.aggregation(g, 2)
+    C, _ = oracle.galerkin(A, P)
+    agg = P.colidx.astype(np.int64)
+    ref = np.zeros((P.ncols, P.ncols))
+    np.add.at(ref, (agg[A.row_ids()], agg[A.colidx]), A.values)
+    assert np.allclose(C.to_dense(), ref, rtol=1e-13, atol=1e-12)
+    patref = np.zeros(ref.shape, dtype=bool)
+    patref[agg[A.row_ids()], agg[A.colidx]] = True
+    assert np.array_equal(_dense_pattern(C) > 0, patref)
+    rng = np.random.default_rng(5)
+    P2 = Csr(P.nrows, P.ncols, P.rowptr, P.colidx, rng.uniform(0.5, 1.5, size=P.nnz))
+    C2, _ = oracle.galerkin(A, P2)
+    u = np.bincount(P2.row_ids(), weights=P2.values, minlength=P2.nrows)
+    Au = np.bincount(A.row_ids(), weights=A.values * u[A.colidx], minlength=A.nrows)
+    assert abs(C2.values.sum() - u @ Au) <= 1e-12 * (np.abs(A.values).sum() * 2.25)
+
+
+def test_galerkin_planted_mistakes_are_caught():
+    """A·P·Pᵀ-style slips (untransposed restriction, dropped factor) fail the dense pin."""
+    rng = np.random.default_rng(9)
+    A = _rand(9, 9, 0.4, 31)
+    P = _rand(9, 9, 0.3, 32)
+    Ad, Pd = A.to_dense(), P.to_dense()
+    ref = Pd.T @ Ad @ Pd
+    wrong_r, _ = oracle.spgemm(P, oracle.spgemm(A, P, with_bounds=False)[0], with_bounds=False)
+    assert not np.allclose(wrong_r.to_dense(), ref)
+    Pt, _ = oracle.transpose(P)
+    dropped, _ = oracle.spgemm(Pt, P, with_bounds=False)
+    assert not np.allclose(dropped.to_dense(), ref)
+    C, _ = oracle.galerkin(A, P)
+    assert np.allclose(C.to_dense(), ref, rtol=1e-13, atol=1e-13)
+
+
 # ---------------------------------------------------------------- compression (§3.2)
 def test_compression_bit_semantics():
     """Bit b of CS at CSI s is set iff column 32·s + b is in the row; CSI distinct."""
