@@ -388,6 +388,7 @@ def run_ours(args):
                          "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                          "algorithmic_bytes": bytes_num},
         "stats_AA": {k: stAA[k] for k in ("f_m", "nnzC", "maxrs", "CF", "CMRF", "compressed")},
+        "rap": rap_summary(S, A, P, t_other, peak, peak_kind),
         "gpu_launches": int(launches),
         "clocks": clk,
     }
@@ -402,6 +403,24 @@ def run_ours(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def rap_summary(S, A, P, t_other, peak, peak_kind):
+    """Times of the one-plan Pᵀ·A·P and the HBM roofline of its numeric call:
+    algorithmic bytes = A and P read once, the pattern of Pᵀ with its entry map
+    (int64 row pointers, int32 rows, int64 entries), C written once."""
+    if S.rap != "fused":
+        return None
+    t_num = t_other["RAP_fused_numeric"]
+    nnzC = S.CRAP.nnz
+    bytes_alg = (csr_bytes(A.nrows, A.nnz, 8) + csr_bytes(P.nrows, P.nnz, 8) + 8 * (P.ncols + 1) + 12 * P.nnz
+                 + csr_bytes(P.ncols, nnzC, 8))
+    achieved = bytes_alg / (t_num * 1e-3) / 1e9
+    return {"symbolic_ms": t_other["RAP_fused_symbolic"], "numeric_ms": t_num,
+            "as_two_products_ms": t_other["RAP_as_two_products"], "nnzC": nnzC,
+            "numeric_roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                                 "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                                 "algorithmic_bytes": bytes_alg, "kernel": "k_rap_num (one call of spgemm_rap_numeric)"}}
 
 
 def run_e2e(torch, S, A, P, args, world, flops_step):
@@ -425,18 +444,31 @@ def run_e2e(torch, S, A, P, args, world, flops_step):
     h2d = sum(t.numel() * t.element_size() for t in hA + hP)
     d2h = sum(t.numel() * t.element_size() for t in out_AA + out_RAP)
     copy = torch.cuda.Stream()
+    upload = torch.cuda.Stream()
     done = [None, None]
+    computed = [None, None]
 
     def e2e_step(i):
         X = sets[i % 2]
         cur = torch.cuda.current_stream()
+        # the upload of this step's inputs runs on its own stream as soon as
+        # this set's previous step has finished with them, overlapping the
+        # other set's kernels and read-back
+        if computed[i % 2] is not None:
+            upload.wait_event(computed[i % 2])
+        with torch.cuda.stream(upload):
+            for d, h in zip([X.Ad.rowptr, X.Ad.colidx, X.Ad.values, X.Pd.rowptr, X.Pd.colidx, X.Pd.values],
+                            hA + hP):
+                d.copy_(h, non_blocking=True)
+            up = torch.cuda.Event()
+            up.record(upload)
+        cur.wait_event(up)
         if done[i % 2] is not None:
             cur.wait_event(done[i % 2])          # this set's previous read-back has finished
-        for d, h in zip([X.Ad.rowptr, X.Ad.colidx, X.Ad.values, X.Pd.rowptr, X.Pd.colidx, X.Pd.values], hA + hP):
-            d.copy_(h, non_blocking=True)
         X.step()
         ev = torch.cuda.Event()
         ev.record(cur)
+        computed[i % 2] = ev
         copy.wait_event(ev)
         with torch.cuda.stream(copy):
             # pieces of at most 64 MB, so the small read-backs of the next step's
@@ -457,9 +489,11 @@ def run_e2e(torch, S, A, P, args, world, flops_step):
     cur = torch.cuda.current_stream()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0.record(cur)
+    upload.wait_event(t0)
     for i in range(n):
         e2e_step(i)
     cur.wait_stream(copy)
+    cur.wait_stream(upload)
     t1.record(cur)
     torch.cuda.synchronize()
     t = t0.elapsed_time(t1) / n
@@ -467,7 +501,7 @@ def run_e2e(torch, S, A, P, args, world, flops_step):
     t, flops_all = reduce_over_ranks(t, flops_step, world, S.Ad.rowptr.device)
     return {"value": round(2.0 * flops_all / (t * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": round(t, 4),
-            "overlap": "two buffer sets; read-back on a copy stream overlaps the next step"}
+            "overlap": "two buffer sets; uploads and read-backs on their own streams overlap the other set's step"}
 
 
 # ----------------------------------------------------------------------------- CPU oracle
@@ -759,11 +793,10 @@ def run_triangles(args):
     import numpy as np
     import torch
     import workloads as w
-    import oracle
     from paper_1801_03065_gb300 import ops
     torch.cuda.set_device(0)
     G = w.rmat_symmetric(scale=18, seed=7)
-    L = oracle.lower_triangle(G)
+    L = w.lower_triangle(G)
     Ld = ops.CsrMatrix.from_host(L.rowptr, L.colidx, None, L.shape, device="cuda:0")
     h = ops.SpGEMM()
     out = torch.empty(L.nrows, dtype=torch.int64, device="cuda:0")
@@ -778,11 +811,57 @@ def run_triangles(args):
     desc = ("rmat18_triangles: per-vertex triangle counts of the symmetrised R-MAT scale-18 graph "
             "(%d edges), masked count of L*L on L with L compressed" % (L.nnz))
     h.close()
+    # algorithmic bytes of one call: L read as X, Y and S (int64 row pointers,
+    # int32 columns), Y's compressed rows written and read once (int64 row
+    # pointers, int32 set index, uint32 bits), one int64 count per row
+    ncomp = int(np.unique(L.row_ids() * (1 << 27) + (L.colidx.astype(np.int64) >> 5)).size)
+    pat = 8 * (L.nrows + 1) + 4 * L.nnz
+    bytes_alg = 3 * pat + 2 * (8 * (L.nrows + 1) + 8 * ncomp) + 8 * L.nrows
+    peak, peak_kind = measured_peaks()
+    achieved = bytes_alg / (t * 1e-3) / 1e9
     out_line = _base_line(args, products / (t * 1e-3) / 1e9, t, desc, "int64", {
-        "unit": "G structural products/s", "triangles": tri, "products": products})
+        "unit": "G structural products/s", "triangles": tri, "products": products,
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_kind": peak_kind, "traffic": None,
+                     "kernel": "spgemm_masked_count (compression of L, then k_masked_count_warp / _cta)",
+                     "algorithmic_bytes": bytes_alg,
+                     "note": "latency- and shared-atomic-bound: hub rows of L reach up to 25 k columns"}})
     out_line["metric"] = "masked count (triangles) throughput"
     out_line["higher_is_better"] = True
+    if not args.no_cpu_baseline:
+        out_line["cpu_baseline"] = triangles_cpu_baseline(L, args.cpu_budget)
     print(json.dumps(out_line), flush=True)
+
+
+def triangles_cpu_baseline(L, budget):
+    """The oracle's masked count (by definition, OpenMP over rows) on a row
+    sample of L, about `budget` seconds."""
+    import numpy as np
+    import oracle
+    from workloads.csr import Csr
+    lens = np.diff(L.rowptr)
+    prod_row = np.zeros(L.nrows, dtype=np.int64)
+    np.add.at(prod_row, L.row_ids(), lens[L.colidx])
+
+    def sample(stride):
+        rows = np.arange(0, L.nrows, stride, dtype=np.int64)
+        rl = lens[rows]
+        rp = np.zeros(rows.size + 1, dtype=np.int64)
+        np.cumsum(rl, out=rp[1:])
+        idx = np.concatenate([np.arange(L.rowptr[r], L.rowptr[r + 1]) for r in rows]) if rows.size else \
+            np.zeros(0, np.int64)
+        X = Csr(rows.size, L.ncols, rp, L.colidx[idx], None)
+        t0 = time.perf_counter()
+        oracle.masked_count(X, L, X)
+        return time.perf_counter() - t0, int(prod_row[rows].sum()), rows.size
+
+    sample(4096)                                  # loads the oracle
+    t1, p1, _ = sample(64)
+    stride = max(1, int(64 * max(t1, 1e-4) / budget))   # the whole graph when it fits the budget
+    t, p, n = sample(stride)
+    what = "all rows of L" if stride == 1 else "every %d-th row of L" % stride
+    return {"value": round(p / t / 1e9, 4), "unit": "G structural products/s", "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": "%s (%d rows, %d structural products), %.1f s" % (what, n, p, t)}
 
 
 def run_differentiation(args):

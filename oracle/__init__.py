@@ -204,15 +204,6 @@ def masked_count(X: Csr, Y: Csr, S: Csr):
     return out
 
 
-def lower_triangle(A: Csr) -> Csr:
-    """The strictly lower triangle of A's pattern (values dropped)."""
-    rid = np.repeat(np.arange(A.nrows), np.diff(A.rowptr))
-    keep = A.colidx < rid
-    rp = np.zeros(A.nrows + 1, dtype=np.int64)
-    np.cumsum(np.bincount(rid[keep], minlength=A.nrows), out=rp[1:])
-    return Csr(A.nrows, A.ncols, rp, A.colidx[keep].astype(np.int32), None)
-
-
 def _abs(M: Csr) -> Csr:
     return Csr(M.nrows, M.ncols, M.rowptr, M.colidx, np.abs(np.asarray(M.values, dtype=np.float64)))
 

@@ -411,7 +411,7 @@ def _graph(n, edges):
 
 
 def _triangles(G):
-    L = oracle.lower_triangle(G)
+    L = w.lower_triangle(G)
     return int(oracle.masked_count(L, L, L).sum())
 
 

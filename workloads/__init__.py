@@ -9,7 +9,7 @@ The shapes and value distributions stand in for the paper's test problems
 triple products), which are not available here.
 """
 
-from .csr import Csr, csr_from_coo, shuffle_rows, identity, permutation_matrix
+from .csr import Csr, csr_from_coo, shuffle_rows, identity, permutation_matrix, lower_triangle
 from .gen import (
     laplace2d_5pt,
     stencil3d_27pt,
@@ -24,7 +24,7 @@ from .gen import (
 )
 
 __all__ = [
-    "Csr", "csr_from_coo", "shuffle_rows", "identity", "permutation_matrix",
+    "Csr", "csr_from_coo", "shuffle_rows", "identity", "permutation_matrix", "lower_triangle",
     "laplace2d_5pt", "stencil3d_27pt", "laplace3d_7pt", "aggregation",
     "rmat_symmetric", "batched_pairs", "batched_fresh_values", "random_csr",
     "values_on_pattern", "config_workload",

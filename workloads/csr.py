@@ -99,3 +99,13 @@ def permutation_matrix(perm: np.ndarray, dtype=np.float64) -> Csr:
     n = perm.shape[0]
     return Csr(n, n, np.arange(n + 1, dtype=np.int64), perm.astype(np.int32),
                np.ones(n, dtype=dtype))
+
+
+def lower_triangle(A: Csr) -> Csr:
+    """The strictly lower triangle of A's pattern (values dropped): the input
+    of triangle counting on an undirected graph."""
+    rid = A.row_ids()
+    keep = A.colidx < rid
+    rp = np.zeros(A.nrows + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rid[keep], minlength=A.nrows), out=rp[1:])
+    return Csr(A.nrows, A.ncols, rp, A.colidx[keep].astype(np.int32), None)
