@@ -40,7 +40,7 @@ enum BufId {
   kBufNumPool2, kBufNumPool3, kBufStatus, kBufMaskRows, kBufMaskHist, kBufMaskPool, kBufTrTmp,
   kBufTrPool, kBufReuseRows, kBufReusePool, kBufBinCnt, kBufBinOfs, kBufMcCnt, kBufMcYcp, kBufMcCsi, kBufMcCs,
   kBufMcMax, kBufRapRf, kBufRapRtp, kBufRapRti, kBufRapRpe, kBufRapW, kBufRapCnt, kBufRapSymRows,
-  kBufRapNumRows, kBufRapMeta, kBufRapTmp, kNumBufs
+  kBufRapNumRows, kBufRapMeta, kBufRapTmp, kBufMcRows, kNumBufs
 };
 
 // Row bins of a masked product, cached for numeric reuse on one pattern.
@@ -1313,7 +1313,8 @@ spgemm_status_t spgemm_masked_count(spgemm_handle_t h, const spgemm_csr_t* X, co
   KKS_ST(ensure(h, kBufStatus, sizeof(DevStatus)));
   KKS_ST(ensure(h, kBufMcCnt, sizeof(long long) * (ny + 1)));
   KKS_ST(ensure(h, kBufMcYcp, sizeof(long long) * (ny + 1)));
-  KKS_ST(ensure(h, kBufMcMax, 16));
+  KKS_ST(ensure(h, kBufMcMax, 128));
+  KKS_ST(ensure(h, kBufMcRows, sizeof(int) * 3 * (X->nrows + 1)));
   KKS_ST(ensure(h, kBufScanTmp, scan_tmp_bytes(ny + 1)));
   KKS_ST(ensure_pinned(h, 64 + sizeof(DevStatus)));
   M.status = B<DevStatus>(h, kBufStatus);
@@ -1333,14 +1334,15 @@ spgemm_status_t spgemm_masked_count(spgemm_handle_t h, const spgemm_csr_t* X, co
   KKS_CU(cudaStreamSynchronize(s));
   KKS_ST(consume_status(h, hs, s));
   const long long nc = *h_nc;
-  const bool big = *h_max > (unsigned long long)kMcBigRow;
   // (2) the compressed Y, (3) the counts
   KKS_ST(ensure(h, kBufMcCsi, sizeof(int) * (nc + 1)));
   KKS_ST(ensure(h, kBufMcCs, sizeof(unsigned) * (nc + 1)));
   KKS_CU(launch_mc_compress(L, M, 1, B<long long>(h, kBufMcYcp), nullptr, B<int>(h, kBufMcCsi),
                             B<unsigned>(h, kBufMcCs)));
   cudaError_t e = launch_masked_count(L, M, B<long long>(h, kBufMcYcp), B<int>(h, kBufMcCsi),
-                                      B<unsigned>(h, kBufMcCs), reinterpret_cast<long long*>(row_counts), big);
+                                      B<unsigned>(h, kBufMcCs), reinterpret_cast<long long*>(row_counts),
+                                      (long long)*h_max, B<int>(h, kBufMcRows),
+                                      B<unsigned long long>(h, kBufMcMax) + 2);
   if (e == cudaErrorInvalidConfiguration) return SPGEMM_ERR_DEVICE_LIMIT;
   KKS_CU(e);
   KKS_CU(to_host(h, hs, h->buf[kBufStatus], sizeof(DevStatus), s));

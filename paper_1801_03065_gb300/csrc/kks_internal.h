@@ -264,8 +264,11 @@ cudaError_t launch_masked(const LaunchCtx&, const MaskedD&, const MaskedLaunch&)
 constexpr int kMcBigRow = 1024;
 cudaError_t launch_mc_compress(const LaunchCtx&, const MaskedD&, int pass, const long long* ycp, long long* cnt,
                                int* csi, unsigned* cs);
+// max_row: the longest row of S (rows above kMcBigRow entries take a CTA each);
+// lists: 3 * X.nrows ints of scratch, ctr: 6 counters of scratch
 cudaError_t launch_masked_count(const LaunchCtx&, const MaskedD&, const long long* Ycp, const int* csi,
-                                const unsigned* cs, long long* counts, bool has_big_rows);
+                                const unsigned* cs, long long* counts, long long max_row, int* lists,
+                                unsigned long long* ctr);
 // *out = the longest row of a pattern with int64 row pointers (device)
 cudaError_t launch_row_len_max(const LaunchCtx&, const long long* Sp, long long nrows, unsigned long long* out);
 

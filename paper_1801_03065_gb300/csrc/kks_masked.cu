@@ -733,7 +733,8 @@ __global__ void __launch_bounds__(256) k_mc_compress_fill(MatD Y, const long lon
 }
 
 constexpr int kMcWarpMaxRow = kMcBigRow;   // S rows up to this size: warp teams with a hash table
-constexpr int kMcWarpSlots = 2048;    // table slots per warp (keys + bits: 16 KB)
+constexpr int kMcWarpSlots = 2048;    // table slots of the largest warp tables (keys + bits: 16 KB)
+constexpr int kMcSmallSlots = 256;    // most rows: tables of up to 256 slots (2 KB per warp)
 
 // Longest row of S (int64 row pointers).
 __global__ void k_row_len_max(const long long* __restrict__ Sp, long long n, unsigned long long* out) {
@@ -746,105 +747,153 @@ __global__ void k_row_len_max(const long long* __restrict__ Sp, long long n, uns
   if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 
-// Warp per row of S with at most kMcWarpMaxRow entries.
-__global__ void __launch_bounds__(128) k_masked_count_warp(MaskedD M, const long long* __restrict__ Ycp,
-                                                           const int* __restrict__ csi,
-                                                           const unsigned* __restrict__ cs,
-                                                           long long* __restrict__ counts) {
+// Row classes of the masked count: 0 = table of at most kMcSmallSlots slots,
+// 1 = larger warp tables, 2 = rows above kMcWarpMaxRow entries (a CTA each).
+// Rows of each class are listed (any order) and fetched by the teams from a
+// shared counter: the heavy rows of skewed graphs have indices with many
+// trailing zero bits, which a fixed row-to-team stride would send to a few
+// teams.  Empty rows get their count here.  cnt: [0..2] list lengths.
+__device__ __forceinline__ int mc_class(long long ns) {
+  if (ns > kMcWarpMaxRow) return 2;
+  return 2 * ns > kMcSmallSlots ? 1 : 0;
+}
+
+__global__ void k_mc_classify(MaskedD M, int* lists, unsigned long long* cnt, long long* counts) {
+  const long long n = M.X.nrows;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  for (long long b0 = (long long)blockIdx.x * blockDim.x; b0 < n; b0 += stride) {
+    const long long i = b0 + threadIdx.x;
+    int c = -1;
+    if (i < n) {
+      const long long ns = M.Sp[i + 1] - M.Sp[i];
+      if (ns <= 0) counts[i] = 0;
+      else c = mc_class(ns);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const unsigned m = __ballot_sync(0xffffffffu, c == k);
+      if (m == 0u) continue;
+      const int leader = __ffs(m) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(cnt + k, (unsigned long long)__popc(m));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (c == k) lists[(long long)k * n + (long long)base + __popc(m & ((1u << lane) - 1u))] = (int)i;
+    }
+  }
+}
+
+// Warp per listed row of S whose table (2 slots per entry, a power of two)
+// holds at most SLOTS slots; rows are taken CHUNK at a time from *next.
+template <int SLOTS, int WARPS, int CHUNK>
+__global__ void __launch_bounds__(WARPS * 32) k_masked_count_warp(MaskedD M, const long long* __restrict__ Ycp,
+                                                                  const int* __restrict__ csi,
+                                                                  const unsigned* __restrict__ cs,
+                                                                  long long* __restrict__ counts,
+                                                                  const int* __restrict__ list,
+                                                                  const unsigned long long* nlist,
+                                                                  unsigned long long* next) {
   extern __shared__ __align__(16) unsigned char smem[];
   Team<32> tm;
-  int* keys = reinterpret_cast<int*>(smem) + (size_t)tm.id * 2 * kMcWarpSlots;
-  unsigned* bits = reinterpret_cast<unsigned*>(keys + kMcWarpSlots);
-  __shared__ int pre_s[4][33];
-  __shared__ long long qs_s[4][32];
+  int* keys = reinterpret_cast<int*>(smem) + (size_t)tm.id * 2 * SLOTS;
+  unsigned* bits = reinterpret_cast<unsigned*>(keys + SLOTS);
+  __shared__ int pre_s[WARPS][33];
+  __shared__ long long qs_s[WARPS][32];
   int* pre = pre_s[tm.id];
   long long* qsv = qs_s[tm.id];
-  const long long nteams = (long long)gridDim.x * tm.per_cta;
-  for (long long i = (long long)blockIdx.x * tm.per_cta + tm.id; i < M.X.nrows; i += nteams) {
-    const long long s0 = M.Sp[i], s1 = M.Sp[i + 1];
-    const long long ns = s1 - s0;
-    if (ns > kMcWarpMaxRow) continue;          // the CTA kernel takes it
-    if (ns <= 0) {
-      if (tm.lane == 0) counts[i] = 0;
-      continue;
-    }
-    int logT = 1;
-    while ((1ll << logT) < 2 * ns) ++logT;
-    const int T = 1 << logT;
-    const LpHash hs(logT, M.hash_mode);
-    for (int x = tm.lane; x < T; x += 32) {
-      keys[x] = kEmpty;
-      bits[x] = 0u;
-    }
-    __syncwarp();
-    int fresh = 0;
-    for (long long p = s0 + tm.lane; p < s1; p += 32) {
-      const int l = M.Sj[p];
-      if ((unsigned long long)(unsigned)l >= (unsigned long long)M.Y.ncols) {
-        dev_fail(M.status, kDevBadIndex, 52, i);
+  const unsigned long long nrows = *nlist;
+  for (;;) {
+    unsigned long long base = 0;
+    if (tm.lane == 0) base = atomicAdd(next, (unsigned long long)CHUNK);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= nrows) break;
+    const unsigned long long end = base + CHUNK < nrows ? base + CHUNK : nrows;
+    for (unsigned long long r = base; r < end; ++r) {
+      const long long i = list[r];
+      const long long s0 = M.Sp[i], s1 = M.Sp[i + 1];
+      const long long ns = s1 - s0;
+      int logT = 1;
+      while ((1ll << logT) < 2 * ns) ++logT;
+      const int T = 1 << logT;
+      if (T > SLOTS) {   // not this class: a malformed list
+        if (tm.lane == 0) dev_fail(M.status, kDevTableFull, 57, i);
         continue;
       }
-      const int slot = slot_insert<1>(keys, hs, l >> 5, &fresh);
-      if (slot >= 0) atomicOr(bits + slot, 1u << (l & 31));
-      else dev_fail(M.status, kDevTableFull, 53, i);
-    }
-    __syncwarp();
-    long long cnt = 0;
-    const long long a0 = rp_at(M.X, i), a1 = rp_at(M.X, i + 1);
-    for (long long c = a0; c < a1; c += 32) {
-      const long long p = c + tm.lane;
-      long long q0 = 0;
-      int ql = 0;
-      if (p < a1) {
-        const int j = M.X.cj[p];
-        if ((unsigned long long)(unsigned)j < (unsigned long long)M.Y.nrows) {
-          q0 = Ycp[j];
-          ql = (int)(Ycp[j + 1] - q0);
-        } else {
-          dev_fail(M.status, kDevBadIndex, 54, i);
-        }
-      }
-      int ex = ql;
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, ex, d);
-        if (tm.lane >= d) ex += y;
-      }
-      const int tot = __shfl_sync(0xffffffffu, ex, 31);
-      pre[tm.lane] = ex - ql;
-      qsv[tm.lane] = q0;
-      if (tm.lane == 0) pre[32] = tot;
-      __syncwarp();
-      int t = 0;
-      for (int xb = 0; xb < tot; xb += 4 * 32) {
-        int key[4];
-        unsigned m[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int x = xb + u * 32 + tm.lane;
-          key[u] = -1;
-          m[u] = 0u;
-          if (x < tot) {
-            while (pre[t + 1] <= x) ++t;
-            const long long q = qsv[t] + (x - pre[t]);
-            key[u] = csi[q];
-            m[u] = cs[q];
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          if (key[u] >= 0) {
-            const int slot = key_slot(keys, hs, key[u]);
-            if (slot >= 0) cnt += __popc(m[u] & bits[slot]);
-          }
-        }
+      const LpHash hs(logT, M.hash_mode);
+      for (int x = tm.lane; x < T; x += 32) {
+        keys[x] = kEmpty;
+        bits[x] = 0u;
       }
       __syncwarp();
-    }
+      int fresh = 0;
+      for (long long p = s0 + tm.lane; p < s1; p += 32) {
+        const int l = M.Sj[p];
+        if ((unsigned long long)(unsigned)l >= (unsigned long long)M.Y.ncols) {
+          dev_fail(M.status, kDevBadIndex, 52, i);
+          continue;
+        }
+        const int slot = slot_insert<1>(keys, hs, l >> 5, &fresh);
+        if (slot >= 0) atomicOr(bits + slot, 1u << (l & 31));
+        else dev_fail(M.status, kDevTableFull, 53, i);
+      }
+      __syncwarp();
+      long long cnt = 0;
+      const long long a0 = rp_at(M.X, i), a1 = rp_at(M.X, i + 1);
+      for (long long c = a0; c < a1; c += 32) {
+        const long long p = c + tm.lane;
+        long long q0 = 0;
+        int ql = 0;
+        if (p < a1) {
+          const int j = M.X.cj[p];
+          if ((unsigned long long)(unsigned)j < (unsigned long long)M.Y.nrows) {
+            q0 = Ycp[j];
+            ql = (int)(Ycp[j + 1] - q0);
+          } else {
+            dev_fail(M.status, kDevBadIndex, 54, i);
+          }
+        }
+        int ex = ql;
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
-    if (tm.lane == 0) counts[i] = cnt;
-    __syncwarp();
+        for (int d = 1; d < 32; d <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, ex, d);
+          if (tm.lane >= d) ex += y;
+        }
+        const int tot = __shfl_sync(0xffffffffu, ex, 31);
+        pre[tm.lane] = ex - ql;
+        qsv[tm.lane] = q0;
+        if (tm.lane == 0) pre[32] = tot;
+        __syncwarp();
+        int t = 0;
+        for (int xb = 0; xb < tot; xb += 4 * 32) {
+          int key[4];
+          unsigned m[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int x = xb + u * 32 + tm.lane;
+            key[u] = -1;
+            m[u] = 0u;
+            if (x < tot) {
+              while (pre[t + 1] <= x) ++t;
+              const long long q = qsv[t] + (x - pre[t]);
+              key[u] = csi[q];
+              m[u] = cs[q];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (key[u] >= 0) {
+              const int slot = key_slot(keys, hs, key[u]);
+              if (slot >= 0) cnt += __popc(m[u] & bits[slot]);
+            }
+          }
+        }
+        __syncwarp();
+      }
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
+      if (tm.lane == 0) counts[i] = cnt;
+      __syncwarp();
+    }
   }
 }
 
@@ -853,17 +902,28 @@ __global__ void __launch_bounds__(128) k_masked_count_warp(MaskedD M, const long
 __global__ void __launch_bounds__(256) k_masked_count_cta(MaskedD M, const long long* __restrict__ Ycp,
                                                           const int* __restrict__ csi,
                                                           const unsigned* __restrict__ cs,
-                                                          long long* __restrict__ counts, long long kw) {
+                                                          long long* __restrict__ counts, long long kw,
+                                                          const int* __restrict__ list,
+                                                          const unsigned long long* nlist,
+                                                          unsigned long long* next) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long scan_scratch[33];
   __shared__ ChunkScratch<256, int> csc;
+  __shared__ long long row_s;
   Team<256> tm;
   unsigned* bm = reinterpret_cast<unsigned*>(smem);
   for (long long w = tm.lane; w < kw; w += 256) bm[w] = 0u;
-  __syncthreads();
-  for (long long i = blockIdx.x; i < M.X.nrows; i += gridDim.x) {
+  const unsigned long long nrows = *nlist;
+  for (;;) {
+    if (tm.lane == 0) {
+      const unsigned long long r = atomicAdd(next, 1ull);
+      row_s = r < nrows ? (long long)list[r] : -1;
+    }
+    __syncthreads();
+    const long long i = row_s;
+    __syncthreads();
+    if (i < 0) break;
     const long long s0 = M.Sp[i], s1 = M.Sp[i + 1];
-    if (s1 - s0 <= kMcWarpMaxRow) continue;
     for (long long p = s0 + tm.lane; p < s1; p += 256) {
       const int l = M.Sj[p];
       if ((unsigned long long)(unsigned)l < (unsigned long long)M.Y.ncols) atomicOr(bm + (l >> 5), 1u << (l & 31));
@@ -1154,28 +1214,47 @@ cudaError_t launch_row_len_max(const LaunchCtx& L, const long long* Sp, long lon
 }
 
 cudaError_t launch_masked_count(const LaunchCtx& L, const MaskedD& M, const long long* Ycp, const int* csi,
-                                const unsigned* cs, long long* counts, bool has_big_rows) {
-  if (M.X.nrows <= 0) return cudaSuccess;
+                                const unsigned* cs, long long* counts, long long max_row, int* lists,
+                                unsigned long long* ctr) {
+  const long long n = M.X.nrows;
+  if (n <= 0) return cudaSuccess;
+  // ctr: [0..2] class list lengths, [3..5] the classes' fetch counters
+  cudaError_t e = cudaMemsetAsync(ctr, 0, 6 * sizeof(unsigned long long), L.stream);
+  if (e != cudaSuccess) return e;
+  KKS_LAUNCHED();
+  k_mc_classify<<<grid_cap(n, 256, L.num_sms, 8), 256, 0, L.stream>>>(M, lists, ctr, counts);
   {
-    auto kern = k_masked_count_warp;
-    const size_t smem = (size_t)4 * 2 * kMcWarpSlots * 4;
-    cudaError_t e = set_smem(kern, smem);
+    auto kern = k_masked_count_warp<kMcSmallSlots, 8, 8>;
+    const size_t smem = (size_t)8 * 2 * kMcSmallSlots * 4;
+    e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
     KKS_LAUNCHED();
-    kern<<<resident_grid(kern, 128, smem, L.num_sms, (M.X.nrows + 3) / 4), 128, smem, L.stream>>>(M, Ycp, csi, cs,
-                                                                                                  counts);
+    kern<<<resident_grid(kern, 256, smem, L.num_sms, (n + 7) / 8), 256, smem, L.stream>>>(
+        M, Ycp, csi, cs, counts, lists, ctr + 0, ctr + 3);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  if (has_big_rows) {
+  if (max_row > kMcSmallSlots / 2) {
+    auto kern = k_masked_count_warp<kMcWarpSlots, 4, 1>;
+    const size_t smem = (size_t)4 * 2 * kMcWarpSlots * 4;
+    e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    KKS_LAUNCHED();
+    kern<<<resident_grid(kern, 128, smem, L.num_sms, (n + 3) / 4), 128, smem, L.stream>>>(
+        M, Ycp, csi, cs, counts, lists + n, ctr + 1, ctr + 4);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (max_row > kMcWarpMaxRow) {
     const long long kw = (M.Y.ncols + 31) >> 5;
     const size_t smem = (size_t)kw * 4;
     if (smem + 16 * 1024 > (size_t)L.max_smem_optin) return cudaErrorInvalidConfiguration;
     auto kern = k_masked_count_cta;
-    cudaError_t e = set_smem(kern, smem);
+    e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
     KKS_LAUNCHED();
-    kern<<<resident_grid(kern, 256, smem, L.num_sms, M.X.nrows), 256, smem, L.stream>>>(M, Ycp, csi, cs, counts, kw);
+    kern<<<resident_grid(kern, 256, smem, L.num_sms, n), 256, smem, L.stream>>>(M, Ycp, csi, cs, counts, kw,
+                                                                              lists + 2 * n, ctr + 2, ctr + 5);
     return cudaGetLastError();
   }
   return cudaSuccess;
