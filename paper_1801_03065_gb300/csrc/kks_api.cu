@@ -40,7 +40,7 @@ enum BufId {
   kBufNumPool2, kBufNumPool3, kBufStatus, kBufMaskRows, kBufMaskHist, kBufMaskPool, kBufTrTmp,
   kBufTrPool, kBufReuseRows, kBufReusePool, kBufBinCnt, kBufBinOfs, kBufMcCnt, kBufMcYcp, kBufMcCsi, kBufMcCs,
   kBufMcMax, kBufRapRf, kBufRapRtp, kBufRapRti, kBufRapRpe, kBufRapW, kBufRapCnt, kBufRapSymRows,
-  kBufRapNumRows, kBufRapMeta, kBufRapTmp, kBufMcRows, kNumBufs
+  kBufRapNumRows, kBufRapMeta, kBufRapTmp, kBufMcRows, kBufFetch, kNumBufs
 };
 
 // Row bins of a masked product, cached for numeric reuse on one pattern.
@@ -525,6 +525,7 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
   KKS_ST(ensure(h, kBufSymRows, sizeof(int) * (totalA + 1)));
   KKS_ST(ensure(h, kBufNumRows, sizeof(int) * (totalA + 1)));
   KKS_ST(ensure(h, kBufStatus, sizeof(DevStatus)));
+  KKS_ST(ensure(h, kBufFetch, 16));
   KKS_ST(ensure(h, kBufCsi, 16));
   KKS_ST(ensure(h, kBufCs, 16));
 
@@ -660,6 +661,7 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
     S.nrows = cnt;
     S.compressed = comp;
     S.max_occ = h->opt.l1_max_occupancy;
+    S.fetch = B<unsigned long long>(h, kBufFetch);
     long long kmax = 0;
     for (int b = 0; b < count; ++b) kmax = std::max<long long>(kmax, h->inst[b].k);
     // dense rows only come from products whose bitmap fits (checked per row)
@@ -819,6 +821,7 @@ cudaError_t launch_bin(kks_handle* h, const BinRun& r, cudaStream_t s) {
   S.max_occ = h->opt.l1_max_occupancy;
   S.positions = (r.compressed && (r.cls == kClsW8 || r.cls == kClsW32)) ? 1 : 0;
   S.b_sorted = h->b_sorted ? 1 : 0;
+  S.fetch = B<unsigned long long>(h, kBufFetch);
   if (r.cls == kClsDense) {
     S.kwords_max = h->num_dense_kw;
   } else if (r.cls == kClsSpill) {

@@ -497,6 +497,17 @@ __device__ __forceinline__ void prefetch_l1(const void* p) {
   asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
+// Rows of a bin for CTA teams, taken one at a time from a counter zeroed
+// before the launch, so that a few heavy rows (skewed graphs) do not leave the
+// CTAs that drew them by a fixed stride running long after the others.  Every
+// call is a barrier of the CTA; the first call gives its first row.
+__device__ __forceinline__ long long cta_next_row(unsigned long long* fetch, long long* slot) {
+  __syncthreads();
+  if (threadIdx.x == 0) *slot = (long long)atomicAdd(fetch, 1ull);
+  __syncthreads();
+  return *slot;
+}
+
 // Exclusive max-scan over a CTA team (int values, -1 before the first thread).
 template <int TW>
 __device__ __forceinline__ int team_excl_max(const Team<TW>& tm, int v, long long* scratch) {

@@ -205,6 +205,7 @@ struct SymLaunch {
   void* l2_pool;         // spill: global pool
   long long l2_chunk_slots;
   int nchunks;
+  unsigned long long* fetch;   // CTA classes: row counter (zeroed by the launcher)
 };
 cudaError_t launch_symbolic(const LaunchCtx&, const ProbD&, const SymLaunch&, long long* rowsize);
 
@@ -225,6 +226,7 @@ struct NumLaunch {
   int nchunks;
   int positions;         // warp classes: compressed-position kernel (every product's B compressed)
   int b_sorted;          // dense class: every B row has increasing columns
+  unsigned long long* fetch;   // CTA classes: row counter (zeroed by the launcher)
 };
 cudaError_t launch_numeric(const LaunchCtx&, const ProbD&, const NumLaunch&);
 

@@ -43,10 +43,12 @@ __host__ __device__ size_t num_cta_bytes(int T, long long kw_cap) {
 }
 
 template <int TW, typename VT>
-__global__ void k_num_hash(ProbD P, const int* __restrict__ rows, long long nrows, int logT, long long kw_cap) {
+__global__ void k_num_hash(ProbD P, const int* __restrict__ rows, long long nrows, int logT, long long kw_cap,
+                           unsigned long long* fetch) {
   static_assert(TW > 32, "CTA teams only");
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long scan_scratch[33];
+  __shared__ long long fetch_s;
   Team<TW> tm;
   const int T = 1 << logT;
   const LpHash tmask(logT, P.hash_mode);
@@ -62,9 +64,7 @@ __global__ void k_num_hash(ProbD P, const int* __restrict__ rows, long long nrow
   unsigned* bm = reinterpret_cast<unsigned*>(tail);                          // kw_cap > 0
   unsigned short* gp = reinterpret_cast<unsigned short*>(bm + ((kw_cap + 3) & ~3ll));
 
-  const long long team = (long long)blockIdx.x * tm.per_cta + tm.id;
-  const long long nteams = (long long)gridDim.x * tm.per_cta;
-  for (long long r = team; r < nrows; r += nteams) {
+  for (long long r = cta_next_row(fetch, &fetch_s); r < nrows; r = cta_next_row(fetch, &fetch_s)) {
     const long long g = rows[r];
     const int b = inst_of(P.arow0s, P.ninst, g);
     const InstD& I = P.inst[b];
@@ -765,9 +765,10 @@ __host__ __device__ size_t dense_win_bytes(int win_log2) {
 
 template <int TW, typename VT>
 __global__ void __launch_bounds__(TW) k_num_dense(ProbD P, const int* __restrict__ rows, long long nrows,
-                                                  int win_log2, int sorted_b) {
+                                                  int win_log2, int sorted_b, unsigned long long* fetch) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long scan_scratch[33];
+  __shared__ long long fetch_s;
   Team<TW> tm;
   const long long W = 1ll << win_log2;
   const long long ww = W / 32;
@@ -777,8 +778,7 @@ __global__ void __launch_bounds__(TW) k_num_dense(ProbD P, const int* __restrict
       reinterpret_cast<ChunkScratch<TW, VT>*>(smem + al16((size_t)W * sizeof(VT)) + al16((size_t)ww * 4));
   for (long long x = tm.lane; x < W; x += TW) acc[x] = VT(0);
   for (long long x = tm.lane; x < ww; x += TW) bm[x] = 0u;
-  __syncthreads();
-  for (long long r = blockIdx.x; r < nrows; r += gridDim.x) {
+  for (long long r = cta_next_row(fetch, &fetch_s); r < nrows; r = cta_next_row(fetch, &fetch_s)) {
     const long long g = rows[r];
     const int b = inst_of(P.arow0s, P.ninst, g);
     const InstD& I = P.inst[b];
@@ -877,8 +877,10 @@ __host__ __device__ size_t spill_l1_bytes(int T) {
 template <int TW, typename VT>
 __global__ void __launch_bounds__(TW) k_num_spill(ProbD P, const int* __restrict__ rows, long long nrows,
                                                   int l1_logT, int cap, unsigned char* pool, long long l2_slots,
-                                                  long long chunk_bytes, unsigned* pool2, long long kw_max) {
+                                                  long long chunk_bytes, unsigned* pool2, long long kw_max,
+                                                  unsigned long long* fetch) {
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long fetch_s;
   __shared__ long long scan_scratch[33];
   Team<TW> tm;
   const int T = 1 << l1_logT;
@@ -894,7 +896,7 @@ __global__ void __launch_bounds__(TW) k_num_spill(ProbD P, const int* __restrict
   unsigned* bm = pool2 + (long long)blockIdx.x * 2 * kw_max;
   unsigned* pre = bm + kw_max;
 
-  for (long long r = blockIdx.x; r < nrows; r += gridDim.x) {
+  for (long long r = cta_next_row(fetch, &fetch_s); r < nrows; r = cta_next_row(fetch, &fetch_s)) {
     const long long g = rows[r];
     const int b = inst_of(P.arow0s, P.ninst, g);
     const InstD& I = P.inst[b];
@@ -1033,8 +1035,10 @@ cudaError_t run_hash(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   const unsigned grid = resident_grid(kern, TW, smem, L.num_sms, S.nrows);
+  e = cudaMemsetAsync(S.fetch, 0, sizeof(unsigned long long), L.stream);
+  if (e != cudaSuccess) return e;
   KKS_LAUNCHED();
-  kern<<<grid, TW, smem, L.stream>>>(P, S.rows, S.nrows, S.logT, kw_cap);
+  kern<<<grid, TW, smem, L.stream>>>(P, S.rows, S.nrows, S.logT, kw_cap, S.fetch);
   return cudaGetLastError();
 }
 
@@ -1089,8 +1093,10 @@ cudaError_t run_dense(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   const unsigned grid = resident_grid(kern, TW, smem, L.num_sms, S.nrows);
+  e = cudaMemsetAsync(S.fetch, 0, sizeof(unsigned long long), L.stream);
+  if (e != cudaSuccess) return e;
   KKS_LAUNCHED();
-  kern<<<grid, TW, smem, L.stream>>>(P, S.rows, S.nrows, wl, S.b_sorted);
+  kern<<<grid, TW, smem, L.stream>>>(P, S.rows, S.nrows, wl, S.b_sorted, S.fetch);
   return cudaGetLastError();
 }
 
@@ -1109,9 +1115,11 @@ cudaError_t run_spill(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
   long long grid = S.nchunks;
   if (grid > S.nrows) grid = S.nrows;
   const long long l2_slots = 1ll << S.logT;
+  e = cudaMemsetAsync(S.fetch, 0, sizeof(unsigned long long), L.stream);
+  if (e != cudaSuccess) return e;
   KKS_LAUNCHED();
   kern<<<(unsigned)grid, TW, smem, L.stream>>>(P, S.rows, S.nrows, S.l1_logT, cap, (unsigned char*)S.pool, l2_slots,
-                                               S.chunk_bytes, (unsigned*)S.pool2, S.kwords_max);
+                                               S.chunk_bytes, (unsigned*)S.pool2, S.kwords_max, S.fetch);
   return cudaGetLastError();
 }
 

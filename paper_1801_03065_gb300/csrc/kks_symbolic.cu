@@ -31,9 +31,11 @@ __host__ __device__ size_t sym_team_bytes(int T) {
 
 template <int TW, bool COMP, bool SPILL>
 __global__ void k_sym_hash(ProbD P, const int* __restrict__ rows, long long nrows, int logT, int cap,
-                           int* l2_pool, long long l2_slots, long long* __restrict__ rowsize) {
+                           int* l2_pool, long long l2_slots, long long* __restrict__ rowsize,
+                           unsigned long long* fetch) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long scan_scratch[33];
+  __shared__ long long fetch_s;
   Team<TW> tm;
   const int T = 1 << logT;
   const LpHash tmask(logT, P.hash_mode);
@@ -54,7 +56,10 @@ __global__ void k_sym_hash(ProbD P, const int* __restrict__ rows, long long nrow
     m2 = reinterpret_cast<unsigned*>(k2 + l2_slots);
   }
 
-  for (long long r = team; r < nrows; r += nteams) {
+  // CTA teams take their rows from the counter, warp teams by a fixed stride
+  constexpr bool kFetch = Team<TW>::kCta;
+  for (long long r = kFetch ? cta_next_row(fetch, &fetch_s) : team; r < nrows;
+       r = kFetch ? cta_next_row(fetch, &fetch_s) : r + nteams) {
     const long long g = rows[r];
     const int b = inst_of(P.arow0s, P.ninst, g);
     const InstD& I = P.inst[b];
@@ -283,15 +288,16 @@ __global__ void __launch_bounds__(kSymThreads) k_sym_thread(ProbD P, const int* 
 
 template <int TW, bool COMP>
 __global__ void __launch_bounds__(TW) k_sym_dense(ProbD P, const int* __restrict__ rows, long long nrows,
-                                                  long long kw_max, long long* __restrict__ rowsize) {
+                                                  long long kw_max, long long* __restrict__ rowsize,
+                                                  unsigned long long* fetch) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long scan_scratch[33];
+  __shared__ long long fetch_s;
   Team<TW> tm;
   unsigned* bm = reinterpret_cast<unsigned*>(smem);
   ChunkScratch<TW, int>* csc = reinterpret_cast<ChunkScratch<TW, int>*>(smem + al16((size_t)kw_max * 4));
   for (long long w = tm.lane; w < kw_max; w += TW) bm[w] = 0u;
-  __syncthreads();
-  for (long long r = blockIdx.x; r < nrows; r += gridDim.x) {
+  for (long long r = cta_next_row(fetch, &fetch_s); r < nrows; r = cta_next_row(fetch, &fetch_s)) {
     const long long g = rows[r];
     const int b = inst_of(P.arow0s, P.ninst, g);
     const InstD& I = P.inst[b];
@@ -365,9 +371,11 @@ cudaError_t run_hash(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, lon
   auto kern = k_sym_hash<TW, COMP, false>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(S.fetch, 0, sizeof(unsigned long long), L.stream);
+  if (e != cudaSuccess) return e;
   KKS_LAUNCHED();
   kern<<<resident_grid(kern, TW * teams, smem, L.num_sms, (S.nrows + teams - 1) / teams), TW * teams, smem,
-         L.stream>>>(P, S.rows, S.nrows, S.logT, -1, nullptr, 0, rowsize);
+         L.stream>>>(P, S.rows, S.nrows, S.logT, -1, nullptr, 0, rowsize, S.fetch);
   return cudaGetLastError();
 }
 
@@ -413,9 +421,11 @@ cudaError_t run_spill(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, lo
   if (cap > T - 1) cap = T - 1;
   int grid = S.nchunks;
   if (grid > S.nrows) grid = (int)S.nrows;
+  e = cudaMemsetAsync(S.fetch, 0, sizeof(unsigned long long), L.stream);
+  if (e != cudaSuccess) return e;
   KKS_LAUNCHED();
   kern<<<grid, TW, smem, L.stream>>>(P, S.rows, S.nrows, S.l1_logT, cap, (int*)S.l2_pool, S.l2_chunk_slots,
-                                     rowsize);
+                                     rowsize, S.fetch);
   return cudaGetLastError();
 }
 
@@ -432,8 +442,10 @@ cudaError_t run_dense(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, lo
   if (per_sm > 4) per_sm = 4;
   long long grid = (long long)L.num_sms * per_sm;
   if (grid > S.nrows) grid = S.nrows;
+  e = cudaMemsetAsync(S.fetch, 0, sizeof(unsigned long long), L.stream);
+  if (e != cudaSuccess) return e;
   KKS_LAUNCHED();
-  kern<<<(unsigned)grid, TW, smem, L.stream>>>(P, S.rows, S.nrows, S.kwords_max, rowsize);
+  kern<<<(unsigned)grid, TW, smem, L.stream>>>(P, S.rows, S.nrows, S.kwords_max, rowsize, S.fetch);
   return cudaGetLastError();
 }
 
