@@ -57,6 +57,8 @@ def parse_args(argv=None):
     p.add_argument("--repeats", type=int, default=20, help="batched512: numeric-reuse repeats")
     p.add_argument("--numeric-only", action="store_true",
                    help="profiling aid: one symbolic and two numeric calls of A*A on --grid, no timing")
+    p.add_argument("--serial", action="store_true",
+                   help="stencil27_100: run the one-plan triple product after A*A on one stream")
     p.add_argument("--rap", choices=["fused", "two"], default="fused",
                    help="stencil27_100: the triple product in one plan, or as transpose + two products")
     p.add_argument("--numeric-positions", type=int, default=1, choices=(0, 1),
@@ -159,9 +161,12 @@ class StencilStep:
     """Device buffers and library handles of one step (NoReuse A·A and Pᵀ·A·P).
 
     rap="fused": the triple product in one plan (spgemm_rap_symbolic / _numeric);
-    rap="two": Pᵀ by transpose, then A·P and Pᵀ·(A·P) as two products."""
+    rap="two": Pᵀ by transpose, then A·P and Pᵀ·(A·P) as two products.
+    concurrent: the one-plan triple product runs on a second stream, issued from
+    a worker thread, while A·A runs on the current stream (the two products are
+    independent); the step ends when both have."""
 
-    def __init__(self, A, P, device, positions=True, rap="fused"):
+    def __init__(self, A, P, device, positions=True, rap="fused", concurrent=True):
         import torch
         from paper_1801_03065_gb300 import ops
         self.torch, self.ops = torch, ops
@@ -175,6 +180,12 @@ class StencilStep:
                                          ops.SpGEMM(numeric_positions=pos))
         self.hT = ops.SpGEMM()
         self._fm_two = None
+        self.concurrent = bool(concurrent) and rap == "fused"
+        self.device = device
+        if self.concurrent:
+            import concurrent.futures as cf
+            self.side = torch.cuda.Stream(device=device)
+            self.pool = cf.ThreadPoolExecutor(max_workers=1)
         dev = self.Ad.rowptr.device
         self.rpAA = torch.empty(A.nrows + 1, dtype=torch.int64, device=dev)
         self.rpAP = torch.empty(A.nrows + 1, dtype=torch.int64, device=dev)
@@ -189,16 +200,35 @@ class StencilStep:
                                       t.empty(nnz, dtype=dtype, device=rp.device), (0, 0))
         return C
 
+    def _rap(self, stream=None):
+        Ad, Pd = self.Ad, self.Pd
+        rp, nnz = self.hRAP.rap_symbolic(Ad, Pd, C_rowptr=self.rpRAP, stream=stream)
+        self.CRAP = self._out(self.CRAP, rp, nnz, self.torch.float64)
+        self.hRAP.rap_numeric(Ad, Pd, rp, nnz, self.CRAP.colidx, self.CRAP.values, stream=stream)
+
+    def _rap_worker(self):
+        self.torch.cuda.set_device(self.device)
+        self._rap(self.side)
+
     def step(self):
         t = self.torch
         Ad, Pd = self.Ad, self.Pd
+        fut = None
+        if self.concurrent:
+            cur = t.cuda.current_stream()
+            fork = t.cuda.Event()
+            fork.record(cur)
+            self.side.wait_event(fork)
+            fut = self.pool.submit(self._rap_worker)
         rp, nnz = self.hAA.symbolic(Ad, Ad, C_rowptr=self.rpAA)
         self.CAA = self._out(self.CAA, rp, nnz, t.float64)
         self.hAA.numeric(Ad, Ad, rp, nnz, self.CAA.colidx, self.CAA.values)
+        if fut is not None:
+            fut.result()
+            cur.wait_stream(self.side)
+            return
         if self.rap == "fused":
-            rp, nnz = self.hRAP.rap_symbolic(Ad, Pd, C_rowptr=self.rpRAP)
-            self.CRAP = self._out(self.CRAP, rp, nnz, t.float64)
-            self.hRAP.rap_numeric(Ad, Pd, rp, nnz, self.CRAP.colidx, self.CRAP.values)
+            self._rap()
             return
         self.Pt = self.hT.transpose(Pd, out=self.Pt)
         rp, nnz = self.hAP.symbolic(Ad, Pd, C_rowptr=self.rpAP)
@@ -230,6 +260,8 @@ class StencilStep:
         return self.hAA.stats()["f_m"] + self.two_step_flops()
 
     def close(self):
+        if self.concurrent:
+            self.pool.shutdown()
         for h in (self.hAA, self.hAP, self.hRAP, self.hT):
             h.close()
 
@@ -283,7 +315,8 @@ def run_ours(args):
 
     A = w.stencil3d_27pt(args.grid, seed=1)
     P = w.aggregation(args.grid, 3)
-    S = StencilStep(A, P, device, positions=bool(args.numeric_positions), rap=args.rap)
+    S = StencilStep(A, P, device, positions=bool(args.numeric_positions), rap=args.rap,
+                    concurrent=not args.serial)
     for _ in range(max(args.warmup, 1)):
         S.step()
     torch.cuda.synchronize()
@@ -319,7 +352,7 @@ def run_ours(args):
     # the other products of the step, one phase at a time (each on its own handle)
     Pd = S.Pd
     if S.rap == "fused":
-        T2 = StencilStep(A, P, device, positions=S.positions, rap="two")
+        T2 = StencilStep(A, P, device, positions=S.positions, rap="two", concurrent=False)
         T2.step()
         two_step = lambda: (T2.hT.transpose(Pd, out=T2.Pt),
                             T2.hAP.symbolic(Ad, Pd, C_rowptr=T2.rpAP),
@@ -368,8 +401,10 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD if args.grid == 100 else WORKLOAD.replace("100^3", "%d^3" % args.grid),
                    "global_batch": world, "flops_per_step": 2 * flops_step,
-                   "triple_product": ("one plan (spgemm_rap_symbolic / spgemm_rap_numeric); flops counted as "
-                                      "A*P and P^T*(A*P)") if S.rap == "fused" else "transpose, A*P, P^T*(A*P)",
+                   "triple_product": ("one plan (spgemm_rap_symbolic / spgemm_rap_numeric)%s; flops counted as "
+                                      "A*P and P^T*(A*P)" % (", on a second stream beside A*A" if S.concurrent
+                                                              else "")) if S.rap == "fused"
+                   else "transpose, A*P, P^T*(A*P)",
                    "l2": "inputs larger than L2 (A = %.0f MB, C = %.0f MB)" % (
                        csr_bytes(A.nrows, A.nnz, 8) / 1e6, csr_bytes(A.nrows, nnzC, 8) / 1e6),
                    "parallelism": "one independent problem per GPU (row blocks), no data-path collective"},
@@ -430,7 +465,7 @@ def run_e2e(torch, S, A, P, args, world, flops_step):
     step's C (on a copy stream) overlaps the next step's upload and kernels; the
     region ends when the last read-back has landed in host memory."""
     pin = lambda x: torch.from_numpy(x).pin_memory()
-    S2 = StencilStep(A, P, S.Ad.rowptr.device, positions=S.positions, rap=S.rap)
+    S2 = StencilStep(A, P, S.Ad.rowptr.device, positions=S.positions, rap=S.rap, concurrent=S.concurrent)
     S2.step()
     sets = [S, S2]
     hA = [pin(A.rowptr), pin(A.colidx), pin(A.values)]
