@@ -305,6 +305,29 @@ spgemm_status_t spgemm_batch_numeric(spgemm_handle_t h, int32_t count, const spg
                                      const spgemm_csr_t *B, int64_t *const *C_rowptr,
                                      int32_t *const *C_colidx, void *const *C_values, spgemm_stream_t stream);
 
+/*
+ * Row flops for partitioning: prefix[0] = 0 and prefix[i + 1] = prefix[i] + the
+ * multiplications of row i of A*B (the sum over A(i,:) of the lengths of the
+ * rows of B: f_m row by row, Section 2).  prefix: device, int64[A.nrows + 1],
+ * caller-owned.  Synchronises the stream once (for the status).  Out-of-range
+ * columns of A or malformed row pointers give SPGEMM_ERR_BAD_INDEX.
+ */
+spgemm_status_t spgemm_row_flops(spgemm_handle_t h, const spgemm_csr_t *A, const spgemm_csr_t *B,
+                                 int64_t *prefix, spgemm_stream_t stream);
+
+/*
+ * Row-range sharding of C = A*B over `parts` devices (the 1-D row partition
+ * of Section 3.1.1 applied across GPUs): bounds[0] = 0 <= bounds[1] <= ... <=
+ * bounds[parts] = m, each boundary the row nearest to an equal share of the
+ * flops in `prefix` (host memory, int64[m + 1], non-decreasing, e.g. a copy of
+ * spgemm_row_flops's output); rows are never split.  Shard p multiplies the
+ * rows [bounds[p], bounds[p + 1]) of A by the whole B on its own device, with
+ * no exchange but the shards' nnz (to place its block of C).  With no flops
+ * at all the rows are split evenly.  Host only: needs no handle and no GPU.
+ * SPGEMM_ERR_INVALID_ARG for a decreasing prefix, parts < 1 or m < 0.
+ */
+spgemm_status_t spgemm_partition_rows(const int64_t *prefix, int64_t m, int32_t parts, int64_t *bounds);
+
 /* Human-readable name of a status code (static string). */
 const char *spgemm_status_string(spgemm_status_t s);
 

@@ -72,6 +72,8 @@ SIGNATURES = {
                                         C.POINTER(_P), C.POINTER(C.c_int64), _P]),
     "spgemm_batch_numeric": (C.c_int, [_P, C.c_int32, C.POINTER(CsrT), C.POINTER(CsrT),
                                        C.POINTER(_P), C.POINTER(_P), C.POINTER(_P), _P]),
+    "spgemm_row_flops": (C.c_int, [_P, C.POINTER(CsrT), C.POINTER(CsrT), _P, _P]),
+    "spgemm_partition_rows": (C.c_int, [_P, C.c_int64, C.c_int32, _P]),
     "spgemm_status_string": (C.c_char_p, [C.c_int]),
     "spgemm_version": (C.c_int32, []),
     "spgemm_launch_count": (C.c_int64, []),

@@ -1580,6 +1580,57 @@ int32_t spgemm_version(void) { return 100; }
 
 int64_t spgemm_launch_count(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
 
+spgemm_status_t spgemm_row_flops(spgemm_handle_t h, const spgemm_csr_t* A, const spgemm_csr_t* Bm, int64_t* prefix,
+                                 spgemm_stream_t stream) {
+  if (!h || !A || !Bm || !prefix) return SPGEMM_ERR_INVALID_ARG;
+  KKS_ST(check_csr(A, false));
+  KKS_ST(check_csr(Bm, false));
+  if (A->ncols != Bm->nrows) return SPGEMM_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  KKS_CU(cudaSetDevice(h->opt.device));
+  const long long m = A->nrows;
+  KKS_ST(ensure(h, kBufStatus, sizeof(DevStatus)));
+  KKS_ST(ensure(h, kBufRf, sizeof(long long) * (m + 1)));
+  KKS_ST(ensure(h, kBufScanTmp, scan_tmp_bytes(m + 1)));
+  KKS_ST(ensure_pinned(h, sizeof(DevStatus)));
+  LaunchCtx L = ctx(h, s);
+  KKS_CU(cudaMemsetAsync(h->buf[kBufStatus], 0, sizeof(DevStatus), s));
+  KKS_CU(launch_row_flops(L, matd(A), matd(Bm), B<long long>(h, kBufRf), B<DevStatus>(h, kBufStatus)));
+  KKS_CU(launch_scan(L, B<long long>(h, kBufRf), reinterpret_cast<long long*>(prefix), m, h->buf[kBufScanTmp]));
+  DevStatus* hs = (DevStatus*)h->pinned;
+  KKS_CU(to_host(h, hs, h->buf[kBufStatus], sizeof(DevStatus), s));
+  KKS_CU(cudaStreamSynchronize(s));
+  return consume_status(h, hs, s);
+}
+
+spgemm_status_t spgemm_partition_rows(const int64_t* prefix, int64_t m, int32_t parts, int64_t* bounds) {
+  if (!prefix || !bounds || m < 0 || parts < 1) return SPGEMM_ERR_INVALID_ARG;
+  for (int64_t i = 0; i < m; ++i)
+    if (prefix[i + 1] < prefix[i]) return SPGEMM_ERR_INVALID_ARG;
+  const long double total = (long double)prefix[m];
+  bounds[0] = 0;
+  bounds[parts] = m;
+  if (total <= 0) {   // no products: equal row counts
+    for (int32_t p = 1; p < parts; ++p) bounds[p] = (int64_t)((long double)m * p / parts);
+    return SPGEMM_OK;
+  }
+  for (int32_t p = 1; p < parts; ++p) {
+    // the first row whose prefix reaches p / parts of the work (rows stay whole)
+    const long double target = total * (long double)p / (long double)parts;
+    int64_t lo = bounds[p - 1], hi = m;
+    while (lo < hi) {
+      const int64_t mid = lo + (hi - lo) / 2;
+      if ((long double)prefix[mid] < target) lo = mid + 1;
+      else hi = mid;
+    }
+    // of the two rows around the target, the boundary nearer to it
+    if (lo > bounds[p - 1] && target - (long double)prefix[lo - 1] < (long double)prefix[lo] - target) --lo;
+    bounds[p] = lo;
+  }
+  bounds[parts] = m;
+  return SPGEMM_OK;
+}
+
 }  // extern "C"
 
 

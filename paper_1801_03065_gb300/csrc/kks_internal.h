@@ -123,6 +123,8 @@ cudaError_t launch_copy_to_host(const LaunchCtx&, void* dst_mapped, const void* 
 cudaError_t launch_compress_count(const LaunchCtx&, const ProbD&, long long totalB, long long* cnt,
                                   unsigned long long* unsorted);
 cudaError_t launch_compress_fill(const LaunchCtx&, const ProbD&, long long totalB, int* csi, unsigned* cs);
+// rf[i] = multiplications of row i of A*B (one plain product, no instance table)
+cudaError_t launch_row_flops(const LaunchCtx&, const MatD& A, const MatD& B, long long* rf, DevStatus* st);
 cudaError_t launch_row_stats(const LaunchCtx&, const ProbD&, long long totalA, int use_bc,
                              long long* rf, long long* rfc, unsigned long long* inst_stats);
 // exclusive scan of in[0, n) into out[0, n], out[n] = total; tmp >= scan_tmp_bytes(n)

@@ -593,6 +593,35 @@ cudaError_t launch_compress_fill(const LaunchCtx& L, const ProbD& P, long long t
   return cudaGetLastError();
 }
 
+namespace {
+// rf[i] = sum over A(i,:) of |B(j,:)| (Algorithm 1's multiplications of row i).
+__global__ void k_row_flops(MatD A, MatD B, long long* rf, DevStatus* st) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < A.nrows; i += stride) {
+    const long long a0 = rp_at(A, i), a1 = rp_at(A, i + 1);
+    long long w = 0;
+    if (a0 < 0 || a0 > a1 || a1 > A.nnz) {
+      dev_fail(st, kDevBadIndex, 45, i);
+    } else {
+#pragma unroll 4
+      for (long long p = a0; p < a1; ++p) {
+        const int j = A.cj[p];
+        if ((unsigned long long)(unsigned)j < (unsigned long long)B.nrows) w += rp_at(B, j + 1) - rp_at(B, j);
+        else dev_fail(st, kDevBadIndex, 46, i);
+      }
+    }
+    rf[i] = w;
+  }
+}
+}  // namespace
+
+cudaError_t launch_row_flops(const LaunchCtx& L, const MatD& A, const MatD& B, long long* rf, DevStatus* st) {
+  if (A.nrows <= 0) return cudaSuccess;
+  KKS_LAUNCHED();
+  k_row_flops<<<grid_for(A.nrows, 256, L.num_sms, 16), 256, 0, L.stream>>>(A, B, rf, st);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_row_stats(const LaunchCtx& L, const ProbD& P, long long totalA, int use_bc, long long* rf,
                              long long* rfc, unsigned long long* inst_stats) {
   if (totalA <= 0) return cudaSuccess;

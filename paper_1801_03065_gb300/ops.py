@@ -219,6 +219,17 @@ class SpGEMM:
     def sync(self, stream=None):
         B.check(self._lib.spgemm_handle_sync(self._h, _stream(stream)), "spgemm_handle_sync")
 
+    def row_flops(self, A: CsrMatrix, Bm: CsrMatrix, prefix: Optional[torch.Tensor] = None,
+                  stream=None) -> torch.Tensor:
+        """Inclusive prefix of the per-row multiplications of A*B (int64 [m + 1], on A's device)."""
+        if prefix is None:
+            prefix = torch.empty(A.nrows + 1, dtype=torch.int64, device=A.rowptr.device)
+        hint = A.dtype or Bm.dtype
+        da, db = A.desc(hint), Bm.desc(hint)
+        B.check(self._lib.spgemm_row_flops(self._h, C.byref(da), C.byref(db), C.c_void_p(prefix.data_ptr()),
+                                           _stream(stream)), "spgemm_row_flops")
+        return prefix
+
     def stats(self) -> dict:
         st = B.StatsT()
         B.check(self._lib.spgemm_get_stats(self._h, C.byref(st)), "spgemm_get_stats")
@@ -313,6 +324,55 @@ class SpGEMM:
         B.check(self._lib.spgemm_batch_numeric(self._h, n, da, db, prp, pcj, pcx, _stream(stream)),
                 "spgemm_batch_numeric")
         return [CsrMatrix(r, c, v, (a.nrows, b.ncols)) for r, c, v, a, b in zip(rowptrs, colidx, values, As, Bs)]
+
+
+# -------------------------------------------------------------------- row-range sharding
+def partition_rows(prefix, parts: int) -> List[int]:
+    """Row bounds [0 = b_0 <= ... <= b_parts = m] that split the flops in
+    `prefix` (int64 [m + 1], host or device) into `parts` near-equal shares."""
+    import numpy as np
+    if isinstance(prefix, torch.Tensor):
+        prefix = prefix.detach().cpu().numpy()
+    pre = np.ascontiguousarray(prefix, dtype=np.int64)
+    bounds = np.zeros(int(parts) + 1, dtype=np.int64)
+    B.check(B.load().spgemm_partition_rows(C.c_void_p(pre.ctypes.data), int(pre.size - 1), int(parts),
+                                           C.c_void_p(bounds.ctypes.data)), "spgemm_partition_rows")
+    return [int(x) for x in bounds]
+
+
+def row_block(A: CsrMatrix, r0: int, r1: int) -> CsrMatrix:
+    """Rows [r0, r1) of A: row pointers rebased to 0, columns and values as views."""
+    ends = A.rowptr[[r0, r1]].to("cpu").tolist()
+    rp = (A.rowptr[r0:r1 + 1].to(torch.int64) - int(ends[0])).contiguous()
+    cj = A.colidx[int(ends[0]):int(ends[1])]
+    vx = None if A.values is None else A.values[int(ends[0]):int(ends[1])]
+    return CsrMatrix(rp, cj, vx, (r1 - r0, A.ncols))
+
+
+def shard_offsets(local_nnz: int, group=None) -> Tuple[int, int]:
+    """(this shard's first entry in the global C, nnz of the global C): the one
+    exchange of row-range sharding, an all-gather of the shards' nnz."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return 0, int(local_nnz)
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    dev = "cuda" if dist.get_backend(group) == "nccl" else "cpu"
+    mine = torch.tensor([int(local_nnz)], dtype=torch.int64, device=dev)
+    allv = [torch.zeros(1, dtype=torch.int64, device=dev) for _ in range(world)]
+    dist.all_gather(allv, mine, group=group)
+    counts = [int(t.item()) for t in allv]
+    return sum(counts[:rank]), sum(counts)
+
+
+def shard_multiply(h: "SpGEMM", A: CsrMatrix, Bm: CsrMatrix, rank: int, parts: int, stream=None):
+    """Row shard `rank` of `parts` of C = A*B on this device (B replicated):
+    returns (C block, its first row, its first entry in the global C, global nnz)."""
+    bounds = partition_rows(h.row_flops(A, Bm, stream=stream), parts)
+    r0, r1 = bounds[rank], bounds[rank + 1]
+    Cb = h.multiply(row_block(A, r0, r1), Bm, stream=stream)
+    off, total = shard_offsets(Cb.nnz)
+    return Cb, r0, off, total
 
 
 def launch_count() -> int:
