@@ -100,7 +100,11 @@ typedef struct {
                                     accumulator; masked products and numeric reuse whose pattern rows
                                     are all sorted key their warp-team tables by the pattern's column
                                     sets.  0: hash-and-sort numeric, column-keyed masked tables */
-  int32_t reserved[2];
+  int32_t cta_partition;         /* numeric rows of the CTA hash classes (Section 3.1.1): 0 (default)
+                                    Thread-Flat-Parallel, 1 Team-Sequential with the linked-list
+                                    accumulator (Section 3.1.2), 2 Thread-Parallel; with tune = 1 the
+                                    tuner also times the other two per bin */
+  int32_t reserved;
 } spgemm_options_t;
 
 /* Statistics of the last symbolic call (Section 4 results-table columns). */

@@ -89,6 +89,7 @@ struct BinRun {
   int cls, logT, compressed;
   long long off, count;
   int hash;   // LpHash mode used for this bin (the tuner may change it)
+  int part = 0;   // CTA hash classes: partitioning scheme (0 flat, 1 Team-Sequential + LL, 2 Thread-Parallel)
 };
 
 constexpr int kRing = 8;
@@ -413,6 +414,7 @@ void set_default_options(spgemm_options_t* o) {
   o->hash_function = 1;
   o->verbose = 0;
   o->numeric_positions = 1;
+  o->cta_partition = 0;
 }
 
 // Upload the instance table through a pinned ring slot (numeric path).
@@ -735,7 +737,8 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
     // warp-class rows of a plan whose products all run on the compressed B
     // take their output positions from the column sets
     const int pos = (positions_ok && (cls == kClsW8 || cls == kClsW32)) ? 1 : 0;
-    h->num_bins.push_back(BinRun{cls, bin_logT(t), pos, noff[t], cnt, h->opt.hash_function});
+    h->num_bins.push_back(BinRun{cls, bin_logT(t), pos, noff[t], cnt, h->opt.hash_function,
+                                 (cls == kClsC256 || cls == kClsC1024) ? h->opt.cta_partition : 0});
     if (cls == kClsSpill) {
       spill_rows += cnt;
       spill_logT = std::max(spill_logT, bin_logT(t));
@@ -822,6 +825,7 @@ cudaError_t launch_bin(kks_handle* h, const BinRun& r, cudaStream_t s) {
   S.positions = (r.compressed && (r.cls == kClsW8 || r.cls == kClsW32)) ? 1 : 0;
   S.b_sorted = h->b_sorted ? 1 : 0;
   S.fetch = B<unsigned long long>(h, kBufFetch);
+  S.part = (r.cls == kClsC256 || r.cls == kClsC1024) ? r.part : 0;
   if (r.cls == kClsDense) {
     S.kwords_max = h->num_dense_kw;
   } else if (r.cls == kClsSpill) {
@@ -859,7 +863,9 @@ spgemm_status_t tune_numeric(kks_handle* h, cudaStream_t s) {
         BinRun p = te.pick;
         p.off = r.off;
         p.count = r.count;
-        if (p.cls != r.cls || p.logT != r.logT || p.hash != r.hash || p.compressed != r.compressed) ++changed;
+        if (p.cls != r.cls || p.logT != r.logT || p.hash != r.hash || p.compressed != r.compressed ||
+            p.part != r.part)
+          ++changed;
         r = p;
         cached = true;
         break;
@@ -876,6 +882,15 @@ spgemm_status_t tune_numeric(kks_handle* h, cudaStream_t s) {
       x = r;
       x.compressed = 1 - r.compressed;   // column-set positions against the hash-and-sort kernel
       cand.push_back(x);
+    }
+    if (r.cls == kClsC256 || r.cls == kClsC1024) {
+      // the other partitioning schemes of Section 3.1.1
+      for (int part = 0; part <= 2; ++part) {
+        if (part == r.part) continue;
+        x = r;
+        x.part = part;
+        cand.push_back(x);
+      }
     }
     auto max_logT = [&](int cls) {
       return cls == kClsW8 ? 5 : cls == kClsW32 ? 10 : cls == kClsC256 ? std::min(12, cta_max) : cta_max;
@@ -917,7 +932,9 @@ spgemm_status_t tune_numeric(kks_handle* h, cudaStream_t s) {
         pick = cd;
       }
     }
-    if (pick.cls != r.cls || pick.logT != r.logT || pick.hash != r.hash || pick.compressed != r.compressed) ++changed;
+    if (pick.cls != r.cls || pick.logT != r.logT || pick.hash != r.hash || pick.compressed != r.compressed ||
+        pick.part != r.part)
+      ++changed;
     r = pick;
     h->tune_cache.push_back({cls0, logT0, h->dtype, pos0, r.count, pick});
   }
@@ -1127,6 +1144,7 @@ spgemm_status_t spgemm_handle_create(spgemm_handle_t* out, const spgemm_options_
   if (!(h->opt.l1_max_occupancy > 0.0 && h->opt.l1_max_occupancy <= 1.0) || h->opt.compress_threshold < 0.0 ||
       h->opt.compression < -1 || h->opt.compression > 1 || h->opt.hash_function < 0 || h->opt.hash_function > 1 ||
       h->opt.slots_per_key_log2 < 0 || h->opt.slots_per_key_log2 > 4 || h->opt.numeric_positions < 0 ||
+      h->opt.cta_partition < 0 || h->opt.cta_partition > 2 ||
       h->opt.numeric_positions > 1) {
     delete h;
     return SPGEMM_ERR_INVALID_ARG;

@@ -229,6 +229,9 @@ struct NumLaunch {
   int positions;         // warp classes: compressed-position kernel (every product's B compressed)
   int b_sorted;          // dense class: every B row has increasing columns
   unsigned long long* fetch;   // CTA classes: row counter (zeroed by the launcher)
+  int part;              // CTA hash classes: 0 flat (Thread-Flat-Parallel), 1 Team-Sequential + LL,
+                         // 2 Thread-Parallel (Section 3.1.1)
+  int pad;
 };
 cudaError_t launch_numeric(const LaunchCtx&, const ProbD&, const NumLaunch&);
 

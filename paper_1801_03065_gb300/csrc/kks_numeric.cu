@@ -166,6 +166,165 @@ __global__ void k_num_hash(ProbD P, const int* __restrict__ rows, long long nrow
 }
 
 // ---------------------------------------------------------------------------
+// The other partitioning schemes of Section 3.1.1 for CTA rows, offered to the
+// autotuner beside the flat kernel above (Thread-Flat-Parallel):
+//  kPartTeamSeq, Team-Sequential with the linked-list accumulator (LL) of
+//    Section 3.1.2: the whole CTA takes the entries of A(i,:) one at a time
+//    and spreads B(j,:) over its threads, so the keys of a pass are distinct.
+//    A key is looked up by walking its bucket's list and its value updated
+//    without atomics; a new key takes the next node (an atomic counter) and
+//    is pushed at the head of its list with a compare-and-swap.  Nodes fill
+//    0, 1, ... in order, so the row's keys are compact for the sort.
+//  kPartThreadPar, Thread-Parallel: each warp takes its own entries of A(i,:)
+//    and its lanes share B(j,:); the warps insert into the LP table together,
+//    values with atomic adds.
+// The LP table has 2^logT slots; LL has 2^logT / 2 nodes and as many buckets
+// (a row of the bin has at most 2^logT / 2 columns).
+// ---------------------------------------------------------------------------
+constexpr int kPartTeamSeq = 1;
+constexpr int kPartThreadPar = 2;
+
+template <int TW, typename VT>
+__host__ __device__ size_t part_cta_bytes(int T) {
+  const size_t half = T / 2 > 0 ? (size_t)(T / 2) : 1;
+  const size_t lp = al16((size_t)T * sizeof(VT)) + al16((size_t)T * 4);
+  const size_t ll = al16(half * 4) * 3 + al16(half * sizeof(VT));
+  return (lp > ll ? lp : ll) + al16(half * 8) + 16;
+}
+
+template <int TW, typename VT, int MODE>
+__global__ void __launch_bounds__(TW) k_num_part(ProbD P, const int* __restrict__ rows, long long nrows, int logT,
+                                                 unsigned long long* fetch) {
+  static_assert(TW > 32, "CTA teams only");
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long scan_scratch[33];
+  __shared__ long long fetch_s;
+  Team<TW> tm;
+  const int T = 1 << logT;
+  const int half = T / 2 > 0 ? T / 2 : 1;
+  const size_t lp = al16((size_t)T * sizeof(VT)) + al16((size_t)T * 4);
+  const size_t llb = al16((size_t)half * 4) * 3 + al16((size_t)half * sizeof(VT));
+  unsigned long long* sortb = reinterpret_cast<unsigned long long*>(smem + (lp > llb ? lp : llb));
+  int* counter = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(sortb) + al16((size_t)half * 8));
+  // LP layout
+  VT* lvals = reinterpret_cast<VT*>(smem);
+  int* lkeys = reinterpret_cast<int*>(smem + al16((size_t)T * sizeof(VT)));
+  // LL layout
+  int* begins = reinterpret_cast<int*>(smem);
+  int* ids = reinterpret_cast<int*>(smem + al16((size_t)half * 4));
+  int* nexts = reinterpret_cast<int*>(smem + 2 * al16((size_t)half * 4));
+  VT* nvals = reinterpret_cast<VT*>(smem + 3 * al16((size_t)half * 4));
+  const int lane32 = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int kWarps = TW / 32;
+
+  for (long long r = cta_next_row(fetch, &fetch_s); r < nrows; r = cta_next_row(fetch, &fetch_s)) {
+    const long long g = rows[r];
+    const int b = inst_of(P.arow0s, P.ninst, g);
+    const InstD& I = P.inst[b];
+    const long long i = g - I.arow0;
+    const long long c0 = I.Crp[i];
+    const long long s = I.Crp[i + 1] - c0;
+    const long long a0 = rp_at(I.A, i), a1 = rp_at(I.A, i + 1);
+    const VT* __restrict__ Ax = reinterpret_cast<const VT*>(I.A.vx);
+    const VT* __restrict__ Bx = reinterpret_cast<const VT*>(I.B.vx);
+    const int* __restrict__ Bj = I.B.cj;
+    const int* __restrict__ Aj = I.A.cj;
+    long long cnt = 0;
+    if (MODE == kPartTeamSeq) {
+      for (int x = tm.lane; x < half; x += TW) begins[x] = -1;
+      if (tm.lane == 0) *counter = 0;
+      const LpHash hb(ilog2_ceil(half), P.hash_mode);
+      tm.sync();
+      for (long long p = a0; p < a1; ++p) {
+        const int j = Aj[p];
+        const VT a = Ax[p];
+        const long long bs = rp_at(I.B, j), be = rp_at(I.B, j + 1);
+        for (long long q = bs + tm.lane; q < be; q += TW) {
+          const int key = Bj[q];
+          const VT v = a * Bx[q];
+          const unsigned h = hb(key);
+          int e = *((volatile int*)(begins + h));
+          bool found = false;
+          for (int steps = 0; e >= 0 && steps < half; ++steps) {
+            if (*((volatile int*)(ids + e)) == key) {
+              nvals[e] += v;   // the keys of a pass are distinct: no other thread holds this node
+              found = true;
+              break;
+            }
+            e = *((volatile int*)(nexts + e));
+          }
+          if (found) continue;
+          const int slot = atomicAdd(counter, 1);
+          if (slot >= half) {
+            dev_fail(P.status, kDevTableFull, 14, g);
+            continue;
+          }
+          ids[slot] = key;
+          nvals[slot] = v;
+          // push at the head of the list; a failed compare-and-swap means another
+          // thread pushed first, so the retries are bounded by the CTA's threads
+          int head = *((volatile int*)(begins + h));
+          bool pushed = false;
+          for (int tries = 0; tries <= 2 * TW && !pushed; ++tries) {
+            nexts[slot] = head;
+            __threadfence_block();
+            const int old = atomicCAS(begins + h, head, slot);
+            pushed = old == head;
+            head = old;
+          }
+          if (!pushed) dev_fail(P.status, kDevTableFull, 17, g);
+        }
+        tm.sync();   // the next pass may find these keys
+      }
+      cnt = *counter < half ? *counter : half;
+      for (int x = tm.lane; x < cnt; x += TW) sortb[x] = ((unsigned long long)(unsigned)ids[x] << 32) | (unsigned)x;
+    } else {
+      for (int x = tm.lane; x < T; x += TW) {
+        lkeys[x] = kEmpty;
+        lvals[x] = VT(0);
+      }
+      const LpHash hs(logT, P.hash_mode);
+      tm.sync();
+      for (long long p = a0 + warp; p < a1; p += kWarps) {
+        const int j = Aj[p];
+        const VT a = Ax[p];
+        const long long bs = rp_at(I.B, j), be = rp_at(I.B, j + 1);
+        for (long long q = bs + lane32; q < be; q += 32) {
+          const int slot = lp_insert(lkeys, hs, nullptr, -1, Bj[q]);
+          if (slot >= 0) atomicAdd(lvals + slot, a * Bx[q]);
+          else dev_fail(P.status, kDevTableFull, 15, g);
+        }
+      }
+      tm.sync();
+      for (int xb = 0; xb < T; xb += TW) {
+        const int x = xb + tm.lane;
+        const bool o = x < T && lkeys[x] != kEmpty;
+        long long tot;
+        const long long ex = team_excl_scan<TW>(tm, o ? 1 : 0, &tot, scan_scratch);
+        if (o && cnt + ex < half) sortb[cnt + ex] = ((unsigned long long)(unsigned)lkeys[x] << 32) | (unsigned)x;
+        cnt += tot;
+      }
+    }
+    if (tm.lane == 0 && cnt != s) dev_fail(P.status, kDevRowSizeMismatch, 16, g);
+    const int n = (int)(cnt < half ? cnt : half);
+    int N = 1;
+    while (N < n) N <<= 1;
+    for (int x = n + tm.lane; x < N; x += TW) sortb[x] = ~0ull;
+    tm.sync();
+    team_bitonic<TW>(tm, sortb, N);
+    const long long nw = n < s ? n : s;
+    VT* __restrict__ Cx = reinterpret_cast<VT*>(I.Cx);
+    int* __restrict__ Cj = I.Cj;
+    const VT* vsrc = MODE == kPartTeamSeq ? nvals : lvals;
+    for (long long x = tm.lane; x < nw; x += TW) {
+      const unsigned long long e = sortb[x];
+      Cj[c0 + x] = (int)(e >> 32);
+      Cx[c0 + x] = vsrc[(unsigned)(e & 0xffffffffull)];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Warp / sub-warp teams (TW <= 32).  Products go into the LP table with plain
 // read-modify-writes of the values: no two lanes ever update one slot in the
 // same step, so no floating-point atomics are needed.
@@ -1131,14 +1290,35 @@ cudaError_t run_thread(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
   return cudaGetLastError();
 }
 
+template <int TW, typename VT, int MODE>
+cudaError_t run_part(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
+  const size_t smem = part_cta_bytes<TW, VT>(1 << S.logT);
+  if (smem + 1024 > (size_t)L.max_smem_optin) return cudaErrorInvalidConfiguration;
+  auto kern = k_num_part<TW, VT, MODE>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = resident_grid(kern, TW, smem, L.num_sms, S.nrows);
+  e = cudaMemsetAsync(S.fetch, 0, sizeof(unsigned long long), L.stream);
+  if (e != cudaSuccess) return e;
+  KKS_LAUNCHED();
+  kern<<<grid, TW, smem, L.stream>>>(P, S.rows, S.nrows, S.logT, S.fetch);
+  return cudaGetLastError();
+}
+
 template <typename VT>
 cudaError_t dispatch(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
   switch (S.cls) {
     case kClsT1: return run_thread<VT>(L, P, S);
     case kClsW8: return S.positions ? run_cpn<8, VT>(L, P, S) : run_warp<8, VT>(L, P, S);
     case kClsW32: return S.positions ? run_cpn<32, VT>(L, P, S) : run_warp<32, VT>(L, P, S);
-    case kClsC256: return run_hash<256, VT>(L, P, S);
-    case kClsC1024: return run_hash<1024, VT>(L, P, S);
+    case kClsC256:
+      if (S.part == kPartTeamSeq) return run_part<256, VT, kPartTeamSeq>(L, P, S);
+      if (S.part == kPartThreadPar) return run_part<256, VT, kPartThreadPar>(L, P, S);
+      return run_hash<256, VT>(L, P, S);
+    case kClsC1024:
+      if (S.part == kPartTeamSeq) return run_part<1024, VT, kPartTeamSeq>(L, P, S);
+      if (S.part == kPartThreadPar) return run_part<1024, VT, kPartThreadPar>(L, P, S);
+      return run_hash<1024, VT>(L, P, S);
     case kClsDense: return run_dense<VT>(L, P, S);
     case kClsSpill: return run_spill<VT>(L, P, S);
     default: return cudaErrorInvalidValue;

@@ -633,3 +633,33 @@ def test_masked_count_empty_and_bad_index(ops):
     with pytest.raises(SpGEMMError) as e:
         _count(ops, X, Y, bad)
     assert e.value.status == 8
+
+
+# ------------------------------------------------------------------ CTA partitioning schemes (Section 3.1.1)
+def _cta_rows_problem():
+    # rows of ~1 200 products over 100 000 columns: CTA hash classes, not dense
+    A = w.random_csr(3000, 100000, 40.0, seed=81)
+    B = w.random_csr(100000, 100000, 30.0, seed=82)
+    return A, B
+
+
+@pytest.mark.parametrize("part", [1, 2])
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_cta_partition_variants(ops, part, dtype):
+    """Team-Sequential with the LL accumulator (1) and Thread-Parallel (2) on CTA rows."""
+    A, B = _cta_rows_problem()
+    h, _, _, Cd = run(ops, A, B, dtype, cta_partition=part)
+    st = h.stats()
+    assert st["bin_rows_numeric"][3] + st["bin_rows_numeric"][4] > 1000
+    assert_matches_oracle(A, B, Cd, dtype)
+
+
+def test_tuner_times_partition_candidates(ops):
+    """The tuner's candidates include the other partitioning schemes; any pick is exact."""
+    A, B = _cta_rows_problem()
+    h, Ad, Bd, Cd = run(ops, A, B, np.float64, tune=True)
+    assert_matches_oracle(A, B, Cd, np.float64)
+    # a second numeric call on the tuned plan gives the same result
+    h.numeric(Ad, Bd, Cd.rowptr, Cd.nnz, Cd.colidx, Cd.values)
+    h.sync()
+    assert_matches_oracle(A, B, Cd, np.float64)
