@@ -141,3 +141,30 @@ def test_shards_concatenate_to_the_full_product(parts):
     C, S = oracle.spgemm(A, A)
     assert np.array_equal(rp, C.rowptr) and np.array_equal(cj, C.colidx)
     assert np.all(np.abs(vx - C.values) <= tol_of(np.float64) * S)
+
+
+def test_row_block_rebases_and_views_on_host_tensors():
+    ops = _ops()
+    A = w.random_csr(50, 40, 4.0, seed=91)
+    Ah = ops.CsrMatrix(torch.from_numpy(A.rowptr.copy()), torch.from_numpy(A.colidx.copy()),
+                       torch.from_numpy(A.values.copy()), A.shape)
+    for r0, r1 in ((0, 50), (0, 0), (7, 23), (49, 50), (50, 50)):
+        blk = ops.row_block(Ah, r0, r1)
+        assert blk.shape == (r1 - r0, 40)
+        rp = blk.rowptr.numpy()
+        assert rp[0] == 0 and np.array_equal(rp, A.rowptr[r0:r1 + 1] - A.rowptr[r0])
+        lo, hi = A.rowptr[r0], A.rowptr[r1]
+        assert np.array_equal(blk.colidx.numpy(), A.colidx[lo:hi])
+        assert np.array_equal(blk.values.numpy(), A.values[lo:hi])
+        if hi > lo:   # views of A's arrays, not copies
+            assert blk.colidx.data_ptr() == Ah.colidx[lo:].data_ptr()
+
+
+def test_partition_rows_accepts_tensors():
+    ops = _ops()
+    pre = torch.tensor([0, 3, 3, 9, 12, 20], dtype=torch.int64)
+    assert ops.partition_rows(pre, 2) == ops.partition_rows(pre.numpy(), 2)
+    b = ops.partition_rows(pre, 2)
+    _check_bounds(b, 5, 2)
+    assert b[1] in (3, 4)   # 10 of 20 flops: after row 2 (9) or row 3 (12), whichever is nearer
+    assert b[1] == 3
