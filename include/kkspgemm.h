@@ -204,10 +204,11 @@ spgemm_status_t spgemm_masked(spgemm_handle_t h, const spgemm_csr_t *X, const sp
  * the call, and every compressed product adds the popcount of its set bits
  * that S(i,:) also holds.  S: int64 row pointers [X.nrows + 1] and S_nnz
  * int32 columns, distinct within a row, any order.  row_counts: int64
- * [X.nrows], device.  Synchronises the stream twice.  A row of S with more
- * than 1024 entries is counted against a bitmap of ceil(Y.ncols / 32) words
- * in shared memory: when that does not fit (Y.ncols above about 1.6 M) the
- * call returns SPGEMM_ERR_DEVICE_LIMIT.  Out-of-range indices give
+ * [X.nrows], device.  Synchronises the stream twice.  Rows of S with more
+ * than 128 entries are counted by a CTA each against a bitmap of
+ * ceil(Y.ncols / 32) words in shared memory when that fits; otherwise rows up
+ * to 1024 entries use warp hash tables, and a longer row makes the call
+ * return SPGEMM_ERR_DEVICE_LIMIT (Y.ncols above about 1.6 M).  Out-of-range indices give
  * SPGEMM_ERR_BAD_INDEX.
  */
 spgemm_status_t spgemm_masked_count(spgemm_handle_t h, const spgemm_csr_t *X, const spgemm_csr_t *Y,

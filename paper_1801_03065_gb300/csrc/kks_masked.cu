@@ -748,17 +748,19 @@ __global__ void k_row_len_max(const long long* __restrict__ Sp, long long n, uns
 }
 
 // Row classes of the masked count: 0 = table of at most kMcSmallSlots slots,
-// 1 = larger warp tables, 2 = rows above kMcWarpMaxRow entries (a CTA each).
+// 1 = larger warp tables, 2 = rows of at least cta_from entries (a CTA each,
+// S(i,:) as a bitmap: cta_from is kMcSmallSlots / 2 + 1 when that bitmap fits
+// shared memory, so no row needs the 16 KB warp tables, else kMcWarpMaxRow + 1).
 // Rows of each class are listed (any order) and fetched by the teams from a
 // shared counter: the heavy rows of skewed graphs have indices with many
 // trailing zero bits, which a fixed row-to-team stride would send to a few
 // teams.  Empty rows get their count here.  cnt: [0..2] list lengths.
-__device__ __forceinline__ int mc_class(long long ns) {
-  if (ns > kMcWarpMaxRow) return 2;
+__device__ __forceinline__ int mc_class(long long ns, long long cta_from) {
+  if (ns >= cta_from) return 2;
   return 2 * ns > kMcSmallSlots ? 1 : 0;
 }
 
-__global__ void k_mc_classify(MaskedD M, int* lists, unsigned long long* cnt, long long* counts) {
+__global__ void k_mc_classify(MaskedD M, int* lists, unsigned long long* cnt, long long* counts, long long cta_from) {
   const long long n = M.X.nrows;
   const long long stride = (long long)gridDim.x * blockDim.x;
   const int lane = threadIdx.x & 31;
@@ -768,7 +770,7 @@ __global__ void k_mc_classify(MaskedD M, int* lists, unsigned long long* cnt, lo
     if (i < n) {
       const long long ns = M.Sp[i + 1] - M.Sp[i];
       if (ns <= 0) counts[i] = 0;
-      else c = mc_class(ns);
+      else c = mc_class(ns, cta_from);
     }
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -897,7 +899,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_masked_count_warp(MaskedD M, con
   }
 }
 
-// CTA per row of S with more than kMcWarpMaxRow entries: S(i,:) as a bitmap of
+// CTA per listed row of S (class 2 above): S(i,:) as a bitmap of
 // ceil(k / 32) words in shared memory, set and cleared by its own entries.
 __global__ void __launch_bounds__(256) k_masked_count_cta(MaskedD M, const long long* __restrict__ Ycp,
                                                           const int* __restrict__ csi,
@@ -1218,11 +1220,16 @@ cudaError_t launch_masked_count(const LaunchCtx& L, const MaskedD& M, const long
                                 unsigned long long* ctr) {
   const long long n = M.X.nrows;
   if (n <= 0) return cudaSuccess;
+  const long long kw = (M.Y.ncols + 31) >> 5;
+  const size_t bm_smem = (size_t)kw * 4;
+  const bool bm_fits = bm_smem + 16 * 1024 <= (size_t)L.max_smem_optin;
+  if (max_row > kMcWarpMaxRow && !bm_fits) return cudaErrorInvalidConfiguration;
+  const long long cta_from = bm_fits ? kMcSmallSlots / 2 + 1 : kMcWarpMaxRow + 1;
   // ctr: [0..2] class list lengths, [3..5] the classes' fetch counters
   cudaError_t e = cudaMemsetAsync(ctr, 0, 6 * sizeof(unsigned long long), L.stream);
   if (e != cudaSuccess) return e;
   KKS_LAUNCHED();
-  k_mc_classify<<<grid_cap(n, 256, L.num_sms, 8), 256, 0, L.stream>>>(M, lists, ctr, counts);
+  k_mc_classify<<<grid_cap(n, 256, L.num_sms, 8), 256, 0, L.stream>>>(M, lists, ctr, counts, cta_from);
   {
     auto kern = k_masked_count_warp<kMcSmallSlots, 8, 8>;
     const size_t smem = (size_t)8 * 2 * kMcSmallSlots * 4;
@@ -1234,7 +1241,7 @@ cudaError_t launch_masked_count(const LaunchCtx& L, const MaskedD& M, const long
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  if (max_row > kMcSmallSlots / 2) {
+  if (max_row > kMcSmallSlots / 2 && cta_from > kMcSmallSlots / 2 + 1) {   // mid rows left for warps
     auto kern = k_masked_count_warp<kMcWarpSlots, 4, 1>;
     const size_t smem = (size_t)4 * 2 * kMcWarpSlots * 4;
     e = set_smem(kern, smem);
@@ -1245,10 +1252,8 @@ cudaError_t launch_masked_count(const LaunchCtx& L, const MaskedD& M, const long
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  if (max_row > kMcWarpMaxRow) {
-    const long long kw = (M.Y.ncols + 31) >> 5;
-    const size_t smem = (size_t)kw * 4;
-    if (smem + 16 * 1024 > (size_t)L.max_smem_optin) return cudaErrorInvalidConfiguration;
+  if (max_row >= cta_from) {
+    const size_t smem = bm_smem;
     auto kern = k_masked_count_cta;
     e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
