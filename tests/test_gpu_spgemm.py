@@ -399,6 +399,32 @@ def test_tuned_numeric_and_reuse(ops):
     assert h.stats()["tuned_bins"] >= 0
 
 
+def test_batched512_full_sampled(ops):
+    """The full batched workload in the bench's launch configuration (512 products in one
+    autotuned plan, FP64): every instance's nnz equals the oracle's symbolic count, and 200
+    sampled rows of 8 instances (the largest and smallest included) match the oracle."""
+    torch.cuda.empty_cache()
+    pairs = w.batched_pairs(count=512, seed=11)
+    h = ops.SpGEMM(tune=True)
+    As = [dev(a) for a, _ in pairs]
+    Bs = [dev(b) for _, b in pairs]
+    rps, nnzs = h.batch_symbolic(As, Bs)
+    Cs = h.batch_numeric(As, Bs, rps, nnzs)
+    h.sync()
+    rng = np.random.default_rng(5)
+    sizes = np.array([a.nrows for a, _ in pairs])
+    pick = sorted({int(np.argmax(sizes)), int(np.argmin(sizes))} |
+                  set(int(x) for x in rng.choice(len(pairs), size=6, replace=False)))
+    for i in pick:
+        a, b = pairs[i]
+        assert nnzs[i] == int(oracle.symbolic_plain(a, b)[-1])
+        rows = np.sort(rng.choice(a.nrows, size=min(200, a.nrows), replace=False))
+        assert_rows_match_oracle(a, b, Cs[i], np.float64, rows)
+    del Cs, rps
+    h.close()
+    torch.cuda.empty_cache()
+
+
 def test_batched_tuned_matches(ops):
     pairs = w.batched_pairs(count=10, nmin=500, nmax=20000, seed=11)
     h = ops.SpGEMM(tune=True)
