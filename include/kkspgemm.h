@@ -206,10 +206,10 @@ spgemm_status_t spgemm_masked(spgemm_handle_t h, const spgemm_csr_t *X, const sp
  * int32 columns, distinct within a row, any order.  row_counts: int64
  * [X.nrows], device.  Synchronises the stream twice.  Rows of S with more
  * than 128 entries are counted by a CTA each against a bitmap of
- * ceil(Y.ncols / 32) words in shared memory when that fits; otherwise rows up
- * to 1024 entries use warp hash tables, and a longer row makes the call
- * return SPGEMM_ERR_DEVICE_LIMIT (Y.ncols above about 1.6 M).  Out-of-range indices give
- * SPGEMM_ERR_BAD_INDEX.
+ * ceil(Y.ncols / 32) words in shared memory when that fits (Y.ncols up to
+ * about 1.6 M); otherwise rows up to 1024 entries use warp hash tables and a
+ * longer row makes the call return SPGEMM_ERR_DEVICE_LIMIT.  Out-of-range
+ * indices give SPGEMM_ERR_BAD_INDEX.
  */
 spgemm_status_t spgemm_masked_count(spgemm_handle_t h, const spgemm_csr_t *X, const spgemm_csr_t *Y,
                                     const int64_t *S_rowptr, const int32_t *S_colidx, int64_t S_nnz,
@@ -243,7 +243,7 @@ spgemm_status_t spgemm_masked_count(spgemm_handle_t h, const spgemm_csr_t *X, co
  * SPGEMM_ERR_BAD_INDEX for malformed row pointers or out-of-range columns,
  * SPGEMM_ERR_DEVICE_LIMIT when a row of C needs more shared memory than one
  * CTA has (symbolic: more than about 50 K keys with K above about 1.6 M;
- * numeric: rows of more than 4096 entries in FP64, 6144 in FP32): multiply in
+ * numeric: rows of more than 4096 entries in FP64, 8192 in FP32): multiply in
  * two steps (spgemm_transpose, spgemm_symbolic / spgemm_numeric) instead.
  *
  * spgemm_rap_numeric fills C_colidx and C_values (device, caller-owned, nnzC
