@@ -9,8 +9,12 @@ compression, symbolic, numeric with sorted rows) and the transpose of P.
 
 Metric: GFLOP/s = 2·f_m / t (f_m = multiplications of the three products),
 whole job over all ranks.  Also reported: numeric-reuse GFLOP/s of A·A, the
-HBM roofline fraction of the A·A numeric phase, end-to-end throughput with
-host buffers, and the CPU oracle on a bounded sample of the workload.
+HBM roofline fraction of the A·A numeric phase (and its FP64-pipe fraction),
+end-to-end throughput with host buffers, the CPU oracle on a bounded sample of
+the workload, and, under "workloads", the skewed-graph product (R-MAT scale
+18, FP32) and the batched workload (512 products, FP64 and FP32: batched
+autotuned plan against the plain per-matrix rule, numeric reuse as a CUDA
+graph) at full size with bounded repeats.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -55,6 +59,10 @@ def parse_args(argv=None):
                    help="stencil27_100: the headline step; batched512: batched autotuned vs plain per-matrix")
     p.add_argument("--count", type=int, default=512, help="batched512: number of products")
     p.add_argument("--repeats", type=int, default=20, help="batched512: numeric-reuse repeats")
+    p.add_argument("--no-extra", action="store_true",
+                   help="stencil27_100: skip the rmat18 and batched512 sections of the line")
+    p.add_argument("--extra-repeats", type=int, default=5,
+                   help="numeric-reuse repeats of the batched512 sections of the default line")
     p.add_argument("--numeric-only", action="store_true",
                    help="profiling aid: one symbolic and two numeric calls of A*A on --grid, no timing")
     p.add_argument("--serial", action="store_true",
@@ -84,6 +92,21 @@ def reduce_over_ranks(t_step_ms, flops_step, world, device=None):
 def dist_env():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def fp64_peak(num_sms=152):
+    """FP64 FMA rate from the unit counts: SMs x 2 FP64 FMA per SM per clock
+    x 2 flops x the maximum SM clock (MEASURED_PEAKS sm_max_mhz, else the
+    nominal 2070 MHz)."""
+    mhz, src = 2070.0, "nominal max clock"
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("sm_max_mhz"):
+            mhz, src = float(d["sm_max_mhz"]), "MEASURED_PEAKS sm_max_mhz"
+    kind = "derived: %d SMs x 2 FP64 FMA/clk x 2 flops x %.0f MHz (%s)" % (num_sms, mhz, src)
+    return num_sms * 2 * 2 * mhz * 1e6 / 1e12, kind
 
 
 def measured_peaks():
@@ -389,9 +412,10 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     achieved = bytes_num / (t_num * 1e-3) / 1e9
     traffic_rec = load_traffic_record("numeric_stencil27_traffic.txt") if args.grid == 100 else None
-    # FP64 numeric: one fused multiply-add per product on the FP64 pipe, whose
-    # rate (1.25 TFLOP/s nominal on GB300) sets a higher floor than HBM does
-    fp64_peak_tflops = 1.25
+    # FP64 numeric: one fused multiply-add per product on the FP64 pipe; its
+    # peak from the unit counts: SMs x 2 FP64 FMA per clock x 2 flops x the
+    # maximum SM clock
+    fp64_peak_tflops, fp64_kind = fp64_peak(torch.cuda.get_device_properties(device).multi_processor_count)
     alu_achieved = 2.0 * stAA["f_m"] / (t_num * 1e-3) / 1e12
 
     out = {
@@ -414,15 +438,16 @@ def run_ours(args):
         "numeric_reuse": {"value": round(2.0 * stAA["f_m"] / (t_num * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
                           "probe_only_value": round(2.0 * stAA["f_m"] / (t_reuse * 1e-3) / 1e9, 3),
                           "product": "A*A"},
-        "roofline": {"bound": "alu", "achieved": round(alu_achieved, 4), "peak": fp64_peak_tflops,
-                     "unit": "TFLOP/s", "frac": round(alu_achieved / fp64_peak_tflops, 4),
-                     "peak_kind": "recipe FP64 rate (measured DFMA loop: 1.198 TFLOP/s)",
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_kind": peak_kind + " (MEASURED_PEAKS hbm_gbs)",
                      "traffic": None if traffic_rec is None else traffic_rec.get("traffic_bytes_per_launch"),
-                     "kernel": "numeric phase of A*A (k_num_cpn bins; one call of spgemm_numeric)",
-                     "algorithmic_flops": 2 * stAA["f_m"]},
-        "roofline_hbm": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
-                         "algorithmic_bytes": bytes_num},
+                     "kernel": "numeric phase of A*A (one call of spgemm_numeric, CUDA events on its stream)",
+                     "algorithmic_bytes": bytes_num,
+                     "algorithmic_bytes_rule": "A (8 B row pointer + 12 B per entry) read as A and as B, "
+                                               "C (8 B row pointer + 12 B per entry) written"},
+        "roofline_fp64": {"bound": "alu", "achieved": round(alu_achieved, 4), "peak": round(fp64_peak_tflops, 4),
+                          "unit": "TFLOP/s", "frac": round(alu_achieved / fp64_peak_tflops, 4),
+                          "peak_kind": fp64_kind, "algorithmic_flops": 2 * stAA["f_m"]},
         "stats_AA": {k: stAA[k] for k in ("f_m", "nnzC", "maxrs", "CF", "CMRF", "compressed")},
         "rap": rap_summary(S, A, P, t_other, peak, peak_kind),
         "gpu_launches": int(launches),
@@ -434,6 +459,18 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(A, P, args.cpu_budget)
     S.close()
+    del S
+    torch.cuda.empty_cache()
+    if world == 1 and args.grid == 100 and not args.no_extra:
+        extra = other_workloads(args)
+        out["workloads"] = extra
+        bvp = {}
+        for name in ("batched512_f64", "batched512_f32"):
+            r = extra.get(name, {})
+            if "sym_num" in r and "speedup" in r["sym_num"]:
+                bvp[r["dtype"]] = {"sym_num_speedup": r["sym_num"]["speedup"],
+                                   "numeric_reuse_graph_speedup": r["numeric_reuse_graph"].get("speedup")}
+        out["batched_vs_plain"] = bvp
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -620,7 +657,7 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- batched
-def run_batched(args):
+def batched_measure(pairs, vdtype, steps, warmup, repeats, plain=True):
     """Batched autotuned plan against the plain per-matrix meta-algorithm.
 
     NoReuse: symbolic + numeric of all products (batched: one plan, rows of all
@@ -628,20 +665,18 @@ def run_batched(args):
     with the paper's per-problem rule, called product by product).  Reuse: the
     numeric phase repeated with values refreshed from pinned host memory; the
     batched repeats run as one captured CUDA graph (two host-to-device copies
-    plus the numeric launches), the plain ones product by product.
+    plus the numeric launches), the plain ones product by product.  Values of
+    all instances sit in one device array per operand.  Returns a dict.
     """
     import numpy as np
     import torch
     import workloads as w
     from paper_1801_03065_gb300 import ops
 
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
-    pairs = w.batched_pairs(count=args.count, seed=11, dtype=np.float64)
-    va_h = np.concatenate([a.values for a, _ in pairs])
-    vb_h = np.concatenate([b.values for _, b in pairs])
-    va = torch.from_numpy(va_h).to(dev)
-    vb = torch.from_numpy(vb_h).to(dev)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    tdt = torch.float64 if vdtype == np.float64 else torch.float32
+    va = torch.from_numpy(np.concatenate([a.values for a, _ in pairs]).astype(vdtype)).to(dev)
+    vb = torch.from_numpy(np.concatenate([b.values for _, b in pairs]).astype(vdtype)).to(dev)
     As, Bs = [], []
     oa = ob = 0
     for a, b in pairs:
@@ -651,45 +686,35 @@ def run_batched(args):
                                 vb[ob:ob + b.nnz], b.shape))
         oa += a.nnz
         ob += b.nnz
-    fresh = w.batched_fresh_values(pairs, repeat=0)
+    fresh = w.batched_fresh_values(pairs, repeat=0, dtype=vdtype)
     hva = torch.from_numpy(np.concatenate([x for x, _ in fresh])).pin_memory()
     hvb = torch.from_numpy(np.concatenate([y for _, y in fresh])).pin_memory()
+    del fresh
 
     hb = ops.SpGEMM(tune=True)
     rps, nnzs = hb.batch_symbolic(As, Bs)
     Cj = [torch.empty(z, dtype=torch.int32, device=dev) for z in nnzs]
-    Cx = [torch.empty(z, dtype=torch.float64, device=dev) for z in nnzs]
+    Cx = [torch.empty(z, dtype=tdt, device=dev) for z in nnzs]
     hb.batch_numeric(As, Bs, rps, nnzs, Cj, Cx)   # tunes the numeric bins
     hb.sync()
     st = hb.stats()
     fm = st["f_m"]
-    hp = [ops.SpGEMM(method=1) for _ in pairs]
-    rpp = [torch.empty(a.nrows + 1, dtype=torch.int64, device=dev) for a in As]
+    vbytes = 8 if vdtype == np.float64 else 4
+    l0 = ops.launch_count()
 
     def batched_step():
         hb.batch_symbolic(As, Bs)
         hb.batch_numeric(As, Bs, rps, nnzs, Cj, Cx)
 
-    def plain_step():
-        for i in range(len(pairs)):
-            rp, z = hp[i].symbolic(As[i], Bs[i], C_rowptr=rpp[i])
-            hp[i].numeric(As[i], Bs[i], rp, z, Cj[i], Cx[i])
-
-    for _ in range(max(1, args.warmup)):
+    for _ in range(max(1, warmup)):
         batched_step()
-        plain_step()
     torch.cuda.synchronize()
-    t_b = statistics.mean(time_region(torch, batched_step, args.steps))
-    t_p = statistics.mean(time_region(torch, plain_step, max(1, args.steps // 2)))
+    t_b = statistics.mean(time_region(torch, batched_step, steps))
 
-    # numeric reuse: values refreshed from pinned host memory every repeat
     def batched_num():
         hb.batch_numeric(As, Bs, rps, nnzs, Cj, Cx)
 
-    def plain_num():
-        for i in range(len(pairs)):
-            hp[i].numeric(As[i], Bs[i], rpp[i], nnzs[i], Cj[i], Cx[i])
-
+    t_num = statistics.mean(time_region(torch, batched_num, steps))
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(side):
@@ -700,58 +725,86 @@ def run_batched(args):
         va.copy_(hva, non_blocking=True)
         vb.copy_(hvb, non_blocking=True)
         batched_num()
-    reps = args.repeats
 
     def batched_reuse():
-        for _ in range(reps):
+        for _ in range(repeats):
             graph.replay()
 
-    def plain_reuse():
-        for _ in range(reps):
-            va.copy_(hva, non_blocking=True)
-            vb.copy_(hvb, non_blocking=True)
-            plain_num()
-
     batched_reuse()
-    plain_reuse()
-    t_br = statistics.mean(time_region(torch, batched_reuse, 2))
-    t_pr = statistics.mean(time_region(torch, plain_reuse, 1))
+    t_br = statistics.mean(time_region(torch, batched_reuse, 1))
     hb.sync()
     gf = lambda t, n=1: round(2.0 * fm * n / (t * 1e-3) / 1e9, 3)
+    # algorithmic bytes of one numeric call: A and B of every instance read
+    # once, C written once (int64 row pointers, int32 columns)
+    nrows = sum(a.nrows for a in As)
+    bytes_num = sum(csr_bytes(a.nrows, a.nnz, vbytes) + csr_bytes(b.nrows, b.nnz, vbytes)
+                    for a, b in zip(As, Bs)) + 8 * (nrows + len(As)) + (4 + vbytes) * st["nnzC"]
+    peak, peak_kind = measured_peaks()
     out = {
-        "metric": METRIC, "value": gf(t_b), "unit": "GFLOP/s", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(t_b, 3), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "batched512: %d independent square products, n_i log-uniform in [1e3, 2e5], "
-                               "geometric rows with means U(3, 40), uniform columns, FP64 U(-1, 1), seed 11"
-                               % len(pairs),
-                   "f_m": fm, "nnzC": st["nnzC"], "rows": sum(a.nrows for a in As),
-                   "l2": "inputs larger than L2"},
-        "batched_vs_plain": {
-            "sym_num": {"batched_autotuned": gf(t_b), "plain_per_matrix": gf(t_p), "speedup": round(t_p / t_b, 3),
-                        "ms": [round(t_b, 3), round(t_p, 3)]},
-            "numeric_reuse_%d" % reps: {"batched_graph": gf(t_br, reps), "plain_per_matrix": gf(t_pr, reps),
-                                        "speedup": round(t_pr / t_br, 3), "ms": [round(t_br, 3), round(t_pr, 3)],
-                                        "h2d_bytes_per_repeat": int((hva.numel() + hvb.numel()) * 8)}},
+        "dtype": "f64" if vdtype == np.float64 else "f32",
+        "f_m": fm, "nnzC": st["nnzC"], "rows": nrows, "products": len(pairs),
+        "sym_num": {"batched_autotuned_gflops": gf(t_b), "ms": round(t_b, 3)},
+        "numeric": {"gflops": gf(t_num), "ms": round(t_num, 3),
+                    "roofline": {"bound": "hbm", "achieved": round(bytes_num / (t_num * 1e-3) / 1e9, 2),
+                                 "peak": peak, "unit": "GB/s",
+                                 "frac": round(bytes_num / (t_num * 1e-3) / 1e9 / peak, 4),
+                                 "peak_kind": peak_kind, "algorithmic_bytes": int(bytes_num)}},
+        "numeric_reuse_graph": {"repeats": repeats, "gflops": gf(t_br, repeats), "ms": round(t_br, 3),
+                                "h2d_bytes_per_repeat": int((hva.numel() + hvb.numel()) * vbytes)},
         "tuned_bins": st["tuned_bins"], "numeric_bins": st["nbins_numeric"],
+        "bin_rows_numeric": st["bin_rows_numeric"],
     }
-    print(json.dumps(out), flush=True)
+    if plain:
+        hp = [ops.SpGEMM(method=1) for _ in pairs]
+        rpp = [torch.empty(a.nrows + 1, dtype=torch.int64, device=dev) for a in As]
+
+        def plain_step():
+            for i in range(len(pairs)):
+                rp, z = hp[i].symbolic(As[i], Bs[i], C_rowptr=rpp[i])
+                hp[i].numeric(As[i], Bs[i], rp, z, Cj[i], Cx[i])
+
+        def plain_reuse():
+            for _ in range(repeats):
+                va.copy_(hva, non_blocking=True)
+                vb.copy_(hvb, non_blocking=True)
+                for i in range(len(pairs)):
+                    hp[i].numeric(As[i], Bs[i], rpp[i], nnzs[i], Cj[i], Cx[i])
+
+        plain_step()
+        torch.cuda.synchronize()
+        t_p = statistics.mean(time_region(torch, plain_step, max(1, steps // 2)))
+        plain_reuse()
+        t_pr = statistics.mean(time_region(torch, plain_reuse, 1))
+        for x in hp:
+            x.sync()
+            x.close()
+        out["sym_num"].update({"plain_per_matrix_gflops": gf(t_p), "plain_ms": round(t_p, 3),
+                               "speedup": round(t_p / t_b, 3)})
+        out["numeric_reuse_graph"].update({"plain_per_matrix_gflops": gf(t_pr, repeats),
+                                           "plain_ms": round(t_pr, 3), "speedup": round(t_pr / t_br, 3)})
+    out["gpu_launches"] = int(ops.launch_count() - l0)
+    del graph
+    hb.close()
+    del As, Bs, Cj, Cx, rps, va, vb, hva, hvb
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return out
 
 
-def run_numeric_only(args):
-    """A·A of the 27-point stencil: symbolic once, numeric twice (for ncu captures)."""
+BATCHED_DESC = ("batched512: %d independent square products, n_i log-uniform in [1e3, 2e5], geometric rows "
+                "with means U(3, 40), uniform columns, values U(-1, 1), seed 11")
+
+
+def run_batched(args):
+    import numpy as np
     import torch
     import workloads as w
-    from paper_1801_03065_gb300 import ops
-    A = w.stencil3d_27pt(args.grid, seed=1)
-    Ad = ops.CsrMatrix.from_host(A.rowptr, A.colidx, A.values, A.shape, device="cuda:0")
-    h = ops.SpGEMM(numeric_positions=bool(args.numeric_positions))
-    rp, nnz = h.symbolic(Ad, Ad)
-    C = h.numeric(Ad, Ad, rp, nnz)
-    h.sync()
-    h.numeric(Ad, Ad, rp, nnz, C.colidx, C.values)
-    h.sync()
-    print(json.dumps({"grid": args.grid, "nnzC": nnz}))
+    torch.cuda.set_device(0)
+    pairs = w.batched_pairs(count=args.count, seed=11, dtype=np.float64)
+    res = batched_measure(pairs, np.float64, args.steps, args.warmup, args.repeats)
+    out = _base_line(args, res["sym_num"]["batched_autotuned_gflops"], res["sym_num"]["ms"],
+                     BATCHED_DESC % len(pairs), "f64", {"batched512": res})
+    print(json.dumps(out), flush=True)
 
 
 def _base_line(args, value, t_ms, workload, dtype, extra):
@@ -762,25 +815,20 @@ def _base_line(args, value, t_ms, workload, dtype, extra):
     return out
 
 
-def run_single(args):
+def single_measure(A, vdt, steps, warmup, clocks=False):
     """One product C = A·A: NoReuse (symbolic + numeric), numeric reuse, and the
-    pattern-only symbolic phase; R-MAT (FP32, skewed rows, nnz(C) > 2^31) or the
-    5-point Laplacian (FP64, launch-bound: reported in microseconds too)."""
+    symbolic phase alone, with the HBM roofline of the numeric call."""
     import numpy as np
     import torch
-    import workloads as w
     from paper_1801_03065_gb300 import ops
-    torch.cuda.set_device(0)
-    wl = w.config_workload(args.workload)
-    A = wl["A"]
-    vdt = np.float32 if wl["dtype"] == "f32" else np.float64
+    dev = torch.device("cuda", torch.cuda.current_device())
     tdt = torch.float32 if vdt == np.float32 else torch.float64
-    Ad = ops.CsrMatrix.from_host(A.rowptr, A.colidx, A.values.astype(vdt), A.shape, device="cuda:0")
+    Ad = ops.CsrMatrix.from_host(A.rowptr, A.colidx, A.values.astype(vdt), A.shape, device=dev)
     h = ops.SpGEMM()
-    rp = torch.empty(A.nrows + 1, dtype=torch.int64, device="cuda:0")
+    rp = torch.empty(A.nrows + 1, dtype=torch.int64, device=dev)
     rp, nnz = h.symbolic(Ad, Ad, C_rowptr=rp)
-    Cj = torch.empty(nnz, dtype=torch.int32, device="cuda:0")
-    Cx = torch.empty(nnz, dtype=tdt, device="cuda:0")
+    Cj = torch.empty(nnz, dtype=torch.int32, device=dev)
+    Cx = torch.empty(nnz, dtype=tdt, device=dev)
     h.numeric(Ad, Ad, rp, nnz, Cj, Cx)
     h.sync()
     st = h.stats()
@@ -789,37 +837,91 @@ def run_single(args):
         h.symbolic(Ad, Ad, C_rowptr=rp)
         h.numeric(Ad, Ad, rp, nnz, Cj, Cx)
 
-    for _ in range(max(args.warmup, 1)):
+    for _ in range(max(warmup, 1)):
         step()
     torch.cuda.synchronize()
-    clocks = ClockSampler(0).start()
-    times = time_region(torch, step, args.steps)
-    clk = clocks.stop()
+    sampler = ClockSampler(torch.cuda.current_device()).start() if clocks else None
+    times = time_region(torch, step, steps)
+    clk = sampler.stop() if sampler else None
     t = sum(times) / len(times)
     num = lambda: h.numeric(Ad, Ad, rp, nnz, Cj, Cx)
-    t_num = statistics.mean(time_region(torch, num, max(args.steps, 5)))
+    t_num = statistics.mean(time_region(torch, num, max(steps, 3)))
     sym = lambda: h.symbolic(Ad, Ad, C_rowptr=rp)
-    t_sym = statistics.mean(time_region(torch, sym, max(args.steps, 5)))
+    t_sym = statistics.mean(time_region(torch, sym, max(steps, 3)))
     h.sync()
     fm = st["f_m"]
     vb = 4 if vdt == np.float32 else 8
     bytes_num = 2 * csr_bytes(A.nrows, A.nnz, vb, 8) + csr_bytes(A.nrows, nnz, vb, 8)
     peak, peak_kind = measured_peaks()
+    h.close()
+    del Ad, Cj, Cx, rp
+    torch.cuda.empty_cache()
+    out = {"sym_num_gflops": round(2.0 * fm / (t * 1e-3) / 1e9, 3), "sym_num_ms": round(t, 4),
+           "phases_ms": {"symbolic": round(t_sym, 4), "numeric": round(t_num, 4)},
+           "numeric_reuse": {"value": round(2.0 * fm / (t_num * 1e-3) / 1e9, 3), "unit": "GFLOP/s"},
+           "roofline_hbm": {"bound": "hbm", "achieved": round(bytes_num / (t_num * 1e-3) / 1e9, 2), "peak": peak,
+                            "unit": "GB/s", "frac": round(bytes_num / (t_num * 1e-3) / 1e9 / peak, 4),
+                            "peak_kind": peak_kind, "algorithmic_bytes": bytes_num, "kernel": "numeric phase"},
+           "stats": {k: st[k] for k in ("f_m", "maxrf", "nnzC", "maxrs", "CF", "compressed", "bin_rows_numeric")}}
+    if clk is not None:
+        out["clocks"] = clk
+    return out
+
+
+RMAT_DESC = ("rmat18: C = A*A, A = symmetrised R-MAT scale 18, edge factor 16 (.57,.19,.19,.05), seed 7, "
+             "%d nnz, FP32 U(0,1]")
+
+
+def run_single(args):
+    """R-MAT (FP32, skewed rows, nnz(C) > 2^31) or the 5-point Laplacian (FP64,
+    launch-bound: reported in microseconds too)."""
+    import numpy as np
+    import torch
+    import workloads as w
+    torch.cuda.set_device(0)
+    wl = w.config_workload(args.workload)
+    A = wl["A"]
+    vdt = np.float32 if wl["dtype"] == "f32" else np.float64
+    res = single_measure(A, vdt, args.steps, args.warmup, clocks=True)
     if args.workload == "rmat18":
-        desc = ("rmat18: C = A*A, A = symmetrised R-MAT scale 18, edge factor 16 (.57,.19,.19,.05), seed 7, "
-                "%d nnz, FP32 U(0,1]" % A.nnz)
+        desc = RMAT_DESC % A.nnz
     else:
         desc = "laplace5_64: C = A*A, A = 5-point Laplacian on a 64^2 grid (4096 rows, %d nnz, FP64 4/-1)" % A.nnz
-    h.close()
-    print(json.dumps(_base_line(args, 2.0 * fm / (t * 1e-3) / 1e9, t, desc, wl["dtype"], {
-        "phases_ms": {"symbolic": round(t_sym, 4), "numeric": round(t_num, 4),
-                      "sym_num_us": round(1e3 * t, 2)},
-        "numeric_reuse": {"value": round(2.0 * fm / (t_num * 1e-3) / 1e9, 3), "unit": "GFLOP/s"},
-        "roofline_hbm": {"bound": "hbm", "achieved": round(bytes_num / (t_num * 1e-3) / 1e9, 2), "peak": peak,
-                         "unit": "GB/s", "frac": round(bytes_num / (t_num * 1e-3) / 1e9 / peak, 4),
-                         "peak_kind": peak_kind, "algorithmic_bytes": bytes_num, "kernel": "numeric phase"},
-        "stats": {k: st[k] for k in ("f_m", "maxrf", "nnzC", "maxrs", "CF", "compressed", "bin_rows_numeric")},
-        "clocks": clk})), flush=True)
+    res["phases_ms"]["sym_num_us"] = round(1e3 * res["sym_num_ms"], 2)
+    print(json.dumps(_base_line(args, res.pop("sym_num_gflops"), res.pop("sym_num_ms"), desc, wl["dtype"], res)),
+          flush=True)
+
+
+def other_workloads(args):
+    """The skewed-graph and batched workloads at full size, bounded repeats,
+    for the default bench line.  Each section reports its own error instead
+    of failing the line."""
+    import numpy as np
+    import torch
+    import workloads as w
+    out = {}
+    try:
+        G = w.rmat_symmetric(scale=18, seed=7)
+        r = single_measure(G, np.float32, 3, 1)
+        r["workload"] = RMAT_DESC % G.nnz
+        out["rmat18"] = r
+        del G
+    except Exception as e:   # noqa: BLE001 - reported in the line
+        out["rmat18"] = {"error": repr(e)[:300]}
+    torch.cuda.empty_cache()
+    try:
+        pairs = w.batched_pairs(count=512, seed=11, dtype=np.float64)
+        for name, vdt in (("batched512_f64", np.float64), ("batched512_f32", np.float32)):
+            try:
+                r = batched_measure(pairs, vdt, 2, 1, args.extra_repeats)
+                r["workload"] = BATCHED_DESC % len(pairs)
+                out[name] = r
+            except Exception as e:   # noqa: BLE001
+                out[name] = {"error": repr(e)[:300]}
+            torch.cuda.empty_cache()
+    except Exception as e:   # noqa: BLE001
+        out["batched512"] = {"error": repr(e)[:300]}
+    return out
 
 
 def run_triangles(args):

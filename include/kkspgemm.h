@@ -279,14 +279,19 @@ spgemm_status_t spgemm_transpose(spgemm_handle_t h, const spgemm_csr_t *A, int64
  * fixed GPU memory budget.  Same arguments and results as spgemm_transpose,
  * without a handle.  Its scratch is one fixed 32 MiB device buffer inside the
  * library, held by every GPU that loads it until the process exits:
- *  - the first call on a device looks up the buffer's address, so make that
- *    first call before any stream capture;
+ *  - the first call on a device looks up the buffer's address on that device
+ *    (once; the device must be current);
+ *  - every call synchronises its stream, so no call can be made while that
+ *    stream is being captured into a CUDA graph;
  *  - all calls share the buffer and it keeps the last call's contents (each
  *    call clears what it needs); calls that overlap on the GPU race on it, so
  *    serialise them;
  *  - a problem needing more scratch (about 16 bytes per column of A plus 12
  *    bytes per nonzero) returns SPGEMM_ERR_OOM before any kernel runs.
- * Synchronises the stream twice (the longest column, then the status).
+ * Synchronises the stream twice (the longest column and the status of the
+ * counting pass, then the final status).  Row pointers that do not start at 0
+ * and end at nnz, or out-of-range columns, give SPGEMM_ERR_BAD_INDEX before
+ * any entry is scattered.
  */
 spgemm_status_t spgemm_transpose_noalloc(const spgemm_csr_t *A, int64_t *At_rowptr, int32_t *At_colidx,
                                          void *At_values, int64_t *perm, spgemm_stream_t stream);
@@ -302,6 +307,14 @@ spgemm_status_t spgemm_gather(spgemm_handle_t h, spgemm_dtype_t dtype, const voi
  * C_colidx, C_values: host arrays of count device pointers; nnzC: host array
  * of count outputs.  All instances share one dtype.  Numeric reuse rules are
  * those of the single calls.
+ *
+ * Plan lifecycle: there is no separate plan object.  spgemm_batch_symbolic
+ * plans the batch (row statistics, compression, bins, pools) and keeps the
+ * plan in the handle; spgemm_batch_numeric runs it any number of times (new
+ * values, same patterns); the plan is released by the next symbolic call on
+ * the handle (single or batched) or by spgemm_handle_destroy.  So a plan is
+ * created with spgemm_handle_create + spgemm_batch_symbolic and destroyed
+ * with spgemm_handle_destroy; use one handle per live plan.
  */
 spgemm_status_t spgemm_batch_symbolic(spgemm_handle_t h, int32_t count, const spgemm_csr_t *A,
                                       const spgemm_csr_t *B, int64_t *const *C_rowptr, int64_t *nnzC,

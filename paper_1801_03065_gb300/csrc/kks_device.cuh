@@ -12,8 +12,10 @@
 //
 // Accumulators are linear-probing hash tables (LP, Section 3.1.2) addressed
 // through generic pointers, so the same code serves the level-1 table in
-// shared memory and the level-2 table in a global-memory pool chunk.  The hash
-// of a key is key & (size - 1) with a power-of-two size (Section 3.1.2).
+// shared memory and the level-2 table in a global-memory pool chunk.  Table
+// sizes are powers of two; the slot of a key is the paper's key & (size - 1)
+// (Section 3.1.2) with option hash_function = 0, and by default (1) the top
+// log2(size) bits of key * 2654435761 (multiplicative hashing, see LpHash).
 #pragma once
 
 #include <cstdint>

@@ -963,6 +963,10 @@ __global__ void __launch_bounds__(256) k_masked_count_cta(MaskedD M, const long 
 // ---------------------------------------------------------------- transpose
 __global__ void k_tr_count(MatD A, unsigned long long* cnt, DevStatus* st) {
   const long long stride = (long long)gridDim.x * blockDim.x;
+  // the rows must cover the entries exactly: every counted entry is scattered
+  // once, so no slot of the transpose is left unwritten
+  if (blockIdx.x == 0 && threadIdx.x == 0 && (rp_at(A, 0) != 0 || rp_at(A, A.nrows) != A.nnz))
+    dev_fail(st, kDevBadIndex, 34, rp_at(A, A.nrows));
   for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < A.nnz; p += stride) {
     const int c = A.cj[p];
     if ((unsigned long long)(unsigned)c < (unsigned long long)A.ncols) atomicAdd(&cnt[c], 1ull);
@@ -997,10 +1001,13 @@ __global__ void k_tr_scatter(MatD A, const long long* Atp, unsigned long long* c
 }
 
 // sort row c of A^T by row index; buffers of N = nextpow2(len) keys
+// Entries whose row or source entry is out of range (a slot the scatter never
+// wrote, because of malformed row pointers) are recorded in st and skipped.
 template <int TW, bool GBUF>
 __global__ void k_tr_sort(long long n, const long long* Atp, const int* trow, const long long* tperm, int* Atj,
                           long long* perm, const void* Ax, void* Atx, int vbytes, long long min_len, long long max_len,
-                          unsigned long long* gbuf, long long gbuf_len) {
+                          unsigned long long* gbuf, long long gbuf_len, long long a_nrows, long long a_nnz,
+                          DevStatus* st) {
   extern __shared__ __align__(16) unsigned char smem[];
   Team<TW> tm;
   unsigned long long* buf;
@@ -1022,7 +1029,12 @@ __global__ void k_tr_sort(long long n, const long long* Atp, const int* trow, co
       const unsigned long long e = buf[x];
       const long long src = t0 + (long long)(e & 0xffffffffull);
       const long long p = tperm[src];
-      Atj[t0 + x] = (int)(e >> 32);
+      const int row = (int)(e >> 32);
+      if (p < 0 || p >= a_nnz || row < 0 || (long long)row >= a_nrows) {
+        dev_fail(st, kDevBadIndex, 35, c);
+        continue;
+      }
+      Atj[t0 + x] = row;
       if (perm) perm[t0 + x] = p;
       if (Atx) {
         if (vbytes == 8) reinterpret_cast<double*>(Atx)[t0 + x] = reinterpret_cast<const double*>(Ax)[p];
@@ -1338,7 +1350,7 @@ cudaError_t launch_transpose_fill(const LaunchCtx& L, const MatD& A, int dtype, 
     if (e != cudaSuccess) return e;
     KKS_LAUNCHED();
     kern<<<grid_cap(n, 8, L.num_sms, 16), 256, smem, L.stream>>>(n, Atp, trow, tperm, Atj, perm, A.vx, Atx, vbytes, 1,
-                                                                 cap, nullptr, 0);
+                                                                 cap, nullptr, 0, A.nrows, A.nnz, st);
   }
   if (max_len > 256) {
     const long long cap = 16384;
@@ -1348,13 +1360,13 @@ cudaError_t launch_transpose_fill(const LaunchCtx& L, const MatD& A, int dtype, 
     if (e != cudaSuccess) return e;
     KKS_LAUNCHED();
     kern<<<grid_cap(n, 1, L.num_sms, 2), 1024, smem, L.stream>>>(n, Atp, trow, tperm, Atj, perm, A.vx, Atx, vbytes,
-                                                                 257, cap, nullptr, 0);
+                                                                 257, cap, nullptr, 0, A.nrows, A.nnz, st);
   }
   if (max_len > 16384) {
     auto kern = k_tr_sort<1024, true>;
     KKS_LAUNCHED();
     kern<<<gbuf_chunks, 1024, 0, L.stream>>>(n, Atp, trow, tperm, Atj, perm, A.vx, Atx, vbytes, 16385, gbuf_len, gbuf,
-                                            gbuf_len);
+                                            gbuf_len, A.nrows, A.nnz, st);
   }
   return cudaGetLastError();
 }

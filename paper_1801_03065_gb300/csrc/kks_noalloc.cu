@@ -12,8 +12,10 @@
 //
 // Rules of the buffer:
 //  * Its device address is looked up once per device, on that device's first
-//    call (cudaGetSymbolAddress), so make the first call on a device before
-//    any stream capture begins.
+//    call (cudaGetSymbolAddress); host code cannot use the symbol itself.
+//  * Every call synchronises its stream (twice) and reads results into host
+//    variables, so a call cannot be made while its stream is being captured
+//    into a CUDA graph.
 //  * All calls share it and it keeps the last call's contents; each call
 //    clears what must start at zero.  Calls that overlap on the GPU (other
 //    streams, other host threads) race on it: serialise them.
@@ -105,8 +107,13 @@ extern "C" spgemm_status_t spgemm_transpose_noalloc(const spgemm_csr_t* A, int64
   e = cudaMemsetAsync(d_status, 0, sizeof(DevStatus), s);
   if (e == cudaSuccess)
     e = launch_transpose_count(L, M, reinterpret_cast<long long*>(At_rowptr), tmp, &longest, d_status);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h_status, d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return to_status(e);
+  // out-of-range columns or row pointers that do not cover the entries: stop
+  // before the scatter and sort read anything through them
+  if (h_status.code == kDevBadIndex) return SPGEMM_ERR_BAD_INDEX;
+  if (h_status.code != kDevOk) return SPGEMM_ERR_DEVICE_LIMIT;
 
   unsigned long long* gbuf = nullptr;
   long long gbuf_len = 0;

@@ -158,20 +158,20 @@ def _distinct_random_rows(rng, nrows, ncols, lengths):
     total = int(rowptr[-1])
     rid = np.repeat(np.arange(nrows, dtype=np.int64), lengths)
     cols = rng.integers(0, ncols, size=total, dtype=np.int64)
+    # keys row * ncols + col, sorted; equal keys are equal values, so sorting
+    # the keys themselves orders (row, col) exactly as a stable argsort would
+    key = rid * ncols + cols
+    del rid, cols
     while True:
-        key = rid * ncols + cols
-        order = np.argsort(key, kind="stable")
-        key_s = key[order]
+        key.sort()
         dup = np.zeros(total, dtype=bool)
         if total > 1:
-            dup[1:] = key_s[1:] == key_s[:-1]
-        nd = int(dup.sum())
-        cols = cols[order]
-        rid = rid[order]
+            np.equal(key[1:], key[:-1], out=dup[1:])
+        nd = int(np.count_nonzero(dup))
         if nd == 0:
             break
-        cols[dup] = rng.integers(0, ncols, size=nd, dtype=np.int64)
-    return Csr(nrows, ncols, rowptr, cols.astype(np.int32), None)
+        key[dup] = (key[dup] // ncols) * ncols + rng.integers(0, ncols, size=nd, dtype=np.int64)
+    return Csr(nrows, ncols, rowptr, (key % ncols).astype(np.int32), None)
 
 
 def random_csr(m, n, mean_len=4.0, seed=0, dtype=np.float64, lengths=None,
