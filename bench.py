@@ -58,6 +58,7 @@ def parse_args(argv=None):
                    default="stencil27_100",
                    help="stencil27_100: the headline step; batched512: batched autotuned vs plain per-matrix")
     p.add_argument("--count", type=int, default=512, help="batched512: number of products")
+    p.add_argument("--scale", type=int, default=18, help="rmat18: R-MAT scale (18 = the full workload)")
     p.add_argument("--repeats", type=int, default=20, help="batched512: numeric-reuse repeats")
     p.add_argument("--no-extra", action="store_true",
                    help="stencil27_100: skip the rmat18 and batched512 sections of the line")
@@ -879,12 +880,14 @@ def run_single(args):
     import torch
     import workloads as w
     torch.cuda.set_device(0)
-    wl = w.config_workload(args.workload)
+    wl = w.config_workload(args.workload, **({"scale": args.scale} if args.workload == "rmat18" else {}))
     A = wl["A"]
     vdt = np.float32 if wl["dtype"] == "f32" else np.float64
     res = single_measure(A, vdt, args.steps, args.warmup, clocks=True)
     if args.workload == "rmat18":
         desc = RMAT_DESC % A.nnz
+        if args.scale != 18:
+            desc = desc.replace("scale 18", "scale %d" % args.scale)
     else:
         desc = "laplace5_64: C = A*A, A = 5-point Laplacian on a 64^2 grid (4096 rows, %d nnz, FP64 4/-1)" % A.nnz
     res["phases_ms"]["sym_num_us"] = round(1e3 * res["sym_num_ms"], 2)
