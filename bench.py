@@ -59,6 +59,8 @@ def parse_args(argv=None):
                    help="stencil27_100: the headline step; batched512: batched autotuned vs plain per-matrix")
     p.add_argument("--count", type=int, default=512, help="batched512: number of products")
     p.add_argument("--scale", type=int, default=18, help="rmat18: R-MAT scale (18 = the full workload)")
+    p.add_argument("--tune", type=int, default=1, choices=(0, 1),
+                   help="batched512: 1 autotunes the numeric bins (the workload's configuration); 0 profiling aid")
     p.add_argument("--repeats", type=int, default=20, help="batched512: numeric-reuse repeats")
     p.add_argument("--no-extra", action="store_true",
                    help="stencil27_100: skip the rmat18 and batched512 sections of the line")
@@ -70,6 +72,8 @@ def parse_args(argv=None):
                    help="stencil27_100: run the one-plan triple product after A*A on one stream")
     p.add_argument("--rap", choices=["fused", "two"], default="fused",
                    help="stencil27_100: the triple product in one plan, or as transpose + two products")
+    p.add_argument("--window", type=int, default=1, choices=(0, 1),
+                   help="1: warp rows of compressed products on sorted B use the bitmap window of column sets")
     p.add_argument("--numeric-positions", type=int, default=1, choices=(0, 1),
                    help="1: warp rows of compressed products take positions from the column sets; "
                         "0: hash-and-sort numeric kernel")
@@ -190,7 +194,7 @@ class StencilStep:
     a worker thread, while A·A runs on the current stream (the two products are
     independent); the step ends when both have."""
 
-    def __init__(self, A, P, device, positions=True, rap="fused", concurrent=True):
+    def __init__(self, A, P, device, positions=True, rap="fused", concurrent=True, window=True):
         import torch
         from paper_1801_03065_gb300 import ops
         self.torch, self.ops = torch, ops
@@ -200,8 +204,9 @@ class StencilStep:
         pos = bool(positions)
         self.positions = pos
         self.rap = rap
-        self.hAA, self.hAP, self.hRAP = (ops.SpGEMM(numeric_positions=pos), ops.SpGEMM(numeric_positions=pos),
-                                         ops.SpGEMM(numeric_positions=pos))
+        self.window = bool(window)
+        kw = dict(numeric_positions=pos, window_positions=self.window)
+        self.hAA, self.hAP, self.hRAP = ops.SpGEMM(**kw), ops.SpGEMM(**kw), ops.SpGEMM(**kw)
         self.hT = ops.SpGEMM()
         self._fm_two = None
         self.concurrent = bool(concurrent) and rap == "fused"
@@ -340,7 +345,7 @@ def run_ours(args):
     A = w.stencil3d_27pt(args.grid, seed=1)
     P = w.aggregation(args.grid, 3)
     S = StencilStep(A, P, device, positions=bool(args.numeric_positions), rap=args.rap,
-                    concurrent=not args.serial)
+                    concurrent=not args.serial, window=bool(args.window))
     for _ in range(max(args.warmup, 1)):
         S.step()
     torch.cuda.synchronize()
@@ -376,7 +381,7 @@ def run_ours(args):
     # the other products of the step, one phase at a time (each on its own handle)
     Pd = S.Pd
     if S.rap == "fused":
-        T2 = StencilStep(A, P, device, positions=S.positions, rap="two", concurrent=False)
+        T2 = StencilStep(A, P, device, positions=S.positions, rap="two", concurrent=False, window=S.window)
         T2.step()
         two_step = lambda: (T2.hT.transpose(Pd, out=T2.Pt),
                             T2.hAP.symbolic(Ad, Pd, C_rowptr=T2.rpAP),
@@ -504,7 +509,8 @@ def run_e2e(torch, S, A, P, args, world, flops_step):
     step's C (on a copy stream) overlaps the next step's upload and kernels; the
     region ends when the last read-back has landed in host memory."""
     pin = lambda x: torch.from_numpy(x).pin_memory()
-    S2 = StencilStep(A, P, S.Ad.rowptr.device, positions=S.positions, rap=S.rap, concurrent=S.concurrent)
+    S2 = StencilStep(A, P, S.Ad.rowptr.device, positions=S.positions, rap=S.rap, concurrent=S.concurrent,
+                     window=S.window)
     S2.step()
     sets = [S, S2]
     hA = [pin(A.rowptr), pin(A.colidx), pin(A.values)]
@@ -658,7 +664,7 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- batched
-def batched_measure(pairs, vdtype, steps, warmup, repeats, plain=True):
+def batched_measure(pairs, vdtype, steps, warmup, repeats, plain=True, tune=True):
     """Batched autotuned plan against the plain per-matrix meta-algorithm.
 
     NoReuse: symbolic + numeric of all products (batched: one plan, rows of all
@@ -692,7 +698,7 @@ def batched_measure(pairs, vdtype, steps, warmup, repeats, plain=True):
     hvb = torch.from_numpy(np.concatenate([y for _, y in fresh])).pin_memory()
     del fresh
 
-    hb = ops.SpGEMM(tune=True)
+    hb = ops.SpGEMM(tune=bool(tune))
     rps, nnzs = hb.batch_symbolic(As, Bs)
     Cj = [torch.empty(z, dtype=torch.int32, device=dev) for z in nnzs]
     Cx = [torch.empty(z, dtype=tdt, device=dev) for z in nnzs]
@@ -716,23 +722,26 @@ def batched_measure(pairs, vdtype, steps, warmup, repeats, plain=True):
         hb.batch_numeric(As, Bs, rps, nnzs, Cj, Cx)
 
     t_num = statistics.mean(time_region(torch, batched_num, steps))
-    side = torch.cuda.Stream()
-    side.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(side):
-        batched_num()
-    torch.cuda.current_stream().wait_stream(side)
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph):
-        va.copy_(hva, non_blocking=True)
-        vb.copy_(hvb, non_blocking=True)
-        batched_num()
+    graph = None
+    t_br = float("nan")
+    if repeats > 0:
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            batched_num()
+        torch.cuda.current_stream().wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            va.copy_(hva, non_blocking=True)
+            vb.copy_(hvb, non_blocking=True)
+            batched_num()
 
-    def batched_reuse():
-        for _ in range(repeats):
-            graph.replay()
+        def batched_reuse():
+            for _ in range(repeats):
+                graph.replay()
 
-    batched_reuse()
-    t_br = statistics.mean(time_region(torch, batched_reuse, 1))
+        batched_reuse()
+        t_br = statistics.mean(time_region(torch, batched_reuse, 1))
     hb.sync()
     gf = lambda t, n=1: round(2.0 * fm * n / (t * 1e-3) / 1e9, 3)
     # algorithmic bytes of one numeric call: A and B of every instance read
@@ -750,7 +759,8 @@ def batched_measure(pairs, vdtype, steps, warmup, repeats, plain=True):
                                  "peak": peak, "unit": "GB/s",
                                  "frac": round(bytes_num / (t_num * 1e-3) / 1e9 / peak, 4),
                                  "peak_kind": peak_kind, "algorithmic_bytes": int(bytes_num)}},
-        "numeric_reuse_graph": {"repeats": repeats, "gflops": gf(t_br, repeats), "ms": round(t_br, 3),
+        "numeric_reuse_graph": {"repeats": repeats, "gflops": gf(t_br, repeats) if repeats > 0 else None,
+                                "ms": round(t_br, 3) if repeats > 0 else None,
                                 "h2d_bytes_per_repeat": int((hva.numel() + hvb.numel()) * vbytes)},
         "tuned_bins": st["tuned_bins"], "numeric_bins": st["nbins_numeric"],
         "bin_rows_numeric": st["bin_rows_numeric"],
@@ -774,15 +784,16 @@ def batched_measure(pairs, vdtype, steps, warmup, repeats, plain=True):
         plain_step()
         torch.cuda.synchronize()
         t_p = statistics.mean(time_region(torch, plain_step, max(1, steps // 2)))
-        plain_reuse()
-        t_pr = statistics.mean(time_region(torch, plain_reuse, 1))
+        out["sym_num"].update({"plain_per_matrix_gflops": gf(t_p), "plain_ms": round(t_p, 3),
+                               "speedup": round(t_p / t_b, 3)})
+        if repeats > 0:
+            plain_reuse()
+            t_pr = statistics.mean(time_region(torch, plain_reuse, 1))
+            out["numeric_reuse_graph"].update({"plain_per_matrix_gflops": gf(t_pr, repeats),
+                                               "plain_ms": round(t_pr, 3), "speedup": round(t_pr / t_br, 3)})
         for x in hp:
             x.sync()
             x.close()
-        out["sym_num"].update({"plain_per_matrix_gflops": gf(t_p), "plain_ms": round(t_p, 3),
-                               "speedup": round(t_p / t_b, 3)})
-        out["numeric_reuse_graph"].update({"plain_per_matrix_gflops": gf(t_pr, repeats),
-                                           "plain_ms": round(t_pr, 3), "speedup": round(t_pr / t_br, 3)})
     out["gpu_launches"] = int(ops.launch_count() - l0)
     del graph
     hb.close()
@@ -802,10 +813,31 @@ def run_batched(args):
     import workloads as w
     torch.cuda.set_device(0)
     pairs = w.batched_pairs(count=args.count, seed=11, dtype=np.float64)
-    res = batched_measure(pairs, np.float64, args.steps, args.warmup, args.repeats)
+    res = batched_measure(pairs, np.float64, args.steps, args.warmup, args.repeats, tune=bool(args.tune))
     out = _base_line(args, res["sym_num"]["batched_autotuned_gflops"], res["sym_num"]["ms"],
                      BATCHED_DESC % len(pairs), "f64", {"batched512": res})
     print(json.dumps(out), flush=True)
+
+
+def run_numeric_only(args):
+    """A·A of the 27-point stencil: symbolic once, numeric twice, then numeric
+    reuse on C's pattern twice (profiling aid for ncu captures)."""
+    import torch
+    import workloads as w
+    from paper_1801_03065_gb300 import ops
+    A = w.stencil3d_27pt(args.grid, seed=1)
+    Ad = ops.CsrMatrix.from_host(A.rowptr, A.colidx, A.values, A.shape, device="cuda:0")
+    h = ops.SpGEMM(numeric_positions=bool(args.numeric_positions), window_positions=bool(args.window))
+    rp, nnz = h.symbolic(Ad, Ad)
+    C = h.numeric(Ad, Ad, rp, nnz)
+    h.sync()
+    h.numeric(Ad, Ad, rp, nnz, C.colidx, C.values)
+    h.sync()
+    h.numeric_reuse(Ad, Ad, C)
+    h.numeric_reuse(Ad, Ad, C)
+    h.sync()
+    torch.cuda.synchronize()
+    print(json.dumps({"grid": args.grid, "nnzC": nnz}))
 
 
 def _base_line(args, value, t_ms, workload, dtype, extra):

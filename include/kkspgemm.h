@@ -104,7 +104,12 @@ typedef struct {
                                     Thread-Flat-Parallel, 1 Team-Sequential with the linked-list
                                     accumulator (Section 3.1.2), 2 Thread-Parallel; with tune = 1 the
                                     tuner also times the other two per bin */
-  int32_t reserved;
+  int32_t window_positions;      /* 1 (default): with numeric_positions, warp-team rows of compressed
+                                    products whose B rows are all sorted keep their column sets in a
+                                    bitmap over the row's window of sets (first to last set, at most
+                                    1344 sets = 43 008 columns), addressed directly instead of hashed
+                                    (Section 3.1.2's dense accumulator over the row's own range);
+                                    wider rows use the hash tables.  0: hash tables only */
 } spgemm_options_t;
 
 /* Statistics of the last symbolic call (Section 4 results-table columns). */

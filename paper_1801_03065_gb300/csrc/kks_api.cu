@@ -40,7 +40,7 @@ enum BufId {
   kBufNumPool2, kBufNumPool3, kBufStatus, kBufMaskRows, kBufMaskHist, kBufMaskPool, kBufTrTmp,
   kBufTrPool, kBufReuseRows, kBufReusePool, kBufBinCnt, kBufBinOfs, kBufMcCnt, kBufMcYcp, kBufMcCsi, kBufMcCs,
   kBufMcMax, kBufRapRf, kBufRapRtp, kBufRapRti, kBufRapRpe, kBufRapW, kBufRapCnt, kBufRapSymRows,
-  kBufRapNumRows, kBufRapMeta, kBufRapTmp, kBufMcRows, kBufFetch, kNumBufs
+  kBufRapNumRows, kBufRapMeta, kBufRapTmp, kBufMcRows, kBufFetch, kBufLongB, kBufLongA, kNumBufs
 };
 
 // Row bins of a masked product, cached for numeric reuse on one pattern.
@@ -90,6 +90,7 @@ struct BinRun {
   long long off, count;
   int hash;   // LpHash mode used for this bin (the tuner may change it)
   int part = 0;   // CTA hash classes: partitioning scheme (0 flat, 1 Team-Sequential + LL, 2 Thread-Parallel)
+  int window = 0;   // W32 positions rows: bitmap window over the row's column sets
 };
 
 constexpr int kRing = 8;
@@ -415,6 +416,22 @@ void set_default_options(spgemm_options_t* o) {
   o->verbose = 0;
   o->numeric_positions = 1;
   o->cta_partition = 0;
+  o->window_positions = 1;
+}
+
+// Long-row queue in buffer id (rows first, then three counters).
+LongQueue long_queue(kks_handle* h, int id, long long rows) {
+  LongQueue q;
+  q.list = B<int>(h, id);
+  const size_t off = (sizeof(int) * (size_t)(rows + 1) + 15) & ~size_t(15);
+  q.ctr = reinterpret_cast<unsigned long long*>(reinterpret_cast<unsigned char*>(h->buf[id]) + off);
+  return q;
+}
+
+// The 15 % rule of Section 3.2 for one product (mode: the option compression).
+int compress_decision(int mode, double threshold, long long fm, long long fmc) {
+  if (mode == 1) return 1;
+  return (mode < 0 && fm > 0 && (double)fmc < threshold * (double)fm) ? 1 : 0;
 }
 
 // Upload the instance table through a pinned ring slot (numeric path).
@@ -528,6 +545,8 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
   KKS_ST(ensure(h, kBufNumRows, sizeof(int) * (totalA + 1)));
   KKS_ST(ensure(h, kBufStatus, sizeof(DevStatus)));
   KKS_ST(ensure(h, kBufFetch, 16));
+  KKS_ST(ensure(h, kBufLongB, sizeof(int) * (totalB + 1) + 64));
+  KKS_ST(ensure(h, kBufLongA, sizeof(int) * (totalA + 1) + 64));
   KKS_ST(ensure(h, kBufCsi, 16));
   KKS_ST(ensure(h, kBufCs, 16));
 
@@ -556,17 +575,48 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
   // (1) compression pass 1 and (2) row statistics
   if (comp_on) {
     KKS_CU(launch_compress_count(L, P, totalB, B<long long>(h, kBufCnt),
-                                 B<unsigned long long>(h, kBufInstStats) + 4 * ni));
+                                 B<unsigned long long>(h, kBufInstStats) + 4 * ni, long_queue(h, kBufLongB, totalB)));
     KKS_CU(launch_scan(L, B<long long>(h, kBufCnt), B<long long>(h, kBufBcp), totalB, h->buf[kBufScanTmp]));
   }
   KKS_CU(launch_row_stats(L, P, totalA, comp_on ? 1 : 0, B<long long>(h, kBufRf),
-                          comp_on ? B<long long>(h, kBufRfc) : nullptr, B<unsigned long long>(h, kBufInstStats)));
+                          comp_on ? B<long long>(h, kBufRfc) : nullptr, B<unsigned long long>(h, kBufInstStats),
+                          long_queue(h, kBufLongA, totalA)));
   unsigned long long* h_stats = (unsigned long long*)rd;
   long long* h_nbc = (long long*)(rd + sizeof(unsigned long long) * 4 * ni);
   DevStatus* h_status = (DevStatus*)(rd + sizeof(unsigned long long) * (4 * ni + 2 * ni + 2 * kNumBins + 8));
   unsigned long long* h_unsorted = (unsigned long long*)(rd + sizeof(unsigned long long) * (4 * ni + 2 * ni + 2 * kNumBins));
+  unsigned long long* d_hist = B<unsigned long long>(h, kBufHist);
+  unsigned long long* h_hist = (unsigned long long*)(rd + sizeof(unsigned long long) * (4 * ni + 2 * ni));
   *h_nbc = 0;
   *h_unsorted = 1;
+  BinCfg cfg_c = sym_cfg(h, 1), cfg_u = sym_cfg(h, 0);
+  std::vector<unsigned long long> hist(2 * kNumBins, 0);
+  // With compression on and no per-problem rule, the 15 % rule is taken on the
+  // device and the compressed B is sized by nnz(B): the statistics are read at
+  // the same synchronisation as the symbolic bins (one host round trip fewer).
+  long long nnzB_all = 0;
+  for (int b = 0; b < count; ++b) nnzB_all += Bm[b].nnz;
+  bool merged = comp_on && h->opt.method != 1;
+  if (merged && (ensure(h, kBufCsi, sizeof(int) * (nnzB_all + 1)) != SPGEMM_OK ||
+                 ensure(h, kBufCs, sizeof(unsigned) * (nnzB_all + 1)) != SPGEMM_OK)) {
+    merged = false;   // no room for the bound: size it by the counted runs after a synchronisation
+    KKS_ST(ensure(h, kBufCsi, 16));
+    KKS_ST(ensure(h, kBufCs, 16));
+  }
+  if (merged) {
+    P = prob(h);
+    KKS_CU(launch_decide_compression(L, B<InstD>(h, kBufInst), B<unsigned long long>(h, kBufInstStats), count,
+                                     h->opt.compression, h->opt.compress_threshold));
+    KKS_CU(launch_compress_fill(L, P, totalB, B<int>(h, kBufCsi), B<unsigned>(h, kBufCs), long_queue(h, kBufLongB, totalB)));
+    for (int pass = 0; pass < 2; ++pass) {
+      BinCfg c = pass ? cfg_c : cfg_u;
+      KKS_CU(launch_bin_count(L, P, totalA, pass ? 2 : 3, B<long long>(h, kBufRf), B<long long>(h, kBufRfc), nullptr,
+                              c, d_hist + pass * kNumBins, B<long long>(h, kBufBinCnt) + pass * (nbc + 1)));
+      KKS_CU(launch_scan(L, B<long long>(h, kBufBinCnt) + pass * (nbc + 1),
+                         B<long long>(h, kBufBinOfs) + pass * (nbc + 1), nbc, h->buf[kBufScanTmp]));
+    }
+    KKS_CU(to_host(h, h_hist, d_hist, sizeof(unsigned long long) * 2 * kNumBins, s));
+  }
   KKS_CU(to_host(h, h_stats, h->buf[kBufInstStats], sizeof(unsigned long long) * 4 * ni, s));
   if (comp_on) {
     KKS_CU(to_host(h, h_nbc, B<long long>(h, kBufBcp) + totalB, sizeof(long long), s));
@@ -576,8 +626,10 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
   KKS_CU(cudaStreamSynchronize(s));
   KKS_ST(consume_status(h, h_status, s));
   h->b_sorted = comp_on && *h_unsorted == 0;
+  if (merged)
+    for (int t = 0; t < 2 * kNumBins; ++t) hist[t] = h_hist[t];
 
-  // (3) the 15 % rule, per product
+  // (3) the 15 % rule, per product (the same test as the device's)
   long long fm_all = 0, fmc_all = 0, maxrf_all = 0, maxrfc_all = 0;
   int any_comp = 0, ncomp = 0;
   for (int b = 0; b < count; ++b) {
@@ -586,47 +638,42 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
     fmc_all += fmc;
     maxrf_all = std::max(maxrf_all, (long long)h_stats[4 * b + 1]);
     maxrfc_all = std::max(maxrfc_all, (long long)h_stats[4 * b + 3]);
-    int c = 0;
-    if (h->opt.compression == 1) c = 1;
-    else if (h->opt.compression < 0 && fm > 0 && (double)fmc < h->opt.compress_threshold * (double)fm) c = 1;
+    int c = compress_decision(h->opt.compression, h->opt.compress_threshold, fm, fmc);
     h->inst[b].compressed = c;
     any_comp |= c;
     ncomp += c;
   }
-  if (any_comp) {
-    const long long nbc = *h_nbc;
-    KKS_ST(ensure(h, kBufCsi, sizeof(int) * (nbc + 1)));
-    KKS_ST(ensure(h, kBufCs, sizeof(unsigned) * (nbc + 1)));
-    P = prob(h);
-    memcpy(up, h->inst.data(), sizeof(InstD) * count);
-    KKS_CU(cudaMemcpyAsync(h->buf[kBufInst], up, sizeof(InstD) * count, cudaMemcpyHostToDevice, s));
-    KKS_CU(launch_compress_fill(L, P, totalB, B<int>(h, kBufCsi), B<unsigned>(h, kBufCs)));
-  }
-
-  // (4) symbolic bins: the compressed and plain rows use separate bin ranges
-  BinCfg cfg_c = sym_cfg(h, 1), cfg_u = sym_cfg(h, 0);
-  if (h->opt.method == 1 && totalA > 0) {
-    const double avg = (double)fm_all / (double)totalA;
-    plain_rule(cfg_u, avg, (double)fm_all / 8.0 / (double)totalA);
-    plain_rule(cfg_c, avg, (double)fmc_all / 8.0 / (double)totalA);
-  }
-  unsigned long long* d_hist = B<unsigned long long>(h, kBufHist);
-  unsigned long long* h_hist = (unsigned long long*)(rd + sizeof(unsigned long long) * (4 * ni + 2 * ni));
-  // one launch per compression flag keeps the device bin function simple
-  // (rows of the other kind land in the class-none bin of that launch and are ignored)
-  std::vector<unsigned long long> hist(2 * kNumBins, 0);
-  for (int pass = 0; pass < 2; ++pass) {
-    if (pass == 1 && !any_comp) break;
-    if (pass == 0 && ncomp == count && count > 0) continue;
-    KKS_CU(cudaMemsetAsync(d_hist, 0, sizeof(unsigned long long) * kNumBins, s));
-    BinCfg c = pass ? cfg_c : cfg_u;
-    KKS_CU(launch_bin_count(L, P, totalA, pass ? 2 : 3, B<long long>(h, kBufRf), B<long long>(h, kBufRfc), nullptr, c,
-                            d_hist, B<long long>(h, kBufBinCnt) + pass * (nbc + 1)));
-    KKS_CU(launch_scan(L, B<long long>(h, kBufBinCnt) + pass * (nbc + 1), B<long long>(h, kBufBinOfs) + pass * (nbc + 1),
-                       nbc, h->buf[kBufScanTmp]));
-    KKS_CU(to_host(h, h_hist, d_hist, sizeof(unsigned long long) * kNumBins, s));
-    KKS_CU(cudaStreamSynchronize(s));
-    for (int t = 0; t < kNumBins; ++t) hist[pass * kNumBins + t] = h_hist[t];
+  if (!merged) {
+    if (any_comp) {
+      const long long nbcomp = *h_nbc;
+      KKS_ST(ensure(h, kBufCsi, sizeof(int) * (nbcomp + 1)));
+      KKS_ST(ensure(h, kBufCs, sizeof(unsigned) * (nbcomp + 1)));
+      P = prob(h);
+      memcpy(up, h->inst.data(), sizeof(InstD) * count);
+      KKS_CU(cudaMemcpyAsync(h->buf[kBufInst], up, sizeof(InstD) * count, cudaMemcpyHostToDevice, s));
+      KKS_CU(launch_compress_fill(L, P, totalB, B<int>(h, kBufCsi), B<unsigned>(h, kBufCs), long_queue(h, kBufLongB, totalB)));
+    }
+    // (4) symbolic bins: the compressed and plain rows use separate bin ranges
+    if (h->opt.method == 1 && totalA > 0) {
+      const double avg = (double)fm_all / (double)totalA;
+      plain_rule(cfg_u, avg, (double)fm_all / 8.0 / (double)totalA);
+      plain_rule(cfg_c, avg, (double)fmc_all / 8.0 / (double)totalA);
+    }
+    // one launch per compression flag keeps the device bin function simple
+    // (rows of the other kind land in the class-none bin of that launch and are ignored)
+    for (int pass = 0; pass < 2; ++pass) {
+      if (pass == 1 && !any_comp) break;
+      if (pass == 0 && ncomp == count && count > 0) continue;
+      KKS_CU(cudaMemsetAsync(d_hist, 0, sizeof(unsigned long long) * kNumBins, s));
+      BinCfg c = pass ? cfg_c : cfg_u;
+      KKS_CU(launch_bin_count(L, P, totalA, pass ? 2 : 3, B<long long>(h, kBufRf), B<long long>(h, kBufRfc), nullptr,
+                              c, d_hist, B<long long>(h, kBufBinCnt) + pass * (nbc + 1)));
+      KKS_CU(launch_scan(L, B<long long>(h, kBufBinCnt) + pass * (nbc + 1),
+                         B<long long>(h, kBufBinOfs) + pass * (nbc + 1), nbc, h->buf[kBufScanTmp]));
+      KKS_CU(to_host(h, h_hist, d_hist, sizeof(unsigned long long) * kNumBins, s));
+      KKS_CU(cudaStreamSynchronize(s));
+      for (int t = 0; t < kNumBins; ++t) hist[pass * kNumBins + t] = h_hist[t];
+    }
   }
   // offsets over both passes (class-none rows are not listed)
   std::vector<long long> off(2 * kNumBins + 1, 0);
@@ -664,6 +711,7 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
     S.compressed = comp;
     S.max_occ = h->opt.l1_max_occupancy;
     S.fetch = B<unsigned long long>(h, kBufFetch);
+    S.window = (comp && h->b_sorted && h->opt.window_positions && h->opt.numeric_positions) ? 1 : 0;
     long long kmax = 0;
     for (int b = 0; b < count; ++b) kmax = std::max<long long>(kmax, h->inst[b].k);
     // dense rows only come from products whose bitmap fits (checked per row)
@@ -738,7 +786,8 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
     // take their output positions from the column sets
     const int pos = (positions_ok && (cls == kClsW8 || cls == kClsW32)) ? 1 : 0;
     h->num_bins.push_back(BinRun{cls, bin_logT(t), pos, noff[t], cnt, h->opt.hash_function,
-                                 (cls == kClsC256 || cls == kClsC1024) ? h->opt.cta_partition : 0});
+                                 (cls == kClsC256 || cls == kClsC1024) ? h->opt.cta_partition : 0,
+                                 (pos && cls == kClsW32 && h->b_sorted && h->opt.window_positions) ? 1 : 0});
     if (cls == kClsSpill) {
       spill_rows += cnt;
       spill_logT = std::max(spill_logT, bin_logT(t));
@@ -826,6 +875,7 @@ cudaError_t launch_bin(kks_handle* h, const BinRun& r, cudaStream_t s) {
   S.b_sorted = h->b_sorted ? 1 : 0;
   S.fetch = B<unsigned long long>(h, kBufFetch);
   S.part = (r.cls == kClsC256 || r.cls == kClsC1024) ? r.part : 0;
+  S.window = (S.positions && r.cls == kClsW32) ? r.window : 0;
   if (r.cls == kClsDense) {
     S.kwords_max = h->num_dense_kw;
   } else if (r.cls == kClsSpill) {
@@ -864,7 +914,7 @@ spgemm_status_t tune_numeric(kks_handle* h, cudaStream_t s) {
         p.off = r.off;
         p.count = r.count;
         if (p.cls != r.cls || p.logT != r.logT || p.hash != r.hash || p.compressed != r.compressed ||
-            p.part != r.part)
+            p.part != r.part || p.window != r.window)
           ++changed;
         r = p;
         cached = true;
@@ -881,6 +931,12 @@ spgemm_status_t tune_numeric(kks_handle* h, cudaStream_t s) {
     if (h->positions_ok && (r.cls == kClsW8 || r.cls == kClsW32)) {
       x = r;
       x.compressed = 1 - r.compressed;   // column-set positions against the hash-and-sort kernel
+      x.window = 0;
+      cand.push_back(x);
+    }
+    if (r.compressed && r.cls == kClsW32 && h->b_sorted) {
+      x = r;
+      x.window = 1 - r.window;   // bitmap window against hash tables of column sets
       cand.push_back(x);
     }
     if (r.cls == kClsC256 || r.cls == kClsC1024) {
@@ -905,6 +961,7 @@ spgemm_status_t tune_numeric(kks_handle* h, cudaStream_t s) {
       x = r;
       x.cls = up;
       if (up != kClsW32) x.compressed = 0;
+      x.window = (x.compressed && up == kClsW32 && h->b_sorted && h->opt.window_positions) ? 1 : 0;
       cand.push_back(x);
     }
     const int down = r.cls == kClsW32 ? kClsW8 : r.cls == kClsC256 ? kClsW32 : r.cls == kClsC1024 ? kClsC256 : 0;
@@ -912,6 +969,7 @@ spgemm_status_t tune_numeric(kks_handle* h, cudaStream_t s) {
       x = r;
       x.cls = down;
       x.compressed = (h->positions_ok && (down == kClsW8 || down == kClsW32)) ? 1 : 0;
+      x.window = (x.compressed && down == kClsW32 && h->b_sorted && h->opt.window_positions) ? 1 : 0;
       cand.push_back(x);
     }
     float best = 1e30f;
@@ -933,7 +991,7 @@ spgemm_status_t tune_numeric(kks_handle* h, cudaStream_t s) {
       }
     }
     if (pick.cls != r.cls || pick.logT != r.logT || pick.hash != r.hash || pick.compressed != r.compressed ||
-        pick.part != r.part)
+        pick.part != r.part || pick.window != r.window)
       ++changed;
     r = pick;
     h->tune_cache.push_back({cls0, logT0, h->dtype, pos0, r.count, pick});
@@ -1112,6 +1170,7 @@ spgemm_status_t run_masked_plan(kks_handle* h, const MaskedD& M, int dtype, int 
     S.nrows = plan.cnt[b];
     S.dtype = dtype;
     S.positions = (plan.sorted && (S.cls == kClsW8 || S.cls == kClsW32)) ? 1 : 0;
+    S.window = (S.positions && S.cls == kClsW32 && h->opt.window_positions) ? 1 : 0;
     if (S.cls == kClsSpill) {
       S.pool = h->buf[pool_buf];
       S.chunk_slots = plan.gslots;
@@ -1145,7 +1204,7 @@ spgemm_status_t spgemm_handle_create(spgemm_handle_t* out, const spgemm_options_
       h->opt.compression < -1 || h->opt.compression > 1 || h->opt.hash_function < 0 || h->opt.hash_function > 1 ||
       h->opt.slots_per_key_log2 < 0 || h->opt.slots_per_key_log2 > 4 || h->opt.numeric_positions < 0 ||
       h->opt.cta_partition < 0 || h->opt.cta_partition > 2 ||
-      h->opt.numeric_positions > 1) {
+      h->opt.numeric_positions > 1 || h->opt.window_positions < 0 || h->opt.window_positions > 1) {
     delete h;
     return SPGEMM_ERR_INVALID_ARG;
   }

@@ -371,6 +371,63 @@ __device__ __forceinline__ int union_chunk(unsigned team_mask, int lane, int* pr
   return BITS ? nbits : fresh;
 }
 
+// Union of compressed products into a bitmap window (direct addressing, no
+// hashing): lane t holds the compressed range [qs, qs + ql) of the B row of its
+// entry of the chunk; the set bits of every product go into bits[csi - smin]
+// (a window of span words starting at set smin).  Products are spread flat
+// over the lanes as in union_chunk.  With COUNT the return value is the number
+// of column bits this lane was first to set (their team sum is the row size).
+template <int TW, bool COUNT>
+__device__ __forceinline__ int wb_union_chunk(unsigned team_mask, int lane, int* pre, long long* qsv, long long qs,
+                                              int ql, const int* __restrict__ csi, const unsigned* __restrict__ cs,
+                                              unsigned* bits, unsigned smin, unsigned span, DevStatus* status,
+                                              int code, long long g) {
+  int ex = ql;
+#pragma unroll
+  for (int d = 1; d < TW; d <<= 1) {
+    const int y = __shfl_up_sync(team_mask, ex, d, TW);
+    if (lane >= d) ex += y;
+  }
+  const int tot = __shfl_sync(team_mask, ex, TW - 1, TW);
+  pre[lane] = ex - ql;
+  qsv[lane] = qs;
+  if (lane == 0) pre[TW] = tot;
+  __syncwarp(team_mask);
+  int nbits = 0;
+  int t = 0;
+  for (int xb = 0; xb < tot; xb += kUnionPasses * TW) {
+    unsigned w[kUnionPasses];
+    unsigned m[kUnionPasses];
+#pragma unroll
+    for (int u = 0; u < kUnionPasses; ++u) {
+      const int x = xb + u * TW + lane;
+      w[u] = 0xffffffffu;
+      m[u] = 0u;
+      if (x < tot) {
+        while (pre[t + 1] <= x) ++t;
+        const long long q = qsv[t] + (x - pre[t]);
+        w[u] = (unsigned)csi[q] - smin;
+        m[u] = cs[q];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kUnionPasses; ++u) {
+      if (w[u] < span) {
+        if (COUNT) {
+          const unsigned old = atomicOr(bits + w[u], m[u]);
+          nbits += __popc(m[u] & ~old);
+        } else {
+          atomicOr(bits + w[u], m[u]);
+        }
+      } else if (m[u] != 0u) {
+        dev_fail(status, kDevBadIndex, code, g);
+      }
+    }
+  }
+  __syncwarp(team_mask);
+  return nbits;
+}
+
 // Tables of 16-byte slots (column-set index, set bits, base, unused): the
 // place of column c in a sorted row is base(c >> 5) + the number of set bits
 // below bit c & 31.  Lookups once the table is complete.

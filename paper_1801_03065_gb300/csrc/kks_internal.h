@@ -119,14 +119,28 @@ inline unsigned resident_grid(K kernel, int threads, size_t smem, int num_sms, l
 cudaError_t launch_copy_to_host(const LaunchCtx&, void* dst_mapped, const void* src, size_t bytes);
 
 // prep: statistics, compression, scans, binning
+// A queue of the rows longer than 1024 entries (row indices of A or B, and
+// three counters) that the per-block passes hand to a second launch where
+// whole warps take them one at a time.
+struct LongQueue {
+  int* list;                 // >= totalA (totalB) entries
+  unsigned long long* ctr;   // 3 counters
+};
 // per-row compressed lengths; *unsorted += rows of B whose columns do not increase
 cudaError_t launch_compress_count(const LaunchCtx&, const ProbD&, long long totalB, long long* cnt,
-                                  unsigned long long* unsorted);
-cudaError_t launch_compress_fill(const LaunchCtx&, const ProbD&, long long totalB, int* csi, unsigned* cs);
+                                  unsigned long long* unsorted, const LongQueue& q);
+// (the queue of the preceding count pass)
+cudaError_t launch_compress_fill(const LaunchCtx&, const ProbD&, long long totalB, int* csi, unsigned* cs,
+                                 const LongQueue& q);
+// the 15 % rule on the device: inst[b].compressed from the row statistics
+// (inst_stats[4b] = f_m, [4b + 2] = f_m on the compressed B); mode is the
+// option compression (-1 auto, 1 always)
+cudaError_t launch_decide_compression(const LaunchCtx&, InstD* inst, const unsigned long long* inst_stats, int count,
+                                      int mode, double threshold);
 // rf[i] = multiplications of row i of A*B (one plain product, no instance table)
 cudaError_t launch_row_flops(const LaunchCtx&, const MatD& A, const MatD& B, long long* rf, DevStatus* st);
 cudaError_t launch_row_stats(const LaunchCtx&, const ProbD&, long long totalA, int use_bc,
-                             long long* rf, long long* rfc, unsigned long long* inst_stats);
+                             long long* rf, long long* rfc, unsigned long long* inst_stats, const LongQueue& q);
 // exclusive scan of in[0, n) into out[0, n], out[n] = total; tmp >= scan_tmp_bytes(n)
 size_t scan_tmp_bytes(long long n);
 cudaError_t launch_scan(const LaunchCtx&, const long long* in, long long* out, long long n, void* tmp);
@@ -208,6 +222,8 @@ struct SymLaunch {
   long long l2_chunk_slots;
   int nchunks;
   unsigned long long* fetch;   // CTA classes: row counter (zeroed by the launcher)
+  int window;            // compressed W32 rows with every B row sorted: bitmap-window kernel
+  int pad;
 };
 cudaError_t launch_symbolic(const LaunchCtx&, const ProbD&, const SymLaunch&, long long* rowsize);
 
@@ -231,7 +247,8 @@ struct NumLaunch {
   unsigned long long* fetch;   // CTA classes: row counter (zeroed by the launcher)
   int part;              // CTA hash classes: 0 flat (Thread-Flat-Parallel), 1 Team-Sequential + LL,
                          // 2 Thread-Parallel (Section 3.1.1)
-  int pad;
+  int window;            // warp positions rows with b_sorted: bitmap-window kernel (rows whose set
+                         // window is too wide fall back to the hash path inside it)
 };
 cudaError_t launch_numeric(const LaunchCtx&, const ProbD&, const NumLaunch&);
 
@@ -256,6 +273,7 @@ struct MaskedLaunch {
   long long chunk_slots;
   int nchunks;
   int positions;         // warp classes: S's rows are sorted, places from its column sets
+  int window;            // with positions, W32 rows: bitmap window of S(i,:)'s column sets
 };
 cudaError_t launch_pattern_unsorted(const LaunchCtx&, const MaskedD&, long long nrows, unsigned long long* count);
 // stable binning of the pattern's rows (bcnt / bofs as launch_bin_count / launch_bin_scatter)

@@ -299,15 +299,13 @@ __host__ __device__ size_t mskp_team_bytes(int T) {
          al16(sizeof(ChunkScratch<TW, VT>)) + al16((size_t)TW * sizeof(VT));
 }
 
+// One row i of S by the team, in its shared memory at base
+// (mskp_team_bytes<TW, VT>(2^logT) bytes).
 template <int TW, typename VT>
-__global__ void __launch_bounds__(256, 4) k_masked_pos(MaskedD M, const int* __restrict__ rows, long long nrows,
-                                                       int logT) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  Team<TW> tm;
+__device__ __forceinline__ void masked_pos_row(const Team<TW>& tm, const MaskedD& M, unsigned char* base, int logT,
+                                               const LpHash& hs, long long i) {
   const int T = 1 << logT;
-  const LpHash hs(logT, M.hash_mode);
   const int half = T / 2 > 0 ? T / 2 : 1;
-  unsigned char* base = smem + (size_t)tm.id * mskp_team_bytes<TW, VT>(T);
   int* keys = reinterpret_cast<int*>(base);
   int2* mb = reinterpret_cast<int2*>(base + al16((size_t)T * 4));   // (set bits, position of the set's first column)
   const size_t tabb = al16((size_t)T * 4) + al16((size_t)T * 8);
@@ -325,10 +323,7 @@ __global__ void __launch_bounds__(256, 4) k_masked_pos(MaskedD M, const int* __r
   const int lane_base = (threadIdx.x & 31) & ~(TW - 1);
   const unsigned tbits = (TW == 32) ? 0xffffffffu : ((1u << TW) - 1u);
 
-  const long long team = (long long)blockIdx.x * tm.per_cta + tm.id;
-  const long long nteams = (long long)gridDim.x * tm.per_cta;
-  for (long long r = team; r < nrows; r += nteams) {
-    const long long i = rows[r];
+  {
     const long long s0 = M.Sp[i];
     const int s = (int)(M.Sp[i + 1] - s0);
     const long long a0 = rp_at(M.X, i), a1 = rp_at(M.X, i + 1);
@@ -490,6 +485,228 @@ __global__ void __launch_bounds__(256, 4) k_masked_pos(MaskedD M, const int* __r
     }
     for (int p = tm.lane; p < sw; p += TW) out[s0 + p] = acc[p];
     __syncwarp(tm.mask);
+  }
+}
+
+template <int TW, typename VT>
+__global__ void __launch_bounds__(256, 4) k_masked_pos(MaskedD M, const int* __restrict__ rows, long long nrows,
+                                                       int logT) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Team<TW> tm;
+  const LpHash hs(logT, M.hash_mode);
+  unsigned char* base = smem + (size_t)tm.id * mskp_team_bytes<TW, VT>(1 << logT);
+  const long long team = (long long)blockIdx.x * tm.per_cta + tm.id;
+  const long long nteams = (long long)gridDim.x * tm.per_cta;
+  for (long long r = team; r < nrows; r += nteams) masked_pos_row<TW, VT>(tm, M, base, logT, hs, rows[r]);
+}
+
+// Warp teams on a sorted pattern whose row S(i,:) spans at most kMwLimit
+// column sets (first to last column): the sets of S(i,:) are kept in a bitmap
+// window addressed directly by set index, each word with the position of its
+// first column in S(i,:), so the place of a product's column is that position
+// + the set bits below it, and a column outside the pattern meets a clear bit
+// (the words of the row are cleared after it).  No hashing and no probing;
+// wider rows take the hashed path (masked_pos_row) in the same shared memory.
+constexpr int kMwLimit = 1344;
+constexpr int kMwTeams = 4;
+
+template <typename VT>
+__host__ __device__ size_t mskw_team_bytes(int T) {
+  const int half = T / 2 > 0 ? T / 2 : 1;
+  const size_t wb = al16((size_t)kMwLimit * 4) + al16((size_t)kMwLimit * 2) + al16((size_t)half * sizeof(VT)) +
+                    al16(sizeof(ChunkScratch<32, VT>)) + al16(32 * sizeof(VT));
+  const size_t hp = mskp_team_bytes<32, VT>(T);
+  return wb > hp ? wb : hp;
+}
+
+template <typename VT>
+__global__ void __launch_bounds__(32 * kMwTeams, 5) k_masked_win(MaskedD M, const int* __restrict__ rows,
+                                                                 long long nrows, int logT) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Team<32> tm;
+  const int T = 1 << logT;
+  const int half = T / 2 > 0 ? T / 2 : 1;
+  const LpHash hs(logT, M.hash_mode);
+  unsigned char* base = smem + (size_t)tm.id * mskw_team_bytes<VT>(T);
+  unsigned* wbits = reinterpret_cast<unsigned*>(base);
+  unsigned short* wpos = reinterpret_cast<unsigned short*>(base + al16((size_t)kMwLimit * 4));
+  VT* acc = reinterpret_cast<VT*>(base + al16((size_t)kMwLimit * 4) + al16((size_t)kMwLimit * 2));
+  ChunkScratch<32, VT>* csc =
+      reinterpret_cast<ChunkScratch<32, VT>*>(reinterpret_cast<unsigned char*>(acc) + al16((size_t)half * sizeof(VT)));
+  VT* xchg = reinterpret_cast<VT*>(reinterpret_cast<unsigned char*>(csc) + al16(sizeof(ChunkScratch<32, VT>)));
+  const VT* __restrict__ Xx = reinterpret_cast<const VT*>(M.X.vx);
+  const VT* __restrict__ Yx = reinterpret_cast<const VT*>(M.Y.vx);
+  auto XV = [&](long long p) -> VT { return Xx[M.xperm ? M.xperm[p] : p]; };
+  auto YV = [&](long long q) -> VT { return Yx[M.yperm ? M.yperm[q] : q]; };
+  const int* __restrict__ Yj = M.Y.cj;
+  const int* __restrict__ Xj = M.X.cj;
+  VT* __restrict__ out = reinterpret_cast<VT*>(M.out);
+  const int lane = tm.lane;
+  const unsigned lane_lt = (1u << lane) - 1u;
+  const unsigned full = 0xffffffffu;
+  bool clean = false;
+  const long long team = (long long)blockIdx.x * tm.per_cta + tm.id;
+  const long long nteams = (long long)gridDim.x * tm.per_cta;
+  for (long long r = team; r < nrows; r += nteams) {
+    const long long i = rows[r];
+    const long long s0 = M.Sp[i];
+    const int s = (int)(M.Sp[i + 1] - s0);
+    if (s <= 0) continue;
+    const unsigned smin = (unsigned)M.Sj[s0] >> 5, smax = (unsigned)M.Sj[s0 + s - 1] >> 5;
+    if (smin > smax || smax - smin >= (unsigned)kMwLimit || s > half) {
+      masked_pos_row<32, VT>(tm, M, base, logT, hs, i);
+      clean = false;
+      __syncwarp();
+      continue;
+    }
+    const unsigned span = smax - smin + 1u;
+    const long long a0 = rp_at(M.X, i), a1 = rp_at(M.X, i + 1);
+    // the first chunk of X(i,:) is fetched before the pattern is placed
+    long long bs = 0;
+    int len = 0;
+    VT av = VT(0);
+    if (a0 + lane < a1) {
+      const int j = Xj[a0 + lane];
+      bs = rp_at(M.Y, j);
+      len = (int)(rp_at(M.Y, j + 1) - bs);
+      av = XV(a0 + lane);
+    }
+    if (!clean) {
+      uint4* c4 = reinterpret_cast<uint4*>(wbits);
+      for (int x = lane; x < kMwLimit / 4; x += 32) c4[x] = make_uint4(0u, 0u, 0u, 0u);
+      clean = true;
+      __syncwarp();
+    }
+    for (int x = lane; x < s; x += 32) acc[x] = VT(0);
+    // the pattern's sets: the first column of each set records its position,
+    // then every column sets its bit
+    for (int pb = 0; pb < s; pb += 32) {
+      const int p = pb + lane;
+      const int col = p < s ? M.Sj[s0 + p] : -1;
+      int prev = __shfl_up_sync(full, col, 1);
+      if (lane == 0) prev = pb > 0 ? M.Sj[s0 + pb - 1] : -1;
+      const unsigned w = (unsigned)(col >> 5) - smin;
+      if (col >= 0 && p > 0 && prev >= col) dev_fail(M.status, kDevBadIndex, 40, i);   // not sorted
+      const bool ok = col >= 0 && w < span;
+      if (ok && (p == 0 || (prev >> 5) != (col >> 5))) wpos[w] = (unsigned short)p;
+      __syncwarp();
+      if (ok) atomicOr(wbits + w, 1u << (col & 31));
+      __syncwarp();
+    }
+    auto pos_of = [&](int c) -> int {
+      const unsigned w = (unsigned)(c >> 5) - smin;
+      if (w >= span) return -1;
+      const unsigned m = wbits[w];
+      const unsigned bit = 1u << (c & 31);
+      if (!(m & bit)) return -1;
+      return (int)wpos[w] + __popc(m & (bit - 1u));
+    };
+    for (long long c = a0; c < a1; c += 32) {
+      if (c != a0) {
+        const long long p = c + lane;
+        bs = 0;
+        len = 0;
+        av = VT(0);
+        if (p < a1) {
+          const int j = Xj[p];
+          bs = rp_at(M.Y, j);
+          len = (int)(rp_at(M.Y, j + 1) - bs);
+          av = XV(p);
+        }
+      }
+      const int nc = (a1 - c) < 32 ? (int)(a1 - c) : 32;
+      const int tot = (int)__reduce_add_sync(full, (unsigned)len);
+      if (2 * tot >= nc * 32) {
+        constexpr int kU = 4;
+        for (int t0 = 0; t0 < nc; t0 += kU) {
+          int key[kU], lent[kU];
+          long long bst[kU];
+          VT at[kU], yv[kU];
+#pragma unroll
+          for (int u = 0; u < kU; ++u) {
+            const int t = (t0 + u < nc) ? t0 + u : nc - 1;
+            bst[u] = __shfl_sync(full, bs, t);
+            const int l = __shfl_sync(full, len, t);
+            at[u] = __shfl_sync(full, av, t);
+            lent[u] = (t0 + u < nc) ? l : 0;
+            key[u] = -1;
+            yv[u] = VT(0);
+            if (lane < lent[u]) {
+              key[u] = Yj[bst[u] + lane];
+              yv[u] = YV(bst[u] + lane);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < kU; ++u) {
+            if (key[u] >= 0) {
+              const int o = pos_of(key[u]);
+              if (o >= 0) acc[o] = fma_acc(at[u], yv[u], acc[o]);
+            }
+            for (int x = lane + 32; x < lent[u]; x += 32) {
+              const int o = pos_of(Yj[bst[u] + x]);
+              if (o >= 0) acc[o] = fma_acc(at[u], YV(bst[u] + x), acc[o]);
+            }
+            __syncwarp();
+          }
+        }
+      } else {
+        int ex = len;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const int y = __shfl_up_sync(full, ex, d);
+          if (lane >= d) ex += y;
+        }
+        ex -= len;
+        csc->pre[lane] = ex;
+        csc->bs[lane] = bs;
+        csc->av[lane] = av;
+        if (lane == 0) csc->pre[32] = tot;
+        __syncwarp();
+        int t = 0;
+        for (int xb = 0; xb < tot; xb += 32) {
+          const int x = xb + lane;
+          int q = -1 - lane;
+          VT v = VT(0);
+          if (x < tot) {
+            while (csc->pre[t + 1] <= x) ++t;
+            const long long yq = csc->bs[t] + (x - csc->pre[t]);
+            const int o = pos_of(Yj[yq]);
+            if (o >= 0) {
+              q = o;
+              v = csc->av[t] * YV(yq);
+            }
+          }
+          const unsigned grp = __match_any_sync(full, q);
+          const bool leader = (grp & lane_lt) == 0;
+          if (__any_sync(full, __popc(grp) > 1)) {
+            xchg[lane] = v;
+            __syncwarp();
+            if (leader) {
+              unsigned rest = grp & ~(1u << lane);
+              while (rest) {
+                const int o = __ffs(rest) - 1;
+                rest &= rest - 1u;
+                v += xchg[o];
+              }
+            }
+            __syncwarp();
+          }
+          if (q >= 0 && leader) acc[q] += v;
+          __syncwarp();
+        }
+        __syncwarp();
+      }
+    }
+    for (int x = lane; x < s; x += 32) out[s0 + x] = acc[x];
+    // clear the row's words
+    for (int pb = 0; pb < s; pb += 32) {
+      const int p = pb + lane;
+      if (p < s) {
+        const unsigned w = (unsigned)(M.Sj[s0 + p] >> 5) - smin;
+        if (w < span) wbits[w] = 0u;
+      }
+    }
+    __syncwarp();
   }
 }
 
@@ -1116,6 +1333,19 @@ cudaError_t run_masked_warp(const LaunchCtx& L, const MaskedD& M, const MaskedLa
   return cudaGetLastError();
 }
 
+template <typename VT>
+cudaError_t run_masked_win(const LaunchCtx& L, const MaskedD& M, const MaskedLaunch& S) {
+  const size_t smem = mskw_team_bytes<VT>(1 << S.logT) * kMwTeams;
+  if (smem > (size_t)L.max_smem_optin) return cudaErrorInvalidConfiguration;
+  auto kern = k_masked_win<VT>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  KKS_LAUNCHED();
+  kern<<<resident_grid(kern, 32 * kMwTeams, smem, L.num_sms, (S.nrows + kMwTeams - 1) / kMwTeams), 32 * kMwTeams,
+         smem, L.stream>>>(M, S.rows, S.nrows, S.logT);
+  return cudaGetLastError();
+}
+
 template <int TW, typename VT>
 cudaError_t run_masked_pos(const LaunchCtx& L, const MaskedD& M, const MaskedLaunch& S) {
   const int T = 1 << S.logT;
@@ -1163,7 +1393,9 @@ cudaError_t masked_dispatch(const LaunchCtx& L, const MaskedD& M, const MaskedLa
       return cudaGetLastError();
     }
     case kClsW8: return S.positions ? run_masked_pos<8, VT>(L, M, S) : run_masked_warp<8, VT>(L, M, S);
-    case kClsW32: return S.positions ? run_masked_pos<32, VT>(L, M, S) : run_masked_warp<32, VT>(L, M, S);
+    case kClsW32:
+      if (!S.positions) return run_masked_warp<32, VT>(L, M, S);
+      return S.window ? run_masked_win<VT>(L, M, S) : run_masked_pos<32, VT>(L, M, S);
     case kClsC256: return run_masked_hash<256, VT>(L, M, S);
     case kClsC1024: return run_masked_hash<1024, VT>(L, M, S);
     case kClsSpill: return run_masked_global<VT>(L, M, S);

@@ -335,6 +335,10 @@ __global__ void __launch_bounds__(TW) k_num_part(ProbD P, const int* __restrict_
 //    keys are grouped with __match_any_sync, their values summed through a
 //    per-team exchange buffer, and only the group's first lane updates.
 // ---------------------------------------------------------------------------
+// Warp rows of more than 2 * TW keys are emitted by a bucket sort (below)
+// unless a bucket would hold more than this many keys.
+constexpr int kBucketMax = 24;
+
 template <int TW, typename VT>
 __host__ __device__ size_t warp_team_bytes(int T) {
   const int half = T / 2 > 0 ? T / 2 : 1;
@@ -486,24 +490,124 @@ __global__ void __launch_bounds__(256, 3) k_num_warp(ProbD P, const int* __restr
     }
     // compaction of the occupied slots into (column << 32 | slot)
     int cnt = 0;
+    unsigned kmn = 0xffffffffu, kmx = 0u;
     for (int xb = 0; xb < T; xb += TW) {
       const int x = xb + tm.lane;
-      const bool o = x < T && keys[x] != kEmpty;
+      const int key = x < T ? keys[x] : kEmpty;
+      const bool o = key != kEmpty;
       const unsigned bal = (__ballot_sync(tm.mask, o) >> lane_base) & ((TW == 32) ? 0xffffffffu : ((1u << TW) - 1u));
       const int pos = cnt + __popc(bal & lane_lt);
-      if (o && pos < half) sortb[pos] = ((unsigned long long)(unsigned)keys[x] << 32) | (unsigned)x;
+      if (o && pos < half) sortb[pos] = ((unsigned long long)(unsigned)key << 32) | (unsigned)x;
+      if (o) {
+        kmn = min(kmn, (unsigned)key);
+        kmx = max(kmx, (unsigned)key);
+      }
       cnt += __popc(bal);
     }
     if (tm.lane == 0 && cnt != s) dev_fail(P.status, kDevRowSizeMismatch, 19, g);
     const int n = cnt < half ? cnt : half;
+    const long long nw = n < s ? n : s;
+    VT* __restrict__ Cx = reinterpret_cast<VT*>(I.Cx);
+    int* __restrict__ Cj = I.Cj;
+    if (TW == 32 && n > 2 * TW) {
+      // Bucket sort by column (rows of many keys): the values move to a
+      // compact array in the key region, then each entry goes to its bucket
+      // (an equal share of [kmin, kmax]) by a count, a scan and a scatter
+      // into the value region, and each lane sorts its buckets by insertion.
+      // Rows whose fullest bucket holds more than kBucketMax entries (keys
+      // bunched unevenly) take the bitonic sort instead.
+      kmn = __reduce_min_sync(tm.mask, kmn);
+      kmx = __reduce_max_sync(tm.mask, kmx);
+      __syncwarp(tm.mask);
+      VT* cv = reinterpret_cast<VT*>(keys);                                       // half values
+      unsigned long long* outb = reinterpret_cast<unsigned long long*>(vals);     // half entries
+      int* bcnt = sizeof(VT) == 8 ? reinterpret_cast<int*>(outb + half) : reinterpret_cast<int*>(cv + half);
+      int nb = 32;
+      while (nb < n) nb <<= 1;   // buckets: a power of two >= n, <= half
+      int sh = 0;
+      while (((kmx - kmn) >> sh) >= (unsigned)nb) ++sh;
+      // values by compact position, into the key region (every key was read above)
+      for (int x = tm.lane; x < n; x += TW) cv[x] = vals[(unsigned)(sortb[x] & 0xffffffffull)];
+      __syncwarp(tm.mask);   // the value region is free from here on
+      for (int b = tm.lane; b < nb; b += TW) bcnt[b] = 0;
+      __syncwarp(tm.mask);
+      for (int x = tm.lane; x < n; x += TW) {
+        const unsigned key = (unsigned)(sortb[x] >> 32);
+        atomicAdd(&bcnt[(key - kmn) >> sh], 1);
+      }
+      __syncwarp(tm.mask);
+      // exclusive scan of the counts: each lane a contiguous run of nb / 32 buckets
+      const int per = nb / TW;
+      int run = 0, mxb = 0;
+      for (int q = 0; q < per; ++q) {
+        const int c = bcnt[tm.lane * per + q];
+        run += c;
+        mxb = max(mxb, c);
+      }
+      int incl = run;
+#pragma unroll
+      for (int d = 1; d < TW; d <<= 1) {
+        const int y = __shfl_up_sync(tm.mask, incl, d, TW);
+        if (tm.lane >= d) incl += y;
+      }
+      mxb = __reduce_max_sync(tm.mask, (unsigned)mxb);
+      int start = incl - run;
+      for (int q = 0; q < per; ++q) {
+        const int c = bcnt[tm.lane * per + q];
+        bcnt[tm.lane * per + q] = start;
+        start += c;
+      }
+      __syncwarp(tm.mask);
+      if (mxb <= kBucketMax) {
+        for (int x = tm.lane; x < n; x += TW) {
+          const unsigned long long e = sortb[x];
+          const int b = (int)(((unsigned)(e >> 32) - kmn) >> sh);
+          const int at = atomicAdd(&bcnt[b], 1);
+          outb[at] = (e & 0xffffffff00000000ull) | (unsigned)x;   // (column, compact position)
+        }
+        __syncwarp(tm.mask);
+        // bcnt[b] is now the end of bucket b; the start is the end of b - 1
+        for (int b = tm.lane; b < nb; b += TW) {
+          const int e1 = bcnt[b], e0 = b > 0 ? bcnt[b - 1] : 0;
+          for (int x = e0 + 1; x < e1; ++x) {
+            const unsigned long long v = outb[x];
+            int y = x - 1;
+            while (y >= e0 && outb[y] > v) {
+              outb[y + 1] = outb[y];
+              --y;
+            }
+            outb[y + 1] = v;
+          }
+        }
+        __syncwarp(tm.mask);
+        for (long long x = tm.lane; x < nw; x += TW) {
+          const unsigned long long e = outb[x];
+          Cj[c0 + x] = (int)(e >> 32);
+          Cx[c0 + x] = cv[(unsigned)(e & 0xffffffffull)];
+        }
+        __syncwarp(tm.mask);
+        continue;
+      }
+      // uneven keys: bitonic sort of (column, compact position)
+      for (int x = tm.lane; x < n; x += TW) sortb[x] = (sortb[x] & 0xffffffff00000000ull) | (unsigned)x;
+      int N = 1;
+      while (N < n) N <<= 1;
+      for (int x = n + tm.lane; x < N; x += TW) sortb[x] = ~0ull;
+      __syncwarp(tm.mask);
+      team_bitonic<TW>(tm, sortb, N);
+      for (long long x = tm.lane; x < nw; x += TW) {
+        const unsigned long long e = sortb[x];
+        Cj[c0 + x] = (int)(e >> 32);
+        Cx[c0 + x] = cv[(unsigned)(e & 0xffffffffull)];
+      }
+      __syncwarp(tm.mask);
+      continue;
+    }
     int N = 1;
     while (N < n) N <<= 1;
     for (int x = n + tm.lane; x < N; x += TW) sortb[x] = ~0ull;
     __syncwarp(tm.mask);
     team_bitonic<TW>(tm, sortb, N);
-    const long long nw = n < s ? n : s;
-    VT* __restrict__ Cx = reinterpret_cast<VT*>(I.Cx);
-    int* __restrict__ Cj = I.Cj;
     for (long long x = tm.lane; x < nw; x += TW) {
       const unsigned long long e = sortb[x];
       Cj[c0 + x] = (int)(e >> 32);
@@ -536,14 +640,13 @@ __host__ __device__ size_t cpn_team_bytes(int T) {
          al16((size_t)TW * sizeof(VT));
 }
 
+// One row g of C by the team, in the team's shared memory at base_p
+// (cpn_team_bytes<TW, VT>(2^logT) bytes).
 template <int TW, typename VT>
-__global__ void __launch_bounds__(256, 4) k_num_cpn(ProbD P, const int* __restrict__ rows, long long nrows, int logT) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  Team<TW> tm;
+__device__ __forceinline__ void cpn_row(const Team<TW>& tm, const ProbD& P, unsigned char* base_p, int logT,
+                                        const LpHash& hs, long long g) {
   const int T = 1 << logT;
-  const LpHash hs(logT, P.hash_mode);
   const int half = T / 2 > 0 ? T / 2 : 1;
-  unsigned char* base_p = smem + (size_t)tm.id * cpn_team_bytes<TW, VT>(T);
   int4* tab = reinterpret_cast<int4*>(base_p);
   // step 2 sorts (set << 32 | slot) and stages C's columns here; steps 3-4 accumulate here
   unsigned long long* sortb = reinterpret_cast<unsigned long long*>(base_p + al16((size_t)T * 16));
@@ -556,10 +659,7 @@ __global__ void __launch_bounds__(256, 4) k_num_cpn(ProbD P, const int* __restri
   const int lane_base = (threadIdx.x & 31) & ~(TW - 1);
   const unsigned tbits = (TW == 32) ? 0xffffffffu : ((1u << TW) - 1u);
 
-  const long long team = (long long)blockIdx.x * tm.per_cta + tm.id;
-  const long long nteams = (long long)gridDim.x * tm.per_cta;
-  for (long long r = team; r < nrows; r += nteams) {
-    const long long g = rows[r];
+  {
     const int b = inst_of(P.arow0s, P.ninst, g);
     const InstD& I = P.inst[b];
     const long long i = g - I.arow0;
@@ -806,6 +906,310 @@ __global__ void __launch_bounds__(256, 4) k_num_cpn(ProbD P, const int* __restri
   }
 }
 
+template <int TW, typename VT>
+__global__ void __launch_bounds__(256, 4) k_num_cpn(ProbD P, const int* __restrict__ rows, long long nrows, int logT) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Team<TW> tm;
+  const LpHash hs(logT, P.hash_mode);
+  unsigned char* base_p = smem + (size_t)tm.id * cpn_team_bytes<TW, VT>(1 << logT);
+  const long long team = (long long)blockIdx.x * tm.per_cta + tm.id;
+  const long long nteams = (long long)gridDim.x * tm.per_cta;
+  for (long long r = team; r < nrows; r += nteams) cpn_row<TW, VT>(tm, P, base_p, logT, hs, rows[r]);
+}
+
+// ---------------------------------------------------------------------------
+// Bitmap-window positions (warp teams, compressed products, B rows sorted).
+// The column sets of C(i,:) lie between the first set of the first and the
+// last set of the last column among the compressed B rows over A(i,:) (each
+// compressed row is sorted, so its first and last entries bound it).  When
+// that window is at most kWbLimit sets wide, the row's union of column sets is
+// a bitmap over the window addressed directly by set index: the dense
+// accumulator of Section 3.1.2 restricted to the row's own column range, in
+// the 32-column sets of Section 3.2.
+//   1. OR every compressed product's set bits into bits[set - smin]
+//   2. per set word, the count of set bits before it in the window (its base):
+//      lanes take contiguous runs of words, a warp scan joins them
+//   3. each product goes to base + the set bits below its column: one fused
+//      multiply-add into the row's value array; its column is staged at the
+//      same place (every column of C(i,:) receives at least one product)
+//   4. the row's columns and values are written in order; the window's words
+//      are cleared for the next row
+// No hashing, no probing, no sort of the sets.  Rows with a wider window take
+// the hash path of k_num_cpn (cpn_row) in the same shared memory.
+// ---------------------------------------------------------------------------
+constexpr int kWbLimit = 1344;   // widest window in column sets (43 008 columns)
+constexpr int kWbWords = 1408;   // bitmap words per team: the scan's per-lane runs round a window up to this
+constexpr int kWbTeams = 4;      // warp teams per CTA
+
+template <typename VT>
+__host__ __device__ size_t wb_team_bytes(int T) {
+  const int half = T / 2 > 0 ? T / 2 : 1;
+  const size_t wb = al16((size_t)kWbWords * 4) + al16((size_t)kWbWords * 2) + al16((size_t)half * 4) +
+                    al16((size_t)half * sizeof(VT)) + al16(sizeof(ChunkScratch<32, VT>)) + al16(32 * sizeof(VT));
+  const size_t hp = cpn_team_bytes<32, VT>(T);
+  return wb > hp ? wb : hp;
+}
+
+// Words per lane of the base scan over a window of span words: a multiple of
+// 4 (16-byte loads) that is not a multiple of 8, so the eight lanes of each
+// 16-byte load phase hit distinct banks.  32 * the result <= kWbWords for
+// span <= kWbLimit.
+__device__ __forceinline__ int wb_words_per_lane(unsigned span) {
+  int pw = ((int)((span + 31u) >> 5) + 3) & ~3;
+  if ((pw & 7) == 0) pw += 4;
+  return pw;
+}
+
+template <typename VT>
+__global__ void __launch_bounds__(32 * kWbTeams, 5) k_num_wb(ProbD P, const int* __restrict__ rows, long long nrows,
+                                                             int logT) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Team<32> tm;
+  const int T = 1 << logT;
+  const int half = T / 2 > 0 ? T / 2 : 1;
+  const LpHash hs(logT, P.hash_mode);
+  unsigned char* base_p = smem + (size_t)tm.id * wb_team_bytes<VT>(T);
+  unsigned* bits = reinterpret_cast<unsigned*>(base_p);
+  unsigned short* wbase = reinterpret_cast<unsigned short*>(base_p + al16((size_t)kWbWords * 4));
+  int* colst = reinterpret_cast<int*>(base_p + al16((size_t)kWbWords * 4) + al16((size_t)kWbWords * 2));
+  VT* outv = reinterpret_cast<VT*>(reinterpret_cast<unsigned char*>(colst) + al16((size_t)half * 4));
+  ChunkScratch<32, VT>* csc = reinterpret_cast<ChunkScratch<32, VT>*>(reinterpret_cast<unsigned char*>(outv) +
+                                                                      al16((size_t)half * sizeof(VT)));
+  VT* xchg = reinterpret_cast<VT*>(reinterpret_cast<unsigned char*>(csc) + al16(sizeof(ChunkScratch<32, VT>)));
+  int* upre = reinterpret_cast<int*>(csc);
+  long long* uqs = reinterpret_cast<long long*>(reinterpret_cast<unsigned char*>(csc) + al16((size_t)33 * 4));
+  const int lane = tm.lane;
+  const unsigned lane_lt = (1u << lane) - 1u;
+  const unsigned full = 0xffffffffu;
+  bool clean = false;   // every word of bits[] is zero
+
+  const long long team = (long long)blockIdx.x * tm.per_cta + tm.id;
+  const long long nteams = (long long)gridDim.x * tm.per_cta;
+  for (long long r = team; r < nrows; r += nteams) {
+    const long long g = rows[r];
+    const int b = inst_of(P.arow0s, P.ninst, g);
+    const InstD& I = P.inst[b];
+    const long long i = g - I.arow0;
+    const long long a0 = rp_at(I.A, i), a1 = rp_at(I.A, i + 1);
+    const VT* __restrict__ Ax = reinterpret_cast<const VT*>(I.A.vx);
+    const VT* __restrict__ Bx = reinterpret_cast<const VT*>(I.B.vx);
+    const int* __restrict__ Bj = I.B.cj;
+    const int* __restrict__ Aj = I.A.cj;
+    const long long brow0 = I.brow0;
+    long long bs = 0, cbs = 0;
+    int len = 0, clen = 0;
+    VT av = VT(0);
+    auto load_chunk = [&](long long c) {
+      const long long p = c + lane;
+      bs = 0;
+      cbs = 0;
+      len = 0;
+      clen = 0;
+      av = VT(0);
+      if (p < a1) {
+        const int j = Aj[p];
+        av = Ax[p];
+        bs = rp_at(I.B, j);
+        len = (int)(rp_at(I.B, j + 1) - bs);
+        cbs = P.Bcp[brow0 + j];
+        clen = (int)(P.Bcp[brow0 + j + 1] - cbs);
+      }
+    };
+    // 0. the window
+    unsigned smin = 0xffffffffu, smax = 0u;
+    for (long long c = a0; c < a1; c += 32) {
+      load_chunk(c);
+      if (clen > 0) {
+        smin = min(smin, (unsigned)P.csi[cbs]);
+        smax = max(smax, (unsigned)P.csi[cbs + clen - 1]);
+      }
+    }
+    smin = __reduce_min_sync(full, smin);
+    smax = __reduce_max_sync(full, smax);
+    if (smin > smax || smax - smin >= (unsigned)kWbLimit) {
+      cpn_row<32, VT>(tm, P, base_p, logT, hs, g);
+      clean = false;
+      __syncwarp();
+      continue;
+    }
+    const unsigned span = smax - smin + 1u;
+    const int pw = wb_words_per_lane(span);
+    if (!clean) {
+      uint4* c4 = reinterpret_cast<uint4*>(bits);
+      for (int x = lane; x < kWbWords / 4; x += 32) c4[x] = make_uint4(0u, 0u, 0u, 0u);
+      clean = true;
+      __syncwarp();
+    }
+    const long long c0 = I.Crp[i];
+    const int s = (int)(I.Crp[i + 1] - c0);
+    const bool one_chunk = a1 - a0 <= 32;
+    // 1. union of the compressed B rows
+    for (long long c = a0; c < a1; c += 32) {
+      if (!one_chunk) load_chunk(c);
+      wb_union_chunk<32, false>(full, lane, upre, uqs, cbs, clen, P.csi, P.cs, bits, smin, span, P.status, 36, g);
+    }
+    if (!one_chunk) load_chunk(a0);
+    // 2. bases of the set words
+    const uint4* b4 = reinterpret_cast<const uint4*>(bits + lane * pw);
+    int cnt = 0;
+    unsigned nz = 0u;   // this lane's 16-byte groups that hold set bits (pw / 4 <= 11)
+    for (int k = 0; k < pw / 4; ++k) {
+      const uint4 v = b4[k];
+      cnt += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+      if ((v.x | v.y | v.z | v.w) != 0u) nz |= 1u << k;
+    }
+    int incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int y = __shfl_up_sync(full, incl, d);
+      if (lane >= d) incl += y;
+    }
+    const int total = __shfl_sync(full, incl, 31);
+    int run = incl - cnt;
+    unsigned short* wb = wbase + lane * pw;
+    for (unsigned m = nz; m != 0u; m &= m - 1u) {
+      const int k = __ffs(m) - 1;
+      const uint4 v = b4[k];
+      if (v.x) wb[4 * k] = (unsigned short)run;
+      run += __popc(v.x);
+      if (v.y) wb[4 * k + 1] = (unsigned short)run;
+      run += __popc(v.y);
+      if (v.z) wb[4 * k + 2] = (unsigned short)run;
+      run += __popc(v.z);
+      if (v.w) wb[4 * k + 3] = (unsigned short)run;
+      run += __popc(v.w);
+    }
+    if (lane == 0 && total != s) dev_fail(P.status, kDevRowSizeMismatch, 37, g);
+    const int sw = s < half ? s : half;
+    for (int x = lane; x < sw; x += 32) outv[x] = VT(0);
+    __syncwarp();
+    // 3. products to their places
+    auto pos_of = [&](int col) -> int {
+      const unsigned w = (unsigned)(col >> 5) - smin;
+      if (w >= span) return -1;
+      const unsigned m = bits[w];
+      const unsigned bit = 1u << (col & 31);
+      if (!(m & bit)) return -1;
+      const int o = (int)wbase[w] + __popc(m & (bit - 1u));
+      return o < sw ? o : -1;
+    };
+    for (long long c = a0; c < a1; c += 32) {
+      if (!one_chunk && c != a0) load_chunk(c);
+      const int nc = (a1 - c) < 32 ? (int)(a1 - c) : 32;
+      const int tot = __reduce_add_sync(full, (unsigned)len);
+      if (2 * tot >= nc * 32) {
+        // sequential: one B row per pass, distinct places inside a pass
+        constexpr int kU = 4;
+        for (int t0 = 0; t0 < nc; t0 += kU) {
+          int q[kU], lent[kU];
+          long long bst[kU];
+          VT at[kU], bv[kU];
+#pragma unroll
+          for (int u = 0; u < kU; ++u) {
+            const int t = (t0 + u < nc) ? t0 + u : nc - 1;
+            bst[u] = __shfl_sync(full, bs, t);
+            const int l = __shfl_sync(full, len, t);
+            at[u] = __shfl_sync(full, av, t);
+            lent[u] = (t0 + u < nc) ? l : 0;
+            q[u] = -1;
+            bv[u] = VT(0);
+            if (lane < lent[u]) {
+              q[u] = Bj[bst[u] + lane];
+              bv[u] = Bx[bst[u] + lane];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < kU; ++u) {
+            if (q[u] >= 0) {
+              const int o = pos_of(q[u]);
+              if (o >= 0) {
+                outv[o] = fma_acc(at[u], bv[u], outv[o]);
+                colst[o] = q[u];
+              } else {
+                dev_fail(P.status, kDevTableFull, 38, g);
+              }
+            }
+            for (int x = lane + 32; x < lent[u]; x += 32) {
+              const int col = Bj[bst[u] + x];
+              const int o = pos_of(col);
+              if (o >= 0) {
+                outv[o] = fma_acc(at[u], Bx[bst[u] + x], outv[o]);
+                colst[o] = col;
+              } else {
+                dev_fail(P.status, kDevTableFull, 38, g);
+              }
+            }
+            __syncwarp();
+          }
+        }
+      } else {
+        // flat: the chunk's products over the lanes, equal places pre-summed
+        int ex = len;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const int y = __shfl_up_sync(full, ex, d);
+          if (lane >= d) ex += y;
+        }
+        ex -= len;
+        csc->pre[lane] = ex;
+        csc->bs[lane] = bs;
+        csc->av[lane] = av;
+        if (lane == 0) csc->pre[32] = tot;
+        __syncwarp();
+        int t = 0;
+        for (int xb = 0; xb < tot; xb += 32) {
+          const int x = xb + lane;
+          int o = -1 - lane;
+          VT v = VT(0);
+          if (x < tot) {
+            while (csc->pre[t + 1] <= x) ++t;
+            const long long qq = csc->bs[t] + (x - csc->pre[t]);
+            const int col = Bj[qq];
+            const int oo = pos_of(col);
+            if (oo >= 0) {
+              o = oo;
+              v = csc->av[t] * Bx[qq];
+              colst[oo] = col;
+            } else {
+              dev_fail(P.status, kDevTableFull, 39, g);
+            }
+          }
+          const unsigned grp = __match_any_sync(full, o);
+          const bool leader = (grp & lane_lt) == 0;
+          if (__any_sync(full, __popc(grp) > 1)) {
+            xchg[lane] = v;
+            __syncwarp();
+            if (leader) {
+              unsigned rest = grp & ~(1u << lane);
+              while (rest) {
+                const int oo = __ffs(rest) - 1;
+                rest &= rest - 1u;
+                v += xchg[oo];
+              }
+            }
+            __syncwarp();
+          }
+          if (o >= 0 && leader) outv[o] += v;
+          __syncwarp();
+        }
+        __syncwarp();
+      }
+    }
+    __syncwarp();
+    // 4. the row in order; the window cleared
+    int* __restrict__ Cj = I.Cj;
+    VT* __restrict__ Cx = reinterpret_cast<VT*>(I.Cx);
+    for (int x = lane; x < sw; x += 32) {
+      Cj[c0 + x] = colst[x];
+      Cx[c0 + x] = outv[x];
+    }
+    // the window's words: each lane clears its own groups that hold bits
+    uint4* c4 = reinterpret_cast<uint4*>(bits + lane * pw);
+    for (unsigned m = nz; m != 0u; m &= m - 1u) c4[__ffs(m) - 1] = make_uint4(0u, 0u, 0u, 0u);
+    __syncwarp();
+  }
+}
+
 // One thread per row for rows of C with at most kT1MaxKeys columns and few
 // products (Thread-Sequential with a team of one, Section 3.1.1): the keys
 // stay in registers, a product is matched with integer compares and goes to
@@ -1000,24 +1404,33 @@ __global__ void __launch_bounds__(TW) k_num_dense(ProbD P, const int* __restrict
         for_each_product<TW, VT>(tm, csc, scan_scratch, I.A.cj, a0, a1, range, aval, body, pf);
         __syncthreads();
       }
-      // the window's columns in order: word-wise prefix of set bits, then emit
+      // the window's columns in order: a prefix of the words' set-bit counts
+      // over the CTA, then each warp emits its 32 words one word at a time,
+      // lane l taking bit l, so the reads of the accumulator are consecutive
+      // and the writes of C(i,:) coalesced
       const long long nw = ((k - w0 + 31) >> 5) < ww ? ((k - w0 + 31) >> 5) : ww;
+      const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
       for (long long wb = 0; wb < nw; wb += TW) {
         const long long wi = wb + tm.lane;
-        unsigned word = (wi < nw) ? bm[wi] : 0u;
+        const unsigned word = (wi < nw) ? bm[wi] : 0u;
         long long tot;
-        long long pos = run + team_excl_scan<TW>(tm, __popc(word), &tot, scan_scratch);
-        while (word) {
-          const int bit = __ffs(word) - 1;
-          word &= word - 1u;
-          const long long x = wi * 32 + bit;
-          const VT v = acc[x];
-          acc[x] = VT(0);
-          if (pos < s) {
-            Cj[c0 + pos] = (int)(w0 + x);
-            Cx[c0 + pos] = v;
+        const long long pos = run + team_excl_scan<TW>(tm, __popc(word), &tot, scan_scratch);
+        const long long wfirst = wi - (threadIdx.x & 31);   // first word of this warp
+#pragma unroll 4
+        for (int q = 0; q < 32; ++q) {
+          const unsigned wd = __shfl_sync(0xffffffffu, word, q);
+          if (wd == 0u) continue;
+          const long long base = __shfl_sync(0xffffffffu, pos, q);
+          if ((wd >> (threadIdx.x & 31)) & 1u) {
+            const long long at = base + __popc(wd & lt);
+            const long long x = (wfirst + q) * 32 + (threadIdx.x & 31);
+            const VT v = acc[x];
+            acc[x] = VT(0);
+            if (at < s) {
+              Cj[c0 + at] = (int)(w0 + x);
+              Cx[c0 + at] = v;
+            }
           }
-          ++pos;
         }
         if (wi < nw) bm[wi] = 0u;
         run += tot;
@@ -1240,6 +1653,19 @@ cudaError_t run_cpn(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
 }
 
 template <typename VT>
+cudaError_t run_wb(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
+  const size_t smem = wb_team_bytes<VT>(1 << S.logT) * kWbTeams;
+  if (smem > (size_t)L.max_smem_optin) return cudaErrorInvalidConfiguration;
+  auto kern = k_num_wb<VT>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = resident_grid(kern, 32 * kWbTeams, smem, L.num_sms, (S.nrows + kWbTeams - 1) / kWbTeams);
+  KKS_LAUNCHED();
+  kern<<<grid, 32 * kWbTeams, smem, L.stream>>>(P, S.rows, S.nrows, S.logT);
+  return cudaGetLastError();
+}
+
+template <typename VT>
 cudaError_t run_dense(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
   constexpr int TW = 1024;
   // the widest window that fits one CTA's shared memory (a 1024-thread CTA
@@ -1310,7 +1736,9 @@ cudaError_t dispatch(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
   switch (S.cls) {
     case kClsT1: return run_thread<VT>(L, P, S);
     case kClsW8: return S.positions ? run_cpn<8, VT>(L, P, S) : run_warp<8, VT>(L, P, S);
-    case kClsW32: return S.positions ? run_cpn<32, VT>(L, P, S) : run_warp<32, VT>(L, P, S);
+    case kClsW32:
+      if (!S.positions) return run_warp<32, VT>(L, P, S);
+      return S.b_sorted && S.window ? run_wb<VT>(L, P, S) : run_cpn<32, VT>(L, P, S);
     case kClsC256:
       if (S.part == kPartTeamSeq) return run_part<256, VT, kPartTeamSeq>(L, P, S);
       if (S.part == kPartThreadPar) return run_part<256, VT, kPartThreadPar>(L, P, S);

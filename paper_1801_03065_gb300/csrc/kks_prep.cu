@@ -41,9 +41,45 @@ constexpr int kShortRowB = 32;
 // Compressed row lengths: runs of equal CSI in row order.  Also counts the B
 // rows whose columns are not strictly increasing (the dense numeric windows
 // look up column ranges by binary search only when none is).
+// Rows longer than this go to a queue served by whole warps in a second
+// launch, so a few very long rows (graph hubs) do not hold their block while
+// the rest of the grid has finished.
+constexpr int kLongRow = 1024;
+
+// The next entry of a long-row queue for the calling warp (warp-uniform).
+__device__ __forceinline__ long long long_next(unsigned long long* fetch) {
+  unsigned long long x = 0;
+  if ((threadIdx.x & 31) == 0) x = atomicAdd(fetch, 1ull);
+  return (long long)__shfl_sync(0xffffffffu, x, 0);
+}
+
+// Compressed length of B row gb by a team of TW lanes.
+template <int TW>
+__device__ __forceinline__ void compress_count_team(const Team<TW>& tm, const ProbD& P, long long gb, long long* cnt,
+                                                    unsigned long long* unsorted) {
+  const int b = inst_of(P.brow0s, P.ninst, gb);
+  const InstD& I = P.inst[b];
+  const long long j = gb - I.brow0;
+  const long long s = rp_at(I.B, j), e = rp_at(I.B, j + 1);
+  const int* cj = I.B.cj;
+  long long c = 0;
+  bool bad = false;
+  for (long long p = s + tm.lane; p < e; p += TW) {
+    int col = cj[p];
+    if ((unsigned long long)(unsigned)col >= (unsigned long long)I.k) dev_fail(P.status, kDevBadIndex, 41, gb);
+    const int prev = p > s ? cj[p - 1] : -1;
+    if (p == s || (col >> 5) != (prev >> 5)) ++c;
+    bad |= p > s && col <= prev;
+  }
+  c = warp_team_sum<TW>(tm, c);
+  if (tm.lane == 0) cnt[gb] = c;
+  if (__any_sync(tm.mask, bad) && tm.lane == 0) atomicAdd(unsorted, 1ull);
+}
+
 template <int TW>
 __global__ void __launch_bounds__(kBlock) k_compress_count(ProbD P, long long totalB, long long* cnt,
-                                                           unsigned long long* unsorted) {
+                                                           unsigned long long* unsorted, int* list,
+                                                           unsigned long long* nlist) {
   Team<TW> tm;
   __shared__ int nlong;
   __shared__ int longrows[kBlock];
@@ -77,32 +113,25 @@ __global__ void __launch_bounds__(kBlock) k_compress_count(ProbD P, long long to
         }
         cnt[gb] = c;
         if (bad) atomicAdd(unsorted, 1ull);
+      } else if (e - s > kLongRow) {
+        list[atomicAdd(nlist, 1ull)] = (int)gb;
       } else {
         longrows[atomicAdd(&nlong, 1)] = (int)(gb - g0);
       }
     }
   }
   __syncthreads();
-  for (int x = tm.id; x < nlong; x += tm.per_cta) {
-    const long long gb = g0 + longrows[x];
-    const int b = inst_of(P.brow0s, P.ninst, gb);
-    const InstD& I = P.inst[b];
-    const long long j = gb - I.brow0;
-    const long long s = rp_at(I.B, j), e = rp_at(I.B, j + 1);
-    const int* cj = I.B.cj;
-    long long c = 0;
-    bool bad = false;
-    for (long long p = s + tm.lane; p < e; p += TW) {
-      int col = cj[p];
-      if ((unsigned long long)(unsigned)col >= (unsigned long long)I.k) dev_fail(P.status, kDevBadIndex, 41, gb);
-      const int prev = p > s ? cj[p - 1] : -1;
-      if (p == s || (col >> 5) != (prev >> 5)) ++c;
-      bad |= p > s && col <= prev;
-    }
-    c = warp_team_sum<TW>(tm, c);
-    if (tm.lane == 0) cnt[gb] = c;
-    if (__any_sync(tm.mask, bad) && tm.lane == 0) atomicAdd(unsorted, 1ull);
-  }
+  for (int x = tm.id; x < nlong; x += tm.per_cta) compress_count_team<TW>(tm, P, g0 + longrows[x], cnt, unsorted);
+}
+
+// Rows of B longer than kLongRow entries, from the queue the block pass built,
+// one warp each (a warp takes the next row from a counter).
+__global__ void __launch_bounds__(kBlock) k_compress_count_long(ProbD P, const int* list, const unsigned long long* n,
+                                                                unsigned long long* fetch, long long* cnt,
+                                                                unsigned long long* unsorted) {
+  Team<32> tm;
+  for (long long x = long_next(fetch); x < (long long)*n; x = long_next(fetch))
+    compress_count_team<32>(tm, P, list[x], cnt, unsorted);
 }
 
 // Runs of equal CSI in row order become one compressed entry; rows with sorted
@@ -110,6 +139,49 @@ __global__ void __launch_bounds__(kBlock) k_compress_count(ProbD P, long long to
 // written by their thread run by run.  In the team loop of long rows the
 // chunk where a run starts stores its bits and later chunks of the same run
 // OR in theirs (cs needs no clearing).
+// Compressed row gb of B by a team of TW lanes (lanes in order over the row).
+template <int TW>
+__device__ __forceinline__ void compress_fill_team(const Team<TW>& tm, const ProbD& P, long long gb, int* csi,
+                                                   unsigned* cs) {
+  const int base_lane = (threadIdx.x & 31) & ~(TW - 1);
+  const int b = inst_of(P.brow0s, P.ninst, gb);
+  const InstD& I = P.inst[b];
+  const long long j = gb - I.brow0;
+  const long long s = rp_at(I.B, j), e = rp_at(I.B, j + 1);
+  const int* cj = I.B.cj;
+  long long run = P.Bcp[gb] - 1;   // index of the last run opened so far
+  for (long long c0 = s; c0 < e; c0 += TW) {
+    const long long p = c0 + tm.lane;
+    const bool valid = p < e;
+    const int col = valid ? cj[p] : 0;
+    const bool head = valid && (p == s || (col >> 5) != (cj[p - 1] >> 5));
+    const unsigned hb = (__ballot_sync(tm.mask, head) >> base_lane) & ((TW == 32) ? 0xffffffffu : ((1u << TW) - 1u));
+    const unsigned le = (tm.lane == 31) ? 0xffffffffu : ((2u << tm.lane) - 1u);
+    const long long ridx = run + __popc(hb & le);
+    if (head) csi[ridx] = col >> 5;
+    // segmented OR over the lanes of each run inside this chunk
+    unsigned v = valid ? (1u << (col & 31)) : 0u;
+    int f = (head || tm.lane == 0) ? 1 : 0;
+#pragma unroll
+    for (int d = 1; d < TW; d <<= 1) {
+      unsigned vu = __shfl_up_sync(tm.mask, v, d, TW);
+      int fu = __shfl_up_sync(tm.mask, f, d, TW);
+      if (tm.lane >= d && !f) {
+        v |= vu;
+        f = fu;
+      }
+    }
+    const bool next_head = (tm.lane + 1 < TW) && ((hb >> (tm.lane + 1)) & 1u);
+    const bool tail = valid && (tm.lane == TW - 1 || p + 1 >= e || next_head);
+    if (tail) {
+      if (hb & le) cs[ridx] = v;     // the run starts in this chunk
+      else atomicOr(cs + ridx, v);   // continuation of the previous chunk's last run
+    }
+    run += __popc(hb);
+    tm.sync();
+  }
+}
+
 template <int TW>
 __global__ void __launch_bounds__(kBlock) k_compress_fill(ProbD P, long long totalB, int* csi, unsigned* cs) {
   Team<TW> tm;
@@ -147,51 +219,22 @@ __global__ void __launch_bounds__(kBlock) k_compress_fill(ProbD P, long long tot
             bits |= 1u << (col & 31);
           }
           if (e > s) cs[run] = bits;
-        } else {
+        } else if (e - s <= kLongRow) {
           longrows[atomicAdd(&nlong, 1)] = (int)(gb - g0);
-        }
+        }   // longer rows: k_compress_fill_long, from the queue of the count pass
       }
     }
   }
   __syncthreads();
-  for (int x = tm.id; x < nlong; x += tm.per_cta) {
-    const long long gb = g0 + longrows[x];
-    const int b = inst_of(P.brow0s, P.ninst, gb);
-    const InstD& I = P.inst[b];
-    const long long j = gb - I.brow0;
-    const long long s = rp_at(I.B, j), e = rp_at(I.B, j + 1);
-    const int* cj = I.B.cj;
-    long long run = P.Bcp[gb] - 1;   // index of the last run opened so far
-    for (long long c0 = s; c0 < e; c0 += TW) {
-      const long long p = c0 + tm.lane;
-      const bool valid = p < e;
-      const int col = valid ? cj[p] : 0;
-      const bool head = valid && (p == s || (col >> 5) != (cj[p - 1] >> 5));
-      const unsigned hb = (__ballot_sync(tm.mask, head) >> base_lane) & ((TW == 32) ? 0xffffffffu : ((1u << TW) - 1u));
-      const unsigned le = (tm.lane == 31) ? 0xffffffffu : ((2u << tm.lane) - 1u);
-      const long long ridx = run + __popc(hb & le);
-      if (head) csi[ridx] = col >> 5;
-      // segmented OR over the lanes of each run inside this chunk
-      unsigned v = valid ? (1u << (col & 31)) : 0u;
-      int f = (head || tm.lane == 0) ? 1 : 0;
-#pragma unroll
-      for (int d = 1; d < TW; d <<= 1) {
-        unsigned vu = __shfl_up_sync(tm.mask, v, d, TW);
-        int fu = __shfl_up_sync(tm.mask, f, d, TW);
-        if (tm.lane >= d && !f) {
-          v |= vu;
-          f = fu;
-        }
-      }
-      const bool next_head = (tm.lane + 1 < TW) && ((hb >> (tm.lane + 1)) & 1u);
-      const bool tail = valid && (tm.lane == TW - 1 || p + 1 >= e || next_head);
-      if (tail) {
-        if (hb & le) cs[ridx] = v;     // the run starts in this chunk
-        else atomicOr(cs + ridx, v);   // continuation of the previous chunk's last run
-      }
-      run += __popc(hb);
-      tm.sync();
-    }
+  for (int x = tm.id; x < nlong; x += tm.per_cta) compress_fill_team<TW>(tm, P, g0 + longrows[x], csi, cs);
+}
+
+__global__ void __launch_bounds__(kBlock) k_compress_fill_long(ProbD P, const int* list, const unsigned long long* n,
+                                                               unsigned long long* fetch, int* csi, unsigned* cs) {
+  Team<32> tm;
+  for (long long x = long_next(fetch); x < (long long)*n; x = long_next(fetch)) {
+    const long long gb = list[x];
+    if (P.inst[inst_of(P.brow0s, P.ninst, gb)].compressed) compress_fill_team<32>(tm, P, gb, csi, cs);
   }
 }
 
@@ -205,9 +248,82 @@ __global__ void __launch_bounds__(kBlock) k_compress_fill(ProbD P, long long tot
 // kernel that follows A's indices into B, so it validates them.
 constexpr int kShortRow = 32;
 
+// Adds to *f / *fc the lengths of the B (compressed B) rows of the entries
+// p0, p0 + step, ... < e of A row g; the loads of four entries at a time are
+// issued together.
+__device__ __forceinline__ void row_stats_entries(const ProbD& P, const InstD& I, long long g, long long p0,
+                                                  long long e, long long step, int use_bc, long long* f,
+                                                  long long* fc) {
+  constexpr int kU = 4;
+  for (; p0 < e; p0 += (long long)kU * step) {
+    int jj[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const long long p = p0 + (long long)u * step;
+      jj[u] = p < e ? I.A.cj[p] : -1;
+      if (p < e && (unsigned long long)(unsigned)jj[u] >= (unsigned long long)I.A.ncols) {
+        dev_fail(P.status, kDevBadIndex, 43, g);
+        jj[u] = -1;
+      }
+    }
+    long long bs[kU], be[kU], cs[kU], ce[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      bs[u] = be[u] = cs[u] = ce[u] = 0;
+      if (jj[u] >= 0) {
+        bs[u] = rp_at(I.B, jj[u]);
+        be[u] = rp_at(I.B, jj[u] + 1);
+        if (use_bc) {
+          cs[u] = P.Bcp[I.brow0 + jj[u]];
+          ce[u] = P.Bcp[I.brow0 + jj[u] + 1];
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      if (bs[u] < 0 || bs[u] > be[u] || be[u] > I.B.nnz) {
+        dev_fail(P.status, kDevBadIndex, 44, g);
+        continue;
+      }
+      *f += be[u] - bs[u];
+      *fc += ce[u] - cs[u];
+    }
+  }
+}
+
+// Row statistics of the A rows longer than kLongRow entries (queued by
+// k_row_stats), one warp each; instance totals by atomics.
+__global__ void __launch_bounds__(kBlock) k_row_stats_long(ProbD P, int use_bc, const int* list,
+                                                           const unsigned long long* n, unsigned long long* fetch,
+                                                           long long* rf, long long* rfc,
+                                                           unsigned long long* inst_stats) {
+  Team<32> tm;
+  for (long long x = long_next(fetch); x < (long long)*n; x = long_next(fetch)) {
+    const long long g = list[x];
+    const int b = inst_of(P.arow0s, P.ninst, g);
+    const InstD& I = P.inst[b];
+    const long long i = g - I.arow0;
+    const long long s = rp_at(I.A, i), e = rp_at(I.A, i + 1);
+    long long f = 0, fc = 0;
+    row_stats_entries(P, I, g, s + tm.lane, e, 32, use_bc, &f, &fc);
+    f = warp_team_sum<32>(tm, f);
+    fc = warp_team_sum<32>(tm, fc);
+    if (tm.lane == 0) {
+      rf[g] = f;
+      if (rfc) rfc[g] = fc;
+      unsigned long long* st = inst_stats + 4ll * b;
+      atomicAdd(st + 0, (unsigned long long)f);
+      atomicMax(st + 1, (unsigned long long)f);
+      atomicAdd(st + 2, (unsigned long long)fc);
+      atomicMax(st + 3, (unsigned long long)fc);
+    }
+  }
+}
+
 template <int TW>
 __global__ void __launch_bounds__(kBlock) k_row_stats(ProbD P, long long totalA, int use_bc, long long* rf,
-                                                      long long* rfc, unsigned long long* inst_stats) {
+                                                      long long* rfc, unsigned long long* inst_stats, int* list,
+                                                      unsigned long long* nlist) {
   Team<TW> tm;
   __shared__ unsigned long long acc[4];
   __shared__ int b_first, b_last, nlong;
@@ -240,45 +356,8 @@ __global__ void __launch_bounds__(kBlock) k_row_stats(ProbD P, long long totalA,
       atomicMax(st + 3, (unsigned long long)fc);
     }
   };
-  // the B (and compressed B) ranges of up to four entries of A at a time
-  constexpr int kU = 4;
   auto entries = [&](const InstD& I, long long g, long long p0, long long e, long long step, long long* f,
-                     long long* fc) {
-    for (; p0 < e; p0 += (long long)kU * step) {
-      int jj[kU];
-#pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        const long long p = p0 + (long long)u * step;
-        jj[u] = p < e ? I.A.cj[p] : -1;
-        if (p < e && (unsigned long long)(unsigned)jj[u] >= (unsigned long long)I.A.ncols) {
-          dev_fail(P.status, kDevBadIndex, 43, g);
-          jj[u] = -1;
-        }
-      }
-      long long bs[kU], be[kU], cs[kU], ce[kU];
-#pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        bs[u] = be[u] = cs[u] = ce[u] = 0;
-        if (jj[u] >= 0) {
-          bs[u] = rp_at(I.B, jj[u]);
-          be[u] = rp_at(I.B, jj[u] + 1);
-          if (use_bc) {
-            cs[u] = P.Bcp[I.brow0 + jj[u]];
-            ce[u] = P.Bcp[I.brow0 + jj[u] + 1];
-          }
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        if (bs[u] < 0 || bs[u] > be[u] || be[u] > I.B.nnz) {
-          dev_fail(P.status, kDevBadIndex, 44, g);
-          continue;
-        }
-        *f += be[u] - bs[u];
-        *fc += ce[u] - cs[u];
-      }
-    }
-  };
+                     long long* fc) { row_stats_entries(P, I, g, p0, e, step, use_bc, f, fc); };
   // (1) short rows, one thread each
   {
     const long long g = g0 + threadIdx.x;
@@ -293,6 +372,8 @@ __global__ void __launch_bounds__(kBlock) k_row_stats(ProbD P, long long totalA,
         long long f = 0, fc = 0;
         entries(I, g, s, e, 1, &f, &fc);
         record(g, b, f, fc);
+      } else if (e - s > kLongRow) {
+        list[atomicAdd(nlist, 1ull)] = (int)g;
       } else {
         longrows[atomicAdd(&nlong, 1)] = (int)(g - g0);
       }
@@ -576,20 +657,31 @@ int resident_per_sm(const void* kernel, int threads, size_t smem) {
   return n;
 }
 
+// Long-row queue layout: queue[0] = entries, [1] = fetch counter of the
+// count pass, [2] = fetch counter of the fill pass (zeroed here).
 cudaError_t launch_compress_count(const LaunchCtx& L, const ProbD& P, long long totalB, long long* cnt,
-                                  unsigned long long* unsorted) {
+                                  unsigned long long* unsorted, const LongQueue& q) {
   if (totalB <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(q.ctr, 0, 3 * sizeof(unsigned long long), L.stream);
+  if (e != cudaSuccess) return e;
   const long long grid = (totalB + kBlock - 1) / kBlock;
   KKS_LAUNCHED();
-  k_compress_count<8><<<(unsigned)grid, kBlock, 0, L.stream>>>(P, totalB, cnt, unsorted);
+  k_compress_count<8><<<(unsigned)grid, kBlock, 0, L.stream>>>(P, totalB, cnt, unsorted, q.list, q.ctr);
+  KKS_LAUNCHED();
+  k_compress_count_long<<<grid_for(totalB, kBlock, L.num_sms, 4), kBlock, 0, L.stream>>>(P, q.list, q.ctr, q.ctr + 1,
+                                                                                        cnt, unsorted);
   return cudaGetLastError();
 }
 
-cudaError_t launch_compress_fill(const LaunchCtx& L, const ProbD& P, long long totalB, int* csi, unsigned* cs) {
+cudaError_t launch_compress_fill(const LaunchCtx& L, const ProbD& P, long long totalB, int* csi, unsigned* cs,
+                                 const LongQueue& q) {
   if (totalB <= 0) return cudaSuccess;
   const long long grid = (totalB + kBlock - 1) / kBlock;
   KKS_LAUNCHED();
   k_compress_fill<8><<<(unsigned)grid, kBlock, 0, L.stream>>>(P, totalB, csi, cs);
+  KKS_LAUNCHED();
+  k_compress_fill_long<<<grid_for(totalB, kBlock, L.num_sms, 4), kBlock, 0, L.stream>>>(P, q.list, q.ctr, q.ctr + 2,
+                                                                                       csi, cs);
   return cudaGetLastError();
 }
 
@@ -622,12 +714,35 @@ cudaError_t launch_row_flops(const LaunchCtx& L, const MatD& A, const MatD& B, l
   return cudaGetLastError();
 }
 
+__global__ void k_decide_compression(InstD* inst, const unsigned long long* st, int count, int mode, double thr) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < count; b += gridDim.x * blockDim.x) {
+    const long long fm = (long long)st[4 * b], fmc = (long long)st[4 * b + 2];
+    int c = 0;
+    if (mode == 1) c = 1;
+    else if (mode < 0 && fm > 0 && (double)fmc < thr * (double)fm) c = 1;
+    inst[b].compressed = c;
+  }
+}
+
+cudaError_t launch_decide_compression(const LaunchCtx& L, InstD* inst, const unsigned long long* inst_stats, int count,
+                                      int mode, double threshold) {
+  if (count <= 0) return cudaSuccess;
+  KKS_LAUNCHED();
+  k_decide_compression<<<(count + 255) / 256, 256, 0, L.stream>>>(inst, inst_stats, count, mode, threshold);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_row_stats(const LaunchCtx& L, const ProbD& P, long long totalA, int use_bc, long long* rf,
-                             long long* rfc, unsigned long long* inst_stats) {
+                             long long* rfc, unsigned long long* inst_stats, const LongQueue& q) {
   if (totalA <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(q.ctr, 0, 2 * sizeof(unsigned long long), L.stream);
+  if (e != cudaSuccess) return e;
   const long long grid = (totalA + kBlock - 1) / kBlock;
   KKS_LAUNCHED();
-  k_row_stats<8><<<(unsigned)grid, kBlock, 0, L.stream>>>(P, totalA, use_bc, rf, rfc, inst_stats);
+  k_row_stats<8><<<(unsigned)grid, kBlock, 0, L.stream>>>(P, totalA, use_bc, rf, rfc, inst_stats, q.list, q.ctr);
+  KKS_LAUNCHED();
+  k_row_stats_long<<<grid_for(totalA, kBlock, L.num_sms, 4), kBlock, 0, L.stream>>>(P, use_bc, q.list, q.ctr,
+                                                                                   q.ctr + 1, rf, rfc, inst_stats);
   return cudaGetLastError();
 }
 

@@ -148,6 +148,49 @@ __host__ __device__ size_t symw_team_bytes(int T) {
   return al16((size_t)T * 4 * (COMP ? 2 : 1)) + al16((size_t)(TW + 1) * 4) + al16((size_t)TW * 8);
 }
 
+// One row g by a warp team whose table of 2^logT slots sits at words.
+template <int TW, bool COMP>
+__device__ __forceinline__ void sym_warp_row(const Team<TW>& tm, const ProbD& P, int* words, int* pre, long long* qsv,
+                                             int logT, const LpHash& hs, long long g, long long* __restrict__ rowsize) {
+  constexpr int S = COMP ? 2 : 1;
+  const int T = 1 << logT;
+  const int b = inst_of(P.arow0s, P.ninst, g);
+  const InstD& I = P.inst[b];
+  const long long i = g - I.arow0;
+  for (int x = tm.lane; x < T; x += TW) {
+    if (COMP) reinterpret_cast<int2*>(words)[x] = make_int2(kEmpty, 0);
+    else words[x] = kEmpty;
+  }
+  __syncwarp(tm.mask);
+  const long long a0 = rp_at(I.A, i), a1 = rp_at(I.A, i + 1);
+  const long long brow0 = I.brow0;
+  const int* __restrict__ Aj = I.A.cj;
+  int fresh = 0;
+  for (long long c = a0; c < a1; c += TW) {
+    const long long p = c + tm.lane;
+    long long qs = 0;
+    int ql = 0;
+    if (p < a1) {
+      const int j = Aj[p];
+      if (COMP) {
+        qs = P.Bcp[brow0 + j];
+        ql = (int)(P.Bcp[brow0 + j + 1] - qs);
+      } else {
+        qs = rp_at(I.B, j);
+        ql = (int)(rp_at(I.B, j + 1) - qs);
+      }
+    }
+    fresh += union_chunk<TW, S, COMP>(tm.mask, tm.lane, pre, qsv, qs, ql, COMP ? P.csi : I.B.cj, P.cs, words,
+                                      hs, P.status, 1, g);
+  }
+  // claimed slots, or (compressed) newly set column bits, summed over the team
+  long long cnt = fresh;
+#pragma unroll
+  for (int d = TW / 2; d > 0; d >>= 1) cnt += __shfl_xor_sync(tm.mask, cnt, d, TW);
+  if (tm.lane == 0) rowsize[g] = cnt;
+  __syncwarp(tm.mask);
+}
+
 template <int TW, bool COMP>
 __global__ void __launch_bounds__(256, 4) k_sym_warp(ProbD P, const int* __restrict__ rows, long long nrows,
                                                      int logT, long long* __restrict__ rowsize) {
@@ -162,43 +205,95 @@ __global__ void __launch_bounds__(256, 4) k_sym_warp(ProbD P, const int* __restr
   long long* qsv = reinterpret_cast<long long*>(base + al16((size_t)T * 4 * S) + al16((size_t)(TW + 1) * 4));
   const long long team = (long long)blockIdx.x * tm.per_cta + tm.id;
   const long long nteams = (long long)gridDim.x * tm.per_cta;
+  for (long long r = team; r < nrows; r += nteams)
+    sym_warp_row<TW, COMP>(tm, P, words, pre, qsv, logT, hs, rows[r], rowsize);
+}
+
+// Compressed warp rows on a bitmap window (B rows sorted): the column sets of
+// row i lie between the first set of the first and the last set of the last
+// column among the compressed B rows over A(i,:); when that window is at most
+// kSymWbWords sets wide the union is a bitmap over it, addressed directly by
+// set index (no hashing, no probing), and the row size is the number of
+// column bits the inserts set first.  The words of the window are cleared
+// after the row.  Wider rows take the hash path (sym_warp_row) in the same
+// shared memory.
+constexpr int kSymWbWords = 1344;
+
+__host__ __device__ size_t symwb_team_bytes(int T) {
+  const size_t a = al16((size_t)kSymWbWords * 4), h = al16((size_t)T * 8);
+  return (a > h ? a : h) + al16((size_t)33 * 4) + al16((size_t)32 * 8);
+}
+
+__global__ void __launch_bounds__(256, 4) k_sym_wb(ProbD P, const int* __restrict__ rows, long long nrows, int logT,
+                                                   long long* __restrict__ rowsize) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Team<32> tm;
+  const int T = 1 << logT;
+  const LpHash hs(logT, P.hash_mode);
+  const size_t tb = symwb_team_bytes(T);
+  unsigned char* base = smem + (size_t)tm.id * tb;
+  const size_t tab = tb - al16((size_t)33 * 4) - al16((size_t)32 * 8);
+  unsigned* bits = reinterpret_cast<unsigned*>(base);
+  int* pre = reinterpret_cast<int*>(base + tab);
+  long long* qsv = reinterpret_cast<long long*>(base + tab + al16((size_t)33 * 4));
+  const int lane = tm.lane;
+  const unsigned full = 0xffffffffu;
+  bool clean = false;
+  const long long team = (long long)blockIdx.x * tm.per_cta + tm.id;
+  const long long nteams = (long long)gridDim.x * tm.per_cta;
   for (long long r = team; r < nrows; r += nteams) {
     const long long g = rows[r];
     const int b = inst_of(P.arow0s, P.ninst, g);
     const InstD& I = P.inst[b];
     const long long i = g - I.arow0;
-    for (int x = tm.lane; x < T; x += TW) {
-      if (COMP) reinterpret_cast<int2*>(words)[x] = make_int2(kEmpty, 0);
-      else words[x] = kEmpty;
-    }
-    __syncwarp(tm.mask);
     const long long a0 = rp_at(I.A, i), a1 = rp_at(I.A, i + 1);
     const long long brow0 = I.brow0;
     const int* __restrict__ Aj = I.A.cj;
-    int fresh = 0;
-    for (long long c = a0; c < a1; c += TW) {
-      const long long p = c + tm.lane;
-      long long qs = 0;
-      int ql = 0;
+    long long qs = 0;
+    int ql = 0;
+    auto load_chunk = [&](long long c) {
+      const long long p = c + lane;
+      qs = 0;
+      ql = 0;
       if (p < a1) {
         const int j = Aj[p];
-        if (COMP) {
-          qs = P.Bcp[brow0 + j];
-          ql = (int)(P.Bcp[brow0 + j + 1] - qs);
-        } else {
-          qs = rp_at(I.B, j);
-          ql = (int)(rp_at(I.B, j + 1) - qs);
-        }
+        qs = P.Bcp[brow0 + j];
+        ql = (int)(P.Bcp[brow0 + j + 1] - qs);
       }
-      fresh += union_chunk<TW, S, COMP>(tm.mask, tm.lane, pre, qsv, qs, ql, COMP ? P.csi : I.B.cj, P.cs, words,
-                                        hs, P.status, 1, g);
+    };
+    unsigned smin = 0xffffffffu, smax = 0u;
+    for (long long c = a0; c < a1; c += 32) {
+      load_chunk(c);
+      if (ql > 0) {
+        smin = min(smin, (unsigned)P.csi[qs]);
+        smax = max(smax, (unsigned)P.csi[qs + ql - 1]);
+      }
     }
-    // claimed slots, or (compressed) newly set column bits, summed over the team
-    long long cnt = fresh;
-#pragma unroll
-    for (int d = TW / 2; d > 0; d >>= 1) cnt += __shfl_xor_sync(tm.mask, cnt, d, TW);
-    if (tm.lane == 0) rowsize[g] = cnt;
-    __syncwarp(tm.mask);
+    smin = __reduce_min_sync(full, smin);
+    smax = __reduce_max_sync(full, smax);
+    if (smin > smax || smax - smin >= (unsigned)(kSymWbWords - 3)) {
+      sym_warp_row<32, true>(tm, P, reinterpret_cast<int*>(bits), pre, qsv, logT, hs, g, rowsize);
+      clean = false;
+      continue;
+    }
+    const unsigned span = smax - smin + 1u;
+    if (!clean) {
+      uint4* c4 = reinterpret_cast<uint4*>(bits);
+      for (int x = lane; x < kSymWbWords / 4; x += 32) c4[x] = make_uint4(0u, 0u, 0u, 0u);
+      clean = true;
+      __syncwarp();
+    }
+    int nb = 0;
+    const bool one_chunk = a1 - a0 <= 32;
+    for (long long c = a0; c < a1; c += 32) {
+      if (!one_chunk) load_chunk(c);
+      nb += wb_union_chunk<32, true>(full, lane, pre, qsv, qs, ql, P.csi, P.cs, bits, smin, span, P.status, 4, g);
+    }
+    const unsigned cnt = __reduce_add_sync(full, (unsigned)nb);
+    if (lane == 0) rowsize[g] = (long long)cnt;
+    uint4* c4 = reinterpret_cast<uint4*>(bits);
+    for (int x = lane; x < (int)((span + 3u) >> 2); x += 32) c4[x] = make_uint4(0u, 0u, 0u, 0u);
+    __syncwarp();
   }
 }
 
@@ -398,6 +493,20 @@ cudaError_t run_warp(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, lon
   return cudaGetLastError();
 }
 
+cudaError_t run_wb(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, long long* rowsize) {
+  const size_t tb = symwb_team_bytes(1 << S.logT);
+  const int teams = 8;
+  const size_t smem = tb * teams;
+  if (smem > (size_t)L.max_smem_optin) return cudaErrorInvalidConfiguration;
+  auto kern = k_sym_wb;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  KKS_LAUNCHED();
+  kern<<<resident_grid(kern, 32 * teams, smem, L.num_sms, (S.nrows + teams - 1) / teams), 32 * teams, smem,
+         L.stream>>>(P, S.rows, S.nrows, S.logT, rowsize);
+  return cudaGetLastError();
+}
+
 template <bool COMP>
 cudaError_t run_thread(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, long long* rowsize) {
   auto kern = k_sym_thread<COMP>;
@@ -454,7 +563,7 @@ cudaError_t dispatch(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, lon
   switch (S.cls) {
     case kClsT1: return run_thread<COMP>(L, P, S, rowsize);
     case kClsW8: return run_warp<8, COMP>(L, P, S, rowsize);
-    case kClsW32: return run_warp<32, COMP>(L, P, S, rowsize);
+    case kClsW32: return (COMP && S.window) ? run_wb(L, P, S, rowsize) : run_warp<32, COMP>(L, P, S, rowsize);
     case kClsC256: return run_hash<256, COMP>(L, P, S, rowsize);
     case kClsC1024: return run_hash<1024, COMP>(L, P, S, rowsize);
     case kClsDense: return run_dense<COMP>(L, P, S, rowsize);

@@ -568,6 +568,112 @@ def test_positions_straddling_and_colliding_sets(ops):
             assert_matches_oracle(A, B, Cd, np.float64)
 
 
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_warp_row_sorts(ops, dtype):
+    """Warp rows of more than 64 columns on the hash-and-sort path (compression
+    off): uniform columns take the bucket sort, rows whose columns bunch in a
+    narrow range next to a far outlier take the bitonic sort, and short rows
+    the register sort; all against the oracle."""
+    rng = np.random.default_rng(12)
+    # uniform: 40 random columns per B row over 200 000 columns
+    B1 = w.random_csr(400, 200000, lengths=np.full(400, 40), seed=13)
+    A1 = w.random_csr(600, 400, lengths=rng.integers(1, 12, 600), seed=14)
+    # bunched: B row j holds columns j .. j + 39 and one far column
+    n, k = 64, 100000
+    rows = np.repeat(np.arange(n), 41)
+    cols = np.concatenate([np.append(np.arange(j, j + 40), k - 1 - j) for j in range(n)])
+    B2 = csr_from_coo(n, k, rows, cols, rng.uniform(-1, 1, rows.size))
+    A2 = w.random_csr(300, n, lengths=np.full(300, 8), seed=15)
+    for A, B in ((A1, B1), (A2, B2)):
+        h, _, _, Cd = run(ops, A, B, dtype, compression=0)
+        assert h.stats()["bin_rows_numeric"][2] > 0
+        assert_matches_oracle(A, B, Cd, dtype)
+        h.close()
+
+
+@pytest.mark.parametrize("comp", [-1, 0, 1])
+def test_long_rows_queue(ops, comp):
+    """Rows of A and of B longer than 1024 entries (graph hubs) go to the
+    warp-served queues of the row-statistics and compression passes; short,
+    medium and long rows mix in one block of rows."""
+    rng = np.random.default_rng(21)
+    la = rng.integers(0, 40, 600)
+    la[[3, 200, 201, 599]] = [2500, 1100, 4000, 1500]
+    A = w.random_csr(600, 5000, lengths=la, seed=22)
+    lb = rng.integers(0, 30, 5000)
+    lb[rng.choice(5000, 12, replace=False)] = rng.integers(1025, 6000, 12)
+    B = w.random_csr(5000, 8000, lengths=lb, seed=23)
+    for dtype in (np.float64, np.float32):
+        h, _, _, Cd = run(ops, A, B, dtype, compression=comp)
+        assert_matches_oracle(A, B, Cd, dtype)
+        st = h.stats()
+        fm_ref = oracle.row_flops(A, B)[1]
+        assert st["f_m"] == fm_ref
+        h.close()
+
+
+def _banded_with_far_columns(seed):
+    """B (5000 x 200 000): row j holds 8 sorted columns in [30 j, 30 j + 60), and
+    every 97th row one more column 100 000 further on; A (3000 x 5000): row i
+    holds 5 to 45 consecutive entries from column i.  Rows of C whose A row
+    reaches a B row with a far column have a window of column sets far wider
+    than the bitmap window; the others fit it.  Rows of more than 32 entries
+    of A run over several chunks, and the short B rows take the flat product
+    mode."""
+    rng = np.random.default_rng(seed)
+    n, k = 5000, 200000
+    rows, cols = [], []
+    for j in range(n):
+        c = np.sort(rng.choice(60, size=8, replace=False)) + 30 * j
+        if j % 97 == 0:
+            c = np.append(c, 30 * j + 100000)
+        c = c[c < k]
+        rows.append(np.full(c.size, j))
+        cols.append(c)
+    B = csr_from_coo(n, k, np.concatenate(rows), np.concatenate(cols),
+                     rng.uniform(-1, 1, sum(x.size for x in cols)))
+    m = 3000
+    lens = rng.integers(5, 46, m)
+    ra = np.repeat(np.arange(m), lens)
+    ca = np.concatenate([np.arange(i, i + l) for i, l in zip(range(m), lens)])
+    A = csr_from_coo(m, n, ra, ca, rng.uniform(-1, 1, ra.size))
+    return A, B
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_window_positions(ops, dtype):
+    """Compressed warp rows on the bitmap window of column sets (B rows sorted)
+    against the hash tables of column sets and the oracle: rows whose window
+    fits, rows that fall back to the hash path inside the same kernel, rows of
+    several chunks of A, the flat and the one-B-row-per-pass product modes."""
+    cases = [(w.stencil3d_27pt(20, seed=1),) * 2, _banded_with_far_columns(7)]
+    for A, B in cases:
+        ref = None
+        for win in (True, False):
+            h, _, _, Cd = run(ops, A, B, dtype, compression=1, window_positions=win)
+            st = h.stats()
+            assert st["rows_positions"] > 0
+            ref = assert_matches_oracle(A, B, Cd, dtype, ref)
+            # numeric reuse through the same plan, new values
+            A2 = A.with_values(np.random.default_rng(3).uniform(-1, 1, A.nnz))
+            Ad2 = dev(A2, dtype)
+            Bd = dev(B, dtype)
+            h2 = ops.SpGEMM(compression=1, window_positions=win)
+            rp, nnz = h2.symbolic(Ad2, Bd)
+            C2 = h2.numeric(Ad2, Bd, rp, nnz)
+            h2.numeric(Ad2, Bd, rp, nnz, C2.colidx, C2.values)
+            h2.sync()
+            assert_matches_oracle(A2, B, C2, dtype)
+            # values only on C's known pattern (masked product keyed by C(i,:))
+            B3 = B.with_values(np.random.default_rng(4).uniform(-1, 1, B.nnz))
+            Bd.values.copy_(torch.as_tensor(B3.values.astype(dtype)))
+            h2.numeric_reuse(Ad2, Bd, C2)
+            h2.sync()
+            assert_matches_oracle(A2, B3, C2, dtype)
+            h2.close()
+            h.close()
+
+
 def test_positions_batched_all_or_none(ops):
     """A plan takes positions only when every product is compressed."""
     pairs = w.batched_pairs(count=6, nmin=500, nmax=6000, seed=11)
