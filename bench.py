@@ -18,8 +18,9 @@ graph) at full size with bounded repeats.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Multi-GPU (torchrun): every rank multiplies its own copy of the workload
-(independent row blocks; no collective on the data path), scaling "weak".
+Multi-GPU (torchrun, N > 1): the row partition of the step (flop-balanced
+row ranges of A for A·A and of Pᵀ for Pᵀ·(A·P), operands replicated), an
+all-gather of the shard sizes as the one exchange, scaling "strong".
 """
 
 from __future__ import annotations
@@ -68,12 +69,21 @@ def parse_args(argv=None):
                    help="numeric-reuse repeats of the batched512 sections of the default line")
     p.add_argument("--numeric-only", action="store_true",
                    help="profiling aid: one symbolic and two numeric calls of A*A on --grid, no timing")
+    p.add_argument("--timeline", action="store_true",
+                   help="profiling aid: kernel timeline (torch.profiler) of one step of --workload "
+                        "(stencil27_100, rmat18 or batched512): per-kernel totals and the GPU's idle gaps")
     p.add_argument("--serial", action="store_true",
                    help="stencil27_100: run the one-plan triple product after A*A on one stream")
     p.add_argument("--rap", choices=["fused", "two"], default="fused",
                    help="stencil27_100: the triple product in one plan, or as transpose + two products")
-    p.add_argument("--window", type=int, default=1, choices=(0, 1),
-                   help="1: warp rows of compressed products on sorted B use the bitmap window of column sets")
+    p.add_argument("--window", type=int, default=1, choices=tuple(range(8)),
+                   help="option window_positions: bitmap windows of column sets in the symbolic phase (bit 0), "
+                        "the numeric phase (bit 1), masked products / numeric reuse (bit 2)")
+    p.add_argument("--stage-b", type=int, default=0, choices=(0, 1),
+                   help="option stage_b: dense-window rows stage their B entries with cp.async")
+    p.add_argument("--tune-aa", type=int, default=0, choices=(0, 1),
+                   help="stencil27_100: 1 lets the autotuner pick the numeric kernels of A*A per row bin "
+                        "(on the first numeric call, in the warm-up)")
     p.add_argument("--numeric-positions", type=int, default=1, choices=(0, 1),
                    help="1: warp rows of compressed products take positions from the column sets; "
                         "0: hash-and-sort numeric kernel")
@@ -194,7 +204,7 @@ class StencilStep:
     a worker thread, while A·A runs on the current stream (the two products are
     independent); the step ends when both have."""
 
-    def __init__(self, A, P, device, positions=True, rap="fused", concurrent=True, window=True):
+    def __init__(self, A, P, device, positions=True, rap="fused", concurrent=True, window=1, tune_aa=False):
         import torch
         from paper_1801_03065_gb300 import ops
         self.torch, self.ops = torch, ops
@@ -204,9 +214,11 @@ class StencilStep:
         pos = bool(positions)
         self.positions = pos
         self.rap = rap
-        self.window = bool(window)
+        self.window = int(window)
+        self.tune_aa = bool(tune_aa)
         kw = dict(numeric_positions=pos, window_positions=self.window)
-        self.hAA, self.hAP, self.hRAP = ops.SpGEMM(**kw), ops.SpGEMM(**kw), ops.SpGEMM(**kw)
+        self.hAA = ops.SpGEMM(tune=self.tune_aa, **kw)
+        self.hAP, self.hRAP = ops.SpGEMM(**kw), ops.SpGEMM(**kw)
         self.hT = ops.SpGEMM()
         self._fm_two = None
         self.concurrent = bool(concurrent) and rap == "fused"
@@ -295,6 +307,139 @@ class StencilStep:
             h.close()
 
 
+def shard_bounds(prefix, rank, world):
+    """Rows [r0, r1) of this rank's shard: boundaries at equal shares of the
+    flops in `prefix` (int64 [m + 1], host), rows never split (host only)."""
+    from paper_1801_03065_gb300 import ops
+    b = ops.partition_rows(prefix, world)
+    return b[rank], b[rank + 1]
+
+
+def shard_exchange(nnz_list, world, device=None):
+    """The one exchange of row sharding: an all-gather of every rank's shard
+    sizes (one int64 per product).  Returns (this rank's first entry of each
+    product's global C, each product's global nnz)."""
+    import torch
+    mine = torch.tensor([int(x) for x in nnz_list], dtype=torch.int64, device=device)
+    if world == 1:
+        return [0] * len(nnz_list), [int(x) for x in nnz_list]
+    import torch.distributed as dist
+    allv = [torch.zeros_like(mine) for _ in range(world)]
+    dist.all_gather(allv, mine)
+    rank = dist.get_rank()
+    rows = [[int(v) for v in t.tolist()] for t in allv]
+    first = [sum(rows[r][k] for r in range(rank)) for k in range(len(nnz_list))]
+    total = [sum(rows[r][k] for r in range(world)) for k in range(len(nnz_list))]
+    return first, total
+
+
+class ShardedStencilStep:
+    """Row-sharded stencil27_100 step for N ranks (the 1-D row partition of
+    Section 3.1.1 across GPUs): rank r multiplies the rows of its flop-balanced
+    range of A by the whole (replicated) A, and the rows of its range of P^T by
+    A*P, which every rank forms in full (3.6 % of the step's multiplications,
+    counted once); the shards' sizes are all-gathered to place each block in
+    the global C.  Partitions come from the patterns only and are computed at
+    set-up."""
+
+    def __init__(self, A, P, device, rank, world):
+        import torch
+        from paper_1801_03065_gb300 import ops
+        self.torch, self.ops, self.rank, self.world, self.device = torch, ops, rank, world, device
+        self.Ad = ops.CsrMatrix.from_host(A.rowptr, A.colidx, A.values, A.shape, device=device)
+        self.Pd = ops.CsrMatrix.from_host(P.rowptr, P.colidx, P.values, P.shape, device=device)
+        self.hAA, self.hAP, self.hR, self.hT = ops.SpGEMM(), ops.SpGEMM(), ops.SpGEMM(), ops.SpGEMM()
+        self.Pt = self.hT.transpose(self.Pd)[0]
+        pre_aa = self.hAA.row_flops(self.Ad, self.Ad).cpu().numpy()
+        self.aa_rows = shard_bounds(pre_aa, rank, world)
+        self.AP = self.hAP.multiply(self.Ad, self.Pd)
+        pre_r = self.hR.row_flops(self.Pt, self.AP).cpu().numpy()
+        self.r_rows = shard_bounds(pre_r, rank, world)
+        self.Ablk = ops.row_block(self.Ad, *self.aa_rows)
+        self.Ptblk = ops.row_block(self.Pt, *self.r_rows)
+        self.fm_shards = int(pre_aa[self.aa_rows[1]] - pre_aa[self.aa_rows[0]]) + \
+            int(pre_r[self.r_rows[1]] - pre_r[self.r_rows[0]])
+        self.fm_ap = int(self.hAP.stats()["f_m"])
+        self.C1 = self.C2 = None
+        self.offsets = None
+
+    def step(self):
+        Ad, Pd, ops = self.Ad, self.Pd, self.ops
+        self.C1 = self.hAA.multiply(self.Ablk, Ad)
+        self.AP = self.hAP.multiply(Ad, Pd)
+        self.C2 = self.hR.multiply(self.Ptblk, self.AP)
+        self.offsets = shard_exchange([self.C1.nnz, self.C2.nnz], self.world, self.device)
+
+    def flops(self):
+        """Multiplications of this rank's shards, plus A*P on rank 0 only."""
+        return self.fm_shards + (self.fm_ap if self.rank == 0 else 0)
+
+    def close(self):
+        for h in (self.hAA, self.hAP, self.hR, self.hT):
+            h.close()
+
+
+def run_sharded(args):
+    """--gpus N > 1 under torchrun: the row-sharded step on every rank (NCCL
+    for the shard-size exchange), strong scaling; rank 0 prints the line."""
+    import torch
+    import torch.distributed as dist
+    import workloads as w
+    from paper_1801_03065_gb300 import ops
+    rank, world, local = dist_env()
+    dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    A = w.stencil3d_27pt(args.grid, seed=1)
+    P = w.aggregation(args.grid, 3)
+    S = ShardedStencilStep(A, P, device, rank, world)
+    for _ in range(max(args.warmup, 3)):
+        S.step()
+    torch.cuda.synchronize()
+    dist.barrier()
+    clocks = ClockSampler(local).start()
+    l0 = ops.launch_count()
+    times = time_region(torch, S.step, args.steps)
+    launches = ops.launch_count() - l0
+    clk = clocks.stop()
+    dist.barrier()
+    t_step, flops_all = reduce_over_ranks(sum(times) / len(times), S.flops(), world, device)
+    # end to end: A and P from pinned host memory, the rank's C blocks back
+    pin = lambda x: torch.from_numpy(x).pin_memory()
+    hin = [pin(A.rowptr), pin(A.colidx), pin(A.values), pin(P.rowptr), pin(P.colidx), pin(P.values)]
+    dins = [S.Ad.rowptr, S.Ad.colidx, S.Ad.values, S.Pd.rowptr, S.Pd.colidx, S.Pd.values]
+
+    def e2e():
+        for d, hh in zip(dins, hin):
+            d.copy_(hh, non_blocking=True)
+        S.step()
+        outs = [x.cpu() for C in (S.C1, S.C2) for x in (C.rowptr, C.colidx, C.values)]
+        return sum(o.numel() * o.element_size() for o in outs)
+
+    d2h = e2e()
+    torch.cuda.synchronize()
+    te = time_region(torch, e2e, max(2, args.steps // 2))
+    t_e2e, _ = reduce_over_ranks(sum(te) / len(te), 0.0, world, device)
+    h2d = sum(x.numel() * x.element_size() for x in hin)
+    S.close()
+    dist.barrier()
+    if rank == 0:
+        value = 2.0 * flops_all / (t_step * 1e-3) / 1e9
+        print(json.dumps({
+            "metric": METRIC, "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(t_step, 4), "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "global_batch": 1, "flops_per_step": 2 * flops_all,
+                       "parallelism": "row partition over %d ranks (flop-balanced ranges of A and of P^T, "
+                                      "B = A and A*P replicated), all-gather of the shard sizes" % world,
+                       "l2": "inputs larger than L2"},
+            "gpu_launches": int(launches), "clocks": clk,
+            "e2e": {"value": round(2.0 * flops_all / (t_e2e * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
+                    "h2d_bytes_per_step": int(h2d) * world, "d2h_bytes_per_step": int(d2h) * world,
+                    "ms_per_step": round(t_e2e, 4)}}), flush=True)
+    dist.destroy_process_group()
+
+
 def time_region(torch, fn, steps):
     """Per-step CUDA-event times (ms) on the current stream; sync on both sides."""
     stream = torch.cuda.current_stream()
@@ -345,7 +490,7 @@ def run_ours(args):
     A = w.stencil3d_27pt(args.grid, seed=1)
     P = w.aggregation(args.grid, 3)
     S = StencilStep(A, P, device, positions=bool(args.numeric_positions), rap=args.rap,
-                    concurrent=not args.serial, window=bool(args.window))
+                    concurrent=not args.serial, window=int(args.window), tune_aa=bool(args.tune_aa))
     for _ in range(max(args.warmup, 1)):
         S.step()
     torch.cuda.synchronize()
@@ -381,7 +526,8 @@ def run_ours(args):
     # the other products of the step, one phase at a time (each on its own handle)
     Pd = S.Pd
     if S.rap == "fused":
-        T2 = StencilStep(A, P, device, positions=S.positions, rap="two", concurrent=False, window=S.window)
+        T2 = StencilStep(A, P, device, positions=S.positions, rap="two", concurrent=False, window=S.window,
+                         tune_aa=S.tune_aa)
         T2.step()
         two_step = lambda: (T2.hT.transpose(Pd, out=T2.Pt),
                             T2.hAP.symbolic(Ad, Pd, C_rowptr=T2.rpAP),
@@ -454,7 +600,8 @@ def run_ours(args):
         "roofline_fp64": {"bound": "alu", "achieved": round(alu_achieved, 4), "peak": round(fp64_peak_tflops, 4),
                           "unit": "TFLOP/s", "frac": round(alu_achieved / fp64_peak_tflops, 4),
                           "peak_kind": fp64_kind, "algorithmic_flops": 2 * stAA["f_m"]},
-        "stats_AA": {k: stAA[k] for k in ("f_m", "nnzC", "maxrs", "CF", "CMRF", "compressed")},
+        "stats_AA": {k: stAA[k] for k in ("f_m", "nnzC", "maxrs", "CF", "CMRF", "compressed", "tuned_bins",
+                                           "nbins_numeric", "rows_positions")},
         "rap": rap_summary(S, A, P, t_other, peak, peak_kind),
         "gpu_launches": int(launches),
         "clocks": clk,
@@ -510,7 +657,7 @@ def run_e2e(torch, S, A, P, args, world, flops_step):
     region ends when the last read-back has landed in host memory."""
     pin = lambda x: torch.from_numpy(x).pin_memory()
     S2 = StencilStep(A, P, S.Ad.rowptr.device, positions=S.positions, rap=S.rap, concurrent=S.concurrent,
-                     window=S.window)
+                     window=S.window, tune_aa=S.tune_aa)
     S2.step()
     sets = [S, S2]
     hA = [pin(A.rowptr), pin(A.colidx), pin(A.values)]
@@ -827,7 +974,7 @@ def run_numeric_only(args):
     from paper_1801_03065_gb300 import ops
     A = w.stencil3d_27pt(args.grid, seed=1)
     Ad = ops.CsrMatrix.from_host(A.rowptr, A.colidx, A.values, A.shape, device="cuda:0")
-    h = ops.SpGEMM(numeric_positions=bool(args.numeric_positions), window_positions=bool(args.window))
+    h = ops.SpGEMM(numeric_positions=bool(args.numeric_positions), window_positions=int(args.window))
     rp, nnz = h.symbolic(Ad, Ad)
     C = h.numeric(Ad, Ad, rp, nnz)
     h.sync()
@@ -840,6 +987,68 @@ def run_numeric_only(args):
     print(json.dumps({"grid": args.grid, "nnzC": nnz}))
 
 
+def run_timeline(args):
+    """One step of the workload under torch.profiler (CUPTI kernel records):
+    kernel time per name, span, busy and idle time of the GPU, largest gaps."""
+    import collections
+    import numpy as np
+    import torch
+    import workloads as w
+    from paper_1801_03065_gb300 import ops
+    from torch.profiler import ProfilerActivity, profile
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    if args.workload == "stencil27_100":
+        A = w.stencil3d_27pt(args.grid, seed=1)
+        S = StencilStep(A, w.aggregation(args.grid, 3), dev, window=int(args.window), tune_aa=bool(args.tune_aa))
+        fn, close = S.step, S.close
+    elif args.workload == "rmat18":
+        G = w.rmat_symmetric(scale=args.scale, seed=7)
+        Ad = ops.CsrMatrix.from_host(G.rowptr, G.colidx, G.values.astype(np.float32), G.shape, device=dev)
+        h = ops.SpGEMM(window_positions=int(args.window))
+        rp, nnz = h.symbolic(Ad, Ad)
+        C = h.numeric(Ad, Ad, rp, nnz)
+        fn = lambda: (h.symbolic(Ad, Ad, C_rowptr=rp), h.numeric(Ad, Ad, rp, nnz, C.colidx, C.values))
+        close = h.close
+    elif args.workload == "batched512":
+        pairs = w.batched_pairs(count=args.count, seed=11)
+        As = [ops.CsrMatrix.from_host(a.rowptr, a.colidx, a.values, a.shape, device=dev) for a, _ in pairs]
+        Bs = [ops.CsrMatrix.from_host(b.rowptr, b.colidx, b.values, b.shape, device=dev) for _, b in pairs]
+        h = ops.SpGEMM(tune=bool(args.tune))
+        rps, nnzs = h.batch_symbolic(As, Bs)
+        Cs = h.batch_numeric(As, Bs, rps, nnzs)
+        fn = lambda: (h.batch_symbolic(As, Bs), h.batch_numeric(As, Bs, rps, nnzs, [c.colidx for c in Cs],
+                                                                 [c.values for c in Cs]))
+        close = h.close
+    else:
+        raise SystemExit("--timeline: stencil27_100, rmat18 or batched512")
+    for _ in range(max(args.warmup, 1)):
+        fn()
+    torch.cuda.synchronize()
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        fn()
+        torch.cuda.synchronize()
+    ks = sorted((e.time_range.start, e.time_range.end, e.name) for e in prof.events()
+                if e.device_type == torch.autograd.DeviceType.CUDA)
+    close()
+    out = {"workload": args.workload, "kernels": len(ks)}
+    if ks:
+        t0, last, busy, gaps = ks[0][0], ks[0][0], 0.0, []
+        agg = collections.defaultdict(lambda: [0, 0.0])
+        for a, b, n in ks:
+            if a > last:
+                gaps.append((round(a - last, 1), n[:80]))
+            busy += max(0.0, b - max(a, last))
+            last = max(last, b)
+            agg[n][0] += 1
+            agg[n][1] += b - a
+        out.update({"span_us": round(last - t0, 1), "busy_us": round(busy, 1),
+                    "kernels_us": [(n[:100], c, round(t, 1)) for n, (c, t) in
+                                   sorted(agg.items(), key=lambda x: -x[1][1])[:30]],
+                    "largest_gaps_us": sorted(gaps, reverse=True)[:10]})
+    print(json.dumps(out), flush=True)
+
+
 def _base_line(args, value, t_ms, workload, dtype, extra):
     out = {"metric": METRIC, "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(t_ms, 4), "higher_is_better": True, "scaling": "weak",
@@ -848,7 +1057,7 @@ def _base_line(args, value, t_ms, workload, dtype, extra):
     return out
 
 
-def single_measure(A, vdt, steps, warmup, clocks=False):
+def single_measure(A, vdt, steps, warmup, clocks=False, **opts):
     """One product C = A·A: NoReuse (symbolic + numeric), numeric reuse, and the
     symbolic phase alone, with the HBM roofline of the numeric call."""
     import numpy as np
@@ -857,7 +1066,7 @@ def single_measure(A, vdt, steps, warmup, clocks=False):
     dev = torch.device("cuda", torch.cuda.current_device())
     tdt = torch.float32 if vdt == np.float32 else torch.float64
     Ad = ops.CsrMatrix.from_host(A.rowptr, A.colidx, A.values.astype(vdt), A.shape, device=dev)
-    h = ops.SpGEMM()
+    h = ops.SpGEMM(**opts)
     rp = torch.empty(A.nrows + 1, dtype=torch.int64, device=dev)
     rp, nnz = h.symbolic(Ad, Ad, C_rowptr=rp)
     Cj = torch.empty(nnz, dtype=torch.int32, device=dev)
@@ -915,7 +1124,8 @@ def run_single(args):
     wl = w.config_workload(args.workload, **({"scale": args.scale} if args.workload == "rmat18" else {}))
     A = wl["A"]
     vdt = np.float32 if wl["dtype"] == "f32" else np.float64
-    res = single_measure(A, vdt, args.steps, args.warmup, clocks=True)
+    res = single_measure(A, vdt, args.steps, args.warmup, clocks=True, stage_b=bool(args.stage_b),
+                         window_positions=int(args.window))
     if args.workload == "rmat18":
         desc = RMAT_DESC % A.nnz
         if args.scale != 18:
@@ -1083,8 +1293,13 @@ def main(argv=None):
     if args.numeric_only:
         run_numeric_only(args)
         return
+    if args.timeline:
+        run_timeline(args)
+        return
     if args.impl == "reference":
         run_reference(args)
+    elif dist_env()[1] > 1 and args.workload == "stencil27_100":
+        run_sharded(args)
     elif args.workload == "batched512":
         run_batched(args)
     elif args.workload in ("rmat18", "laplace5_64"):

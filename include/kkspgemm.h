@@ -104,12 +104,21 @@ typedef struct {
                                     Thread-Flat-Parallel, 1 Team-Sequential with the linked-list
                                     accumulator (Section 3.1.2), 2 Thread-Parallel; with tune = 1 the
                                     tuner also times the other two per bin */
-  int32_t window_positions;      /* 1 (default): with numeric_positions, warp-team rows of compressed
+  int32_t window_positions;      /* bitmap windows of column sets: warp-team rows of compressed
                                     products whose B rows are all sorted keep their column sets in a
                                     bitmap over the row's window of sets (first to last set, at most
                                     1344 sets = 43 008 columns), addressed directly instead of hashed
                                     (Section 3.1.2's dense accumulator over the row's own range);
-                                    wider rows use the hash tables.  0: hash tables only */
+                                    wider rows use the hash tables.  bit 0 (default on): symbolic
+                                    phase; bit 1: numeric phase with numeric_positions (the tuner
+                                    also times it per bin); bit 2: masked products and numeric reuse
+                                    on sorted patterns.  0: hash tables only.  Values 0 to 7 */
+  int32_t stage_b;               /* dense-window numeric rows (one chunk of A, sorted B rows): 1 copies
+                                    the B entries of the next block of products into shared memory with
+                                    asynchronous copies (cp.async) while the current block is added,
+                                    instead of loading them from global memory per product; 0 (default)
+                                    loads them per product */
+  int32_t reserved;
 } spgemm_options_t;
 
 /* Statistics of the last symbolic call (Section 4 results-table columns). */

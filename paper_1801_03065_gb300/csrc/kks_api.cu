@@ -91,6 +91,7 @@ struct BinRun {
   int hash;   // LpHash mode used for this bin (the tuner may change it)
   int part = 0;   // CTA hash classes: partitioning scheme (0 flat, 1 Team-Sequential + LL, 2 Thread-Parallel)
   int window = 0;   // W32 positions rows: bitmap window over the row's column sets
+  int stage = 0;    // dense rows: B entries staged into shared memory by asynchronous copies
 };
 
 constexpr int kRing = 8;
@@ -355,7 +356,7 @@ BinCfg sym_cfg(kks_handle* h, int comp) {
   BinCfg c = base_cfg(h);
   c.cta_max_logT = cta_max_logT_sym(h, comp);
   // 512-thread dense team: bitmap + chunk scratch in shared memory
-  c.dense_max_kwords = ((long long)h->max_smem - 12 * 1024) / 4;
+  c.dense_max_kwords = ((long long)h->max_smem - 21 * 1024) / 4;
   // the bitmap (kw words) is preferred once the hash table would be as large
   c.dense_ratio = comp ? 4 : 64;
   // one thread per row when the row has at most kT1SymKeys products
@@ -711,7 +712,7 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
     S.compressed = comp;
     S.max_occ = h->opt.l1_max_occupancy;
     S.fetch = B<unsigned long long>(h, kBufFetch);
-    S.window = (comp && h->b_sorted && h->opt.window_positions && h->opt.numeric_positions) ? 1 : 0;
+    S.window = (comp && h->b_sorted && (h->opt.window_positions & 1)) ? 1 : 0;
     long long kmax = 0;
     for (int b = 0; b < count; ++b) kmax = std::max<long long>(kmax, h->inst[b].k);
     // dense rows only come from products whose bitmap fits (checked per row)
@@ -787,7 +788,8 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
     const int pos = (positions_ok && (cls == kClsW8 || cls == kClsW32)) ? 1 : 0;
     h->num_bins.push_back(BinRun{cls, bin_logT(t), pos, noff[t], cnt, h->opt.hash_function,
                                  (cls == kClsC256 || cls == kClsC1024) ? h->opt.cta_partition : 0,
-                                 (pos && cls == kClsW32 && h->b_sorted && h->opt.window_positions) ? 1 : 0});
+                                 (pos && cls == kClsW32 && h->b_sorted && (h->opt.window_positions & 2)) ? 1 : 0,
+                                 cls == kClsDense ? h->opt.stage_b : 0});
     if (cls == kClsSpill) {
       spill_rows += cnt;
       spill_logT = std::max(spill_logT, bin_logT(t));
@@ -876,6 +878,7 @@ cudaError_t launch_bin(kks_handle* h, const BinRun& r, cudaStream_t s) {
   S.fetch = B<unsigned long long>(h, kBufFetch);
   S.part = (r.cls == kClsC256 || r.cls == kClsC1024) ? r.part : 0;
   S.window = (S.positions && r.cls == kClsW32) ? r.window : 0;
+  S.stage = r.cls == kClsDense ? r.stage : 0;
   if (r.cls == kClsDense) {
     S.kwords_max = h->num_dense_kw;
   } else if (r.cls == kClsSpill) {
@@ -898,14 +901,21 @@ cudaError_t launch_bin(kks_handle* h, const BinRun& r, cudaStream_t s) {
 // launch computes the bin's rows of C completely, so tuning runs inside the
 // first numeric call and leaves a correct C behind.
 spgemm_status_t tune_numeric(kks_handle* h, cudaStream_t s) {
-  BinCfg c = num_cfg(h, h->dtype, h->num_kmax);
   const int cta_max = cta_max_logT_num(h, h->dtype, h->num_kmax);
-  cudaEvent_t e0, e1;
-  KKS_CU(cudaEventCreate(&e0));
-  KKS_CU(cudaEventCreate(&e1));
+  // timing events only when some bin is not in the cache (a re-plan of a
+  // tuned problem costs no device work here)
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto events = [&]() -> cudaError_t {
+    if (e0) return cudaSuccess;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    return e;
+  };
   int changed = 0;
   for (BinRun& r : h->num_bins) {
-    if (r.cls != kClsW8 && r.cls != kClsW32 && r.cls != kClsC256 && r.cls != kClsC1024) continue;
+    if (r.cls != kClsW8 && r.cls != kClsW32 && r.cls != kClsC256 && r.cls != kClsC1024 &&
+        !(r.cls == kClsDense && h->b_sorted))
+      continue;
     bool cached = false;
     for (const auto& te : h->tune_cache) {
       if (te.cls == r.cls && te.logT == r.logT && te.count == r.count && te.dtype == h->dtype &&
@@ -914,7 +924,7 @@ spgemm_status_t tune_numeric(kks_handle* h, cudaStream_t s) {
         p.off = r.off;
         p.count = r.count;
         if (p.cls != r.cls || p.logT != r.logT || p.hash != r.hash || p.compressed != r.compressed ||
-            p.part != r.part || p.window != r.window)
+            p.part != r.part || p.window != r.window || p.stage != r.stage)
           ++changed;
         r = p;
         cached = true;
@@ -926,8 +936,13 @@ spgemm_status_t tune_numeric(kks_handle* h, cudaStream_t s) {
     std::vector<BinRun> cand;
     cand.push_back(r);
     BinRun x = r;
-    x.hash = 1 - r.hash;
-    cand.push_back(x);
+    if (r.cls == kClsDense) {
+      x.stage = 1 - r.stage;   // staged B entries against per-product loads
+      cand.push_back(x);
+    } else {
+      x.hash = 1 - r.hash;
+      cand.push_back(x);
+    }
     if (h->positions_ok && (r.cls == kClsW8 || r.cls == kClsW32)) {
       x = r;
       x.compressed = 1 - r.compressed;   // column-set positions against the hash-and-sort kernel
@@ -951,7 +966,7 @@ spgemm_status_t tune_numeric(kks_handle* h, cudaStream_t s) {
     auto max_logT = [&](int cls) {
       return cls == kClsW8 ? 5 : cls == kClsW32 ? 10 : cls == kClsC256 ? std::min(12, cta_max) : cta_max;
     };
-    if (r.logT + 1 <= max_logT(r.cls)) {
+    if (r.cls != kClsDense && r.logT + 1 <= max_logT(r.cls)) {
       x = r;
       x.logT = r.logT + 1;
       cand.push_back(x);
@@ -961,7 +976,15 @@ spgemm_status_t tune_numeric(kks_handle* h, cudaStream_t s) {
       x = r;
       x.cls = up;
       if (up != kClsW32) x.compressed = 0;
-      x.window = (x.compressed && up == kClsW32 && h->b_sorted && h->opt.window_positions) ? 1 : 0;
+      x.window = (x.compressed && up == kClsW32 && h->b_sorted && (h->opt.window_positions & 2)) ? 1 : 0;
+      cand.push_back(x);
+    }
+    if ((r.cls == kClsC256 || r.cls == kClsC1024) && h->opt.dense != 0) {
+      x = r;   // the accumulator: dense windows of the row's columns instead of the hash table
+      x.cls = kClsDense;
+      x.logT = 0;
+      x.compressed = 0;
+      x.part = 0;
       cand.push_back(x);
     }
     const int down = r.cls == kClsW32 ? kClsW8 : r.cls == kClsC256 ? kClsW32 : r.cls == kClsC1024 ? kClsC256 : 0;
@@ -969,11 +992,12 @@ spgemm_status_t tune_numeric(kks_handle* h, cudaStream_t s) {
       x = r;
       x.cls = down;
       x.compressed = (h->positions_ok && (down == kClsW8 || down == kClsW32)) ? 1 : 0;
-      x.window = (x.compressed && down == kClsW32 && h->b_sorted && h->opt.window_positions) ? 1 : 0;
+      x.window = (x.compressed && down == kClsW32 && h->b_sorted && (h->opt.window_positions & 2)) ? 1 : 0;
       cand.push_back(x);
     }
     float best = 1e30f;
     BinRun pick = r;
+    KKS_CU(events());
     for (const BinRun& cd : cand) {
       float t_min = 1e30f;
       for (int rep = 0; rep < 3; ++rep) {
@@ -991,14 +1015,13 @@ spgemm_status_t tune_numeric(kks_handle* h, cudaStream_t s) {
       }
     }
     if (pick.cls != r.cls || pick.logT != r.logT || pick.hash != r.hash || pick.compressed != r.compressed ||
-        pick.part != r.part || pick.window != r.window)
+        pick.part != r.part || pick.window != r.window || pick.stage != r.stage)
       ++changed;
     r = pick;
     h->tune_cache.push_back({cls0, logT0, h->dtype, pos0, r.count, pick});
   }
-  (void)c;
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
   h->tuned = true;
   h->stats.tuned_bins = changed;
   h->stats.rows_positions = rows_positions(h);
@@ -1170,7 +1193,7 @@ spgemm_status_t run_masked_plan(kks_handle* h, const MaskedD& M, int dtype, int 
     S.nrows = plan.cnt[b];
     S.dtype = dtype;
     S.positions = (plan.sorted && (S.cls == kClsW8 || S.cls == kClsW32)) ? 1 : 0;
-    S.window = (S.positions && S.cls == kClsW32 && h->opt.window_positions) ? 1 : 0;
+    S.window = (S.positions && S.cls == kClsW32 && (h->opt.window_positions & 4)) ? 1 : 0;
     if (S.cls == kClsSpill) {
       S.pool = h->buf[pool_buf];
       S.chunk_slots = plan.gslots;
@@ -1204,7 +1227,8 @@ spgemm_status_t spgemm_handle_create(spgemm_handle_t* out, const spgemm_options_
       h->opt.compression < -1 || h->opt.compression > 1 || h->opt.hash_function < 0 || h->opt.hash_function > 1 ||
       h->opt.slots_per_key_log2 < 0 || h->opt.slots_per_key_log2 > 4 || h->opt.numeric_positions < 0 ||
       h->opt.cta_partition < 0 || h->opt.cta_partition > 2 ||
-      h->opt.numeric_positions > 1 || h->opt.window_positions < 0 || h->opt.window_positions > 1) {
+      h->opt.numeric_positions > 1 || h->opt.window_positions < 0 || h->opt.window_positions > 7 ||
+      h->opt.stage_b < 0 || h->opt.stage_b > 1) {
     delete h;
     return SPGEMM_ERR_INVALID_ARG;
   }

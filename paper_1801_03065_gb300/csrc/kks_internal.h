@@ -249,6 +249,8 @@ struct NumLaunch {
                          // 2 Thread-Parallel (Section 3.1.1)
   int window;            // warp positions rows with b_sorted: bitmap-window kernel (rows whose set
                          // window is too wide fall back to the hash path inside it)
+  int stage;             // dense class: B entries of one-chunk rows staged by cp.async
+  int pad;
 };
 cudaError_t launch_numeric(const LaunchCtx&, const ProbD&, const NumLaunch&);
 

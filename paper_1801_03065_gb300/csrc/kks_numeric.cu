@@ -985,12 +985,39 @@ __global__ void __launch_bounds__(32 * kWbTeams, 5) k_num_wb(ProbD P, const int*
 
   const long long team = (long long)blockIdx.x * tm.per_cta + tm.id;
   const long long nteams = (long long)gridDim.x * tm.per_cta;
+  // The next row's head (id, instance, row range of A, first chunk of A's
+  // columns and values) is loaded while the current row runs.
+  long long g_n = -1, a0_n = 0, a1_n = 0;
+  int b_n = 0, j_n = 0;
+  VT av_n = VT(0);
+  auto fetch_head = [&](long long rr) {
+    g_n = -1;
+    if (rr < nrows) {
+      g_n = rows[rr];
+      b_n = inst_of(P.arow0s, P.ninst, g_n);
+      const InstD& In = P.inst[b_n];
+      a0_n = rp_at(In.A, g_n - In.arow0);
+      a1_n = rp_at(In.A, g_n - In.arow0 + 1);
+    }
+  };
+  auto fetch_first = [&]() {
+    if (g_n >= 0 && a0_n + lane < a1_n) {
+      const InstD& In = P.inst[b_n];
+      j_n = In.A.cj[a0_n + lane];
+      av_n = reinterpret_cast<const VT*>(In.A.vx)[a0_n + lane];
+    }
+  };
+  fetch_head(team);
+  fetch_first();
   for (long long r = team; r < nrows; r += nteams) {
-    const long long g = rows[r];
-    const int b = inst_of(P.arow0s, P.ninst, g);
+    const long long g = g_n;
+    const int b = b_n;
     const InstD& I = P.inst[b];
     const long long i = g - I.arow0;
-    const long long a0 = rp_at(I.A, i), a1 = rp_at(I.A, i + 1);
+    const long long a0 = a0_n, a1 = a1_n;
+    const int j0 = j_n;
+    const VT av0 = av_n;
+    fetch_head(r + nteams);
     const VT* __restrict__ Ax = reinterpret_cast<const VT*>(I.A.vx);
     const VT* __restrict__ Bx = reinterpret_cast<const VT*>(I.B.vx);
     const int* __restrict__ Bj = I.B.cj;
@@ -1007,8 +1034,8 @@ __global__ void __launch_bounds__(32 * kWbTeams, 5) k_num_wb(ProbD P, const int*
       clen = 0;
       av = VT(0);
       if (p < a1) {
-        const int j = Aj[p];
-        av = Ax[p];
+        const int j = c == a0 ? j0 : Aj[p];
+        av = c == a0 ? av0 : Ax[p];
         bs = rp_at(I.B, j);
         len = (int)(rp_at(I.B, j + 1) - bs);
         cbs = P.Bcp[brow0 + j];
@@ -1029,6 +1056,7 @@ __global__ void __launch_bounds__(32 * kWbTeams, 5) k_num_wb(ProbD P, const int*
     if (smin > smax || smax - smin >= (unsigned)kWbLimit) {
       cpn_row<32, VT>(tm, P, base_p, logT, hs, g);
       clean = false;
+      fetch_first();
       __syncwarp();
       continue;
     }
@@ -1048,6 +1076,7 @@ __global__ void __launch_bounds__(32 * kWbTeams, 5) k_num_wb(ProbD P, const int*
       if (!one_chunk) load_chunk(c);
       wb_union_chunk<32, false>(full, lane, upre, uqs, cbs, clen, P.csi, P.cs, bits, smin, span, P.status, 36, g);
     }
+    fetch_first();
     if (!one_chunk) load_chunk(a0);
     // 2. bases of the set words
     const uint4* b4 = reinterpret_cast<const uint4*>(bits + lane * pw);
@@ -1320,13 +1349,136 @@ __device__ __forceinline__ long long lower_col(const int* __restrict__ cj, long 
   return lo;
 }
 
-template <int TW, typename VT>
+// Staged products (option stage_b): blocks of kStageE * TW products, two
+// blocks in flight.
+constexpr int kStageE = 2;
+
+template <int TW, typename VT, bool STAGE>
 __host__ __device__ size_t dense_win_bytes(int win_log2) {
   const size_t W = (size_t)1 << win_log2;
-  return al16(W * sizeof(VT)) + al16((W / 32) * 4) + al16(sizeof(ChunkScratch<TW, VT>));
+  const size_t base = al16(W * sizeof(VT)) + al16((W / 32) * 4) + al16(sizeof(ChunkScratch<TW, VT>));
+  if (STAGE) {
+    const size_t S = (size_t)kStageE * TW;
+    return base + 2 * al16(S * 4) + 2 * al16(S * 4) + 2 * al16(S * sizeof(VT));
+  }
+  return base + al16((size_t)kStagedPasses * TW * 4);
+}
+
+__device__ __forceinline__ void cp_async_4(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const size_t g = __cvta_generic_to_global(src);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_8(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const size_t g = __cvta_generic_to_global(src);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// The products of one chunk of A entries (thread t: B range [bs, be), value
+// av) with their B entries staged in shared memory: blocks of S = kStageE *
+// TW products, each product's A entry found through a segment map (a forward
+// max-fill of where each range starts), its column and value copied by
+// cp.async into the block's buffer while the previous block is added.  The
+// copies of block b + 1 are issued before block b is consumed, so a block's
+// loads are in flight during the previous block's atomics instead of one
+// dependent global load per product.  body(col, bval, t).  Returns the
+// chunk's product count.
+template <int TW, typename VT, class Body>
+__device__ __forceinline__ long long staged_products(const Team<TW>& tm, ChunkScratch<TW, VT>* cs,
+                                                     long long* scan_scratch, long long bs, long long be, VT av,
+                                                     const int* __restrict__ Bj, const VT* __restrict__ Bx,
+                                                     int* seg2, int* sj2, VT* sx2, Body body) {
+  constexpr int E = kStageE;
+  constexpr long long S = (long long)kStageE * TW;
+  long long total;
+  const long long ex = team_excl_scan<TW>(tm, be - bs, &total, scan_scratch);
+  cs->pre[tm.lane] = ex;
+  cs->bs[tm.lane] = bs;
+  cs->av[tm.lane] = av;
+  if (tm.lane == 0) cs->pre[TW] = total;
+  tm.sync();
+  const long long nblk = (total + S - 1) / S;
+  int carry = -1;
+  // segment map of block b into seg2 + (b & 1) * S
+  auto build = [&](long long b) {
+    int* sg = seg2 + (b & 1) * S;
+    const long long x0 = b * S;
+#pragma unroll
+    for (int e = 0; e < E; ++e) sg[tm.lane * E + e] = -1;
+    tm.sync();
+    if (be > bs && ex >= x0 && ex < x0 + S) sg[ex - x0] = tm.lane;
+    tm.sync();
+    int v[E];
+    int m = -1;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      v[e] = sg[tm.lane * E + e];
+      m = max(m, v[e]);
+    }
+    int run = max(carry, team_excl_max<TW>(tm, m, scan_scratch));
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      run = max(run, v[e]);
+      sg[tm.lane * E + e] = run;
+    }
+    tm.sync();
+    carry = sg[S - 1];
+  };
+  // asynchronous copies of block b's B entries
+  auto issue = [&](long long b) {
+    const int* sg = seg2 + (b & 1) * S;
+    int* dj = sj2 + (b & 1) * S;
+    VT* dx = sx2 + (b & 1) * S;
+#pragma unroll
+    for (int u = 0; u < E; ++u) {
+      const long long k = (long long)u * TW + tm.lane;
+      const long long xu = b * S + k;
+      if (xu < total) {
+        const int t = sg[k];
+        const long long q = cs->bs[t] + (xu - cs->pre[t]);
+        cp_async_4(dj + k, Bj + q);
+        if (sizeof(VT) == 8) cp_async_8(dx + k, Bx + q);
+        else cp_async_4(dx + k, Bx + q);
+      }
+    }
+    cp_async_commit();
+  };
+  if (nblk > 0) {
+    build(0);
+    issue(0);
+  }
+  for (long long b = 0; b < nblk; ++b) {
+    if (b + 1 < nblk) {
+      build(b + 1);
+      issue(b + 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    tm.sync();   // every thread's copies of block b have landed
+    const int* sg = seg2 + (b & 1) * S;
+    const int* dj = sj2 + (b & 1) * S;
+    const VT* dx = sx2 + (b & 1) * S;
+#pragma unroll
+    for (int u = 0; u < E; ++u) {
+      const long long k = (long long)u * TW + tm.lane;
+      if (b * S + k < total) body(dj[k], dx[k], sg[k]);
+    }
+    tm.sync();   // block b's buffers are free for block b + 2
+  }
+  return total;
 }
 
 template <int TW, typename VT>
+__host__ __device__ size_t dense_win_bytes(int win_log2) {
+  return dense_win_bytes<TW, VT, false>(win_log2);
+}
+
+template <int TW, typename VT, bool STAGE>
 __global__ void __launch_bounds__(TW) k_num_dense(ProbD P, const int* __restrict__ rows, long long nrows,
                                                   int win_log2, int sorted_b, unsigned long long* fetch) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1339,6 +1491,13 @@ __global__ void __launch_bounds__(TW) k_num_dense(ProbD P, const int* __restrict
   unsigned* bm = reinterpret_cast<unsigned*>(smem + al16((size_t)W * sizeof(VT)));
   ChunkScratch<TW, VT>* csc =
       reinterpret_cast<ChunkScratch<TW, VT>*>(smem + al16((size_t)W * sizeof(VT)) + al16((size_t)ww * 4));
+  // products find their A entry through a segment map (a window holds many
+  // short or empty B ranges, where a search per product takes many steps)
+  int* seg = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(csc) + al16(sizeof(ChunkScratch<TW, VT>)));
+  // staged variant: two segment maps, two blocks of columns and of values
+  constexpr size_t kS = (size_t)kStageE * TW;
+  int* sj2 = seg + 2 * kS;
+  VT* sx2 = reinterpret_cast<VT*>(sj2 + 2 * kS);
   for (long long x = tm.lane; x < W; x += TW) acc[x] = VT(0);
   for (long long x = tm.lane; x < ww; x += TW) bm[x] = 0u;
   for (long long r = cta_next_row(fetch, &fetch_s); r < nrows; r = cta_next_row(fetch, &fetch_s)) {
@@ -1396,12 +1555,26 @@ __global__ void __launch_bounds__(TW) k_num_dense(ProbD P, const int* __restrict
       if (one_chunk) {
         long long ub = cur;
         if (cur < end && (long long)Bj[cur] < w0 + W) ub = lower_col(Bj, cur, end, w0 + W);
-        const long long tot = for_each_product_chunk<TW, VT>(tm, csc, scan_scratch, cur, ub, av1, body, pf, nullptr);
+        long long tot;
+        if (STAGE) {
+          auto sbody = [&](int col, VT bv, int t) {
+            const long long x = (long long)col - w0;
+            if ((unsigned long long)x < (unsigned long long)W) {
+              atomicAdd(acc + x, csc->av[t] * bv);
+              atomicOr(bm + (x >> 5), 1u << (x & 31));
+            } else if ((unsigned long long)(unsigned)col >= (unsigned long long)k) {
+              dev_fail(P.status, kDevBadIndex, 14, g);
+            }
+          };
+          tot = staged_products<TW, VT>(tm, csc, scan_scratch, cur, ub, av1, Bj, Bx, seg, sj2, sx2, sbody);
+        } else {
+          tot = for_each_product_chunk<TW, VT>(tm, csc, scan_scratch, cur, ub, av1, body, pf, seg);
+        }
         cur = ub;
         __syncthreads();
         if (tot == 0) continue;
       } else {
-        for_each_product<TW, VT>(tm, csc, scan_scratch, I.A.cj, a0, a1, range, aval, body, pf);
+        for_each_product<TW, VT>(tm, csc, scan_scratch, I.A.cj, a0, a1, range, aval, body, pf, seg);
         __syncthreads();
       }
       // the window's columns in order: a prefix of the words' set-bit counts
@@ -1665,16 +1838,16 @@ cudaError_t run_wb(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
   return cudaGetLastError();
 }
 
-template <typename VT>
+template <typename VT, bool STAGE>
 cudaError_t run_dense(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
   constexpr int TW = 1024;
   // the widest window that fits one CTA's shared memory (a 1024-thread CTA
   // of this kernel holds a whole SM's registers, so one CTA runs per SM)
   int wl = 17;
-  while (wl > 10 && dense_win_bytes<TW, VT>(wl) + 1024 > (size_t)L.max_smem_optin) --wl;
-  const size_t smem = dense_win_bytes<TW, VT>(wl);
+  while (wl > 10 && dense_win_bytes<TW, VT, STAGE>(wl) + 1024 > (size_t)L.max_smem_optin) --wl;
+  const size_t smem = dense_win_bytes<TW, VT, STAGE>(wl);
   if (smem > (size_t)L.max_smem_optin) return cudaErrorInvalidConfiguration;
-  auto kern = k_num_dense<TW, VT>;
+  auto kern = k_num_dense<TW, VT, STAGE>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   const unsigned grid = resident_grid(kern, TW, smem, L.num_sms, S.nrows);
@@ -1747,7 +1920,7 @@ cudaError_t dispatch(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
       if (S.part == kPartTeamSeq) return run_part<1024, VT, kPartTeamSeq>(L, P, S);
       if (S.part == kPartThreadPar) return run_part<1024, VT, kPartThreadPar>(L, P, S);
       return run_hash<1024, VT>(L, P, S);
-    case kClsDense: return run_dense<VT>(L, P, S);
+    case kClsDense: return (S.stage && S.b_sorted) ? run_dense<VT, true>(L, P, S) : run_dense<VT, false>(L, P, S);
     case kClsSpill: return run_spill<VT>(L, P, S);
     default: return cudaErrorInvalidValue;
   }

@@ -241,12 +241,34 @@ __global__ void __launch_bounds__(256, 4) k_sym_wb(ProbD P, const int* __restric
   bool clean = false;
   const long long team = (long long)blockIdx.x * tm.per_cta + tm.id;
   const long long nteams = (long long)gridDim.x * tm.per_cta;
+  // The next row's head (its id, instance, row range and first chunk of A
+  // column indices) is loaded while the current row runs, so a row starts
+  // with its loads of the compressed B row ranges.
+  long long g_n = -1, a0_n = 0, a1_n = 0;
+  int b_n = 0, j_n = -1;
+  auto fetch_head = [&](long long rr) {
+    g_n = -1;
+    if (rr < nrows) {
+      g_n = rows[rr];
+      b_n = inst_of(P.arow0s, P.ninst, g_n);
+      const InstD& In = P.inst[b_n];
+      a0_n = rp_at(In.A, g_n - In.arow0);
+      a1_n = rp_at(In.A, g_n - In.arow0 + 1);
+    }
+  };
+  auto fetch_j = [&]() {
+    j_n = -1;
+    if (g_n >= 0 && a0_n + lane < a1_n) j_n = P.inst[b_n].A.cj[a0_n + lane];
+  };
+  fetch_head(team);
+  fetch_j();
   for (long long r = team; r < nrows; r += nteams) {
-    const long long g = rows[r];
-    const int b = inst_of(P.arow0s, P.ninst, g);
+    const long long g = g_n;
+    const int b = b_n;
     const InstD& I = P.inst[b];
-    const long long i = g - I.arow0;
-    const long long a0 = rp_at(I.A, i), a1 = rp_at(I.A, i + 1);
+    const long long a0 = a0_n, a1 = a1_n;
+    const int j0 = j_n;
+    fetch_head(r + nteams);
     const long long brow0 = I.brow0;
     const int* __restrict__ Aj = I.A.cj;
     long long qs = 0;
@@ -256,7 +278,7 @@ __global__ void __launch_bounds__(256, 4) k_sym_wb(ProbD P, const int* __restric
       qs = 0;
       ql = 0;
       if (p < a1) {
-        const int j = Aj[p];
+        const int j = c == a0 ? j0 : Aj[p];
         qs = P.Bcp[brow0 + j];
         ql = (int)(P.Bcp[brow0 + j + 1] - qs);
       }
@@ -274,6 +296,7 @@ __global__ void __launch_bounds__(256, 4) k_sym_wb(ProbD P, const int* __restric
     if (smin > smax || smax - smin >= (unsigned)(kSymWbWords - 3)) {
       sym_warp_row<32, true>(tm, P, reinterpret_cast<int*>(bits), pre, qsv, logT, hs, g, rowsize);
       clean = false;
+      fetch_j();
       continue;
     }
     const unsigned span = smax - smin + 1u;
@@ -289,6 +312,7 @@ __global__ void __launch_bounds__(256, 4) k_sym_wb(ProbD P, const int* __restric
       if (!one_chunk) load_chunk(c);
       nb += wb_union_chunk<32, true>(full, lane, pre, qsv, qs, ql, P.csi, P.cs, bits, smin, span, P.status, 4, g);
     }
+    fetch_j();
     const unsigned cnt = __reduce_add_sync(full, (unsigned)nb);
     if (lane == 0) rowsize[g] = (long long)cnt;
     uint4* c4 = reinterpret_cast<uint4*>(bits);
@@ -391,6 +415,8 @@ __global__ void __launch_bounds__(TW) k_sym_dense(ProbD P, const int* __restrict
   Team<TW> tm;
   unsigned* bm = reinterpret_cast<unsigned*>(smem);
   ChunkScratch<TW, int>* csc = reinterpret_cast<ChunkScratch<TW, int>*>(smem + al16((size_t)kw_max * 4));
+  // products find their A entry through a segment map
+  int* seg = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(csc) + al16(sizeof(ChunkScratch<TW, int>)));
   for (long long w = tm.lane; w < kw_max; w += TW) bm[w] = 0u;
   for (long long r = cta_next_row(fetch, &fetch_s); r < nrows; r = cta_next_row(fetch, &fetch_s)) {
     const long long g = rows[r];
@@ -431,7 +457,7 @@ __global__ void __launch_bounds__(TW) k_sym_dense(ProbD P, const int* __restrict
         prefetch_l1(Bj + q);
       }
     };
-    for_each_product<TW, int>(tm, csc, scan_scratch, I.A.cj, a0, a1, range, aval, body, pf);
+    for_each_product<TW, int>(tm, csc, scan_scratch, I.A.cj, a0, a1, range, aval, body, pf, seg);
     long long c = 0;
     for (long long w = tm.lane; w < kw; w += TW) {
       c += __popc(bm[w]);
@@ -541,7 +567,8 @@ cudaError_t run_spill(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, lo
 template <bool COMP>
 cudaError_t run_dense(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, long long* rowsize) {
   constexpr int TW = 512;
-  const size_t smem = al16((size_t)S.kwords_max * 4) + al16(sizeof(ChunkScratch<TW, int>));
+  const size_t smem = al16((size_t)S.kwords_max * 4) + al16(sizeof(ChunkScratch<TW, int>)) +
+                      al16((size_t)kStagedPasses * TW * 4);
   if (smem > (size_t)L.max_smem_optin) return cudaErrorInvalidConfiguration;
   auto kern = k_sym_dense<TW, COMP>;
   cudaError_t e = set_smem(kern, smem);

@@ -612,6 +612,27 @@ def test_long_rows_queue(ops, comp):
         h.close()
 
 
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_dense_staged(ops, dtype):
+    """Dense-window rows with the B entries staged into shared memory by
+    asynchronous copies (stage_b): rows over several windows of columns, rows
+    of one chunk of A (staged) and of several chunks (per-product loads),
+    short and long B rows; against the oracle and the unstaged kernel."""
+    rng = np.random.default_rng(31)
+    la = rng.integers(1, 60, 300)
+    la[[5, 77]] = [1500, 1100]
+    A = w.random_csr(300, 3000, lengths=la, seed=32)
+    lb = rng.integers(1, 80, 3000)
+    lb[rng.choice(3000, 20, replace=False)] = rng.integers(2000, 9000, 20)
+    B = w.random_csr(3000, 120000, lengths=lb, seed=33)
+    ref = None
+    for stage in (True, False):
+        h, _, _, Cd = run(ops, A, B, dtype, dense=1, stage_b=stage)
+        assert h.stats()["bin_rows_numeric"][5] > 0
+        ref = assert_matches_oracle(A, B, Cd, dtype, ref)
+        h.close()
+
+
 def _banded_with_far_columns(seed):
     """B (5000 x 200 000): row j holds 8 sorted columns in [30 j, 30 j + 60), and
     every 97th row one more column 100 000 further on; A (3000 x 5000): row i
@@ -649,7 +670,7 @@ def test_window_positions(ops, dtype):
     cases = [(w.stencil3d_27pt(20, seed=1),) * 2, _banded_with_far_columns(7)]
     for A, B in cases:
         ref = None
-        for win in (True, False):
+        for win in (7, 0):   # windows in every phase (masked products too), or hash tables only
             h, _, _, Cd = run(ops, A, B, dtype, compression=1, window_positions=win)
             st = h.stats()
             assert st["rows_positions"] > 0
