@@ -79,6 +79,8 @@ def parse_args(argv=None):
     p.add_argument("--window", type=int, default=1, choices=tuple(range(8)),
                    help="option window_positions: bitmap windows of column sets in the symbolic phase (bit 0), "
                         "the numeric phase (bit 1), masked products / numeric reuse (bit 2)")
+    p.add_argument("--dense", type=int, default=-1, choices=(-1, 0, 1),
+                   help="option dense: -1 auto, 0 no dense accumulator (large rows take L1 + L2), 1 prefer")
     p.add_argument("--stage-b", type=int, default=0, choices=(0, 1),
                    help="option stage_b: dense-window rows stage their B entries with cp.async")
     p.add_argument("--tune-aa", type=int, default=0, choices=(0, 1),
@@ -1125,7 +1127,7 @@ def run_single(args):
     A = wl["A"]
     vdt = np.float32 if wl["dtype"] == "f32" else np.float64
     res = single_measure(A, vdt, args.steps, args.warmup, clocks=True, stage_b=bool(args.stage_b),
-                         window_positions=int(args.window))
+                         window_positions=int(args.window), dense=int(args.dense))
     if args.workload == "rmat18":
         desc = RMAT_DESC % A.nnz
         if args.scale != 18:

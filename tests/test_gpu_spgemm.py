@@ -373,6 +373,27 @@ def test_rmat18_full_sampled(ops):
     assert st["nnzC"] > 2 ** 31   # int64 row pointers
 
 
+def test_rmat18_full_l2_spill(ops):
+    """The full R-MAT product with the dense accumulator off: the rows too large
+    for a shared-memory table (hubs up to 165 386 columns) take the two-level
+    accumulator, L1 in shared memory with the 50 % occupancy cut-off and L2 in
+    a global-memory chunk (Algorithm 3, Section 3.1.2); sampled rows, the hubs
+    included, against the oracle."""
+    torch.cuda.empty_cache()
+    A = w.rmat_symmetric(scale=18, seed=7)
+    h, _, _, Cd = run(ops, A, A, np.float32, dense=0)
+    st = h.stats()
+    assert st["bin_rows_numeric"][6] > 0 and st["bin_rows_numeric"][5] == 0
+    deg = A.row_lengths()
+    hubs = np.argsort(deg)[-4:]
+    rng = np.random.default_rng(2)
+    rows = np.concatenate([hubs, rng.integers(0, A.nrows, 40)])
+    assert_rows_match_oracle(A, A, Cd, np.float32, rows)
+    del Cd
+    h.close()
+    torch.cuda.empty_cache()
+
+
 # ------------------------------------------------------------------ plain meta-algorithm and tuner
 @pytest.mark.parametrize("seed", range(3))
 def test_plain_meta_algorithm_path(ops, seed):
