@@ -1002,7 +1002,10 @@ def run_timeline(args):
     torch.cuda.set_device(0)
     if args.workload == "stencil27_100":
         A = w.stencil3d_27pt(args.grid, seed=1)
-        S = StencilStep(A, w.aggregation(args.grid, 3), dev, window=int(args.window), tune_aa=bool(args.tune_aa))
+        # the step's two products on one stream (the profiler records the
+        # kernels launched from this thread)
+        S = StencilStep(A, w.aggregation(args.grid, 3), dev, window=int(args.window), tune_aa=bool(args.tune_aa),
+                        concurrent=False)
         fn, close = S.step, S.close
     elif args.workload == "rmat18":
         G = w.rmat_symmetric(scale=args.scale, seed=7)

@@ -40,7 +40,8 @@ enum BufId {
   kBufNumPool2, kBufNumPool3, kBufStatus, kBufMaskRows, kBufMaskHist, kBufMaskPool, kBufTrTmp,
   kBufTrPool, kBufReuseRows, kBufReusePool, kBufBinCnt, kBufBinOfs, kBufMcCnt, kBufMcYcp, kBufMcCsi, kBufMcCs,
   kBufMcMax, kBufRapRf, kBufRapRtp, kBufRapRti, kBufRapRpe, kBufRapW, kBufRapCnt, kBufRapSymRows,
-  kBufRapNumRows, kBufRapMeta, kBufRapTmp, kBufMcRows, kBufFetch, kBufLongB, kBufLongA, kNumBufs
+  kBufRapNumRows, kBufRapMeta, kBufRapTmp, kBufMcRows, kBufFetch, kBufLongB, kBufLongA, kBufRowSets, kBufRowSetCnt,
+  kNumBufs
 };
 
 // Row bins of a masked product, cached for numeric reuse on one pattern.
@@ -129,6 +130,7 @@ struct kks_handle {
   MaskPlan masked;   // last plan of spgemm_masked (reused while the patterns are unchanged)
   bool tuned = false;
   bool positions_ok = false;   // every product of the plan runs on the compressed B
+  bool row_sets = false;       // the symbolic phase records the column sets of its window rows
   bool b_sorted = false;       // every B row of the plan has increasing columns
   // tuner results by bin (class, log2 table, rows, dtype): a new plan of the
   // same problem reuses them instead of tuning again
@@ -240,6 +242,8 @@ ProbD prob(kks_handle* h) {
   P.csi = B<int>(h, kBufCsi);
   P.cs = B<unsigned>(h, kBufCs);
   P.status = B<DevStatus>(h, kBufStatus);
+  P.rsets = h->row_sets ? B<int2>(h, kBufRowSets) : nullptr;
+  P.rcnt = h->row_sets ? B<int>(h, kBufRowSetCnt) : nullptr;
   P.ninst = h->ninst;
   P.hash_mode = h->opt.hash_function;
   return P;
@@ -694,6 +698,20 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
                               B<long long>(h, kBufRowsize), c, B<unsigned long long>(h, kBufCursor) + pass * kNumBins,
                               B<long long>(h, kBufBinOfs) + pass * (nbc + 1), B<int>(h, kBufSymRows)));
   }
+
+  // Column sets of the window rows for the numeric phase (compressed rows with
+  // sorted B rows, positions on): kRowSetCap slots per row, for plans of at
+  // most 2 M rows (512 B per row); rows without a record keep -1.
+  h->row_sets = false;
+  if (any_comp && h->b_sorted && h->opt.numeric_positions && (h->opt.window_positions & 1) &&
+      totalA <= (2ll << 20)) {
+    if (ensure(h, kBufRowSets, sizeof(int2) * (size_t)kRowSetCap * (size_t)(totalA + 1)) == SPGEMM_OK &&
+        ensure(h, kBufRowSetCnt, sizeof(int) * (size_t)(totalA + 1)) == SPGEMM_OK) {
+      h->row_sets = true;
+      KKS_CU(cudaMemsetAsync(h->buf[kBufRowSetCnt], 0xff, sizeof(int) * (size_t)(totalA + 1), s));
+    }
+  }
+  P = prob(h);
 
   // (5) symbolic kernels, bin by bin
   int nbins_sym = 0;

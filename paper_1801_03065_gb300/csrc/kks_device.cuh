@@ -78,6 +78,12 @@ struct InstD {
 };
 
 // Per-launch view of a plan.
+// Column sets of the rows of C, left by the symbolic phase for the numeric
+// phase: row g's sets (index, bits; in no particular order) at rsets[g *
+// kRowSetCap ...], their number at rcnt[g], or -1 where the symbolic kernel
+// of that row did not record them (then the numeric phase forms the union).
+constexpr int kRowSetCap = 64;
+
 struct ProbD {
   const InstD* inst;
   const long long* arow0s;   // ninst + 1 prefix of A-row counts
@@ -86,6 +92,8 @@ struct ProbD {
   const int* csi;            // column-set index (col >> 5)
   const unsigned* cs;        // column set bits
   DevStatus* status;
+  int2* rsets;               // nullptr: no column sets recorded
+  int* rcnt;
   int ninst;
   int hash_mode;             // LpHash mode of every table of the plan
 };
@@ -377,11 +385,14 @@ __device__ __forceinline__ int union_chunk(unsigned team_mask, int lane, int* pr
 // (a window of span words starting at set smin).  Products are spread flat
 // over the lanes as in union_chunk.  With COUNT the return value is the number
 // of column bits this lane was first to set (their team sum is the row size).
+// With wl (COUNT only), every word that an insert turns from zero to nonzero
+// is listed: wl[atomicAdd(wn, 1)] = word, for the first wcap such words.
 template <int TW, bool COUNT>
 __device__ __forceinline__ int wb_union_chunk(unsigned team_mask, int lane, int* pre, long long* qsv, long long qs,
                                               int ql, const int* __restrict__ csi, const unsigned* __restrict__ cs,
                                               unsigned* bits, unsigned smin, unsigned span, DevStatus* status,
-                                              int code, long long g) {
+                                              int code, long long g, int* wl = nullptr, int* wn = nullptr,
+                                              int wcap = 0) {
   int ex = ql;
 #pragma unroll
   for (int d = 1; d < TW; d <<= 1) {
@@ -416,6 +427,10 @@ __device__ __forceinline__ int wb_union_chunk(unsigned team_mask, int lane, int*
         if (COUNT) {
           const unsigned old = atomicOr(bits + w[u], m[u]);
           nbits += __popc(m[u] & ~old);
+          if (wl != nullptr && old == 0u) {
+            const int at = atomicAdd(wn, 1);
+            if (at < wcap) wl[at] = (int)w[u];
+          }
         } else {
           atomicOr(bits + w[u], m[u]);
         }

@@ -694,23 +694,43 @@ __device__ __forceinline__ void cpn_row(const Team<TW>& tm, const ProbD& P, unsi
       }
     };
     const bool one_chunk = a1 - a0 <= TW;
-    // 1. union of the compressed B rows
-    int* upre = reinterpret_cast<int*>(csc);
-    long long* uqs = reinterpret_cast<long long*>(reinterpret_cast<unsigned char*>(csc) + al16((size_t)(TW + 1) * 4));
-    for (long long c = a0; c < a1; c += TW) {
-      load_chunk(c);
-      union_chunk<TW, 4, true>(tm.mask, tm.lane, upre, uqs, cbs, clen, P.csi, P.cs, reinterpret_cast<int*>(tab), hs,
-                               P.status, 25, g);
-    }
-    // 2. sorted column sets, their bases, and C(i,:)'s columns
     int cnt = 0;
-    for (int xb = 0; xb < T; xb += TW) {
-      const int x = xb + tm.lane;
-      const bool o = x < T && tab[x].x != kEmpty;
-      const unsigned bal = (__ballot_sync(tm.mask, o) >> lane_base) & tbits;
-      const int pos = cnt + __popc(bal & lane_lt);
-      if (o && pos < half) sortb[pos] = ((unsigned long long)(unsigned)tab[x].x << 32) | (unsigned)x;
-      cnt += __popc(bal);
+    const int stored = (TW == 32 && P.rcnt != nullptr) ? P.rcnt[g] : -1;
+    if (stored >= 0) {
+      // 1'. the row's column sets as the symbolic phase recorded them: no union
+      const int2* src = P.rsets + g * kRowSetCap;
+      for (int x = tm.lane; x < stored; x += TW) {
+        const int2 e = src[x];
+        int fresh = 0;
+        const int slot = slot_insert<4>(reinterpret_cast<int*>(tab), hs, e.x, &fresh);
+        if (slot >= 0) {
+          tab[slot].y = e.y;
+          if (x < half) sortb[x] = ((unsigned long long)(unsigned)e.x << 32) | (unsigned)slot;
+        } else {
+          dev_fail(P.status, kDevTableFull, 29, g);
+        }
+      }
+      cnt = stored;
+      if (one_chunk) load_chunk(a0);
+    } else {
+      // 1. union of the compressed B rows
+      int* upre = reinterpret_cast<int*>(csc);
+      long long* uqs =
+          reinterpret_cast<long long*>(reinterpret_cast<unsigned char*>(csc) + al16((size_t)(TW + 1) * 4));
+      for (long long c = a0; c < a1; c += TW) {
+        load_chunk(c);
+        union_chunk<TW, 4, true>(tm.mask, tm.lane, upre, uqs, cbs, clen, P.csi, P.cs, reinterpret_cast<int*>(tab),
+                                 hs, P.status, 25, g);
+      }
+      // 2. sorted column sets, their bases, and C(i,:)'s columns
+      for (int xb = 0; xb < T; xb += TW) {
+        const int x = xb + tm.lane;
+        const bool o = x < T && tab[x].x != kEmpty;
+        const unsigned bal = (__ballot_sync(tm.mask, o) >> lane_base) & tbits;
+        const int pos = cnt + __popc(bal & lane_lt);
+        if (o && pos < half) sortb[pos] = ((unsigned long long)(unsigned)tab[x].x << 32) | (unsigned)x;
+        cnt += __popc(bal);
+      }
     }
     const int n = cnt < half ? cnt : half;
     const int sw = s < half ? s : half;

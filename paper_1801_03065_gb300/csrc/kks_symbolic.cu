@@ -221,7 +221,7 @@ constexpr int kSymWbWords = 1344;
 
 __host__ __device__ size_t symwb_team_bytes(int T) {
   const size_t a = al16((size_t)kSymWbWords * 4), h = al16((size_t)T * 8);
-  return (a > h ? a : h) + al16((size_t)33 * 4) + al16((size_t)32 * 8);
+  return (a > h ? a : h) + al16((size_t)33 * 4) + al16((size_t)32 * 8) + al16((size_t)(kRowSetCap + 1) * 4);
 }
 
 __global__ void __launch_bounds__(256, 4) k_sym_wb(ProbD P, const int* __restrict__ rows, long long nrows, int logT,
@@ -232,10 +232,14 @@ __global__ void __launch_bounds__(256, 4) k_sym_wb(ProbD P, const int* __restric
   const LpHash hs(logT, P.hash_mode);
   const size_t tb = symwb_team_bytes(T);
   unsigned char* base = smem + (size_t)tm.id * tb;
-  const size_t tab = tb - al16((size_t)33 * 4) - al16((size_t)32 * 8);
+  const size_t tab = tb - al16((size_t)33 * 4) - al16((size_t)32 * 8) - al16((size_t)(kRowSetCap + 1) * 4);
   unsigned* bits = reinterpret_cast<unsigned*>(base);
   int* pre = reinterpret_cast<int*>(base + tab);
   long long* qsv = reinterpret_cast<long long*>(base + tab + al16((size_t)33 * 4));
+  // words of the row's window that became nonzero: the row's column sets for the numeric phase
+  int* wl = reinterpret_cast<int*>(base + tab + al16((size_t)33 * 4) + al16((size_t)32 * 8));
+  int* wn = wl + kRowSetCap;
+  const bool record = P.rcnt != nullptr;
   const int lane = tm.lane;
   const unsigned full = 0xffffffffu;
   bool clean = false;
@@ -308,13 +312,31 @@ __global__ void __launch_bounds__(256, 4) k_sym_wb(ProbD P, const int* __restric
     }
     int nb = 0;
     const bool one_chunk = a1 - a0 <= 32;
+    if (record) {
+      if (lane == 0) *wn = 0;
+      __syncwarp();
+    }
     for (long long c = a0; c < a1; c += 32) {
       if (!one_chunk) load_chunk(c);
-      nb += wb_union_chunk<32, true>(full, lane, pre, qsv, qs, ql, P.csi, P.cs, bits, smin, span, P.status, 4, g);
+      nb += wb_union_chunk<32, true>(full, lane, pre, qsv, qs, ql, P.csi, P.cs, bits, smin, span, P.status, 4, g,
+                                     record ? wl : nullptr, wn, kRowSetCap);
     }
     fetch_j();
     const unsigned cnt = __reduce_add_sync(full, (unsigned)nb);
     if (lane == 0) rowsize[g] = (long long)cnt;
+    if (record) {
+      // the row's column sets (set index, bits) for the numeric phase
+      const int nw = *wn;
+      if (nw <= kRowSetCap) {
+        int2* dst = P.rsets + g * kRowSetCap;
+        for (int x = lane; x < nw; x += 32) {
+          const int wd = wl[x];
+          dst[x] = make_int2((int)smin + wd, (int)bits[wd]);
+        }
+      }
+      if (lane == 0) P.rcnt[g] = nw <= kRowSetCap ? nw : -1;
+      __syncwarp();
+    }
     uint4* c4 = reinterpret_cast<uint4*>(bits);
     for (int x = lane; x < (int)((span + 3u) >> 2); x += 32) c4[x] = make_uint4(0u, 0u, 0u, 0u);
     __syncwarp();
