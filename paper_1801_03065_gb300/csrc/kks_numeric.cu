@@ -834,8 +834,10 @@ __device__ __forceinline__ void cpn_row(const Team<TW>& tm, const ProbD& P, unsi
 #pragma unroll
       for (int d = TW / 2; d > 0; d >>= 1) tot += __shfl_xor_sync(tm.mask, tot, d, TW);
       if (2 * tot >= nc * TW) {
-        // sequential: one B row per pass, distinct positions inside a pass
-        constexpr int kU = 4;
+        // sequential: one B row per pass, distinct positions inside a pass;
+        // the loads of two passes are issued together (four measured slower:
+        // register spills of the 256 x 4 launch bound)
+        constexpr int kU = 2;
         for (int t0 = 0; t0 < nc; t0 += kU) {
           int q[kU], lent[kU];
           long long bst[kU];
