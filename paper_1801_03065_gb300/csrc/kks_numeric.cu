@@ -42,9 +42,20 @@ __host__ __device__ size_t num_cta_bytes(int T, long long kw_cap) {
   return b + al16((size_t)half * 8);
 }
 
+// Direct rows (rank bitmap in use, the row's products fit half the table):
+// no hash table.  Product x of the row is stored at slot x of the table's
+// first half and its column marked in the bitmap; a bit that was already set
+// flags the product as a repeat of its column.  After the prefix of the words
+// each product knows its column's rank in C(i,:): first occurrences are
+// stored at that rank in the second half, repeats added there after a
+// barrier, and the second half is written out in order.  This drops the
+// table reset, the probes and the two sweeps of the table per row, which
+// dominate rows of random columns (few repeats, table half empty).
+constexpr int kRepeatFlag = int(0x80000000u);
+
 template <int TW, typename VT>
-__global__ void k_num_hash(ProbD P, const int* __restrict__ rows, long long nrows, int logT, long long kw_cap,
-                           unsigned long long* fetch) {
+__global__ void __launch_bounds__(TW) k_num_hash(ProbD P, const int* __restrict__ rows, long long nrows, int logT,
+                                                 long long kw_cap, unsigned long long* fetch) {
   static_assert(TW > 32, "CTA teams only");
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long scan_scratch[33];
@@ -71,47 +82,27 @@ __global__ void k_num_hash(ProbD P, const int* __restrict__ rows, long long nrow
     const long long i = g - I.arow0;
     const long long c0 = I.Crp[i];
     const long long s = I.Crp[i + 1] - c0;
-    for (int x = tm.lane; x < T; x += TW) {
-      keys[x] = kEmpty;
-      vals[x] = VT(0);
-    }
-    tm.sync();
     const long long a0 = rp_at(I.A, i), a1 = rp_at(I.A, i + 1);
     const VT* __restrict__ Ax = reinterpret_cast<const VT*>(I.A.vx);
     const VT* __restrict__ Bx = reinterpret_cast<const VT*>(I.B.vx);
     const int* __restrict__ Bj = I.B.cj;
+    const long long kw = (I.k + 31) >> 5;
+    const bool ranked = kw_cap > 0 && kw <= kw_cap;
     auto range = [&](int j, long long* bs, long long* be) {
       *bs = rp_at(I.B, j);
       *be = rp_at(I.B, j + 1);
     };
     auto aval = [&](long long p) { return Ax[p]; };
-    auto body = [&](long long q, int t) {
-      const int key = Bj[q];
-      const VT v = csc->av[t] * Bx[q];
-      const int slot = lp_insert(keys, tmask, nullptr, -1, key);
-      if (slot >= 0) atomicAdd(vals + slot, v);
-      else dev_fail(P.status, kDevTableFull, 10, g);
-    };
     auto pf = [&](long long q) {
       prefetch_l1(Bj + q);
       prefetch_l1(Bx + q);
     };
-    for_each_product<TW, VT>(tm, csc, scan_scratch, I.A.cj, a0, a1, range, aval, body, pf, seg);
-    const long long kw = (I.k + 31) >> 5;
-    if (kw_cap > 0 && kw <= kw_cap) {
-      VT* __restrict__ Cx = reinterpret_cast<VT*>(I.Cx);
-      int* __restrict__ Cj = I.Cj;
-      for (long long w = tm.lane; w < kw; w += TW) bm[w] = 0u;
-      tm.sync();
-      for (int x = tm.lane; x < T; x += TW) {
-        const int kk = keys[x];
-        if (kk != kEmpty) atomicOr(bm + (kk >> 5), 1u << (kk & 31));
-      }
-      tm.sync();
-      // set bits before every word: each thread sums a contiguous run of words,
-      // the runs are scanned across the team, then each word gets its prefix
-      const long long seg = (kw + TW - 1) / TW;
-      const long long w0 = tm.lane * seg, w1 = w0 + seg < kw ? w0 + seg : kw;
+    // set bits before every word of the rank bitmap: each thread sums a
+    // contiguous run of words, the runs are scanned across the team, then
+    // each word gets its prefix; returns the row's column count
+    auto word_prefix = [&]() {
+      const long long sg = (kw + TW - 1) / TW;
+      const long long w0 = tm.lane * sg, w1 = w0 + sg < kw ? w0 + sg : kw;
       int cseg = 0;
       for (long long w = w0; w < w1; ++w) cseg += __popc(bm[w]);
       long long run;
@@ -120,11 +111,111 @@ __global__ void k_num_hash(ProbD P, const int* __restrict__ rows, long long nrow
         gp[w] = (unsigned short)pre;
         pre += __popc(bm[w]);
       }
+      return run;
+    };
+    if (ranked) {
+      for (long long w = tm.lane; w < kw; w += TW) bm[w] = 0u;
+      long long f = 0;
+      for (long long p = a0 + tm.lane; p < a1; p += TW) {
+        const int j = I.A.cj[p];
+        f += rp_at(I.B, j + 1) - rp_at(I.B, j);
+      }
+      f = team_sum<TW>(tm, f, scan_scratch);
+      if (f <= half) {
+        int* okeys = keys + half;
+        VT* ovals = vals + half;
+        long long base = 0;
+        int repeats = 0;
+        auto dbody = [&](long long q, int t) {
+          const int col = Bj[q];
+          const long long x = base + csc->pre[t] + (q - csc->bs[t]);
+          if ((unsigned long long)(unsigned)col < (unsigned long long)I.k) {
+            const unsigned bit = 1u << (col & 31);
+            const unsigned old = atomicOr(bm + (col >> 5), bit);
+            const bool rep = (old & bit) != 0u;
+            repeats |= rep ? 1 : 0;
+            keys[x] = rep ? (col | kRepeatFlag) : col;
+            vals[x] = csc->av[t] * Bx[q];
+          } else {
+            keys[x] = kEmpty;
+            dev_fail(P.status, kDevBadIndex, 15, g);
+          }
+        };
+        for (long long c = a0; c < a1; c += TW) {
+          const long long p = c + tm.lane;
+          long long bs = 0, be = 0;
+          VT av = VT(0);
+          if (p < a1) {
+            range(I.A.cj[p], &bs, &be);
+            av = Ax[p];
+          }
+          base += for_each_product_chunk<TW, VT>(tm, csc, scan_scratch, bs, be, av, dbody, pf, seg);
+        }
+        const long long run = word_prefix();
+        if (tm.lane == 0 && run != s) dev_fail(P.status, kDevRowSizeMismatch, 16, g);
+        tm.sync();
+        auto rank_of = [&](int col) {
+          const int w = col >> 5;
+          return (long long)gp[w] + __popc(bm[w] & ((1u << (col & 31)) - 1u));
+        };
+        for (long long x = tm.lane; x < f; x += TW) {
+          const int kk = keys[x];
+          if (kk < 0) continue;
+          const long long rk = rank_of(kk);
+          if (rk < s) {
+            okeys[rk] = kk;
+            ovals[rk] = vals[x];
+          }
+        }
+        if (__syncthreads_or(repeats)) {
+          for (long long x = tm.lane; x < f; x += TW) {
+            const int kk = keys[x];
+            if (kk >= 0 || kk == kEmpty) continue;
+            const long long rk = rank_of(kk & ~kRepeatFlag);
+            if (rk < s) atomicAdd(ovals + rk, vals[x]);
+          }
+          tm.sync();
+        }
+        VT* __restrict__ Cx = reinterpret_cast<VT*>(I.Cx);
+        int* __restrict__ Cj = I.Cj;
+        const long long nw = run < s ? run : s;
+        for (long long x = tm.lane; x < nw; x += TW) {
+          Cj[c0 + x] = okeys[x];
+          Cx[c0 + x] = ovals[x];
+        }
+        continue;
+      }
+    }
+    for (int x = tm.lane; x < T; x += TW) {
+      keys[x] = kEmpty;
+      vals[x] = VT(0);
+    }
+    tm.sync();
+    auto body = [&](long long q, int t) {
+      const int key = Bj[q];
+      const VT v = csc->av[t] * Bx[q];
+      const int slot = lp_insert(keys, tmask, nullptr, -1, key);
+      if (slot >= 0) atomicAdd(vals + slot, v);
+      else dev_fail(P.status, kDevTableFull, 10, g);
+    };
+    for_each_product<TW, VT>(tm, csc, scan_scratch, I.A.cj, a0, a1, range, aval, body, pf, seg);
+    if (ranked) {
+      VT* __restrict__ Cx = reinterpret_cast<VT*>(I.Cx);
+      int* __restrict__ Cj = I.Cj;
+      // (the bitmap was cleared before the row's products)
+      for (int x = tm.lane; x < T; x += TW) {
+        const int kk = keys[x];
+        if (kk == kEmpty) continue;
+        if ((unsigned long long)(unsigned)kk < (unsigned long long)I.k) atomicOr(bm + (kk >> 5), 1u << (kk & 31));
+        else dev_fail(P.status, kDevBadIndex, 17, g);
+      }
+      tm.sync();
+      const long long run = word_prefix();
       if (tm.lane == 0 && run != s) dev_fail(P.status, kDevRowSizeMismatch, 9, g);
       tm.sync();
       for (int x = tm.lane; x < T; x += TW) {
         const int kk = keys[x];
-        if (kk == kEmpty) continue;
+        if (kk == kEmpty || (unsigned long long)(unsigned)kk >= (unsigned long long)I.k) continue;
         const int w = kk >> 5;
         const long long rk = (long long)gp[w] + __popc(bm[w] & ((1u << (kk & 31)) - 1u));
         if (rk < s) {
