@@ -1030,6 +1030,11 @@ def run_timeline(args):
     for _ in range(max(args.warmup, 1)):
         fn()
     torch.cuda.synchronize()
+    # the first profiler session of a process returns no device records (the
+    # tracer starts during it): one untimed session first
+    with profile(activities=[ProfilerActivity.CUDA]):
+        fn()
+        torch.cuda.synchronize()
     with profile(activities=[ProfilerActivity.CUDA]) as prof:
         fn()
         torch.cuda.synchronize()

@@ -430,6 +430,75 @@ __global__ void __launch_bounds__(TW) k_num_part(ProbD P, const int* __restrict_
 // unless a bucket would hold more than this many keys.
 constexpr int kBucketMax = 24;
 
+// Bucket sort of a warp row's n entries (column << 32 | position) of sortb
+// into outb: each entry goes to its bucket (an equal share of [kmn, kmx], a
+// power of two >= n of them, at most `half`) by a count in bcnt, a scan and a
+// scatter, and each lane sorts its buckets by insertion.  The entries of outb
+// carry their position in sortb.  Returns false (outb undefined) when the
+// fullest bucket would hold more than kBucketMax entries (keys bunched
+// unevenly), for a bitonic sort instead.
+__device__ __forceinline__ bool warp_bucket_sort(const unsigned long long* sortb, unsigned long long* outb,
+                                                 int* bcnt, int n, unsigned kmn, unsigned kmx) {
+  constexpr int TW = 32;
+  const int lane = threadIdx.x & 31;
+  int nb = 32;
+  while (nb < n) nb <<= 1;
+  int sh = 0;
+  while (((kmx - kmn) >> sh) >= (unsigned)nb) ++sh;
+  for (int b = lane; b < nb; b += TW) bcnt[b] = 0;
+  __syncwarp();
+  for (int x = lane; x < n; x += TW) {
+    const unsigned key = (unsigned)(sortb[x] >> 32);
+    atomicAdd(&bcnt[(key - kmn) >> sh], 1);
+  }
+  __syncwarp();
+  // exclusive scan of the counts: each lane a contiguous run of nb / 32 buckets
+  const int per = nb / TW;
+  int run = 0, mxb = 0;
+  for (int q = 0; q < per; ++q) {
+    const int c = bcnt[lane * per + q];
+    run += c;
+    mxb = max(mxb, c);
+  }
+  int incl = run;
+#pragma unroll
+  for (int d = 1; d < TW; d <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += y;
+  }
+  mxb = __reduce_max_sync(0xffffffffu, (unsigned)mxb);
+  if (mxb > kBucketMax) return false;
+  int start = incl - run;
+  for (int q = 0; q < per; ++q) {
+    const int c = bcnt[lane * per + q];
+    bcnt[lane * per + q] = start;
+    start += c;
+  }
+  __syncwarp();
+  for (int x = lane; x < n; x += TW) {
+    const unsigned long long e = sortb[x];
+    const int b = (int)(((unsigned)(e >> 32) - kmn) >> sh);
+    const int at = atomicAdd(&bcnt[b], 1);
+    outb[at] = (e & 0xffffffff00000000ull) | (unsigned)x;
+  }
+  __syncwarp();
+  // bcnt[b] is now the end of bucket b; the start is the end of b - 1
+  for (int b = lane; b < nb; b += TW) {
+    const int e1 = bcnt[b], e0 = b > 0 ? bcnt[b - 1] : 0;
+    for (int x = e0 + 1; x < e1; ++x) {
+      const unsigned long long v = outb[x];
+      int y = x - 1;
+      while (y >= e0 && outb[y] > v) {
+        outb[y + 1] = outb[y];
+        --y;
+      }
+      outb[y + 1] = v;
+    }
+  }
+  __syncwarp();
+  return true;
+}
+
 template <int TW, typename VT>
 __host__ __device__ size_t warp_team_bytes(int T) {
   const int half = T / 2 > 0 ? T / 2 : 1;
@@ -464,16 +533,116 @@ __global__ void __launch_bounds__(256, 3) k_num_warp(ProbD P, const int* __restr
     const long long i = g - I.arow0;
     const long long c0 = I.Crp[i];
     const long long s = I.Crp[i + 1] - c0;
-    for (int x = tm.lane; x < T; x += TW) {
-      keys[x] = kEmpty;
-      vals[x] = VT(0);
-    }
-    __syncwarp(tm.mask);
     const long long a0 = rp_at(I.A, i), a1 = rp_at(I.A, i + 1);
     const VT* __restrict__ Ax = reinterpret_cast<const VT*>(I.A.vx);
     const VT* __restrict__ Bx = reinterpret_cast<const VT*>(I.B.vx);
     const int* __restrict__ Bj = I.B.cj;
     const int* __restrict__ Aj = I.A.cj;
+    VT* __restrict__ Cx = reinterpret_cast<VT*>(I.Cx);
+    int* __restrict__ Cj = I.Cj;
+    if constexpr (TW == 32) {
+      // Direct rows (products fit half the table): no hash table.  Product x
+      // of the row is stored at position x, value in the key region and
+      // (column << 32 | x) in the sort buffer; the entries are sorted by
+      // column (then position), and the first entry of each column sums its
+      // run and writes C(i,:) at its rank.  This drops the table reset, the
+      // probes and the compaction sweep, which dominate rows of random
+      // columns (few repeats, table half empty).
+      long long f = 0;
+      for (long long p = a0 + tm.lane; p < a1; p += TW) {
+        const int j = Aj[p];
+        f += rp_at(I.B, j + 1) - rp_at(I.B, j);
+      }
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) f += __shfl_xor_sync(0xffffffffu, f, d);
+      if (f > 0 && f <= half) {
+        const int n = (int)f;
+        VT* cv = reinterpret_cast<VT*>(keys);   // half values
+        unsigned kmn = 0xffffffffu, kmx = 0u;
+        int base = 0;
+        for (long long c = a0; c < a1; c += TW) {
+          const long long p = c + tm.lane;
+          long long bs = 0;
+          int len = 0;
+          VT av = VT(0);
+          if (p < a1) {
+            const int j = Aj[p];
+            bs = rp_at(I.B, j);
+            len = (int)(rp_at(I.B, j + 1) - bs);
+            av = Ax[p];
+          }
+          int ex = len;
+#pragma unroll
+          for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, ex, d);
+            if (tm.lane >= d) ex += y;
+          }
+          const int tot = __shfl_sync(0xffffffffu, ex, 31);
+          csc->pre[tm.lane] = ex - len;
+          csc->bs[tm.lane] = bs;
+          csc->av[tm.lane] = av;
+          if (tm.lane == 0) csc->pre[TW] = tot;
+          __syncwarp();
+          int t = 0;
+          for (int x = tm.lane; x < tot; x += TW) {
+            while (csc->pre[t + 1] <= x) ++t;
+            const long long q = csc->bs[t] + (x - csc->pre[t]);
+            const int col = Bj[q];
+            if ((unsigned long long)(unsigned)col >= (unsigned long long)I.k) dev_fail(P.status, kDevBadIndex, 20, g);
+            sortb[base + x] = ((unsigned long long)(unsigned)col << 32) | (unsigned)(base + x);
+            cv[base + x] = csc->av[t] * Bx[q];
+            kmn = min(kmn, (unsigned)col);
+            kmx = max(kmx, (unsigned)col);
+          }
+          base += tot;
+          __syncwarp();
+        }
+        kmn = __reduce_min_sync(0xffffffffu, kmn);
+        kmx = __reduce_max_sync(0xffffffffu, kmx);
+        const unsigned long long* srt = sortb;
+        unsigned long long* outb = reinterpret_cast<unsigned long long*>(vals);   // half entries
+        int* bcnt = sizeof(VT) == 8 ? reinterpret_cast<int*>(outb + half) : reinterpret_cast<int*>(cv + half);
+        if (n > 2 * TW && warp_bucket_sort(sortb, outb, bcnt, n, kmn, kmx)) {
+          srt = outb;
+        } else {
+          int N = 1;
+          while (N < n) N <<= 1;
+          for (int x = n + tm.lane; x < N; x += TW) sortb[x] = ~0ull;
+          __syncwarp();
+          team_bitonic<TW>(tm, sortb, N);
+        }
+        // runs of equal columns: the first entry of each sums the run
+        int run = 0;
+        for (int xb = 0; xb < n; xb += TW) {
+          const int x = xb + tm.lane;
+          unsigned col = 0u;
+          bool head = false;
+          if (x < n) {
+            col = (unsigned)(srt[x] >> 32);
+            head = x == 0 || (unsigned)(srt[x - 1] >> 32) != col;
+          }
+          const unsigned bal = __ballot_sync(0xffffffffu, head);
+          if (head) {
+            const long long rk = run + __popc(bal & lane_lt);
+            VT v = cv[(unsigned)(srt[x] & 0xffffffffull)];
+            for (int y = x + 1; y < n && (unsigned)(srt[y] >> 32) == col; ++y) v += cv[(unsigned)(srt[y] & 0xffffffffull)];
+            if (rk < s) {
+              Cj[c0 + rk] = (int)col;
+              Cx[c0 + rk] = v;
+            }
+          }
+          run += __popc(bal);
+        }
+        if (tm.lane == 0 && run != s) dev_fail(P.status, kDevRowSizeMismatch, 21, g);
+        __syncwarp();
+        continue;
+      }
+    }
+    for (int x = tm.lane; x < T; x += TW) {
+      keys[x] = kEmpty;
+      vals[x] = VT(0);
+    }
+    __syncwarp(tm.mask);
     for (long long c = a0; c < a1; c += TW) {
       const long long p = c + tm.lane;
       long long bs = 0;
@@ -598,79 +767,20 @@ __global__ void __launch_bounds__(256, 3) k_num_warp(ProbD P, const int* __restr
     if (tm.lane == 0 && cnt != s) dev_fail(P.status, kDevRowSizeMismatch, 19, g);
     const int n = cnt < half ? cnt : half;
     const long long nw = n < s ? n : s;
-    VT* __restrict__ Cx = reinterpret_cast<VT*>(I.Cx);
-    int* __restrict__ Cj = I.Cj;
     if (TW == 32 && n > 2 * TW) {
-      // Bucket sort by column (rows of many keys): the values move to a
-      // compact array in the key region, then each entry goes to its bucket
-      // (an equal share of [kmin, kmax]) by a count, a scan and a scatter
-      // into the value region, and each lane sorts its buckets by insertion.
-      // Rows whose fullest bucket holds more than kBucketMax entries (keys
-      // bunched unevenly) take the bitonic sort instead.
+      // Bucket sort by column (rows of many keys) into the value region, once
+      // the values have moved to a compact array in the key region; keys
+      // bunched unevenly take the bitonic sort instead.
       kmn = __reduce_min_sync(tm.mask, kmn);
       kmx = __reduce_max_sync(tm.mask, kmx);
       __syncwarp(tm.mask);
       VT* cv = reinterpret_cast<VT*>(keys);                                       // half values
       unsigned long long* outb = reinterpret_cast<unsigned long long*>(vals);     // half entries
       int* bcnt = sizeof(VT) == 8 ? reinterpret_cast<int*>(outb + half) : reinterpret_cast<int*>(cv + half);
-      int nb = 32;
-      while (nb < n) nb <<= 1;   // buckets: a power of two >= n, <= half
-      int sh = 0;
-      while (((kmx - kmn) >> sh) >= (unsigned)nb) ++sh;
       // values by compact position, into the key region (every key was read above)
       for (int x = tm.lane; x < n; x += TW) cv[x] = vals[(unsigned)(sortb[x] & 0xffffffffull)];
       __syncwarp(tm.mask);   // the value region is free from here on
-      for (int b = tm.lane; b < nb; b += TW) bcnt[b] = 0;
-      __syncwarp(tm.mask);
-      for (int x = tm.lane; x < n; x += TW) {
-        const unsigned key = (unsigned)(sortb[x] >> 32);
-        atomicAdd(&bcnt[(key - kmn) >> sh], 1);
-      }
-      __syncwarp(tm.mask);
-      // exclusive scan of the counts: each lane a contiguous run of nb / 32 buckets
-      const int per = nb / TW;
-      int run = 0, mxb = 0;
-      for (int q = 0; q < per; ++q) {
-        const int c = bcnt[tm.lane * per + q];
-        run += c;
-        mxb = max(mxb, c);
-      }
-      int incl = run;
-#pragma unroll
-      for (int d = 1; d < TW; d <<= 1) {
-        const int y = __shfl_up_sync(tm.mask, incl, d, TW);
-        if (tm.lane >= d) incl += y;
-      }
-      mxb = __reduce_max_sync(tm.mask, (unsigned)mxb);
-      int start = incl - run;
-      for (int q = 0; q < per; ++q) {
-        const int c = bcnt[tm.lane * per + q];
-        bcnt[tm.lane * per + q] = start;
-        start += c;
-      }
-      __syncwarp(tm.mask);
-      if (mxb <= kBucketMax) {
-        for (int x = tm.lane; x < n; x += TW) {
-          const unsigned long long e = sortb[x];
-          const int b = (int)(((unsigned)(e >> 32) - kmn) >> sh);
-          const int at = atomicAdd(&bcnt[b], 1);
-          outb[at] = (e & 0xffffffff00000000ull) | (unsigned)x;   // (column, compact position)
-        }
-        __syncwarp(tm.mask);
-        // bcnt[b] is now the end of bucket b; the start is the end of b - 1
-        for (int b = tm.lane; b < nb; b += TW) {
-          const int e1 = bcnt[b], e0 = b > 0 ? bcnt[b - 1] : 0;
-          for (int x = e0 + 1; x < e1; ++x) {
-            const unsigned long long v = outb[x];
-            int y = x - 1;
-            while (y >= e0 && outb[y] > v) {
-              outb[y + 1] = outb[y];
-              --y;
-            }
-            outb[y + 1] = v;
-          }
-        }
-        __syncwarp(tm.mask);
+      if (warp_bucket_sort(sortb, outb, bcnt, n, kmn, kmx)) {
         for (long long x = tm.lane; x < nw; x += TW) {
           const unsigned long long e = outb[x];
           Cj[c0 + x] = (int)(e >> 32);
