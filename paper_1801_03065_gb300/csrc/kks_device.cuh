@@ -620,17 +620,25 @@ __device__ __forceinline__ int team_excl_max(const Team<TW>& tm, int v, long lon
 // windows, short B rows), where the search below needs many steps.
 // One chunk of A(i,:): lane t holds the B range [bs, be) and the value av of
 // its A entry.  Returns the chunk's product count (the same in every lane).
-template <int TW, typename VT, class Body, class Prefetch>
-__device__ __forceinline__ long long for_each_product_chunk(const Team<TW>& tm, ChunkScratch<TW, VT>* cs,
-                                                            long long* scan_scratch, long long bs, long long be,
-                                                            VT av, Body body, Prefetch prefetch, int* seg) {
-  long long total;
-  long long ex = team_excl_scan<TW>(tm, be - bs, &total, scan_scratch);
+// The chunk's scan (the lane's first product ex, the chunk's product count
+// total) and its entries in cs; chunk_products then calls the body.
+template <int TW, typename VT>
+__device__ __forceinline__ long long chunk_scan(const Team<TW>& tm, ChunkScratch<TW, VT>* cs, long long* scan_scratch,
+                                                long long bs, long long be, VT av, long long* total) {
+  long long ex = team_excl_scan<TW>(tm, be - bs, total, scan_scratch);
   cs->pre[tm.lane] = ex;
   cs->bs[tm.lane] = bs;
   cs->av[tm.lane] = av;
-  if (tm.lane == 0) cs->pre[TW] = total;
+  if (tm.lane == 0) cs->pre[TW] = *total;
   tm.sync();
+  return ex;
+}
+
+template <int TW, typename VT, class Body, class Prefetch>
+__device__ __forceinline__ long long chunk_products(const Team<TW>& tm, ChunkScratch<TW, VT>* cs,
+                                                    long long* scan_scratch, long long ex, long long total,
+                                                    long long bs, long long be, Body body, Prefetch prefetch,
+                                                    int* seg) {
   if constexpr (Team<TW>::kCta) {
     if (seg != nullptr) {
       constexpr int E = kStagedPasses;
@@ -722,6 +730,15 @@ __device__ __forceinline__ long long for_each_product_chunk(const Team<TW>& tm, 
   }
   tm.sync();
   return total;
+}
+
+template <int TW, typename VT, class Body, class Prefetch>
+__device__ __forceinline__ long long for_each_product_chunk(const Team<TW>& tm, ChunkScratch<TW, VT>* cs,
+                                                            long long* scan_scratch, long long bs, long long be,
+                                                            VT av, Body body, Prefetch prefetch, int* seg) {
+  long long total;
+  const long long ex = chunk_scan<TW, VT>(tm, cs, scan_scratch, bs, be, av, &total);
+  return chunk_products<TW, VT>(tm, cs, scan_scratch, ex, total, bs, be, body, prefetch, seg);
 }
 
 template <int TW, typename VT, class Range, class AVal, class Body, class Prefetch>

@@ -115,12 +115,25 @@ __global__ void __launch_bounds__(TW) k_num_hash(ProbD P, const int* __restrict_
     };
     if (ranked) {
       for (long long w = tm.lane; w < kw; w += TW) bm[w] = 0u;
-      long long f = 0;
-      for (long long p = a0 + tm.lane; p < a1; p += TW) {
-        const int j = I.A.cj[p];
-        f += rp_at(I.B, j + 1) - rp_at(I.B, j);
+      // the product count: the chunk's scan when A(i,:) is one chunk (kept
+      // for its products), else a sum over the row
+      const bool one = a1 - a0 <= TW;
+      long long f = 0, ex1 = 0, bs1 = 0, be1 = 0;
+      if (one) {
+        const long long p = a0 + tm.lane;
+        VT av = VT(0);
+        if (p < a1) {
+          range(I.A.cj[p], &bs1, &be1);
+          av = Ax[p];
+        }
+        ex1 = chunk_scan<TW, VT>(tm, csc, scan_scratch, bs1, be1, av, &f);
+      } else {
+        for (long long p = a0 + tm.lane; p < a1; p += TW) {
+          const int j = I.A.cj[p];
+          f += rp_at(I.B, j + 1) - rp_at(I.B, j);
+        }
+        f = team_sum<TW>(tm, f, scan_scratch);
       }
-      f = team_sum<TW>(tm, f, scan_scratch);
       if (f <= half) {
         int* okeys = keys + half;
         VT* ovals = vals + half;
@@ -141,15 +154,19 @@ __global__ void __launch_bounds__(TW) k_num_hash(ProbD P, const int* __restrict_
             dev_fail(P.status, kDevBadIndex, 15, g);
           }
         };
-        for (long long c = a0; c < a1; c += TW) {
-          const long long p = c + tm.lane;
-          long long bs = 0, be = 0;
-          VT av = VT(0);
-          if (p < a1) {
-            range(I.A.cj[p], &bs, &be);
-            av = Ax[p];
+        if (one) {
+          chunk_products<TW, VT>(tm, csc, scan_scratch, ex1, f, bs1, be1, dbody, pf, seg);
+        } else {
+          for (long long c = a0; c < a1; c += TW) {
+            const long long p = c + tm.lane;
+            long long bs = 0, be = 0;
+            VT av = VT(0);
+            if (p < a1) {
+              range(I.A.cj[p], &bs, &be);
+              av = Ax[p];
+            }
+            base += for_each_product_chunk<TW, VT>(tm, csc, scan_scratch, bs, be, av, dbody, pf, seg);
           }
-          base += for_each_product_chunk<TW, VT>(tm, csc, scan_scratch, bs, be, av, dbody, pf, seg);
         }
         const long long run = word_prefix();
         if (tm.lane == 0 && run != s) dev_fail(P.status, kDevRowSizeMismatch, 16, g);
@@ -583,16 +600,39 @@ __global__ void __launch_bounds__(256, 3) k_num_warp(ProbD P, const int* __restr
           csc->av[tm.lane] = av;
           if (tm.lane == 0) csc->pre[TW] = tot;
           __syncwarp();
+          // the B entries of kDirectU passes are located and loaded together
+          // (their latencies overlap), then stored
+          constexpr int kDirectU = 4;
           int t = 0;
-          for (int x = tm.lane; x < tot; x += TW) {
-            while (csc->pre[t + 1] <= x) ++t;
-            const long long q = csc->bs[t] + (x - csc->pre[t]);
-            const int col = Bj[q];
-            if ((unsigned long long)(unsigned)col >= (unsigned long long)I.k) dev_fail(P.status, kDevBadIndex, 20, g);
-            sortb[base + x] = ((unsigned long long)(unsigned)col << 32) | (unsigned)(base + x);
-            cv[base + x] = csc->av[t] * Bx[q];
-            kmn = min(kmn, (unsigned)col);
-            kmx = max(kmx, (unsigned)col);
+          for (int xb = 0; xb < tot; xb += kDirectU * TW) {
+            long long q[kDirectU];
+            int tt[kDirectU], col[kDirectU];
+            VT bv[kDirectU];
+#pragma unroll
+            for (int u = 0; u < kDirectU; ++u) {
+              const int x = xb + u * TW + tm.lane;
+              q[u] = -1;
+              if (x < tot) {
+                while (csc->pre[t + 1] <= x) ++t;
+                q[u] = csc->bs[t] + (x - csc->pre[t]);
+              }
+              tt[u] = t;
+            }
+#pragma unroll
+            for (int u = 0; u < kDirectU; ++u) {
+              col[u] = q[u] >= 0 ? Bj[q[u]] : 0;
+              bv[u] = q[u] >= 0 ? Bx[q[u]] : VT(0);
+            }
+#pragma unroll
+            for (int u = 0; u < kDirectU; ++u) {
+              if (q[u] < 0) continue;
+              const int x = base + xb + u * TW + tm.lane;
+              if ((unsigned long long)(unsigned)col[u] >= (unsigned long long)I.k) dev_fail(P.status, kDevBadIndex, 20, g);
+              sortb[x] = ((unsigned long long)(unsigned)col[u] << 32) | (unsigned)x;
+              cv[x] = csc->av[tt[u]] * bv[u];
+              kmn = min(kmn, (unsigned)col[u]);
+              kmx = max(kmx, (unsigned)col[u]);
+            }
           }
           base += tot;
           __syncwarp();
