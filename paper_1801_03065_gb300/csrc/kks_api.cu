@@ -361,8 +361,10 @@ BinCfg sym_cfg(kks_handle* h, int comp) {
   c.cta_max_logT = cta_max_logT_sym(h, comp);
   // 512-thread dense team: bitmap + chunk scratch in shared memory
   c.dense_max_kwords = ((long long)h->max_smem - 21 * 1024) / 4;
-  // the bitmap (kw words) is preferred once the hash table would be as large
-  c.dense_ratio = comp ? 4 : 64;
+  // the bitmap (kw words) is preferred once the hash table (about 2u slots)
+  // would reach half its size (plain rows: u * 128 >= k; 64 and 32 measured
+  // slower on rows of random columns)
+  c.dense_ratio = comp ? 4 : 128;
   // one thread per row when the row has at most kT1SymKeys products
   c.t1_max_keys = kT1SymKeys;
   c.t1_max_work = kT1SymKeys;

@@ -24,7 +24,7 @@ enum TeamClass : int {
   kClsNone = 0,    // empty row: nothing to compute
   kClsW8 = 1,      // 8-lane sub-warp team, shared LP table
   kClsW32 = 2,     // warp team, shared LP table
-  kClsC256 = 3,    // 256-thread CTA team, shared LP table
+  kClsC256 = 3,    // 256-thread CTA team (numeric: 512 from 4096 slots), shared LP table
   kClsC1024 = 4,   // 1024-thread CTA team, shared LP table
   kClsDense = 5,   // CTA team, dense accumulator (bitmap in shared memory)
   kClsSpill = 6,   // CTA team, shared L1 LP table + global L2 LP table

@@ -2178,6 +2178,9 @@ cudaError_t dispatch(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
     case kClsC256:
       if (S.part == kPartTeamSeq) return run_part<256, VT, kPartTeamSeq>(L, P, S);
       if (S.part == kPartThreadPar) return run_part<256, VT, kPartThreadPar>(L, P, S);
+      // tables of 4096 slots or more: 512 threads per row (the shared memory
+      // allows two CTAs per SM either way)
+      if (S.logT >= 12) return run_hash<512, VT>(L, P, S);
       return run_hash<256, VT>(L, P, S);
     case kClsC1024:
       if (S.part == kPartTeamSeq) return run_part<1024, VT, kPartTeamSeq>(L, P, S);
