@@ -385,14 +385,13 @@ __device__ __forceinline__ int union_chunk(unsigned team_mask, int lane, int* pr
 // (a window of span words starting at set smin).  Products are spread flat
 // over the lanes as in union_chunk.  With COUNT the return value is the number
 // of column bits this lane was first to set (their team sum is the row size).
-// With wl (COUNT only), every word that an insert turns from zero to nonzero
-// is listed: wl[atomicAdd(wn, 1)] = word, for the first wcap such words.
+// With summ (COUNT only), every word that an insert turns from zero to nonzero
+// is flagged in the summary bitmap: bit (w & 31) of summ[w >> 5].
 template <int TW, bool COUNT>
 __device__ __forceinline__ int wb_union_chunk(unsigned team_mask, int lane, int* pre, long long* qsv, long long qs,
                                               int ql, const int* __restrict__ csi, const unsigned* __restrict__ cs,
                                               unsigned* bits, unsigned smin, unsigned span, DevStatus* status,
-                                              int code, long long g, int* wl = nullptr, int* wn = nullptr,
-                                              int wcap = 0) {
+                                              int code, long long g, unsigned* summ = nullptr) {
   int ex = ql;
 #pragma unroll
   for (int d = 1; d < TW; d <<= 1) {
@@ -427,10 +426,7 @@ __device__ __forceinline__ int wb_union_chunk(unsigned team_mask, int lane, int*
         if (COUNT) {
           const unsigned old = atomicOr(bits + w[u], m[u]);
           nbits += __popc(m[u] & ~old);
-          if (wl != nullptr && old == 0u) {
-            const int at = atomicAdd(wn, 1);
-            if (at < wcap) wl[at] = (int)w[u];
-          }
+          if (summ != nullptr && old == 0u) atomicOr(summ + (w[u] >> 5), 1u << (w[u] & 31u));
         } else {
           atomicOr(bits + w[u], m[u]);
         }

@@ -936,22 +936,56 @@ __device__ __forceinline__ void cpn_row(const Team<TW>& tm, const ProbD& P, unsi
     };
     const bool one_chunk = a1 - a0 <= TW;
     int cnt = 0;
+    const int sw = s < half ? s : half;
     const int stored = (TW == 32 && P.rcnt != nullptr) ? P.rcnt[g] : -1;
+    int run = 0;
     if (stored >= 0) {
-      // 1'. the row's column sets as the symbolic phase recorded them: no union
+      // 1'-2'. the row's column sets as the symbolic phase recorded them, in
+      // increasing set order (no union, no sort): lane t takes sets 2t and
+      // 2t + 1, their bases are a scan of the set-bit counts
       const int2* src = P.rsets + g * kRowSetCap;
-      for (int x = tm.lane; x < stored; x += TW) {
-        const int2 e = src[x];
+      const int x0 = 2 * tm.lane;
+      int4 e = make_int4(kEmpty, 0, kEmpty, 0);
+      if (x0 + 1 < stored) {
+        e = *reinterpret_cast<const int4*>(src + x0);
+      } else if (x0 < stored) {
+        const int2 e0 = src[x0];
+        e.x = e0.x;
+        e.y = e0.y;
+      }
+      const int n0 = __popc((unsigned)e.y), n1 = __popc((unsigned)e.w);
+      int incl = n0 + n1;
+#pragma unroll
+      for (int d = 1; d < TW; d <<= 1) {
+        const int y = __shfl_up_sync(tm.mask, incl, d, TW);
+        if (tm.lane >= d) incl += y;
+      }
+      run = __shfl_sync(tm.mask, incl, TW - 1, TW);
+      const int b0 = incl - n0 - n1;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int key = h ? e.z : e.x;
+        if (key == kEmpty) continue;
+        const unsigned mk = (unsigned)(h ? e.w : e.y);
+        const int o0 = h ? b0 + n0 : b0;
         int fresh = 0;
-        const int slot = slot_insert<4>(reinterpret_cast<int*>(tab), hs, e.x, &fresh);
+        const int slot = slot_insert<4>(reinterpret_cast<int*>(tab), hs, key, &fresh);
         if (slot >= 0) {
-          tab[slot].y = e.y;
-          if (x < half) sortb[x] = ((unsigned long long)(unsigned)e.x << 32) | (unsigned)slot;
+          tab[slot].y = (int)mk;
+          tab[slot].z = o0;
         } else {
           dev_fail(P.status, kDevTableFull, 29, g);
         }
+        // C(i,:)'s columns staged in shared memory
+        unsigned m = mk;
+        int o = o0;
+        while (m) {
+          const int bit = __ffs(m) - 1;
+          m &= m - 1u;
+          if (o < sw) colst[o] = key * 32 + bit;
+          ++o;
+        }
       }
-      cnt = stored;
       if (one_chunk) load_chunk(a0);
     } else {
       // 1. union of the compressed B rows
@@ -974,10 +1008,10 @@ __device__ __forceinline__ void cpn_row(const Team<TW>& tm, const ProbD& P, unsi
       }
     }
     const int n = cnt < half ? cnt : half;
-    const int sw = s < half ? s : half;
     __syncwarp(tm.mask);
-    int run = 0;
-    if (n <= 2 * TW) {
+    if (stored >= 0) {
+      // (bases and columns above)
+    } else if (n <= 2 * TW) {
       // up to two sets per lane: sorted in registers, slots found again by key
       unsigned v0 = tm.lane < n ? (unsigned)(sortb[tm.lane] >> 32) : 0xffffffffu;
       unsigned v1 = tm.lane + TW < n ? (unsigned)(sortb[tm.lane + TW] >> 32) : 0xffffffffu;
@@ -1078,7 +1112,13 @@ __device__ __forceinline__ void cpn_row(const Team<TW>& tm, const ProbD& P, unsi
         // sequential: one B row per pass, distinct positions inside a pass;
         // the loads of two passes are issued together (four measured slower:
         // register spills of the 256 x 4 launch bound)
+        // the chunk's (B row start, length, a_ij) go to shared memory once;
+        // each pass reads its entry's with broadcast loads
         constexpr int kU = 2;
+        csc->bs[tm.lane] = bs;
+        csc->pre[tm.lane] = len;
+        csc->av[tm.lane] = av;
+        __syncwarp(tm.mask);
         for (int t0 = 0; t0 < nc; t0 += kU) {
           int q[kU], lent[kU];
           long long bst[kU];
@@ -1086,9 +1126,9 @@ __device__ __forceinline__ void cpn_row(const Team<TW>& tm, const ProbD& P, unsi
 #pragma unroll
           for (int u = 0; u < kU; ++u) {
             const int t = (t0 + u < nc) ? t0 + u : nc - 1;
-            bst[u] = __shfl_sync(tm.mask, bs, t, TW);
-            const int l = __shfl_sync(tm.mask, len, t, TW);
-            at[u] = __shfl_sync(tm.mask, av, t, TW);
+            bst[u] = csc->bs[t];
+            const int l = (int)csc->pre[t];
+            at[u] = csc->av[t];
             lent[u] = (t0 + u < nc) ? l : 0;
             q[u] = -1;
             bv[u] = VT(0);

@@ -214,14 +214,18 @@ __global__ void __launch_bounds__(256, 4) k_sym_warp(ProbD P, const int* __restr
 // column among the compressed B rows over A(i,:); when that window is at most
 // kSymWbWords sets wide the union is a bitmap over it, addressed directly by
 // set index (no hashing, no probing), and the row size is the number of
-// column bits the inserts set first.  The words of the window are cleared
-// after the row.  Wider rows take the hash path (sym_warp_row) in the same
-// shared memory.
+// column bits the inserts set first.  Every word an insert turns nonzero is
+// flagged in a summary bitmap (one bit per word); after the row, lane L walks
+// the flags of words [64 L, 64 L + 64), so the row's column sets come out in
+// increasing set order (recorded for the numeric phase) and exactly the words
+// that were set are cleared.  Wider rows take the hash path (sym_warp_row) in
+// the same shared memory.
 constexpr int kSymWbWords = 1344;
+constexpr int kSymWbSumm = 64;   // summary words: 32 lanes x 2 cover 2048 >= kSymWbWords window words
 
 __host__ __device__ size_t symwb_team_bytes(int T) {
   const size_t a = al16((size_t)kSymWbWords * 4), h = al16((size_t)T * 8);
-  return (a > h ? a : h) + al16((size_t)33 * 4) + al16((size_t)32 * 8) + al16((size_t)(kRowSetCap + 1) * 4);
+  return (a > h ? a : h) + al16((size_t)33 * 4) + al16((size_t)32 * 8) + al16((size_t)kSymWbSumm * 4);
 }
 
 __global__ void __launch_bounds__(256, 4) k_sym_wb(ProbD P, const int* __restrict__ rows, long long nrows, int logT,
@@ -232,17 +236,18 @@ __global__ void __launch_bounds__(256, 4) k_sym_wb(ProbD P, const int* __restric
   const LpHash hs(logT, P.hash_mode);
   const size_t tb = symwb_team_bytes(T);
   unsigned char* base = smem + (size_t)tm.id * tb;
-  const size_t tab = tb - al16((size_t)33 * 4) - al16((size_t)32 * 8) - al16((size_t)(kRowSetCap + 1) * 4);
+  const size_t tab = tb - al16((size_t)33 * 4) - al16((size_t)32 * 8) - al16((size_t)kSymWbSumm * 4);
   unsigned* bits = reinterpret_cast<unsigned*>(base);
   int* pre = reinterpret_cast<int*>(base + tab);
   long long* qsv = reinterpret_cast<long long*>(base + tab + al16((size_t)33 * 4));
-  // words of the row's window that became nonzero: the row's column sets for the numeric phase
-  int* wl = reinterpret_cast<int*>(base + tab + al16((size_t)33 * 4) + al16((size_t)32 * 8));
-  int* wn = wl + kRowSetCap;
+  // one flag per window word that became nonzero (the row's column sets)
+  unsigned* summ = reinterpret_cast<unsigned*>(base + tab + al16((size_t)33 * 4) + al16((size_t)32 * 8));
   const bool record = P.rcnt != nullptr;
   const int lane = tm.lane;
   const unsigned full = 0xffffffffu;
   bool clean = false;
+  summ[2 * tm.lane] = 0u;
+  summ[2 * tm.lane + 1] = 0u;
   const long long team = (long long)blockIdx.x * tm.per_cta + tm.id;
   const long long nteams = (long long)gridDim.x * tm.per_cta;
   // The next row's head (its id, instance, row range and first chunk of A
@@ -312,33 +317,41 @@ __global__ void __launch_bounds__(256, 4) k_sym_wb(ProbD P, const int* __restric
     }
     int nb = 0;
     const bool one_chunk = a1 - a0 <= 32;
-    if (record) {
-      if (lane == 0) *wn = 0;
-      __syncwarp();
-    }
     for (long long c = a0; c < a1; c += 32) {
       if (!one_chunk) load_chunk(c);
       nb += wb_union_chunk<32, true>(full, lane, pre, qsv, qs, ql, P.csi, P.cs, bits, smin, span, P.status, 4, g,
-                                     record ? wl : nullptr, wn, kRowSetCap);
+                                     summ);
     }
     fetch_j();
     const unsigned cnt = __reduce_add_sync(full, (unsigned)nb);
     if (lane == 0) rowsize[g] = (long long)cnt;
-    if (record) {
-      // the row's column sets (set index, bits) for the numeric phase
-      const int nw = *wn;
-      if (nw <= kRowSetCap) {
-        int2* dst = P.rsets + g * kRowSetCap;
-        for (int x = lane; x < nw; x += 32) {
-          const int wd = wl[x];
-          dst[x] = make_int2((int)smin + wd, (int)bits[wd]);
-        }
-      }
-      if (lane == 0) P.rcnt[g] = nw <= kRowSetCap ? nw : -1;
-      __syncwarp();
+    // the words that became nonzero, in increasing order: recorded as the
+    // row's column sets (set index, bits) for the numeric phase, then cleared
+    const unsigned f0 = summ[2 * lane], f1 = summ[2 * lane + 1];
+    const int nf = __popc(f0) + __popc(f1);
+    int incl = nf;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int y = __shfl_up_sync(full, incl, d);
+      if (lane >= d) incl += y;
     }
-    uint4* c4 = reinterpret_cast<uint4*>(bits);
-    for (int x = lane; x < (int)((span + 3u) >> 2); x += 32) c4[x] = make_uint4(0u, 0u, 0u, 0u);
+    const int nw = __shfl_sync(full, incl, 31);
+    int2* dst = (record && nw <= kRowSetCap) ? P.rsets + g * kRowSetCap : nullptr;
+    int at = incl - nf;
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+      unsigned f = hh ? f1 : f0;
+      while (f) {
+        const int wd = 64 * lane + 32 * hh + __ffs(f) - 1;
+        f &= f - 1u;
+        if (dst != nullptr) dst[at] = make_int2((int)smin + wd, (int)bits[wd]);
+        bits[wd] = 0u;
+        ++at;
+      }
+    }
+    summ[2 * lane] = 0u;
+    summ[2 * lane + 1] = 0u;
+    if (record && lane == 0) P.rcnt[g] = nw <= kRowSetCap ? nw : -1;
     __syncwarp();
   }
 }
