@@ -317,10 +317,47 @@ __global__ void __launch_bounds__(256, 4) k_sym_wb(ProbD P, const int* __restric
     }
     int nb = 0;
     const bool one_chunk = a1 - a0 <= 32;
-    for (long long c = a0; c < a1; c += 32) {
-      if (!one_chunk) load_chunk(c);
-      nb += wb_union_chunk<32, true>(full, lane, pre, qsv, qs, ql, P.csi, P.cs, bits, smin, span, P.status, 4, g,
-                                     summ);
+    const int mq = one_chunk ? (int)__reduce_max_sync(full, (unsigned)ql) : 0;
+    const int tq = one_chunk ? (int)__reduce_add_sync(full, (unsigned)ql) : 0;
+    if (one_chunk && mq * (int)(a1 - a0) <= 2 * tq) {
+      // one chunk of compressed B rows of similar lengths: each lane ORs the
+      // entries of its own B row (no search for a product's A entry); a lane
+      // starts at offset lane mod ql of its row, so lanes whose B rows carry
+      // nearly the same sets (neighbouring rows of a stencil) do not hit one
+      // word in the same step.  Four entries' loads are issued together.
+      const int rot = ql > 0 ? (int)((unsigned)lane % (unsigned)ql) : 0;
+      for (int u0 = 0; u0 < mq; u0 += 4) {
+        unsigned w[4], m[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int k = u0 + u;
+          w[u] = 0xffffffffu;
+          m[u] = 0u;
+          if (k < ql) {
+            int o = rot + k;
+            if (o >= ql) o -= ql;
+            w[u] = (unsigned)P.csi[qs + o] - smin;
+            m[u] = P.cs[qs + o];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (w[u] < span) {
+            const unsigned old = atomicOr(bits + w[u], m[u]);
+            nb += __popc(m[u] & ~old);
+            if (old == 0u && m[u] != 0u) atomicOr(summ + (w[u] >> 5), 1u << (w[u] & 31u));
+          } else if (m[u] != 0u) {
+            dev_fail(P.status, kDevBadIndex, 4, g);
+          }
+        }
+      }
+      __syncwarp();
+    } else {
+      for (long long c = a0; c < a1; c += 32) {
+        if (!one_chunk) load_chunk(c);
+        nb += wb_union_chunk<32, true>(full, lane, pre, qsv, qs, ql, P.csi, P.cs, bits, smin, span, P.status, 4, g,
+                                       summ);
+      }
     }
     fetch_j();
     const unsigned cnt = __reduce_add_sync(full, (unsigned)nb);
