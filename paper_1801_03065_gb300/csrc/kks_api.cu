@@ -23,6 +23,7 @@
 namespace kks {
 size_t symbolic_team_bytes(int cls, int logT, int compressed);
 size_t numeric_cta_bytes(int logT, int dtype, long long kwords);
+long long numeric_rdense_vcap(long long kwords, int dtype, size_t max_smem, int small);
 size_t numeric_spill_l1_bytes(int logT, int dtype);
 size_t numeric_l2_chunk_bytes(long long slots, int dtype);
 size_t masked_team_bytes(int cls, int logT, int dtype);
@@ -365,6 +366,12 @@ BinCfg sym_cfg(kks_handle* h, int comp) {
   // would reach half its size (plain rows: u * 128 >= k; 64 and 32 measured
   // slower on rows of random columns)
   c.dense_ratio = comp ? 4 : 128;
+  // dense rows whose bitmap is at most 2^11 words (8 KB) take warp teams (on
+  // the uniform-column rows of the 512-product batched workload: 13.5 ms for
+  // the rows with bitmaps up to 2^11 words, which took 30.5 ms of the
+  // 512-thread CTA kernel's 56.6 ms; with 2^12 and 2^13 words only 6 to 8
+  // warps fit an SM and the warp rows ran 53 ms against 26.1 ms)
+  c.dense_warp_log2w = 11;
   // one thread per row when the row has at most kT1SymKeys products
   c.t1_max_keys = kT1SymKeys;
   c.t1_max_work = kT1SymKeys;
@@ -401,6 +408,13 @@ BinCfg num_cfg(kks_handle* h, int dtype, long long kmax) {
   // stay in hash tables, which take fewer passes over their products)
   c.dense_max_kwords = 1ll << 40;
   c.dense_ratio = dtype == 1 ? 0 : 8;
+  // dense rows whose values fit shared memory beside the k-bit bitmap keep
+  // their values by rank (two passes over the products) instead of sweeping
+  // the k columns in windows
+  if (h->opt.dense != 1) {
+    c.rdense_max = numeric_rdense_vcap(kwords_of(kmax), dtype, (size_t)h->max_smem, 0);
+    c.rdense_small = numeric_rdense_vcap(kwords_of(kmax), dtype, (size_t)h->max_smem, 1);
+  }
   // one thread per row: at most kT1MaxKeys columns of C and 64 products
   c.t1_max_keys = kT1MaxKeys;
   c.t1_max_work = 64;
@@ -934,7 +948,7 @@ spgemm_status_t tune_numeric(kks_handle* h, cudaStream_t s) {
   int changed = 0;
   for (BinRun& r : h->num_bins) {
     if (r.cls != kClsW8 && r.cls != kClsW32 && r.cls != kClsC256 && r.cls != kClsC1024 &&
-        !(r.cls == kClsDense && h->b_sorted))
+        !(r.cls == kClsDense && r.logT == 0 && h->b_sorted))
       continue;
     bool cached = false;
     for (const auto& te : h->tune_cache) {
@@ -1006,6 +1020,15 @@ spgemm_status_t tune_numeric(kks_handle* h, cudaStream_t s) {
       x.compressed = 0;
       x.part = 0;
       cand.push_back(x);
+      // or the rank-dense rows, when every row of the bin (at most 2^(logT-1)
+      // columns) fits their values
+      for (int small = 1; small >= 0; --small) {
+        if (numeric_rdense_vcap(h->num_kw_max, h->dtype, (size_t)h->max_smem, small) >= (1ll << (r.logT - 1))) {
+          x.logT = small ? 2 : 1;
+          cand.push_back(x);
+          break;
+        }
+      }
     }
     const int down = r.cls == kClsW32 ? kClsW8 : r.cls == kClsC256 ? kClsW32 : r.cls == kClsC1024 ? kClsC256 : 0;
     if (down && r.logT <= max_logT(down)) {

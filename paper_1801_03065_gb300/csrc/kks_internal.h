@@ -58,6 +58,11 @@ struct BinCfg {
   int slots_log2;          // table slots per key bound, log2 (0 = 1: at most 50 % load; -1: next power of two)
   long long t1_max_work;   // > 0: rows with u <= t1_max_keys and work <= this go to class T1
   int t1_max_keys;         // 0: kT1MaxKeys
+  int dense_warp_log2w;    // > 0: dense rows of at most 2^this bitmap words and w32_max_work products
+                           // take warp teams, binned by the bitmap size (bin logT = its log2, at
+                           // least 5); 0: one CTA class
+  long long rdense_max;    // numeric: dense rows of at most this many columns take the rank-dense
+  long long rdense_small;  // kernel (bin logT 1), of at most rdense_small its 512-thread form (logT 2)
 };
 
 // kk: the key range the dense test compares against (k, or k/32 compressed);
@@ -77,13 +82,18 @@ __host__ __device__ inline int choose_bin(long long u, long long work, long long
   if (c.t1_max_work > 0 && u <= (c.t1_max_keys > 0 ? c.t1_max_keys : kT1MaxKeys) && work <= c.t1_max_work)
     return bin_id(kClsT1, 0);
   bool dense_fit = c.dense_ok && kwords <= c.dense_max_kwords;
-  if (dense_fit && (logT > c.cta_max_logT || u * c.dense_ratio >= kk)) return bin_id(kClsDense, 0);
+  const int dense_bin = (c.dense_warp_log2w > 0 && kwords <= (1ll << c.dense_warp_log2w) && work <= c.w32_max_work)
+                            ? bin_id(kClsDense, ilog2_ceil(kwords) > 5 ? ilog2_ceil(kwords) : 5)
+                        : (u <= c.rdense_small) ? bin_id(kClsDense, 2)
+                        : (u <= c.rdense_max)   ? bin_id(kClsDense, 1)
+                                                : bin_id(kClsDense, 0);
+  if (dense_fit && (logT > c.cta_max_logT || u * c.dense_ratio >= kk)) return dense_bin;
   if (logT <= c.w8_max_logT && work <= c.w8_max_work) return bin_id(kClsW8, logT);
   if (logT <= c.w32_max_logT && work <= c.w32_max_work) return bin_id(kClsW32, logT);
   if (logT <= c.c256_max_logT && work <= c.c256_max_work) return bin_id(kClsC256, logT);
   if (logT <= c.cta_max_logT) return bin_id(kClsC1024, logT);
   if (c.spill_ok || !dense_fit) return bin_id(kClsSpill, logT);
-  return bin_id(kClsDense, 0);
+  return dense_bin;
 }
 
 // ---------------------------------------------------------------------------

@@ -2062,6 +2062,120 @@ __global__ void __launch_bounds__(TW) k_num_spill(ProbD P, const int* __restrict
   }
 }
 
+// ---------------------------------------------------------------------------
+// Rank-dense rows (CTA teams): the dense accumulator of Section 3.1.2 with
+// its values kept by rank instead of by column.  Rows of this class have more
+// columns than the largest shared hash table holds, but few enough that the
+// row's values fit shared memory next to a k-bit column bitmap:
+//   1. every product marks its column in the bitmap (first pass over the
+//      products, columns only)
+//   2. the count of set bits before every word (its rank base)
+//   3. every product adds a_ij * b_jl to the value at its column's rank
+//      (second pass; shared atomic adds)
+//   4. values written in order; columns from the bitmap, each word's set bits
+//      at its base
+// Per row this costs O(k / 32) for the bitmap and O(f) for the products,
+// where the windowed dense rows sweep their k values in windows.
+// ---------------------------------------------------------------------------
+template <int TW, typename VT>
+__host__ __device__ size_t rdense_fixed_bytes(long long kw_cap) {
+  return al16((size_t)((kw_cap + 3) & ~3ll) * 4) + al16((size_t)(kw_cap + 1) * 2) +
+         al16(sizeof(ChunkScratch<TW, VT>)) + al16((size_t)kStagedPasses * TW * 4) + 16;
+}
+
+template <int TW, typename VT>
+__global__ void __launch_bounds__(TW) k_num_rdense(ProbD P, const int* __restrict__ rows, long long nrows,
+                                                   long long kw_cap, long long vcap, unsigned long long* fetch) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long scan_scratch[33];
+  __shared__ long long fetch_s;
+  Team<TW> tm;
+  unsigned* bm = reinterpret_cast<unsigned*>(smem);
+  unsigned short* gp = reinterpret_cast<unsigned short*>(smem + al16((size_t)((kw_cap + 3) & ~3ll) * 4));
+  ChunkScratch<TW, VT>* csc = reinterpret_cast<ChunkScratch<TW, VT>*>(
+      reinterpret_cast<unsigned char*>(gp) + al16((size_t)(kw_cap + 1) * 2));
+  int* seg = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(csc) + al16(sizeof(ChunkScratch<TW, VT>)));
+  VT* vals = reinterpret_cast<VT*>(smem + rdense_fixed_bytes<TW, VT>(kw_cap));
+  for (long long r = cta_next_row(fetch, &fetch_s); r < nrows; r = cta_next_row(fetch, &fetch_s)) {
+    const long long g = rows[r];
+    const int b = inst_of(P.arow0s, P.ninst, g);
+    const InstD& I = P.inst[b];
+    const long long i = g - I.arow0;
+    const long long c0 = I.Crp[i];
+    const long long s = I.Crp[i + 1] - c0;
+    const long long k = I.k;
+    const long long kw = (k + 31) >> 5;
+    if (s > vcap || kw > kw_cap) {   // binning keeps every row of the class within both
+      if (tm.lane == 0) dev_fail(P.status, kDevTableFull, 19, g);
+      continue;
+    }
+    const long long a0 = rp_at(I.A, i), a1 = rp_at(I.A, i + 1);
+    const VT* __restrict__ Ax = reinterpret_cast<const VT*>(I.A.vx);
+    const VT* __restrict__ Bx = reinterpret_cast<const VT*>(I.B.vx);
+    const int* __restrict__ Bj = I.B.cj;
+    auto range = [&](int j, long long* bs, long long* be) {
+      *bs = rp_at(I.B, j);
+      *be = rp_at(I.B, j + 1);
+    };
+    for (long long w = tm.lane; w < kw; w += TW) bm[w] = 0u;
+    tm.sync();
+    // 1. columns
+    auto no_val = [&](long long) { return VT(0); };
+    auto mark = [&](long long q, int) {
+      const int col = Bj[q];
+      if ((unsigned long long)(unsigned)col < (unsigned long long)k) atomicOr(bm + (col >> 5), 1u << (col & 31));
+      else dev_fail(P.status, kDevBadIndex, 20, g);
+    };
+    auto pf_col = [&](long long q) { prefetch_l1(Bj + q); };
+    for_each_product<TW, VT>(tm, csc, scan_scratch, I.A.cj, a0, a1, range, no_val, mark, pf_col, seg);
+    // 2. rank bases: each thread sums a contiguous run of words, the runs are
+    // scanned across the team, then each word of the run gets its base
+    {
+      const long long sg = (kw + TW - 1) / TW;
+      const long long w0 = tm.lane * sg, w1 = w0 + sg < kw ? w0 + sg : kw;
+      int cseg = 0;
+      for (long long w = w0; w < w1; ++w) cseg += __popc(bm[w]);
+      long long run;
+      long long pre = team_excl_scan<TW>(tm, cseg, &run, scan_scratch);
+      for (long long w = w0; w < w1; ++w) {
+        gp[w] = (unsigned short)pre;
+        pre += __popc(bm[w]);
+      }
+      if (tm.lane == 0 && run != s) dev_fail(P.status, kDevRowSizeMismatch, 21, g);
+    }
+    for (long long x = tm.lane; x < s; x += TW) vals[x] = VT(0);
+    tm.sync();
+    // 3. values at their ranks
+    auto aval = [&](long long p) { return Ax[p]; };
+    auto add = [&](long long q, int t) {
+      const int col = Bj[q];
+      if ((unsigned long long)(unsigned)col >= (unsigned long long)k) return;
+      const int w = col >> 5;
+      const long long rk = (long long)gp[w] + __popc(bm[w] & ((1u << (col & 31)) - 1u));
+      if (rk < s) atomicAdd(vals + rk, csc->av[t] * Bx[q]);
+    };
+    auto pf = [&](long long q) {
+      prefetch_l1(Bj + q);
+      prefetch_l1(Bx + q);
+    };
+    for_each_product<TW, VT>(tm, csc, scan_scratch, I.A.cj, a0, a1, range, aval, add, pf, seg);
+    // 4. the row in order
+    VT* __restrict__ Cx = reinterpret_cast<VT*>(I.Cx);
+    int* __restrict__ Cj = I.Cj;
+    for (long long x = tm.lane; x < s; x += TW) Cx[c0 + x] = vals[x];
+    for (long long w = tm.lane; w < kw; w += TW) {
+      unsigned m = bm[w];
+      long long o = gp[w];
+      while (m) {
+        const int bit = __ffs(m) - 1;
+        m &= m - 1u;
+        if (o < s) Cj[c0 + o] = (int)(32 * w + bit);
+        ++o;
+      }
+    }
+  }
+}
+
 template <class K>
 cudaError_t set_smem(K kernel, size_t bytes) {
   // the kernels also hold up to 1 KB of static shared memory: opt in above 47 KB of dynamic
@@ -2161,6 +2275,32 @@ cudaError_t run_dense(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
   return cudaGetLastError();
 }
 
+// Rank-dense rows: bin logT 1 takes 1024-thread CTAs (one per SM, values of
+// rows up to the class limit), logT 2 takes 512-thread CTAs with half the
+// shared memory each (two per SM, smaller rows).
+template <typename VT>
+cudaError_t run_rdense(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
+  const long long kw_cap = S.kwords_max;
+  auto go = [&](auto kern, int tw, size_t fixed, size_t budget) -> cudaError_t {
+    if (fixed + 1024 >= budget) return cudaErrorInvalidConfiguration;
+    long long vcap = (long long)((budget - 1024 - fixed) / sizeof(VT));
+    if (vcap > 65535) vcap = 65535;   // 16-bit rank bases
+    const size_t smem = fixed + al16((size_t)vcap * sizeof(VT));
+    if (smem > (size_t)L.max_smem_optin) return cudaErrorInvalidConfiguration;
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    const unsigned grid = resident_grid(kern, tw, smem, L.num_sms, S.nrows);
+    e = cudaMemsetAsync(S.fetch, 0, sizeof(unsigned long long), L.stream);
+    if (e != cudaSuccess) return e;
+    KKS_LAUNCHED();
+    kern<<<grid, tw, smem, L.stream>>>(P, S.rows, S.nrows, kw_cap, vcap, S.fetch);
+    return cudaGetLastError();
+  };
+  if (S.logT == 2)
+    return go(k_num_rdense<512, VT>, 512, rdense_fixed_bytes<512, VT>(kw_cap), (size_t)L.max_smem_optin / 2);
+  return go(k_num_rdense<1024, VT>, 1024, rdense_fixed_bytes<1024, VT>(kw_cap), (size_t)L.max_smem_optin);
+}
+
 template <typename VT>
 cudaError_t run_spill(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
   constexpr int TW = 1024;
@@ -2226,7 +2366,9 @@ cudaError_t dispatch(const LaunchCtx& L, const ProbD& P, const NumLaunch& S) {
       if (S.part == kPartTeamSeq) return run_part<1024, VT, kPartTeamSeq>(L, P, S);
       if (S.part == kPartThreadPar) return run_part<1024, VT, kPartThreadPar>(L, P, S);
       return run_hash<1024, VT>(L, P, S);
-    case kClsDense: return (S.stage && S.b_sorted) ? run_dense<VT, true>(L, P, S) : run_dense<VT, false>(L, P, S);
+    case kClsDense:
+      if (S.logT == 1 || S.logT == 2) return run_rdense<VT>(L, P, S);
+      return (S.stage && S.b_sorted) ? run_dense<VT, true>(L, P, S) : run_dense<VT, false>(L, P, S);
     case kClsSpill: return run_spill<VT>(L, P, S);
     default: return cudaErrorInvalidValue;
   }
@@ -2244,6 +2386,19 @@ size_t numeric_cta_bytes(int logT, int dtype, long long kwords) {
   }
   const size_t a = num_cta_bytes<1024, float>(T, kw), b = num_cta_bytes<1024, float>(T, 0);
   return a < b ? a : b;
+}
+
+// Largest row (columns) of the rank-dense class: 1024-thread CTAs on the
+// whole shared memory (small = 0) or 512-thread CTAs on half of it (small = 1);
+// 0 when the bitmap of kwords words leaves no room.
+long long numeric_rdense_vcap(long long kwords, int dtype, size_t max_smem, int small) {
+  if (kwords <= 0 || kwords > kRankMaxWords) return 0;
+  const size_t budget = small ? max_smem / 2 : max_smem;
+  const size_t fixed = dtype == 1 ? (small ? rdense_fixed_bytes<512, double>(kwords) : rdense_fixed_bytes<1024, double>(kwords))
+                                  : (small ? rdense_fixed_bytes<512, float>(kwords) : rdense_fixed_bytes<1024, float>(kwords));
+  if (fixed + 1024 >= budget) return 0;
+  long long v = (long long)((budget - 1024 - fixed) / (dtype == 1 ? 8 : 4));
+  return v > 65535 ? 65535 : v;
 }
 
 size_t numeric_spill_l1_bytes(int logT, int dtype) {

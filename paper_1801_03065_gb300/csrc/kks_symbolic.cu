@@ -16,6 +16,8 @@
 //                                 so the count merges them (union)
 //   k_sym_dense<COMP>           : a k-bit bitmap in shared memory (the dense
 //                                 accumulator of Section 3.1.2 in bit form)
+//   k_sym_dwarp<COMP, U>        : the same bitmap per warp team, for bitmaps of
+//                                 at most 2^11 words (rows binned by bitmap size)
 #include "kks_internal.h"
 
 namespace kks {
@@ -541,6 +543,157 @@ __global__ void __launch_bounds__(TW) k_sym_dense(ProbD P, const int* __restrict
   }
 }
 
+// Dense rows by warp teams: each warp ORs the products of its row into its
+// own bitmap of kw_cap words (the dense accumulator of Section 3.1.2 in bit
+// form, one per warp instead of one per CTA, so many rows are in flight on
+// an SM and no block-wide barrier separates them).  The row size is the number
+// of column bits the inserts set first, so no sweep of the bitmap counts the
+// row; every word an insert turns nonzero is flagged in a summary bitmap and
+// the flagged words alone are cleared after the row.  Rows of one bin have
+// bitmaps of at most kw_cap words (the bin is the bitmap size class).
+// Products: when the chunk's B rows (compressed rows on the compressed B) have
+// similar lengths each lane ORs its own row's entries, U loads in flight,
+// from a rotated start (neighbouring rows of a stencil carry nearly equal
+// columns); otherwise the chunk's products are spread flat over the lanes.
+__host__ __device__ inline size_t symdw_team_bytes(long long kw_cap) {
+  return al16((size_t)kw_cap * 4) + al16((size_t)((kw_cap + 31) / 32) * 4) + al16((size_t)33 * 4) +
+         al16((size_t)32 * 8);
+}
+
+template <bool COMP, int U>
+__global__ void __launch_bounds__(256) k_sym_dwarp(ProbD P, const int* __restrict__ rows, long long nrows,
+                                                   long long kw_cap, long long* __restrict__ rowsize) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Team<32> tm;
+  const long long nsum = (kw_cap + 31) / 32;
+  unsigned char* base = smem + (size_t)tm.id * symdw_team_bytes(kw_cap);
+  unsigned* bits = reinterpret_cast<unsigned*>(base);
+  unsigned* summ = reinterpret_cast<unsigned*>(base + al16((size_t)kw_cap * 4));
+  int* pre = reinterpret_cast<int*>(base + al16((size_t)kw_cap * 4) + al16((size_t)nsum * 4));
+  long long* qsv = reinterpret_cast<long long*>(reinterpret_cast<unsigned char*>(pre) + al16((size_t)33 * 4));
+  const int lane = tm.lane;
+  const unsigned full = 0xffffffffu;
+  for (long long w = lane; w < kw_cap; w += 32) bits[w] = 0u;
+  for (long long w = lane; w < nsum; w += 32) summ[w] = 0u;
+  __syncwarp();
+  const long long team = (long long)blockIdx.x * tm.per_cta + tm.id;
+  const long long nteams = (long long)gridDim.x * tm.per_cta;
+  for (long long r = team; r < nrows; r += nteams) {
+    const long long g = rows[r];
+    const int b = inst_of(P.arow0s, P.ninst, g);
+    const InstD& I = P.inst[b];
+    const long long i = g - I.arow0;
+    const long long kw = (I.k + 31) >> 5;
+    const long long a0 = rp_at(I.A, i), a1 = rp_at(I.A, i + 1);
+    if (kw > kw_cap) {   // binning keeps every row of the bin within kw_cap
+      if (lane == 0) dev_fail(P.status, kDevTableFull, 5, g);
+      continue;
+    }
+    const unsigned span = (unsigned)kw;
+    const int* __restrict__ Bj = I.B.cj;
+    // word and bits of entry q of the (compressed) B
+    auto entry = [&](long long q, unsigned* w, unsigned* m) {
+      if (COMP) {
+        *w = (unsigned)P.csi[q];
+        *m = P.cs[q];
+      } else {
+        const int col = Bj[q];
+        *w = (unsigned)col >> 5;
+        *m = 1u << (col & 31);
+      }
+    };
+    auto insert = [&](unsigned w, unsigned m) -> int {
+      if (w < span) {
+        const unsigned old = atomicOr(bits + w, m);
+        if (old == 0u && m != 0u) atomicOr(summ + (w >> 5), 1u << (w & 31u));
+        return __popc(m & ~old);
+      }
+      if (m != 0u) dev_fail(P.status, kDevBadIndex, COMP ? 3 : 4, g);
+      return 0;
+    };
+    int nb = 0;
+    for (long long c = a0; c < a1; c += 32) {
+      const long long p = c + lane;
+      long long qs = 0;
+      int ql = 0;
+      if (p < a1) {
+        const int j = I.A.cj[p];
+        if (COMP) {
+          qs = P.Bcp[I.brow0 + j];
+          ql = (int)(P.Bcp[I.brow0 + j + 1] - qs);
+        } else {
+          qs = rp_at(I.B, j);
+          ql = (int)(rp_at(I.B, j + 1) - qs);
+        }
+      }
+      const int nc = (a1 - c) < 32 ? (int)(a1 - c) : 32;
+      const int mq = (int)__reduce_max_sync(full, (unsigned)ql);
+      const int tq = (int)__reduce_add_sync(full, (unsigned)ql);
+      if ((long long)mq * nc <= 2ll * tq) {
+        const int rot = ql > 0 ? (int)((unsigned)lane % (unsigned)ql) : 0;
+        for (int u0 = 0; u0 < mq; u0 += U) {
+          unsigned w[U], m[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int kq = u0 + u;
+            w[u] = 0xffffffffu;
+            m[u] = 0u;
+            if (kq < ql) {
+              int o = rot + kq;
+              if (o >= ql) o -= ql;
+              entry(qs + o, &w[u], &m[u]);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) nb += insert(w[u], m[u]);
+        }
+      } else {
+        int ex = ql;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const int y = __shfl_up_sync(full, ex, d);
+          if (lane >= d) ex += y;
+        }
+        pre[lane] = ex - ql;
+        qsv[lane] = qs;
+        if (lane == 31) pre[32] = ex;
+        __syncwarp();
+        int t = 0;
+        for (int xb = 0; xb < tq; xb += U * 32) {
+          unsigned w[U], m[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int x = xb + u * 32 + lane;
+            w[u] = 0xffffffffu;
+            m[u] = 0u;
+            if (x < tq) {
+              while (pre[t + 1] <= x) ++t;
+              entry(qsv[t] + (x - pre[t]), &w[u], &m[u]);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) nb += insert(w[u], m[u]);
+        }
+      }
+      __syncwarp();
+    }
+    const unsigned cnt = __reduce_add_sync(full, (unsigned)nb);
+    if (lane == 0) rowsize[g] = (long long)cnt;
+    // clear the words that became nonzero
+    for (long long x = lane; x < (kw + 31) / 32; x += 32) {
+      unsigned f = summ[x];
+      if (f) {
+        summ[x] = 0u;
+        while (f) {
+          bits[32 * x + __ffs(f) - 1] = 0u;
+          f &= f - 1u;
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
 template <class K>
 cudaError_t set_smem(K kernel, size_t bytes) {
   // the kernels also hold up to 1 KB of static shared memory: opt in above 47 KB of dynamic
@@ -637,7 +790,28 @@ cudaError_t run_spill(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, lo
 }
 
 template <bool COMP>
+cudaError_t run_dwarp(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, long long* rowsize) {
+  long long kw_cap = 1ll << S.logT;
+  if (kw_cap > S.kwords_max && S.kwords_max > 0) kw_cap = S.kwords_max;
+  const size_t tb = symdw_team_bytes(kw_cap);
+  // up to 8 warp teams per CTA, within about 200 KB of shared memory
+  int teams = (int)((size_t)(200 * 1024) / tb);
+  if (teams > 8) teams = 8;
+  if (teams < 1) teams = 1;
+  const size_t smem = tb * teams;
+  if (smem > (size_t)L.max_smem_optin) return cudaErrorInvalidConfiguration;
+  auto kern = k_sym_dwarp<COMP, 4>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  KKS_LAUNCHED();
+  kern<<<resident_grid(kern, 32 * teams, smem, L.num_sms, (S.nrows + teams - 1) / teams), 32 * teams, smem,
+         L.stream>>>(P, S.rows, S.nrows, kw_cap, rowsize);
+  return cudaGetLastError();
+}
+
+template <bool COMP>
 cudaError_t run_dense(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, long long* rowsize) {
+  if (S.logT > 0) return run_dwarp<COMP>(L, P, S, rowsize);
   constexpr int TW = 512;
   const size_t smem = al16((size_t)S.kwords_max * 4) + al16(sizeof(ChunkScratch<TW, int>)) +
                       al16((size_t)kStagedPasses * TW * 4);

@@ -841,6 +841,28 @@ def test_dense_windows_wide_k(ops, dtype, shuffled):
     assert_matches_oracle(A, B, Cd, dtype)
 
 
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("shuffled", [False, True])
+def test_rank_dense_rows(ops, dtype, shuffled):
+    """Dense rows whose values fit shared memory beside the k-bit bitmap (the
+    rank-dense kernel, both CTA sizes): rows of about 550 columns over k = 4000
+    (FP32 dense by the k / 8 rule) and rows of about 19 000 columns over
+    k = 20 000 (beyond the largest shared table in FP64), mixed with short rows
+    that take the hash classes."""
+    A1 = w.random_csr(300, 400, 20.0, seed=33)
+    B1 = w.random_csr(400, 4000, 30.0, seed=34)
+    A2 = w.random_csr(60, 300, 150.0, seed=35)
+    B2 = w.random_csr(300, 20000, 200.0, seed=36)
+    for case, (A, B) in enumerate(((A1, B1), (A2, B2))):
+        if shuffled:
+            B = w.shuffle_rows(B, 6)
+        h, _, _, Cd = run(ops, A, B, dtype)
+        if case == 1 or dtype == np.float32:   # FP64 rows of case 0 fit the hash tables
+            assert h.stats()["bin_rows_numeric"][5] > 0
+        assert_matches_oracle(A, B, Cd, dtype)
+        h.close()
+
+
 # ------------------------------------------------------------------ masked counts (symbolic only)
 def _count(ops, X, Y, S):
     h = ops.SpGEMM()
