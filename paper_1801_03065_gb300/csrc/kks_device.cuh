@@ -79,7 +79,7 @@ struct InstD {
 
 // Per-launch view of a plan.
 // Column sets of the rows of C, left by the symbolic phase for the numeric
-// phase: row g's sets (index, bits; in no particular order) at rsets[g *
+// phase: row g's sets (index, bits; in increasing index order) at rsets[g *
 // kRowSetCap ...], their number at rcnt[g], or -1 where the symbolic kernel
 // of that row did not record them (then the numeric phase forms the union).
 constexpr int kRowSetCap = 64;
@@ -553,6 +553,7 @@ struct ChunkScratch {
   long long pre[TW + 1];   // exclusive prefix of B-row lengths
   long long bs[TW];        // B-row start of each entry
   VT av[TW];               // A values of the chunk (numeric only)
+  long long nne;           // non-empty B ranges of the chunk (set by chunk_scan)
 };
 
 // Calls body(q, t) for every product of row i: q indexes B's entry, t the
@@ -613,7 +614,10 @@ __device__ __forceinline__ int team_excl_max(const Team<TW>& tm, int v, long lon
 // products, every non-empty B range marks where it starts and a forward fill
 // (max-scan) gives every product its range, one shared load per product.
 // This pays off when the chunk holds many short or empty B ranges (dense
-// windows, short B rows), where the search below needs many steps.
+// windows, short B rows), where the search below needs many steps; a chunk
+// whose non-empty ranges average kSegMaxAvg products or more takes the search
+// (a few linear steps per pass), which needs no barrier per block.
+constexpr long long kSegMaxAvg = 128;
 // One chunk of A(i,:): lane t holds the B range [bs, be) and the value av of
 // its A entry.  Returns the chunk's product count (the same in every lane).
 // The chunk's scan (the lane's first product ex, the chunk's product count
@@ -621,11 +625,17 @@ __device__ __forceinline__ int team_excl_max(const Team<TW>& tm, int v, long lon
 template <int TW, typename VT>
 __device__ __forceinline__ long long chunk_scan(const Team<TW>& tm, ChunkScratch<TW, VT>* cs, long long* scan_scratch,
                                                 long long bs, long long be, VT av, long long* total) {
-  long long ex = team_excl_scan<TW>(tm, be - bs, total, scan_scratch);
+  // one scan carries the lengths (high bits) and the non-empty count (low 11 bits)
+  long long tp;
+  long long ex = team_excl_scan<TW>(tm, (be - bs) * 2048 + (be > bs ? 1 : 0), &tp, scan_scratch) >> 11;
+  *total = tp >> 11;
   cs->pre[tm.lane] = ex;
   cs->bs[tm.lane] = bs;
   cs->av[tm.lane] = av;
-  if (tm.lane == 0) cs->pre[TW] = *total;
+  if (tm.lane == 0) {
+    cs->pre[TW] = *total;
+    cs->nne = tp & 2047;
+  }
   tm.sync();
   return ex;
 }
@@ -636,7 +646,7 @@ __device__ __forceinline__ long long chunk_products(const Team<TW>& tm, ChunkScr
                                                     long long bs, long long be, Body body, Prefetch prefetch,
                                                     int* seg) {
   if constexpr (Team<TW>::kCta) {
-    if (seg != nullptr) {
+    if (seg != nullptr && total < kSegMaxAvg * cs->nne) {
       constexpr int E = kStagedPasses;
       constexpr long long S = (long long)kStagedPasses * TW;
       int carry = -1;
