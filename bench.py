@@ -458,7 +458,9 @@ def time_region(torch, fn, steps):
 
 def load_traffic_record(name):
     """ncu DRAM bytes of a kernel from a profiles/ summary ("key: value" lines),
-    valid only for the library build (source digest) it was taken on."""
+    valid only while the sources the numeric kernels are compiled from and
+    launched by (build.NUMERIC_SOURCES and the flags) have the digest the
+    record was taken on."""
     path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
@@ -470,7 +472,7 @@ def load_traffic_record(name):
                     k, v = line.split(":", 1)
                     rec[k.strip()] = v.strip()
         from paper_1801_03065_gb300 import build as pkg_build
-        if rec.get("build_digest") != pkg_build._digest():
+        if rec.get("build_digest") != pkg_build._digest(pkg_build.NUMERIC_SOURCES):
             return None
         return {"traffic_bytes_per_launch": int(float(rec["traffic_bytes_per_launch"]))}
     except Exception:

@@ -37,9 +37,18 @@ def _nvcc() -> str:
     return found
 
 
-def _digest() -> str:
+# The sources that a numeric kernel is compiled from and launched by: a
+# profile record of a numeric kernel stays valid while these are unchanged.
+NUMERIC_SOURCES = ["kks_api.cu", "kks_device.cuh", "kks_internal.h", "kks_numeric.cu"]
+
+
+def _digest(names=None) -> str:
+    """SHA-256 of the library sources (all of csrc/ and the header, or only the
+    csrc/ files in names) and of the compiler flags."""
     h = hashlib.sha256()
-    for d, names in ((CSRC, sorted(os.listdir(CSRC))), (INCLUDE, ["kkspgemm.h"])):
+    groups = ((CSRC, sorted(os.listdir(CSRC))), (INCLUDE, ["kkspgemm.h"])) if names is None else \
+        ((CSRC, sorted(names)),)
+    for d, names in groups:
         for n in names:
             p = os.path.join(d, n)
             if os.path.isfile(p):
