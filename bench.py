@@ -44,6 +44,15 @@ WORKLOAD = ("stencil27_100: C = A*A and P^T*(A*P); A = 27-point stencil on a 100
             "P = 3x3x3 aggregation (1,000,000 x 39,304)")
 
 
+def workload_name(A, P, grid):
+    """The stencil workload's description at the grid actually run."""
+    if grid == 100:
+        return WORKLOAD
+    return ("stencil27_%d: C = A*A and P^T*(A*P); A = 27-point stencil on a %d^3 grid (%s rows, %s nnz, FP64, "
+            "26/-1 + U(-1e-3,1e-3), seed 1), P = 3x3x3 aggregation (%s x %s)"
+            % (grid, grid, format(A.nrows, ","), format(A.nnz, ","), format(P.nrows, ","), format(P.ncols, ",")))
+
+
 def parse_args(argv=None):
     p = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     p.add_argument("--gpus", type=int, default=1)
@@ -81,6 +90,8 @@ def parse_args(argv=None):
                         "the numeric phase (bit 1), masked products / numeric reuse (bit 2)")
     p.add_argument("--dense", type=int, default=-1, choices=(-1, 0, 1),
                    help="option dense: -1 auto, 0 no dense accumulator (large rows take L1 + L2), 1 prefer")
+    p.add_argument("--sym-merge", type=int, default=1, choices=(0, 1),
+                   help="option sym_merge: symbolic window rows of one chunk merge their sorted compressed B rows")
     p.add_argument("--stage-b", type=int, default=0, choices=(0, 1),
                    help="option stage_b: dense-window rows stage their B entries with cp.async")
     p.add_argument("--tune-aa", type=int, default=0, choices=(0, 1),
@@ -206,7 +217,8 @@ class StencilStep:
     a worker thread, while A·A runs on the current stream (the two products are
     independent); the step ends when both have."""
 
-    def __init__(self, A, P, device, positions=True, rap="fused", concurrent=True, window=1, tune_aa=False):
+    def __init__(self, A, P, device, positions=True, rap="fused", concurrent=True, window=1, tune_aa=False,
+                 sym_merge=True):
         import torch
         from paper_1801_03065_gb300 import ops
         self.torch, self.ops = torch, ops
@@ -218,7 +230,8 @@ class StencilStep:
         self.rap = rap
         self.window = int(window)
         self.tune_aa = bool(tune_aa)
-        kw = dict(numeric_positions=pos, window_positions=self.window)
+        self.sym_merge = bool(sym_merge)
+        kw = dict(numeric_positions=pos, window_positions=self.window, sym_merge=self.sym_merge)
         self.hAA = ops.SpGEMM(tune=self.tune_aa, **kw)
         self.hAP, self.hRAP = ops.SpGEMM(**kw), ops.SpGEMM(**kw)
         self.hT = ops.SpGEMM()
@@ -494,7 +507,8 @@ def run_ours(args):
     A = w.stencil3d_27pt(args.grid, seed=1)
     P = w.aggregation(args.grid, 3)
     S = StencilStep(A, P, device, positions=bool(args.numeric_positions), rap=args.rap,
-                    concurrent=not args.serial, window=int(args.window), tune_aa=bool(args.tune_aa))
+                    concurrent=not args.serial, window=int(args.window), tune_aa=bool(args.tune_aa),
+                    sym_merge=bool(args.sym_merge))
     for _ in range(max(args.warmup, 1)):
         S.step()
     torch.cuda.synchronize()
@@ -531,7 +545,7 @@ def run_ours(args):
     Pd = S.Pd
     if S.rap == "fused":
         T2 = StencilStep(A, P, device, positions=S.positions, rap="two", concurrent=False, window=S.window,
-                         tune_aa=S.tune_aa)
+                         tune_aa=S.tune_aa, sym_merge=S.sym_merge)
         T2.step()
         two_step = lambda: (T2.hT.transpose(Pd, out=T2.Pt),
                             T2.hAP.symbolic(Ad, Pd, C_rowptr=T2.rpAP),
@@ -580,7 +594,7 @@ def run_ours(args):
         "ms_per_step_min": round(min(times), 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.grid == 100 else WORKLOAD.replace("100^3", "%d^3" % args.grid),
+        "config": {"workload": workload_name(A, P, args.grid),
                    "global_batch": world, "flops_per_step": 2 * flops_step,
                    "triple_product": ("one plan (spgemm_rap_symbolic / spgemm_rap_numeric)%s; flops counted as "
                                       "A*P and P^T*(A*P)" % (", on a second stream beside A*A" if S.concurrent
@@ -661,7 +675,7 @@ def run_e2e(torch, S, A, P, args, world, flops_step):
     region ends when the last read-back has landed in host memory."""
     pin = lambda x: torch.from_numpy(x).pin_memory()
     S2 = StencilStep(A, P, S.Ad.rowptr.device, positions=S.positions, rap=S.rap, concurrent=S.concurrent,
-                     window=S.window, tune_aa=S.tune_aa)
+                     window=S.window, tune_aa=S.tune_aa, sym_merge=S.sym_merge)
     S2.step()
     sets = [S, S2]
     hA = [pin(A.rowptr), pin(A.colidx), pin(A.values)]
@@ -806,7 +820,7 @@ def run_reference(args):
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": round(1e3 * sum(ts) / len(ts), 3), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD if args.grid == 100 else WORKLOAD.replace("100^3", "%d^3" % args.grid),
+           "config": {"workload": workload_name(A, P, args.grid),
                       "global_batch": 1, "parallelism": "host cores (OpenMP)"},
            "cpu_baseline": {"value": round(value, 4), "unit": "GFLOP/s", "cores": oracle.num_threads(),
                             "kind": "oracle", "sample": sample},
@@ -978,7 +992,8 @@ def run_numeric_only(args):
     from paper_1801_03065_gb300 import ops
     A = w.stencil3d_27pt(args.grid, seed=1)
     Ad = ops.CsrMatrix.from_host(A.rowptr, A.colidx, A.values, A.shape, device="cuda:0")
-    h = ops.SpGEMM(numeric_positions=bool(args.numeric_positions), window_positions=int(args.window))
+    h = ops.SpGEMM(numeric_positions=bool(args.numeric_positions), window_positions=int(args.window),
+                   sym_merge=bool(args.sym_merge))
     rp, nnz = h.symbolic(Ad, Ad)
     C = h.numeric(Ad, Ad, rp, nnz)
     h.sync()
@@ -1007,12 +1022,13 @@ def run_timeline(args):
         # the step's two products on one stream (the profiler records the
         # kernels launched from this thread)
         S = StencilStep(A, w.aggregation(args.grid, 3), dev, window=int(args.window), tune_aa=bool(args.tune_aa),
+                        sym_merge=bool(args.sym_merge),
                         concurrent=False)
         fn, close = S.step, S.close
     elif args.workload == "rmat18":
         G = w.rmat_symmetric(scale=args.scale, seed=7)
         Ad = ops.CsrMatrix.from_host(G.rowptr, G.colidx, G.values.astype(np.float32), G.shape, device=dev)
-        h = ops.SpGEMM(window_positions=int(args.window))
+        h = ops.SpGEMM(window_positions=int(args.window), sym_merge=bool(args.sym_merge))
         rp, nnz = h.symbolic(Ad, Ad)
         C = h.numeric(Ad, Ad, rp, nnz)
         fn = lambda: (h.symbolic(Ad, Ad, C_rowptr=rp), h.numeric(Ad, Ad, rp, nnz, C.colidx, C.values))
@@ -1137,6 +1153,7 @@ def run_single(args):
     A = wl["A"]
     vdt = np.float32 if wl["dtype"] == "f32" else np.float64
     res = single_measure(A, vdt, args.steps, args.warmup, clocks=True, stage_b=bool(args.stage_b),
+                         sym_merge=bool(args.sym_merge),
                          window_positions=int(args.window), dense=int(args.dense))
     if args.workload == "rmat18":
         desc = RMAT_DESC % A.nnz

@@ -118,7 +118,12 @@ typedef struct {
                                     asynchronous copies (cp.async) while the current block is added,
                                     instead of loading them from global memory per product; 0 (default)
                                     loads them per product */
-  int32_t reserved;
+  int32_t sym_merge;             /* symbolic window rows (window_positions bit 0) with at most 32 entries
+                                    of A whose compressed B rows hold at most 19 column sets each: 1
+                                    (default) merges the sorted compressed B rows (Section 3.2's OR of
+                                    column sets, one set index at a time, smallest first) instead of
+                                    OR-ing them into the window bitmap with shared-memory atomics;
+                                    0: bitmap only.  The row sizes and recorded sets are the same */
 } spgemm_options_t;
 
 /* Statistics of the last symbolic call (Section 4 results-table columns). */

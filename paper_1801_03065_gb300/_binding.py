@@ -37,7 +37,7 @@ class OptionsT(C.Structure):
                 ("device", C.c_int32), ("hash_function", C.c_int32), ("verbose", C.c_int32),
                 ("slots_per_key_log2", C.c_int32), ("tune", C.c_int32),
                 ("numeric_positions", C.c_int32), ("cta_partition", C.c_int32), ("window_positions", C.c_int32),
-                ("stage_b", C.c_int32), ("reserved", C.c_int32)]
+                ("stage_b", C.c_int32), ("sym_merge", C.c_int32)]
 
 
 class StatsT(C.Structure):

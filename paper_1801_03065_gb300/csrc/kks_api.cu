@@ -438,6 +438,7 @@ void set_default_options(spgemm_options_t* o) {
   o->numeric_positions = 1;
   o->cta_partition = 0;
   o->window_positions = 1;
+  o->sym_merge = 1;
 }
 
 // Long-row queue in buffer id (rows first, then three counters).
@@ -747,6 +748,7 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
     S.max_occ = h->opt.l1_max_occupancy;
     S.fetch = B<unsigned long long>(h, kBufFetch);
     S.window = (comp && h->b_sorted && (h->opt.window_positions & 1)) ? 1 : 0;
+    S.merge = (S.window && h->opt.sym_merge) ? 1 : 0;
     long long kmax = 0;
     for (int b = 0; b < count; ++b) kmax = std::max<long long>(kmax, h->inst[b].k);
     // dense rows only come from products whose bitmap fits (checked per row)
@@ -1271,7 +1273,7 @@ spgemm_status_t spgemm_handle_create(spgemm_handle_t* out, const spgemm_options_
       h->opt.slots_per_key_log2 < 0 || h->opt.slots_per_key_log2 > 4 || h->opt.numeric_positions < 0 ||
       h->opt.cta_partition < 0 || h->opt.cta_partition > 2 ||
       h->opt.numeric_positions > 1 || h->opt.window_positions < 0 || h->opt.window_positions > 7 ||
-      h->opt.stage_b < 0 || h->opt.stage_b > 1) {
+      h->opt.stage_b < 0 || h->opt.stage_b > 1 || h->opt.sym_merge < 0 || h->opt.sym_merge > 1) {
     delete h;
     return SPGEMM_ERR_INVALID_ARG;
   }

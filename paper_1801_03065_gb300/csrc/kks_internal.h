@@ -233,7 +233,7 @@ struct SymLaunch {
   int nchunks;
   unsigned long long* fetch;   // CTA classes: row counter (zeroed by the launcher)
   int window;            // compressed W32 rows with every B row sorted: bitmap-window kernel
-  int pad;
+  int merge;             // window kernel: rows of one chunk merge their sorted compressed B rows
 };
 cudaError_t launch_symbolic(const LaunchCtx&, const ProbD&, const SymLaunch&, long long* rowsize);
 

@@ -222,8 +222,21 @@ __global__ void __launch_bounds__(256, 4) k_sym_warp(ProbD P, const int* __restr
 // increasing set order (recorded for the numeric phase) and exactly the words
 // that were set are cleared.  Wider rows take the hash path (sym_warp_row) in
 // the same shared memory.
+//
+// Rows of one chunk of A (at most 32 entries) whose compressed B rows hold at
+// most kMergeLen sets each can instead merge those rows (option sym_merge):
+// every compressed B row is sorted by set index, so the union of Section 3.2
+// is produced one set at a time, smallest first: the warp takes the minimum
+// of the lanes' current set indices, ORs the bits of the lanes that hold it,
+// and those lanes move to their next entry.  The number of steps is the
+// number of column sets of C(i,:); no atomics, no window limit, and the sets
+// come out in increasing order for the numeric phase.  Each lane's row is
+// staged in shared memory first (the bitmap's words, which are cleared again
+// before a later row ORs into them).
 constexpr int kSymWbWords = 1344;
 constexpr int kSymWbSumm = 64;   // summary words: 32 lanes x 2 cover 2048 >= kSymWbWords window words
+constexpr int kMergeLen = 19;    // staged entries per lane (odd stride: no bank conflicts in the stores)
+static_assert(64 * kMergeLen + 2 * kRowSetCap <= kSymWbWords, "merge staging must fit the window bitmap");
 
 __host__ __device__ size_t symwb_team_bytes(int T) {
   const size_t a = al16((size_t)kSymWbWords * 4), h = al16((size_t)T * 8);
@@ -231,7 +244,7 @@ __host__ __device__ size_t symwb_team_bytes(int T) {
 }
 
 __global__ void __launch_bounds__(256, 4) k_sym_wb(ProbD P, const int* __restrict__ rows, long long nrows, int logT,
-                                                   long long* __restrict__ rowsize) {
+                                                   long long* __restrict__ rowsize, int merge) {
   extern __shared__ __align__(16) unsigned char smem[];
   Team<32> tm;
   const int T = 1 << logT;
@@ -294,6 +307,65 @@ __global__ void __launch_bounds__(256, 4) k_sym_wb(ProbD P, const int* __restric
         ql = (int)(P.Bcp[brow0 + j + 1] - qs);
       }
     };
+    if (merge && a1 - a0 <= 32) {
+      load_chunk(a0);
+      const int mq = (int)__reduce_max_sync(full, (unsigned)ql);
+      if (mq <= kMergeLen) {
+        unsigned* scsi = bits;                  // [32][kMergeLen]: the lanes' set indices
+        unsigned* scs = bits + 32 * kMergeLen;  // [32][kMergeLen]: their bits
+        int2* sout = reinterpret_cast<int2*>(bits + 64 * kMergeLen);   // the row's sets, kRowSetCap
+        for (int u0 = 0; u0 < mq; u0 += 4) {
+          unsigned w[4], m[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (u0 + u < ql) {
+              w[u] = (unsigned)P.csi[qs + u0 + u];
+              m[u] = P.cs[qs + u0 + u];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (u0 + u < ql) {
+              scsi[lane * kMergeLen + u0 + u] = w[u];
+              scs[lane * kMergeLen + u0 + u] = m[u];
+            }
+          }
+        }
+        fetch_j();
+        __syncwarp();
+        constexpr unsigned kNone = 0xffffffffu;   // above every set index (k < 2^31)
+        unsigned hk = ql > 0 ? scsi[lane * kMergeLen] : kNone;
+        unsigned hb = ql > 0 ? scs[lane * kMergeLen] : 0u;
+        int at = 0, nw = 0;
+        unsigned cnt = 0;
+        for (;;) {
+          const unsigned mn = __reduce_min_sync(full, hk);
+          if (mn == kNone) break;
+          const bool mine = hk == mn;
+          const unsigned bb = __reduce_or_sync(full, mine ? hb : 0u);
+          cnt += (unsigned)__popc(bb);
+          if (lane == 0 && nw < kRowSetCap) sout[nw] = make_int2((int)mn, (int)bb);
+          ++nw;
+          if (mine) {
+            ++at;
+            hk = at < ql ? scsi[lane * kMergeLen + at] : kNone;
+            hb = at < ql ? scs[lane * kMergeLen + at] : 0u;
+          }
+        }
+        __syncwarp();
+        if (lane == 0) rowsize[g] = (long long)cnt;
+        if (record) {
+          if (nw <= kRowSetCap) {
+            int2* dst = P.rsets + g * kRowSetCap;
+            for (int x = lane; x < nw; x += 32) dst[x] = sout[x];
+          }
+          if (lane == 0) P.rcnt[g] = nw <= kRowSetCap ? nw : -1;
+        }
+        clean = false;
+        __syncwarp();
+        continue;
+      }
+    }
     unsigned smin = 0xffffffffu, smax = 0u;
     for (long long c = a0; c < a1; c += 32) {
       load_chunk(c);
@@ -754,7 +826,7 @@ cudaError_t run_wb(const LaunchCtx& L, const ProbD& P, const SymLaunch& S, long 
   if (e != cudaSuccess) return e;
   KKS_LAUNCHED();
   kern<<<resident_grid(kern, 32 * teams, smem, L.num_sms, (S.nrows + teams - 1) / teams), 32 * teams, smem,
-         L.stream>>>(P, S.rows, S.nrows, S.logT, rowsize);
+         L.stream>>>(P, S.rows, S.nrows, S.logT, rowsize, S.merge);
   return cudaGetLastError();
 }
 

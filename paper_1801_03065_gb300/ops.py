@@ -106,7 +106,8 @@ class SpGEMM:
                  method: int = 0, workspace_limit_bytes: int = 0, pool_limit_bytes: int = 0,
                  device: int = 0, hash_function: int = 1, slots_per_key_log2: int = 0,
                  tune: bool = False, verbose: bool = False, numeric_positions: bool = True,
-                 cta_partition: int = 0, window_positions: int = 1, stage_b: bool = False):
+                 cta_partition: int = 0, window_positions: int = 1, stage_b: bool = False,
+                 sym_merge: bool = True):
         self._lib = B.load()
         opt = B.OptionsT()
         B.check(self._lib.spgemm_options_default(C.byref(opt)), "spgemm_options_default")
@@ -127,6 +128,7 @@ class SpGEMM:
         opt.cta_partition = int(cta_partition)
         opt.window_positions = int(window_positions)
         opt.stage_b = 1 if stage_b else 0
+        opt.sym_merge = 1 if sym_merge else 0
         self.device = torch.device("cuda", device)
         h = C.c_void_p()
         B.check(self._lib.spgemm_handle_create(C.byref(h), C.byref(opt)), "spgemm_handle_create")

@@ -716,6 +716,73 @@ def test_window_positions(ops, dtype):
             h.close()
 
 
+def _merge_rows_case(seed):
+    """B (4000 x 120 000), rows sorted: row j holds 4 to 12 column sets among
+    the 16 from set j // 2 (1 to 5 columns each); every 97th row 20 to 26 sets
+    among 32 (more than a lane stages: the row takes the bitmap window), every
+    211th row sets spread over 3 000 (wider than the window), every 29th row
+    empty.  A (2500 x 4000): rows of 16 to 32 sorted entries within 20 of
+    column i, every 17th row 32 entries anywhere (unions of more than 64
+    sets), every 11th row 33 to 45 entries within 60 (several chunks), every
+    50th row empty."""
+    rng = np.random.default_rng(seed)
+    n, k = 4000, 120000
+    rows, cols = [], []
+    for j in range(n):
+        if j % 29 == 0:
+            continue
+        ns = int(rng.integers(20, 27)) if j % 97 == 0 else int(rng.integers(4, 13))
+        spread = 3000 if j % 211 == 0 else (32 if j % 97 == 0 else 16)
+        base = j // 2
+        sets = np.unique(base + rng.integers(0, spread, 4 * ns))[:ns]
+        sets = sets[sets < k // 32]
+        c = []
+        for st in sets:
+            c.extend(int(st) * 32 + b for b in np.sort(rng.choice(32, size=int(rng.integers(1, 6)), replace=False)))
+        c = np.asarray(c, dtype=np.int64)
+        rows.append(np.full(c.size, j))
+        cols.append(c)
+    B = csr_from_coo(n, k, np.concatenate(rows), np.concatenate(cols),
+                     rng.uniform(-1, 1, sum(x.size for x in cols)))
+    m = 2500
+    ra, ca = [], []
+    for i in range(m):
+        if i % 50 == 0:
+            continue
+        ln = int(rng.integers(33, 46)) if i % 11 == 0 else int(rng.integers(16, 33))
+        r = 60 if ln > 32 else 20
+        c = np.unique(np.clip(i + rng.integers(-r, r + 1, 3 * ln), 0, n - 1))[:ln]
+        if i % 17 == 0:
+            c = np.sort(rng.choice(n, size=32, replace=False))
+        ra.append(np.full(c.size, i))
+        ca.append(c)
+    A = csr_from_coo(m, n, np.concatenate(ra), np.concatenate(ca),
+                     rng.uniform(-1, 1, sum(x.size for x in ca)))
+    return A, B
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_symbolic_merge_rows(ops, dtype):
+    """Symbolic window rows that merge their sorted compressed B rows (option
+    sym_merge) against the bitmap-only window kernel and the oracle: rows that
+    merge, rows whose B rows exceed the staged length, rows of several chunks,
+    unions of more than 64 column sets (not recorded: the numeric phase forms
+    them again), empty rows of A and of B, and the 27-point stencil."""
+    cases = [_merge_rows_case(5), (w.stencil3d_27pt(16, seed=1),) * 2]
+    for A, B in cases:
+        ref = None
+        nnz_seen = set()
+        for merge in (1, 0):
+            for win in (1, 7):
+                h, _, _, Cd = run(ops, A, B, dtype, compression=1, window_positions=win, sym_merge=bool(merge))
+                st = h.stats()
+                assert st["compressed"] == 1
+                nnz_seen.add(st["nnzC"])
+                ref = assert_matches_oracle(A, B, Cd, dtype, ref)
+                h.close()
+        assert len(nnz_seen) == 1
+
+
 def test_positions_batched_all_or_none(ops):
     """A plan takes positions only when every product is compressed."""
     pairs = w.batched_pairs(count=6, nmin=500, nmax=6000, seed=11)
