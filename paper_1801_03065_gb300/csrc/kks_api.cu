@@ -42,7 +42,7 @@ enum BufId {
   kBufTrPool, kBufReuseRows, kBufReusePool, kBufBinCnt, kBufBinOfs, kBufMcCnt, kBufMcYcp, kBufMcCsi, kBufMcCs,
   kBufMcMax, kBufRapRf, kBufRapRtp, kBufRapRti, kBufRapRpe, kBufRapW, kBufRapCnt, kBufRapSymRows,
   kBufRapNumRows, kBufRapMeta, kBufRapTmp, kBufMcRows, kBufFetch, kBufLongB, kBufLongA, kBufRowSets, kBufRowSetCnt,
-  kNumBufs
+  kBufBlen, kNumBufs
 };
 
 // Row bins of a masked product, cached for numeric reuse on one pattern.
@@ -550,6 +550,7 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
   KKS_ST(ensure(h, kBufBrow0, sizeof(long long) * (ni + 1)));
   KKS_ST(ensure(h, kBufCnt, sizeof(long long) * (totalB + 1)));
   KKS_ST(ensure(h, kBufBcp, sizeof(long long) * (totalB + 1)));
+  if (h->opt.compression != 0) KKS_ST(ensure(h, kBufBlen, sizeof(longlong2) * (totalB + 1)));
   KKS_ST(ensure(h, kBufRf, sizeof(long long) * (totalA + 1)));
   KKS_ST(ensure(h, kBufRfc, sizeof(long long) * (totalA + 1)));
   KKS_ST(ensure(h, kBufRowsize, sizeof(long long) * (totalA + 1)));
@@ -597,12 +598,13 @@ spgemm_status_t do_symbolic(kks_handle* h, int count, const spgemm_csr_t* A, con
   // (1) compression pass 1 and (2) row statistics
   if (comp_on) {
     KKS_CU(launch_compress_count(L, P, totalB, B<long long>(h, kBufCnt),
-                                 B<unsigned long long>(h, kBufInstStats) + 4 * ni, long_queue(h, kBufLongB, totalB)));
+                                 B<unsigned long long>(h, kBufInstStats) + 4 * ni, long_queue(h, kBufLongB, totalB),
+                                 B<longlong2>(h, kBufBlen)));
     KKS_CU(launch_scan(L, B<long long>(h, kBufCnt), B<long long>(h, kBufBcp), totalB, h->buf[kBufScanTmp]));
   }
   KKS_CU(launch_row_stats(L, P, totalA, comp_on ? 1 : 0, B<long long>(h, kBufRf),
                           comp_on ? B<long long>(h, kBufRfc) : nullptr, B<unsigned long long>(h, kBufInstStats),
-                          long_queue(h, kBufLongA, totalA)));
+                          long_queue(h, kBufLongA, totalA), comp_on ? B<longlong2>(h, kBufBlen) : nullptr));
   unsigned long long* h_stats = (unsigned long long*)rd;
   long long* h_nbc = (long long*)(rd + sizeof(unsigned long long) * 4 * ni);
   DevStatus* h_status = (DevStatus*)(rd + sizeof(unsigned long long) * (4 * ni + 2 * ni + 2 * kNumBins + 8));

@@ -136,9 +136,10 @@ struct LongQueue {
   int* list;                 // >= totalA (totalB) entries
   unsigned long long* ctr;   // 3 counters
 };
-// per-row compressed lengths; *unsorted += rows of B whose columns do not increase
+// per-row compressed lengths; *unsorted += rows of B whose columns do not increase;
+// blen (may be null): per B row (length, compressed length) for the row statistics
 cudaError_t launch_compress_count(const LaunchCtx&, const ProbD&, long long totalB, long long* cnt,
-                                  unsigned long long* unsorted, const LongQueue& q);
+                                  unsigned long long* unsorted, const LongQueue& q, longlong2* blen);
 // (the queue of the preceding count pass)
 cudaError_t launch_compress_fill(const LaunchCtx&, const ProbD&, long long totalB, int* csi, unsigned* cs,
                                  const LongQueue& q);
@@ -149,8 +150,11 @@ cudaError_t launch_decide_compression(const LaunchCtx&, InstD* inst, const unsig
                                       int mode, double threshold);
 // rf[i] = multiplications of row i of A*B (one plain product, no instance table)
 cudaError_t launch_row_flops(const LaunchCtx&, const MatD& A, const MatD& B, long long* rf, DevStatus* st);
+// blen (may be null): the (length, compressed length) pairs of the count pass,
+// one load per entry of A instead of two pairs of row pointers
 cudaError_t launch_row_stats(const LaunchCtx&, const ProbD&, long long totalA, int use_bc,
-                             long long* rf, long long* rfc, unsigned long long* inst_stats, const LongQueue& q);
+                             long long* rf, long long* rfc, unsigned long long* inst_stats, const LongQueue& q,
+                             const longlong2* blen);
 // exclusive scan of in[0, n) into out[0, n], out[n] = total; tmp >= scan_tmp_bytes(n)
 size_t scan_tmp_bytes(long long n);
 cudaError_t launch_scan(const LaunchCtx&, const long long* in, long long* out, long long n, void* tmp);

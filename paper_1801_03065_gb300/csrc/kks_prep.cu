@@ -56,7 +56,7 @@ __device__ __forceinline__ long long long_next(unsigned long long* fetch) {
 // Compressed length of B row gb by a team of TW lanes.
 template <int TW>
 __device__ __forceinline__ void compress_count_team(const Team<TW>& tm, const ProbD& P, long long gb, long long* cnt,
-                                                    unsigned long long* unsorted) {
+                                                    unsigned long long* unsorted, longlong2* blen) {
   const int b = inst_of(P.brow0s, P.ninst, gb);
   const InstD& I = P.inst[b];
   const long long j = gb - I.brow0;
@@ -72,14 +72,17 @@ __device__ __forceinline__ void compress_count_team(const Team<TW>& tm, const Pr
     bad |= p > s && col <= prev;
   }
   c = warp_team_sum<TW>(tm, c);
-  if (tm.lane == 0) cnt[gb] = c;
+  if (tm.lane == 0) {
+    cnt[gb] = c;
+    if (blen) blen[gb] = make_longlong2(e - s, c);
+  }
   if (__any_sync(tm.mask, bad) && tm.lane == 0) atomicAdd(unsorted, 1ull);
 }
 
 template <int TW>
 __global__ void __launch_bounds__(kBlock) k_compress_count(ProbD P, long long totalB, long long* cnt,
                                                            unsigned long long* unsorted, int* list,
-                                                           unsigned long long* nlist) {
+                                                           unsigned long long* nlist, longlong2* blen) {
   Team<TW> tm;
   __shared__ int nlong;
   __shared__ int longrows[kBlock];
@@ -98,6 +101,7 @@ __global__ void __launch_bounds__(kBlock) k_compress_count(ProbD P, long long to
       if (s < 0 || s > e || e > I.B.nnz) {   // malformed row pointers: report, read nothing
         dev_fail(P.status, kDevBadIndex, 40, gb);
         cnt[gb] = 0;
+        if (blen) blen[gb] = make_longlong2(0, 0);
       } else if (e - s <= kShortRowB) {
         const int* cj = I.B.cj;
         long long c = 0;
@@ -112,6 +116,7 @@ __global__ void __launch_bounds__(kBlock) k_compress_count(ProbD P, long long to
           prev = col;
         }
         cnt[gb] = c;
+        if (blen) blen[gb] = make_longlong2(e - s, c);
         if (bad) atomicAdd(unsorted, 1ull);
       } else if (e - s > kLongRow) {
         list[atomicAdd(nlist, 1ull)] = (int)gb;
@@ -121,17 +126,18 @@ __global__ void __launch_bounds__(kBlock) k_compress_count(ProbD P, long long to
     }
   }
   __syncthreads();
-  for (int x = tm.id; x < nlong; x += tm.per_cta) compress_count_team<TW>(tm, P, g0 + longrows[x], cnt, unsorted);
+  for (int x = tm.id; x < nlong; x += tm.per_cta)
+    compress_count_team<TW>(tm, P, g0 + longrows[x], cnt, unsorted, blen);
 }
 
 // Rows of B longer than kLongRow entries, from the queue the block pass built,
 // one warp each (a warp takes the next row from a counter).
 __global__ void __launch_bounds__(kBlock) k_compress_count_long(ProbD P, const int* list, const unsigned long long* n,
                                                                 unsigned long long* fetch, long long* cnt,
-                                                                unsigned long long* unsorted) {
+                                                                unsigned long long* unsorted, longlong2* blen) {
   Team<32> tm;
   for (long long x = long_next(fetch); x < (long long)*n; x = long_next(fetch))
-    compress_count_team<32>(tm, P, list[x], cnt, unsorted);
+    compress_count_team<32>(tm, P, list[x], cnt, unsorted, blen);
 }
 
 // Runs of equal CSI in row order become one compressed entry; rows with sorted
@@ -195,12 +201,22 @@ __global__ void __launch_bounds__(kBlock) k_compress_fill(ProbD P, long long tot
   const int base_lane = (threadIdx.x & 31) & ~(TW - 1);
   {
     const long long gb = g0 + threadIdx.x;
+    int b = 0;
+    long long s = 0, e = 0;
     if (gb < g1) {
-      const int b = inst_of(P.brow0s, P.ninst, gb);
+      b = inst_of(P.brow0s, P.ninst, gb);
       const InstD& I = P.inst[b];
       if (I.compressed) {
-        const long long j = gb - I.brow0;
-        const long long s = rp_at(I.B, j), e = rp_at(I.B, j + 1);
+        s = rp_at(I.B, gb - I.brow0);
+        e = rp_at(I.B, gb - I.brow0 + 1);
+        // malformed row pointers (reported by the count pass, which gave the
+        // row no compressed entries): read nothing
+        if (s < 0 || s > e || e > I.B.nnz) s = e = 0;
+      }
+    }
+    if (gb < g1) {
+      const InstD& I = P.inst[b];
+      if (I.compressed) {
         if (e - s <= kShortRowB) {
           const int* cj = I.B.cj;
           long long run = P.Bcp[gb] - 1;
@@ -253,7 +269,7 @@ constexpr int kShortRow = 32;
 // issued together.
 __device__ __forceinline__ void row_stats_entries(const ProbD& P, const InstD& I, long long g, long long p0,
                                                   long long e, long long step, int use_bc, long long* f,
-                                                  long long* fc) {
+                                                  long long* fc, const longlong2* blen) {
   constexpr int kU = 4;
   for (; p0 < e; p0 += (long long)kU * step) {
     int jj[kU];
@@ -265,6 +281,18 @@ __device__ __forceinline__ void row_stats_entries(const ProbD& P, const InstD& I
         dev_fail(P.status, kDevBadIndex, 43, g);
         jj[u] = -1;
       }
+    }
+    if (blen) {
+      // the count pass validated B's row pointers and stored both lengths
+      longlong2 ln[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) ln[u] = jj[u] >= 0 ? blen[I.brow0 + jj[u]] : make_longlong2(0, 0);
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        *f += ln[u].x;
+        *fc += ln[u].y;
+      }
+      continue;
     }
     long long bs[kU], be[kU], cs[kU], ce[kU];
 #pragma unroll
@@ -296,7 +324,7 @@ __device__ __forceinline__ void row_stats_entries(const ProbD& P, const InstD& I
 __global__ void __launch_bounds__(kBlock) k_row_stats_long(ProbD P, int use_bc, const int* list,
                                                            const unsigned long long* n, unsigned long long* fetch,
                                                            long long* rf, long long* rfc,
-                                                           unsigned long long* inst_stats) {
+                                                           unsigned long long* inst_stats, const longlong2* blen) {
   Team<32> tm;
   for (long long x = long_next(fetch); x < (long long)*n; x = long_next(fetch)) {
     const long long g = list[x];
@@ -305,7 +333,7 @@ __global__ void __launch_bounds__(kBlock) k_row_stats_long(ProbD P, int use_bc, 
     const long long i = g - I.arow0;
     const long long s = rp_at(I.A, i), e = rp_at(I.A, i + 1);
     long long f = 0, fc = 0;
-    row_stats_entries(P, I, g, s + tm.lane, e, 32, use_bc, &f, &fc);
+    row_stats_entries(P, I, g, s + tm.lane, e, 32, use_bc, &f, &fc, blen);
     f = warp_team_sum<32>(tm, f);
     fc = warp_team_sum<32>(tm, fc);
     if (tm.lane == 0) {
@@ -323,7 +351,7 @@ __global__ void __launch_bounds__(kBlock) k_row_stats_long(ProbD P, int use_bc, 
 template <int TW>
 __global__ void __launch_bounds__(kBlock) k_row_stats(ProbD P, long long totalA, int use_bc, long long* rf,
                                                       long long* rfc, unsigned long long* inst_stats, int* list,
-                                                      unsigned long long* nlist) {
+                                                      unsigned long long* nlist, const longlong2* blen) {
   Team<TW> tm;
   __shared__ unsigned long long acc[4];
   __shared__ int b_first, b_last, nlong;
@@ -357,7 +385,7 @@ __global__ void __launch_bounds__(kBlock) k_row_stats(ProbD P, long long totalA,
     }
   };
   auto entries = [&](const InstD& I, long long g, long long p0, long long e, long long step, long long* f,
-                     long long* fc) { row_stats_entries(P, I, g, p0, e, step, use_bc, f, fc); };
+                     long long* fc) { row_stats_entries(P, I, g, p0, e, step, use_bc, f, fc, blen); };
   // (1) short rows, one thread each
   {
     const long long g = g0 + threadIdx.x;
@@ -660,16 +688,16 @@ int resident_per_sm(const void* kernel, int threads, size_t smem) {
 // Long-row queue layout: queue[0] = entries, [1] = fetch counter of the
 // count pass, [2] = fetch counter of the fill pass (zeroed here).
 cudaError_t launch_compress_count(const LaunchCtx& L, const ProbD& P, long long totalB, long long* cnt,
-                                  unsigned long long* unsorted, const LongQueue& q) {
+                                  unsigned long long* unsorted, const LongQueue& q, longlong2* blen) {
   if (totalB <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(q.ctr, 0, 3 * sizeof(unsigned long long), L.stream);
   if (e != cudaSuccess) return e;
   const long long grid = (totalB + kBlock - 1) / kBlock;
   KKS_LAUNCHED();
-  k_compress_count<8><<<(unsigned)grid, kBlock, 0, L.stream>>>(P, totalB, cnt, unsorted, q.list, q.ctr);
+  k_compress_count<8><<<(unsigned)grid, kBlock, 0, L.stream>>>(P, totalB, cnt, unsorted, q.list, q.ctr, blen);
   KKS_LAUNCHED();
   k_compress_count_long<<<grid_for(totalB, kBlock, L.num_sms, 4), kBlock, 0, L.stream>>>(P, q.list, q.ctr, q.ctr + 1,
-                                                                                        cnt, unsorted);
+                                                                                        cnt, unsorted, blen);
   return cudaGetLastError();
 }
 
@@ -733,16 +761,19 @@ cudaError_t launch_decide_compression(const LaunchCtx& L, InstD* inst, const uns
 }
 
 cudaError_t launch_row_stats(const LaunchCtx& L, const ProbD& P, long long totalA, int use_bc, long long* rf,
-                             long long* rfc, unsigned long long* inst_stats, const LongQueue& q) {
+                             long long* rfc, unsigned long long* inst_stats, const LongQueue& q,
+                             const longlong2* blen) {
   if (totalA <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(q.ctr, 0, 2 * sizeof(unsigned long long), L.stream);
   if (e != cudaSuccess) return e;
   const long long grid = (totalA + kBlock - 1) / kBlock;
   KKS_LAUNCHED();
-  k_row_stats<8><<<(unsigned)grid, kBlock, 0, L.stream>>>(P, totalA, use_bc, rf, rfc, inst_stats, q.list, q.ctr);
+  k_row_stats<8><<<(unsigned)grid, kBlock, 0, L.stream>>>(P, totalA, use_bc, rf, rfc, inst_stats, q.list, q.ctr,
+                                                          blen);
   KKS_LAUNCHED();
   k_row_stats_long<<<grid_for(totalA, kBlock, L.num_sms, 4), kBlock, 0, L.stream>>>(P, use_bc, q.list, q.ctr,
-                                                                                   q.ctr + 1, rf, rfc, inst_stats);
+                                                                                   q.ctr + 1, rf, rfc, inst_stats,
+                                                                                   blen);
   return cudaGetLastError();
 }
 

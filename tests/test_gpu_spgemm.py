@@ -252,6 +252,27 @@ def test_bad_column_index_reported(ops):
     assert nnz == int(oracle.symbolic_plain(A, B)[-1])
 
 
+@pytest.mark.parametrize("compression", [1, 0])
+def test_bad_row_pointers_reported(ops, compression):
+    """Row pointers of B that decrease or pass nnz(B) are reported as a bad
+    index before any kernel follows them (the compression passes and the row
+    statistics check them), with and without the compressed B."""
+    from paper_1801_03065_gb300._binding import SpGEMMError
+    A = w.random_csr(300, 200, 6.0, seed=3)
+    B = w.random_csr(200, 5000, 6.0, seed=4)
+    for r, v in ((7, B.nnz + 50), (120, int(B.rowptr[118]))):
+        rp = B.rowptr.copy()
+        rp[r] = v
+        Bbad = Csr(B.nrows, B.ncols, rp, B.colidx, B.values)
+        h = ops.SpGEMM(compression=compression)
+        with pytest.raises(SpGEMMError) as e:
+            h.symbolic(dev(A), dev(Bbad))
+        assert e.value.status == 8
+        rp2, nnz = h.symbolic(dev(A), dev(B))
+        assert nnz == int(oracle.symbolic_plain(A, B)[-1])
+        h.close()
+
+
 # ------------------------------------------------------------------ masked / transpose
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
 def test_masked_gradients(ops, dtype):
