@@ -793,9 +793,9 @@ def test_symbolic_merge_rows(ops, dtype):
     for A, B in cases:
         ref = None
         nnz_seen = set()
-        for merge in (1, 0):
+        for merge in (True, False):
             for win in (1, 7):
-                h, _, _, Cd = run(ops, A, B, dtype, compression=1, window_positions=win, sym_merge=bool(merge))
+                h, _, _, Cd = run(ops, A, B, dtype, compression=1, window_positions=win, sym_merge=merge)
                 st = h.stats()
                 assert st["compressed"] == 1
                 nnz_seen.add(st["nnzC"])
