@@ -55,6 +55,8 @@ def test_options_defaults(lib):
     assert lib.spgemm_options_default(C.byref(o)) == 0
     assert o.compression == -1 and abs(o.compress_threshold - 0.85) < 1e-15
     assert abs(o.l1_max_occupancy - 0.5) < 1e-15 and o.dense == -1
+    assert o.hash_function == 1 and o.numeric_positions == 1 and o.window_positions == 1
+    assert o.sym_merge == 1 and o.stage_b == 0 and o.tune == 0
     assert lib.spgemm_options_default(None) == 1
 
 
